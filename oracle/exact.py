@@ -1,0 +1,246 @@
+"""Exact references for the ParRep oracle -- TEST INFRASTRUCTURE ONLY.
+
+Each function is a plain definition written out in numpy/scipy:
+
+* ``schlogl_props`` -- the Schloegl propensities of Table I (Sec. V.A) in the
+  form lambda_j = c_j s_j h_j(x), h = (x(x-1), x(x-1)(x-2), 1, x).
+* ``bd_stationary`` -- the stationary law of a birth-death chain by the
+  detailed-balance product formula pi(x+1)/pi(x) = b(x)/d(x+1), truncated.
+* ``generator`` / ``stationary_dense`` -- the generator Q of Eq. (1) and the
+  solution of pi Q = 0 (a check on the product formula).
+* ``toggle_stationary`` -- the truncated chemical master equation (Eq. 2) at
+  steady state for the two-species toggle switch, solved with scipy.sparse.
+* ``qsd_dtmc`` / ``qsd_ctmc`` -- quasi-stationary distributions in a set W
+  (Sec. III.A): principal left eigenvectors of the jump-chain matrix or of Q
+  restricted to W.
+* ``bd_mfpt`` -- mean first passage time of a birth-death chain (textbook sum).
+* ``fim_exact`` / ``rer_exact`` -- the path-space FIM (Appendix A form
+  E_pi sum_j lambda_j grad log lambda_j grad log lambda_j^T) and the relative
+  entropy rate E_pi sum_j [lambda_j log(lambda_j/lambda'_j) - lambda_j + lambda'_j].
+* ``rre_fixed_points`` -- the real roots of the Schloegl rate equation (Sec. V.A).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+
+# ---------------------------------------------------------------------------
+# propensities (plain formulas, vectorised over states)
+# ---------------------------------------------------------------------------
+def schlogl_props(c, s, x):
+    x = np.asarray(x, dtype=np.float64)
+    c = np.asarray(c, dtype=np.float64)
+    s = np.asarray(s, dtype=np.float64)
+    h = np.stack([x * (x - 1.0), x * (x - 1.0) * (x - 2.0), np.ones_like(x), x])
+    return (c * s)[:, None] * h  # (4, len(x))
+
+
+def toggle_props(c, U, V):
+    aU, nU, dU, aV, nV, dV = [float(v) for v in c]
+    U = np.asarray(U, dtype=np.float64)
+    V = np.asarray(V, dtype=np.float64)
+    return np.stack([aU / (1.0 + V ** nU), aV / (1.0 + U ** nV), dU * U, dV * V])
+
+
+def toggle_grad_log(c, U, V):
+    """d log lambda_j / d c_k, shape (4, 6, n)."""
+    aU, nU, dU, aV, nV, dV = [float(v) for v in c]
+    U = np.asarray(U, dtype=np.float64)
+    V = np.asarray(V, dtype=np.float64)
+    g = np.zeros((4, 6) + U.shape)
+    g[0, 0] = 1.0 / aU
+    with np.errstate(divide="ignore", invalid="ignore"):
+        pV = V ** nU
+        g[0, 1] = np.where(V > 0, -pV * np.log(np.where(V > 0, V, 1.0)) / (1.0 + pV), 0.0)
+        pU = U ** nV
+        g[1, 4] = np.where(U > 0, -pU * np.log(np.where(U > 0, U, 1.0)) / (1.0 + pU), 0.0)
+    g[1, 3] = 1.0 / aV
+    g[2, 2] = 1.0 / dU
+    g[3, 5] = 1.0 / dV
+    return g
+
+
+# ---------------------------------------------------------------------------
+# birth-death chains
+# ---------------------------------------------------------------------------
+def bd_stationary(birth, death):
+    """pi on {0..n-1} for birth rates b(x) (x -> x+1) and death rates d(x)
+    (x -> x-1), by pi(x+1)/pi(x) = b(x)/d(x+1), computed in log space."""
+    b = np.asarray(birth, dtype=np.float64)
+    d = np.asarray(death, dtype=np.float64)
+    logr = np.log(b[:-1]) - np.log(d[1:])
+    logpi = np.concatenate([[0.0], np.cumsum(logr)])
+    logpi -= logpi.max()
+    pi = np.exp(logpi)
+    return pi / pi.sum()
+
+
+def schlogl_stationary(c, s, xmax):
+    x = np.arange(xmax + 1)
+    lam = schlogl_props(c, s, x)
+    return bd_stationary(lam[0] + lam[2], lam[1] + lam[3])
+
+
+def generator(rates_up, rates_down):
+    """Dense generator Q (Eq. 1) of a birth-death chain truncated to n states
+    (births out of the last state and deaths out of state 0 are dropped)."""
+    up = np.asarray(rates_up, dtype=np.float64)
+    dn = np.asarray(rates_down, dtype=np.float64)
+    n = len(up)
+    Q = np.zeros((n, n))
+    for x in range(n):
+        if x + 1 < n:
+            Q[x, x + 1] = up[x]
+        if x - 1 >= 0:
+            Q[x, x - 1] = dn[x]
+        Q[x, x] = -Q[x].sum()
+    return Q
+
+
+def stationary_dense(Q):
+    """Solves pi Q = 0, sum pi = 1 by a dense least-squares solve."""
+    n = Q.shape[0]
+    A = np.vstack([Q.T, np.ones((1, n))])
+    rhs = np.zeros(n + 1)
+    rhs[-1] = 1.0
+    pi, *_ = np.linalg.lstsq(A, rhs, rcond=None)
+    return pi
+
+
+def bd_mfpt(birth, death, x_from, x_to):
+    """Mean first passage time from x_from up to x_to > x_from of a birth-death
+    chain reflecting at 0: sum_{y=x_from}^{x_to-1} 1/(b(y) pi(y)) * sum_{z<=y} pi(z)
+    with pi the (unnormalised) product-form weights."""
+    b = np.asarray(birth, dtype=np.float64)
+    d = np.asarray(death, dtype=np.float64)
+    n = x_to + 1
+    logr = np.log(b[: n - 1]) - np.log(d[1:n])
+    logw = np.concatenate([[0.0], np.cumsum(logr)])
+    t = 0.0
+    for y in range(x_from, x_to):
+        # sum_{z<=y} w(z) / (b(y) w(y))
+        t += np.sum(np.exp(logw[: y + 1] - logw[y])) / b[y]
+    return t
+
+
+def bd_mfpt_down(birth, death, x_from, x_to, xmax):
+    """Mean first passage time from x_from down to x_to < x_from, truncated at xmax."""
+    b = np.asarray(birth, dtype=np.float64)[::-1][: xmax + 1]
+    d = np.asarray(death, dtype=np.float64)[::-1][: xmax + 1]
+    # reflect: state y -> xmax - y, births become deaths
+    return bd_mfpt(d, b, xmax - x_from, xmax - x_to)
+
+
+# ---------------------------------------------------------------------------
+# two-species toggle switch: truncated CME at steady state
+# ---------------------------------------------------------------------------
+def toggle_generator(c, Umax, Vmax):
+    nU, nV = Umax + 1, Vmax + 1
+    U, V = np.meshgrid(np.arange(nU), np.arange(nV), indexing="ij")
+    U = U.ravel()
+    V = V.ravel()
+    lam = toggle_props(c, U, V)
+    idx = U * nV + V
+    rows, cols, vals = [], [], []
+    moves = [(1, 0), (0, 1), (-1, 0), (0, -1)]
+    out = np.zeros(len(idx))
+    for j, (du, dv) in enumerate(moves):
+        U2, V2 = U + du, V + dv
+        ok = (U2 >= 0) & (U2 <= Umax) & (V2 >= 0) & (V2 <= Vmax)
+        rows.append(idx[ok])
+        cols.append((U2 * nV + V2)[ok])
+        vals.append(lam[j][ok])
+        out += np.where(ok, lam[j], 0.0)
+    rows.append(idx)
+    cols.append(idx)
+    vals.append(-out)
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(len(idx), len(idx)))
+
+
+def toggle_stationary(c, Umax, Vmax):
+    """Stationary law on [0,Umax] x [0,Vmax] (truncated CME, reflecting edges),
+    returned as an array of shape (Umax+1, Vmax+1)."""
+    Q = toggle_generator(c, Umax, Vmax)
+    n = Q.shape[0]
+    QT = Q.T.tocsr()
+
+    def solve(row):
+        # pi Q = 0 with the equation of state `row` replaced by sum(pi) = 1
+        A = QT.tolil()
+        A[row, :] = np.ones(n)
+        rhs = np.zeros(n)
+        rhs[row] = 1.0
+        return spla.spsolve(A.tocsc(), rhs)
+
+    pi = solve(0)
+    pi = solve(int(np.argmax(pi)))  # a well-conditioned normalisation row
+    pi = np.maximum(pi, 0.0)
+    pi /= pi.sum()
+    return pi.reshape(Umax + 1, Vmax + 1)
+
+
+# ---------------------------------------------------------------------------
+# quasi-stationary distributions (Sec. III.A)
+# ---------------------------------------------------------------------------
+def qsd_dtmc(P_W):
+    """QSD of a DTMC in W: principal left eigenvector of the sub-stochastic
+    jump matrix restricted to W.  Returns (nu, lambda) with P(N > n) = lambda^n."""
+    w, vl = np.linalg.eig(P_W.T)
+    i = int(np.argmax(w.real))
+    nu = np.abs(vl[:, i].real)
+    return nu / nu.sum(), float(w[i].real)
+
+
+def qsd_ctmc(Q_W):
+    """QSD of a CTMC in W: principal left eigenvector of Q restricted to W."""
+    w, vl = np.linalg.eig(Q_W.T)
+    i = int(np.argmax(w.real))
+    nu = np.abs(vl[:, i].real)
+    return nu / nu.sum(), float(w[i].real)
+
+
+def bd_jump_matrix(birth, death):
+    """Jump (embedded) chain of a birth-death chain on {0..n-1}."""
+    b = np.asarray(birth, dtype=np.float64)
+    d = np.asarray(death, dtype=np.float64)
+    n = len(b)
+    P = np.zeros((n, n + 2))  # columns: -1 .. n (off-range moves kept as exits)
+    a0 = b + d
+    for x in range(n):
+        P[x, x + 2] = b[x] / a0[x]
+        P[x, x] = d[x] / a0[x]
+    return P[:, 1:-1], P
+
+
+# ---------------------------------------------------------------------------
+# path-space FIM and relative entropy rate (Appendix A)
+# ---------------------------------------------------------------------------
+def fim_exact(lam, grad, weights):
+    """sum_x w(x) sum_j lambda_j(x) g_j(x) g_j(x)^T; lam (m, n), grad (m, l, n)."""
+    return np.einsum("n,jn,jan,jbn->ab", weights, lam, grad, grad)
+
+
+def rer_exact(lam, lam_p, weights):
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t = np.where(lam > 0, lam * np.log(lam / lam_p), 0.0) - lam + lam_p
+    return float(np.sum(weights * t.sum(axis=0)))
+
+
+def schlogl_grad_log(c, x):
+    n = len(np.atleast_1d(x))
+    g = np.zeros((4, 4, n))
+    for j in range(4):
+        g[j, j] = 1.0 / c[j]
+    return g
+
+
+def rre_fixed_points(c, s, V=1.0):
+    """Real non-negative roots of d x/dt = A1 x^2 - A2 x^3 + A3 - A4 x (the
+    large-population limit of Table I written in population units)."""
+    A = np.asarray(c, dtype=np.float64) * np.asarray(s, dtype=np.float64)
+    r = np.roots([-A[1], A[0], -A[3], A[2]])
+    r = np.sort(r[np.abs(r.imag) < 1e-9].real)
+    return r[r >= 0]

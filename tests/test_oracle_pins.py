@@ -1,0 +1,371 @@
+"""Pins of the CPU oracle to facts fixed by the paper and by mathematics.
+
+Nothing here touches the CUDA path.  Each test names the passage or the
+textbook fact it checks; the statistical ones use batch means over independent
+seeds and fail beyond 4.5 standard errors.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import exact as E
+from paper_1705_06807_gb300 import configs as K
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _z(samples, target):
+    s = np.asarray(samples, dtype=np.float64)
+    se = s.std(ddof=1) / np.sqrt(len(s))
+    return abs(s.mean() - target) / se
+
+
+# ---------------------------------------------------------------------------
+# random numbers
+# ---------------------------------------------------------------------------
+def test_philox_known_answers():
+    """Philox4x32-10 against the published known-answer vectors."""
+    n = 0
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            v = [int(t, 16) for t in line.split()]
+            out = O.philox(v[0:4], v[4:6])
+            assert list(out) == v[6:10]
+            n += 1
+    assert n == 3
+
+
+def test_uniform_constructions_are_open_interval_and_exact():
+    lo = O.u01_f64(0, 0)
+    hi = O.u01_f64(0xFFFFFFFF, 0xFFFFFFFF)
+    assert lo == 2.0**-53 and hi == 1.0 - 2.0**-53
+    assert O.u01_f32(0) == np.float32(2.0**-24)
+    assert O.u01_f32(0xFFFFFFFF) == np.float32(1.0 - 2.0**-24)
+    # 52 bits: wa supplies the top 32, wb the next 20
+    assert O.u01_f64(1, 0) == (2.0**20 + 0.5) * 2.0**-52
+    assert O.u01_f64(0, 1 << 12) == 1.5 * 2.0**-52
+
+
+# ---------------------------------------------------------------------------
+# exact references pinned to the paper's printed values
+# ---------------------------------------------------------------------------
+def _golden_paper():
+    d = {}
+    with open(os.path.join(GOLDEN, "paper_schlogl_v25.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            k, v, hw = line.split()[:3]
+            d[k] = (float(v), float(hw))
+    return d
+
+
+def test_schlogl_table_reading_reproduces_paper_saddle():
+    """Table I with a=1, b=2, c=(3,0.6,0.25,2.95), V=25: the unstable point of
+    the rate equation times V is 25.9649 (Fig. 1 caption)."""
+    g = _golden_paper()
+    n = K.schlogl_paper()
+    roots = E.rre_fixed_points(n["c"], n["s"])
+    assert len(roots) == 3
+    v, hw = g["saddle_population"]
+    assert abs(roots[1] - v) <= hw
+
+
+def test_product_formula_matches_generator_solve():
+    """Birth-death product formula against a direct solve of pi Q = 0 (Eq. 1)."""
+    n = K.schlogl_paper(hist_max=149)
+    x = np.arange(150)
+    lam = E.schlogl_props(n["c"], n["s"], x)
+    pi1 = E.bd_stationary(lam[0] + lam[2], lam[1] + lam[3])
+    Q = E.generator(lam[0] + lam[2], lam[1] + lam[3])
+    pi2 = E.stationary_dense(Q)
+    assert np.max(np.abs(pi1 - pi2)) < 1e-10
+    assert abs(pi1.sum() - 1.0) < 1e-12
+
+
+def test_exact_fim_reproduces_paper_table():
+    """Path-space FIM of Table II from the exact stationary law: I_33 = 200
+    exactly (lambda_3 is constant); I_11 and I_44 inside the paper's confidence
+    half-widths; I_22 within 3% (the paper's estimate sits 2.6% above the exact
+    value, outside its own half-width)."""
+    g = _golden_paper()
+    n = K.schlogl_paper(hist_max=400)
+    x = np.arange(401)
+    pi = E.schlogl_stationary(n["c"], n["s"], 400)
+    lam = E.schlogl_props(n["c"], n["s"], x)
+    F = E.fim_exact(lam, E.schlogl_grad_log(n["c"], x), pi)
+    assert np.allclose(F - np.diag(np.diag(F)), 0.0)
+    assert abs(F[2, 2] - 200.0) < 1e-10
+    for i, key in [(0, "fim_11"), (3, "fim_44")]:
+        v, hw = g[key]
+        assert abs(F[i, i] - v) <= 2 * hw, (key, F[i, i], v)
+    assert abs(F[1, 1] / g["fim_22"][0] - 1.0) < 0.03
+    # the grad-lambda form printed in the Sec. IV text would give
+    # I_33 = lambda_3 (d lambda_3 / d c_3)^2 = 12.5 * 50^2 = 31250, not 200
+    assert abs(lam[2, 0] * n["s"][2] ** 2 - 31250.0) < 1e-9
+
+
+def test_toggle_cme_reduces_to_independent_poisson():
+    """With Hill exponent 0 the production rates are constant alpha/2, so the
+    truncated CME must give the product of two Poisson(alpha/(2 delta)) laws."""
+    from scipy.stats import poisson
+
+    c = [12.0, 0.0, 1.5, 12.0, 0.0, 1.5]
+    pi = E.toggle_stationary(c, 40, 40)
+    m = 12.0 / 2.0 / 1.5
+    p = poisson.pmf(np.arange(41), m)
+    assert np.max(np.abs(pi - np.outer(p, p) / np.outer(p, p).sum())) < 1e-10
+
+
+def test_toggle_cme_symmetry():
+    """The symmetric toggle's law is symmetric under U <-> V.  The two wells
+    exchange mass only every ~1e7 time units, so the sparse solve is
+    ill-conditioned and holds the symmetry to ~1e-7 relative."""
+    pi = E.toggle_stationary(K.toggle()["c"], 100, 100)
+    assert np.max(np.abs(pi - pi.T)) < 1e-6 * pi.max()
+    U, V = np.meshgrid(np.arange(101), np.arange(101), indexing="ij")
+    assert abs(pi[U > V].sum() - pi[U < V].sum()) < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# the oracle's SSA
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_ssa_immigration_death_is_poisson(precision):
+    """Immigration-death (c1 = c2 = 0): stationary law Poisson(k_in/k_out)."""
+    from scipy.stats import poisson
+
+    net = K.immigration_death(20.0, 1.0, hist_max=120)
+    means = []
+    tot = np.zeros(121)
+    for seed in range(16):
+        h, ev, _ = O.ssa_run(net, 1, [20], 12500.0, 1000 + seed, precision=precision)
+        tot += h
+        means.append((h * np.arange(121)).sum() / h.sum())
+    p = tot / tot.sum()
+    ex = poisson.pmf(np.arange(121), 20.0)
+    assert 0.5 * np.abs(p - ex).sum() < 0.01
+    assert _z(means, 20.0) < 4.5
+
+
+def test_ssa_schlogl_bistable_mean_and_well_mass():
+    """Schloegl (Table I form) at V = 10: time average of x and the mass of
+    {x <= 10} against the exact birth-death law."""
+    net = K.schlogl_paper(V=10, hist_max=200, split=11)
+    pi = E.schlogl_stationary(net["c"], net["s"], 200)
+    x = np.arange(201)
+    means, lows = [], []
+    for seed in range(16):
+        h, ev, _ = O.ssa_run(net, 1, [2], 5000.0, 77 + seed)
+        means.append((h * x).sum() / h.sum())
+        lows.append(h[:11].sum() / h.sum())
+    assert _z(means, (pi * x).sum()) < 4.5
+    assert _z(lows, pi[:11].sum()) < 4.5
+
+
+def test_ssa_toggle_against_cme():
+    """Toggle switch with alpha = 10, n = 1 (fast mixing): 2-D time-weighted
+    histogram against the truncated CME."""
+    net = K.toggle(alpha=10.0, n=1.0, delta=1.0, hist_max=(40, 40))
+    pi = E.toggle_stationary(net["c"], 40, 40).ravel()
+    tot = np.zeros(41 * 41)
+    mU, mV = [], []
+    for seed in range(16):
+        h, ev, _ = O.ssa_run(net, 1, [5, 5], 10000.0, 5 + seed)
+        tot += h
+        h = h.reshape(41, 41) / h.sum()
+        mU.append((h.sum(1) * np.arange(41)).sum())
+        mV.append((h.sum(0) * np.arange(41)).sum())
+    p = tot / tot.sum()
+    assert 0.5 * np.abs(p - pi).sum() < 0.03
+    pi2 = pi.reshape(41, 41)
+    assert _z(mU, (pi2.sum(1) * np.arange(41)).sum()) < 4.5
+    assert _z(mV, (pi2.sum(0) * np.arange(41)).sum()) < 4.5
+
+
+def test_ssa_trace_matches_run():
+    """The trace and the run draw from the same counters."""
+    net = K.schlogl_classic()
+    J, xs, tau = O.ssa_trace(net, [85], 9, 0, 500)
+    assert set(np.unique(J)) <= {0, 1, 2, 3}
+    steps = np.array([1, -1, 1, -1])[J]
+    assert np.all(xs[:, 0] == 85 + np.cumsum(steps))
+    assert np.all(tau > 0)
+
+
+# ---------------------------------------------------------------------------
+# the parallel step: first-escape lemma (Sec. III.A, results 1 and 2)
+# ---------------------------------------------------------------------------
+def _tiny_chain():
+    net = K.immigration_death(1.0, 1.0, hist_max=40, split=3)  # W = {0, 1, 2}
+    x = np.arange(41)
+    lam = E.schlogl_props(net["c"], net["s"], x)
+    b, d = lam[0] + lam[2], lam[1] + lam[3]
+    PW, _ = E.bd_jump_matrix(b[:3], d[:3])
+    # the last column of the restricted matrix would leave W; keep the 3x3 block
+    nu, lmb = E.qsd_dtmc(PW)
+    return net, nu, lmb, b + d
+
+
+@pytest.mark.parametrize("R", [1, 7, 32])
+def test_first_escape_lemma_tiny_chain(R):
+    """With R iid replicas started from the jump-chain QSD, R(N*-1)+K (K
+    1-based) is geometric with parameter 1 - lambda, whatever R; the summed
+    holding time of the contributions has mean E_nu[1/a0] / (1 - lambda)."""
+    net, nu, lmb, a0 = _tiny_chain()
+    rng = np.random.default_rng(R)
+    M, T = [], []
+    trials = 6000
+    for t in range(trials):
+        st = rng.choice(3, size=R, p=nu)
+        states = np.stack([st, np.zeros(R, dtype=int)], axis=1)
+        rc, nstar, k, xe, ts = O.parallel_from(net, states, 0, t, 1234 + R)
+        assert rc == 0 and xe[0] == 3
+        M.append(R * (nstar - 1) + k + 1)
+        T.append(ts)
+    M = np.array(M)
+    mean_geo = 1.0 / (1.0 - lmb)
+    assert _z(M, mean_geo) < 4.5
+    # distribution: P(M > m) = lambda^m
+    for m in [1, 2, 4, 8]:
+        p = (M > m).mean()
+        se = np.sqrt(lmb**m * (1 - lmb**m) / trials)
+        assert abs(p - lmb**m) < 4.5 * se + 1e-12, (m, p, lmb**m)
+    et = float(np.sum(nu / a0[:3])) / (1.0 - lmb)
+    assert _z(T, et) < 4.5
+
+
+# ---------------------------------------------------------------------------
+# dephasing: Fleming-Viot samples the jump-chain QSD
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("G", [32, 4096])
+@pytest.mark.parametrize("n_p", [200, 201])
+def test_dephasing_samples_jump_chain_qsd(G, n_p):
+    """Fleming-Viot dephasing (Algorithm 1) samples the QSD of the jump chain.
+    A birth-death jump chain moves by +-1, so it is bipartite: after n_p
+    lockstep jumps from X~ every replica has the parity of X~ + n_p, and the
+    two-step chain's QSD on that parity class is the QSD nu restricted to it
+    (nu P^2 = lambda^2 nu and P^2 keeps the parity)."""
+    net = K.immigration_death(5.0, 1.0, hist_max=60, split=8)  # W = {0..7}
+    x = np.arange(61)
+    lam = E.schlogl_props(net["c"], net["s"], x)
+    PW, _ = E.bd_jump_matrix((lam[0] + lam[2])[:8], (lam[1] + lam[3])[:8])
+    nu, _ = E.qsd_dtmc(PW)
+    target = np.where(np.arange(8) % 2 == n_p % 2, nu, 0.0)
+    target /= target.sum()
+    cnt = np.zeros(8)
+    for cyc in range(4):
+        xs, steps, ev = O.dephase(net, 4096, [0], 0, cyc, n_p, 99, thresh="steps", fv_group=G)
+        assert steps == n_p and ev == n_p * 4096
+        assert xs[:, 0].max() < 8
+        cnt += np.bincount(xs[:, 0], minlength=8)[:8]
+    p = cnt / cnt.sum()
+    assert 0.5 * np.abs(p - target).sum() < 0.03
+
+
+def test_dephase_steps_time_mode():
+    net = K.schlogl_classic()
+    a0 = E.schlogl_props(net["c"], net["s"], np.array([85.0])).sum()
+    assert O.dephase_steps(net, [85], 1.0) == int(np.ceil(a0))
+    assert O.dephase_steps(net, [85], 7.0, thresh="steps") == 7
+
+
+# ---------------------------------------------------------------------------
+# full ParRep (Algorithm 1)
+# ---------------------------------------------------------------------------
+def test_parrep_clock_and_burn_in_split_are_exact():
+    """T_s ends at T_end; the histograms before and after T_burn sum to T_burn
+    and T_end - T_burn; the constant channel gives I_33 (T_end - T_burn) s3/c3
+    (the I_33 = 200 fact of Table II), and its RER is E[lambda_3] times
+    (eps - log(1 + eps)) per unit time."""
+    net = K.schlogl_paper(V=10, hist_max=200, split=11)
+    eps = 0.1
+    cp = np.array([net["c"]] * 2, dtype=float)
+    cp[0, 2] *= 1 + eps
+    cp[1, 0] *= 1 + eps
+    r = O.parrep_run(net, 16, 300, 300, 2000.0, 5, [2], thresh="steps", T_burn=700.0, rer_cprime=cp)
+    assert r["status"] == 0
+    assert r["T_s"] == 2000.0
+    assert abs(r["hist_pre"].sum() - 700.0) < 1e-9
+    assert abs(r["hist_post"].sum() - 1300.0) < 1e-9
+    F = r["fim"]
+    assert abs(F[2, 2] - 1300.0 * net["s"][2] / net["c"][2]) < 1e-8
+    assert np.allclose(F - np.diag(np.diag(F)), 0.0)
+    A3 = net["c"][2] * net["s"][2]
+    assert abs(r["rer"][0] - 1300.0 * A3 * (eps - np.log1p(eps))) < 1e-8
+    # channel 1: E[lambda_1] integrated = F_11 c1^2
+    assert abs(r["rer"][1] - F[0, 0] * net["c"][0] ** 2 * (eps - np.log1p(eps))) < 1e-6 * abs(r["rer"][1])
+
+
+def test_parrep_without_escapes_is_stationary_poisson():
+    """A single region: after decorrelation and dephasing the parallel step
+    runs R replicas to T_end; the pooled histogram is Poisson and the FIM of
+    the death channel is E[lambda_4]/c4^2 = k_in/k_out^2 (Appendix A)."""
+    from scipy.stats import poisson
+
+    net = K.immigration_death(20.0, 2.0, hist_max=80)
+    p_tot = np.zeros(81)
+    f44 = []
+    for seed in range(8):
+        r = O.parrep_run(net, 8, 50, 50, 3000.0, 40 + seed, [10], thresh="steps", T_burn=100.0)
+        assert r["status"] == 0 and r["escapes"] == 0
+        p_tot += r["hist_pre"] + r["hist_post"]
+        f44.append(r["fim"][3, 3] / 2900.0)
+    p = p_tot / p_tot.sum()
+    assert 0.5 * np.abs(p - poisson.pmf(np.arange(81), 10.0)).sum() < 0.01
+    assert _z(f44, 20.0 / 4.0) < 4.5
+
+
+@pytest.mark.parametrize("thresh,tc", [("steps", 3000), ("time", 4.0)])
+def test_parrep_bistable_schlogl_matches_exact(thresh, tc):
+    """ParRep on the Schloegl network (Table I form, V = 10) with long
+    decorrelation/dephasing: the ergodic mean of x and the mass of the lower
+    well against the exact birth-death law (cf. the Sec. V.A comparison with
+    the CME)."""
+    net = K.schlogl_paper(V=10, hist_max=200, split=11)
+    pi = E.schlogl_stationary(net["c"], net["s"], 200)
+    x = np.arange(201)
+    means, lows, esc = [], [], 0
+    for seed in range(12):
+        r = O.parrep_run(net, 16, tc, tc, 8000.0, 300 + seed, [2], thresh=thresh, fv_group=16)
+        assert r["status"] == 0
+        h = r["hist_pre"] + r["hist_post"]
+        means.append((h * x).sum() / h.sum())
+        lows.append(h[:11].sum() / h.sum())
+        esc += r["escapes"]
+    assert esc > 100
+    assert _z(means, (pi * x).sum()) < 4.5
+    assert _z(lows, pi[:11].sum()) < 4.5
+
+
+def test_parrep_cycle_log_is_consistent():
+    net = K.schlogl_paper(V=10, hist_max=200, split=11)
+    r = O.parrep_run(net, 16, 400, 400, 3000.0, 11, [2], thresh="steps")
+    cyc = r["cycles"]
+    assert len(cyc) == r["n_cycles"] and cyc[-1]["ended"] == 1
+    for a in cyc[:-1]:
+        assert a["k"] >= 0 and a["n_star"] >= 1 and a["dephase_steps"] == 400
+        # X~ after the cycle is outside the region the cycle ran in
+        assert (a["x_tilde"][0] < 11) != (a["W"] == 0)
+    ts = [a["T_s"] for a in cyc]
+    assert all(b >= a for a, b in zip(ts, ts[1:]))
+    assert ts[-1] == 3000.0
+
+
+def test_parrep_x0_draw_is_uniform():
+    net = K.schlogl_classic()
+    xs = [O.initial_state(net, s, [0], 1000)[0] for s in range(4000)]
+    assert min(xs) >= 0 and max(xs) <= 1000
+    assert _z(xs, 500.0) < 4.5
+
+
+def test_parrep_rejects_bad_input():
+    net = K.schlogl_classic()
+    assert O.parrep_run(net, 0, 1, 1, 10.0, 0, [85])["status"] == O.OR_EINVAL
+    assert O.parrep_run(net, 4, 1, 1, 10.0, 0, [5000])["status"] == O.OR_EINVAL
+    small = dict(net, hist_max=120)
+    assert O.parrep_run(small, 4, 1, 1, 100.0, 0, [85])["status"] == O.OR_ERANGE
