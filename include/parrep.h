@@ -1,0 +1,203 @@
+/*
+ * parrep.h -- C ABI of the GB300 (sm_103a) parallel replica (ParRep) library.
+ *
+ * The library runs the hot path of parallel replica dynamics for continuous
+ * time Markov chains on bistable reaction networks (Wang & Plechac, arXiv
+ * 1705.06807): Gillespie direct-method SSA replicas that go through the
+ * decorrelation, Fleming-Viot dephasing and parallel steps of Algorithm 1,
+ * the first-escape vote across replicas, and the time-weighted stationary
+ * histogram from which the path-space Fisher information matrix and relative
+ * entropy rates (Sec. IV, Appendix A) are contracted.
+ *
+ * Conventions for every entry point:
+ *   - Return PARREP_OK (0) on success and a negative PARREP_E* code on error;
+ *     parrep_last_error(h) then holds a one-line message (per handle).
+ *   - Pointers passed in are only read during the call; the library copies
+ *     what it keeps.  The library owns all device memory it allocates and
+ *     frees it in parrep_destroy.
+ *   - Output buffers may be host or device pointers (CUDA unified addressing
+ *     decides); device outputs are written on the handle's stream and the
+ *     call returns after the copy has completed.
+ *   - One handle must not be used from two host threads at once.
+ *   - Random numbers are Philox4x32-10 keyed by the 64-bit seed with the
+ *     counter (replica, step, cycle, stage tag), so a run is reproducible
+ *     from (network, options, T_end, seed) alone.
+ *   - Time sums are kept in 64-bit fixed point with 2^-40 resolution (exact,
+ *     order-independent addition); T_end must stay below 2^23.
+ */
+#ifndef PARREP_H
+#define PARREP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PARREP_OK 0
+#define PARREP_EINVAL (-1)   /* invalid argument (sizes, region spec, N < 1, ...) */
+#define PARREP_ENOMEM (-2)   /* device allocation failed or the grid does not fit */
+#define PARREP_ECUDA (-3)    /* a CUDA runtime call failed */
+#define PARREP_ETIMEOUT (-4) /* a bounded device wait expired without progress */
+#define PARREP_ERANGE (-5)   /* a state left [0, hist_max], or a counter overflowed */
+#define PARREP_ESTATE (-6)   /* the call needs a completed run */
+
+typedef struct parrep_s* parrep_t;
+
+enum { PARREP_SCHLOGL = 1, PARREP_TOGGLE = 2 };
+enum { PARREP_THRESH_TIME = 0, PARREP_THRESH_STEPS = 1 };
+enum { PARREP_FP64 = 0, PARREP_FP32 = 1 };
+
+/* Reaction network (Sec. II.A).  Two kinds, each with four channels:
+ *   PARREP_SCHLOGL (Table I, 1 species x):
+ *     lambda_j = c[j] * s[j] * h_j(x),  h = (x(x-1), x(x-1)(x-2), 1, x),
+ *     eta = (+1, -1, +1, -1).  s holds the fixed factors (1/2, 1/6, 1, 1 for
+ *     combinatorial mass action; a/V, 1/V^2, bV, 1 for the volume form).
+ *   PARREP_TOGGLE (2 species U = x[0], V = x[1]):
+ *     lambda = (c0/(1+V^c1), c3/(1+U^c4), c2 U, c5 V),
+ *     eta = (+U, +V, -U, -V).
+ * The sensitivity parameters are c (4 for Schloegl, 6 for the toggle). */
+typedef struct {
+    int32_t kind;          /* PARREP_SCHLOGL or PARREP_TOGGLE */
+    int32_t n_species;     /* 1 for Schloegl, 2 for the toggle */
+    double c[6];           /* rate constants */
+    double s[4];           /* Schloegl fixed factors (ignored for the toggle) */
+    int32_t x0[2];         /* initial state X~ = x_0 (Algorithm 1 set-up) */
+    int32_t x0_uniform_hi; /* > 0: each species of x_0 drawn uniformly from {0..hi} */
+    int32_t hist_max[2];   /* states must stay in [0, hist_max]; histogram bins */
+} parrep_network;
+
+/* Metastable sets (Sec. III.A): region(x) = the first i with
+ * a[i][0]*x[0] + a[i][1]*x[1] < b[i], else n.  Integer arithmetic. */
+typedef struct {
+    int32_t n;          /* 1..4 tests, giving n+1 regions */
+    int32_t a[4][2];
+    int64_t b[4];
+} parrep_regions;
+
+typedef struct {
+    int32_t thresh_mode;   /* PARREP_THRESH_TIME (default) or _STEPS */
+    int32_t precision;     /* PARREP_FP64 (default) or PARREP_FP32 propensities */
+    int32_t fv_group;      /* Fleming-Viot group size: 1,2,4,8,16 or 32 (default 32) */
+    int32_t block_threads; /* CUDA block size, multiple of 32 up to 512 (0 = auto) */
+    int32_t chunk_steps;   /* lockstep steps between escape votes (0 = auto) */
+    int32_t debug_stall_barrier; /* fault injection: >= 0 makes block 0 leave at that
+                                    grid barrier so the others time out; -1 = off */
+    double T_burn;         /* FIM / RER integrate over [T_burn, T_end] (default 0) */
+    double wait_timeout_s; /* device wait limit without progress (default 10 s) */
+    void* stream;          /* cudaStream_t to run on (NULL = legacy default stream) */
+} parrep_options;
+
+typedef struct {
+    double T_s;                    /* simulated time reached (= T_end on success) */
+    int64_t events_decorr;         /* decorrelation jumps (all count toward T_s) */
+    int64_t events_dephase;        /* dephasing jumps (embedded chain, not in T_s) */
+    int64_t events_parallel_useful;   /* parallel-step jumps whose time entered T_s */
+    int64_t events_parallel_executed; /* parallel-step jumps simulated (first pass) */
+    int64_t events_replay;         /* jumps re-simulated at the cut of a chunk */
+    int64_t cycles;                /* ParRep cycles started */
+    int64_t escapes;               /* parallel steps that ended by an escape */
+    int64_t chunks;                /* escape votes */
+    int64_t special_chunks;        /* votes that found an escape or a time cut */
+    int32_t x0[2];                 /* the initial state used */
+    int32_t x_final[2];            /* X~ at the end of the run */
+    int32_t status;                /* PARREP_OK or the error of the run */
+    int32_t grid_blocks;           /* blocks of the persistent launch */
+    int32_t block_threads;
+    int32_t chunk_steps;
+    float kernel_ms;               /* device time of the run (CUDA events) */
+    float pad;
+} parrep_stats;
+
+typedef struct {
+    int64_t cycle;
+    int32_t W;             /* region of the cycle's dephasing and parallel step */
+    int32_t ended;         /* 1 if T_end was reached inside this cycle */
+    int64_t decorr_steps;  /* decorrelation jumps of the cycle */
+    int64_t dephase_steps; /* lockstep dephasing jumps n_p */
+    int64_t n_star;        /* N*: lockstep steps of the parallel step (0: not reached) */
+    int64_t k;             /* K, 0-based index of the first escaping replica; -1: none */
+    int32_t x_tilde[2];    /* X~ after the cycle (the escape state X^K_{N*}) */
+    double T_s;            /* clock at the end of the cycle */
+} parrep_cycle;
+
+/* Fills *opt with the defaults listed above. */
+void parrep_default_options(parrep_options* opt);
+
+/* Creates a ParRep engine for `net` with n_replicas = R replicas (Algorithm 1),
+ * regions `reg`, and thresholds t_corr / t_phase.  TIME mode (default): the
+ * decorrelation ends after t_corr time units of consecutive in-W time and the
+ * dephasing makes ceil(t_phase * a0(X~)) lockstep jumps.  STEPS mode: t_corr
+ * and t_phase are the paper's jump counts n_c and n_p (integers).
+ * Allocates the device buffers; returns EINVAL, ENOMEM or ECUDA on failure. */
+int parrep_create(const parrep_network* net, int64_t n_replicas, const parrep_regions* reg,
+                  double t_corr, double t_phase, parrep_t* out);
+
+/* Sets options (NULL restores the defaults).  Takes effect at the next run. */
+int parrep_set_options(parrep_t h, const parrep_options* opt);
+
+/* Runs Algorithm 1 from x_0 until the clock T_s reaches T_end (the crossing
+ * holding time is truncated), in one persistent cooperative launch on the
+ * handle's stream, and waits for it.  Resets all accumulators first.
+ * Errors: EINVAL (T_end < 0 or >= 2^23, T_burn > T_end), ERANGE (a state left
+ * [0, hist_max]), ETIMEOUT, ECUDA. */
+int parrep_run(parrep_t h, double T_end, uint64_t seed);
+
+/* Number of histogram bins: (hist_max[0]+1) * (hist_max[1]+1); bin of (U,V)
+ * is U*(hist_max[1]+1)+V. */
+int64_t parrep_n_bins(parrep_t h);
+
+/* Time-weighted histogram of the run normalised by T_s: out[b] = (time spent
+ * in bin b) / T_s -- the estimate of the stationary law pi (Sec. II.A ergodic
+ * average).  len must equal parrep_n_bins. */
+int parrep_histogram(parrep_t h, double* out, int64_t len);
+
+/* Raw time sums per bin before and after T_burn (either pointer may be NULL). */
+int parrep_histogram_raw(parrep_t h, double* pre, double* post, int64_t len);
+
+/* Path-space FIM (Sec. IV; Appendix A form): the time average over
+ * [T_burn, T_end] of sum_j lambda_j grad_c log lambda_j grad_c log lambda_j^T,
+ * row-major l x l with l = 4 (Schloegl) or 6 (toggle); len = l*l. */
+int parrep_fim(parrep_t h, double* out, int32_t len);
+
+/* Relative entropy rates (Appendix A) H(P^c | P^{c'}) for n perturbed
+ * parameter vectors c_prime (n x l, row-major): the time average over
+ * [T_burn, T_end] of sum_j lambda_j log(lambda_j/lambda'_j) - lambda_j + lambda'_j. */
+int parrep_rer(parrep_t h, const double* c_prime, int32_t n, double* out);
+
+/* Run statistics (host pointer). */
+int parrep_stats_get(parrep_t h, parrep_stats* out);
+
+/* Per-cycle log of the last run (host pointer): up to cap records, *n_out set
+ * to the number of cycles of the run (may exceed cap). */
+int parrep_cycle_log(parrep_t h, parrep_cycle* out, int64_t cap, int64_t* n_out);
+
+/* One dephasing stage (Algorithm 1) from x_tilde in region W for cycle index
+ * `cycle` and `seed`, with the handle's replicas, thresholds and options;
+ * out_states (host or device) receives n_replicas x 2 int32 states. */
+int parrep_dephase(parrep_t h, const int32_t* x_tilde, int32_t W, uint32_t cycle, uint64_t seed,
+                   int32_t* out_states);
+
+void parrep_destroy(parrep_t h);
+
+/* Message of the last error on h (or of the last failed parrep_create when
+ * h is NULL).  Valid until the next call on h. */
+const char* parrep_last_error(parrep_t h);
+
+/* Plain Gillespie SSA (Sec. II.A) for n_traj independent trajectories, one
+ * device thread each, from x0 to T_end.  Trajectory t draws from counter
+ * (t, step low, step high, SSA tag).  hist_out (host or device, len = bins):
+ * summed time-weighted histogram (time units); events_out (host, may be NULL):
+ * total jumps; kernel_ms (host, may be NULL): device time.  stream may be NULL. */
+int parrep_ssa(const parrep_network* net, int32_t precision, int64_t n_traj, double T_end, uint64_t seed,
+               double* hist_out, int64_t len, int64_t* events_out, float* kernel_ms, void* stream);
+
+/* Device Philox4x32-10 of n counters (ctr: n x 4, key: n x 2, out: n x 4
+ * uint32, all host pointers) -- exposes the generator the kernels use. */
+int parrep_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PARREP_H */

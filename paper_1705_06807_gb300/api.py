@@ -1,0 +1,211 @@
+"""Python face of the C ABI (include/parrep.h): the same entry points, with
+numpy / torch buffers marshalled to plain pointers.  Every step of the method
+runs in the CUDA library; this module only converts arguments and results.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib as L
+
+
+class ParRepError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{L.ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _check(rc, h=None):
+    if rc != L.PARREP_OK:
+        lib = L.load()
+        msg = lib.parrep_last_error(h)
+        raise ParRepError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def make_network(spec: dict, x0=None, x0_uniform_hi: int = 0) -> L.parrep_network:
+    """parrep_network from a network spec dict (see configs)."""
+    n = L.parrep_network()
+    n.kind = L.PARREP_SCHLOGL if spec["kind"] == "schlogl" else L.PARREP_TOGGLE
+    n.n_species = 1 if n.kind == L.PARREP_SCHLOGL else 2
+    for i, v in enumerate(spec["c"]):
+        n.c[i] = float(v)
+    for i, v in enumerate(spec.get("s", [1.0] * 4)):
+        n.s[i] = float(v)
+    hm = spec["hist_max"]
+    hm = [hm] if np.isscalar(hm) else list(hm)
+    n.hist_max[0] = int(hm[0])
+    n.hist_max[1] = int(hm[1]) if len(hm) > 1 else 0
+    x0 = [0, 0] if x0 is None else ([x0] if np.isscalar(x0) else list(x0))
+    n.x0[0] = int(x0[0])
+    n.x0[1] = int(x0[1]) if len(x0) > 1 else 0
+    n.x0_uniform_hi = int(x0_uniform_hi)
+    return n
+
+
+def make_regions(spec: dict) -> L.parrep_regions:
+    r = L.parrep_regions()
+    regs = spec["regions"]
+    r.n = len(regs)
+    for i, (a, b) in enumerate(regs):
+        a = list(a) + [0] * (2 - len(a))
+        r.a[i][0] = int(a[0])
+        r.a[i][1] = int(a[1])
+        r.b[i] = int(b)
+    return r
+
+
+def _buf(x):
+    """Pointer of a numpy array or a torch tensor (host or CUDA)."""
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return C.c_void_p(x.ctypes.data)
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous()
+        return C.c_void_p(x.data_ptr())
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+class ParRep:
+    """Handle of parrep_create / parrep_destroy with the other entry points as
+    methods of the same names (without the prefix)."""
+
+    def __init__(self, spec: dict, n_replicas: int, t_corr: float, t_phase: float, *, x0=None,
+                 x0_uniform_hi: int = 0, thresh: str = "time", precision: str = "f64", fv_group: int = 32,
+                 T_burn: float = 0.0, block_threads: int = 0, chunk_steps: int = 0, stream=None,
+                 wait_timeout_s: float = 10.0, debug_stall_barrier: int = -1):
+        self._lib = L.load()
+        self.spec = spec
+        self.L = 4 if spec["kind"] == "schlogl" else 6
+        self._net = make_network(spec, x0, x0_uniform_hi)
+        self._reg = make_regions(spec)
+        h = C.c_void_p()
+        _check(self._lib.parrep_create(C.byref(self._net), int(n_replicas), C.byref(self._reg), float(t_corr),
+                                       float(t_phase), C.byref(h)))
+        self.h = h
+        self.n_replicas = int(n_replicas)
+        self.set_options(thresh=thresh, precision=precision, fv_group=fv_group, T_burn=T_burn,
+                         block_threads=block_threads, chunk_steps=chunk_steps, stream=stream,
+                         wait_timeout_s=wait_timeout_s, debug_stall_barrier=debug_stall_barrier)
+
+    def set_options(self, *, thresh="time", precision="f64", fv_group=32, T_burn=0.0, block_threads=0,
+                    chunk_steps=0, stream=None, wait_timeout_s=10.0, debug_stall_barrier=-1):
+        o = L.parrep_options()
+        self._lib.parrep_default_options(C.byref(o))
+        o.thresh_mode = L.PARREP_THRESH_STEPS if thresh == "steps" else L.PARREP_THRESH_TIME
+        o.precision = L.PARREP_FP32 if precision == "f32" else L.PARREP_FP64
+        o.fv_group = int(fv_group)
+        o.block_threads = int(block_threads)
+        o.chunk_steps = int(chunk_steps)
+        o.T_burn = float(T_burn)
+        o.wait_timeout_s = float(wait_timeout_s)
+        o.debug_stall_barrier = int(debug_stall_barrier)
+        if stream is not None:
+            o.stream = C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+        _check(self._lib.parrep_set_options(self.h, C.byref(o)), self.h)
+        self._opt = o
+
+    # -- run --
+    def run(self, T_end: float, seed: int):
+        _check(self._lib.parrep_run(self.h, float(T_end), int(seed) & 0xFFFFFFFFFFFFFFFF), self.h)
+        return self.stats()
+
+    def run_status(self, T_end: float, seed: int) -> int:
+        """parrep_run returning the status code instead of raising."""
+        return self._lib.parrep_run(self.h, float(T_end), int(seed) & 0xFFFFFFFFFFFFFFFF)
+
+    @property
+    def n_bins(self) -> int:
+        return int(self._lib.parrep_n_bins(self.h))
+
+    # -- outputs --
+    def histogram(self, out=None):
+        if out is None:
+            out = np.zeros(self.n_bins)
+        _check(self._lib.parrep_histogram(self.h, _buf(out), self.n_bins), self.h)
+        return out
+
+    def histogram_raw(self):
+        pre = np.zeros(self.n_bins)
+        post = np.zeros(self.n_bins)
+        _check(self._lib.parrep_histogram_raw(self.h, _buf(pre), _buf(post), self.n_bins), self.h)
+        return pre, post
+
+    def fim(self, out=None):
+        if out is None:
+            out = np.zeros((self.L, self.L))
+        _check(self._lib.parrep_fim(self.h, _buf(out), self.L * self.L), self.h)
+        return out
+
+    def rer(self, c_prime):
+        cp = np.ascontiguousarray(c_prime, dtype=np.float64).reshape(-1, self.L)
+        out = np.zeros(len(cp))
+        _check(self._lib.parrep_rer(self.h, _buf(cp), len(cp), _buf(out)), self.h)
+        return out
+
+    def stats(self) -> dict:
+        s = L.parrep_stats()
+        _check(self._lib.parrep_stats_get(self.h, C.byref(s)), self.h)
+        d = {k: getattr(s, k) for k, _ in L.parrep_stats._fields_ if k != "pad"}
+        d["x0"] = (s.x0[0], s.x0[1])
+        d["x_final"] = (s.x_final[0], s.x_final[1])
+        return d
+
+    def cycle_log(self, cap: int = 65536):
+        buf = (L.parrep_cycle * max(cap, 1))()
+        n = C.c_int64(0)
+        _check(self._lib.parrep_cycle_log(self.h, buf, cap, C.byref(n)), self.h)
+        m = min(n.value, cap)
+        return [dict(cycle=buf[i].cycle, W=buf[i].W, ended=buf[i].ended, decorr_steps=buf[i].decorr_steps,
+                     dephase_steps=buf[i].dephase_steps, n_star=buf[i].n_star, k=buf[i].k,
+                     x_tilde=(buf[i].x_tilde[0], buf[i].x_tilde[1]), T_s=buf[i].T_s) for i in range(m)]
+
+    def dephase(self, x_tilde, W: int, cycle: int, seed: int):
+        xt = (C.c_int32 * 2)(*(list(x_tilde) + [0] * (2 - len(x_tilde))))
+        out = np.zeros((self.n_replicas, 2), dtype=np.int32)
+        _check(self._lib.parrep_dephase(self.h, xt, int(W), int(cycle), int(seed), _buf(out)), self.h)
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.parrep_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def parrep_ssa(spec: dict, n_traj: int, x0, T_end: float, seed: int, *, precision: str = "f64", stream=None,
+               hist_out=None):
+    """Plain SSA on the GPU.  Returns (histogram in time units, events, kernel ms)."""
+    lib = L.load()
+    net = make_network(spec, x0)
+    nb = int(np.prod([h + 1 for h in ([spec["hist_max"]] if np.isscalar(spec["hist_max"]) else spec["hist_max"])]))
+    hist = np.zeros(nb) if hist_out is None else hist_out
+    ev = C.c_int64(0)
+    ms = C.c_float(0.0)
+    st = None if stream is None else C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+    _check(lib.parrep_ssa(C.byref(net), L.PARREP_FP32 if precision == "f32" else L.PARREP_FP64, int(n_traj),
+                          float(T_end), int(seed), _buf(hist), nb, C.byref(ev), C.byref(ms), st))
+    return hist, int(ev.value), float(ms.value)
+
+
+def parrep_philox(ctr, key):
+    """Device Philox4x32-10 on n counters (n x 4) and keys (n x 2)."""
+    lib = L.load()
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    key = np.ascontiguousarray(key, dtype=np.uint32).reshape(-1, 2)
+    out = np.zeros_like(ctr)
+    _check(lib.parrep_philox(_buf(ctr), _buf(key), len(ctr), _buf(out)))
+    return out

@@ -1,0 +1,655 @@
+// Host side of the C ABI declared in include/parrep.h: argument checks,
+// device buffers, launch configuration and result read-back.  All arithmetic
+// of the method runs in the kernels of parrep_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "parrep.h"
+#include "parrep_internal.h"
+
+using namespace parrep;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+constexpr long long kLogCap = 1 << 16;
+constexpr int kMaxChunk = 1 << 16;
+constexpr int kSmemHistLimit = 160 * 1024;
+
+}  // namespace
+
+struct parrep_s {
+    parrep_network net;
+    parrep_regions reg;
+    int64_t R = 0;
+    double t_corr = 0, t_phase = 0;
+    parrep_options opt;
+    int nbins = 0, L = 4;
+    NetDev nd{};
+    // device buffers
+    double *d_prodU_d = nullptr, *d_prodV_d = nullptr;
+    float *d_prodU_f = nullptr, *d_prodV_f = nullptr;
+    double *d_gradU_n = nullptr, *d_gradV_n = nullptr, *d_c = nullptr, *d_s = nullptr;
+    RunCtl* d_ctl = nullptr;
+    unsigned long long *d_hist_pre = nullptr, *d_hist_post = nullptr, *d_step_sum = nullptr, *d_tau_at = nullptr;
+    CycleRecDev* d_log = nullptr;
+    double *d_out = nullptr, *d_out2 = nullptr, *d_fim = nullptr, *d_rer = nullptr, *d_cprime = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // last run
+    bool has_run = false;
+    RunCtl h_ctl{};
+    double T_end = 0, T_burn = 0;
+    parrep_stats stats{};
+    std::string err;
+};
+
+static int fail(parrep_t h, int code, const std::string& msg) {
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+static int cuda_fail(parrep_t h, cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(h, PARREP_ECUDA, m);
+}
+
+#define CK(h, call)                                           \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+    } while (0)
+
+static cudaStream_t stream_of(parrep_t h) { return (cudaStream_t)h->opt.stream; }
+
+extern "C" void parrep_default_options(parrep_options* o) {
+    memset(o, 0, sizeof(*o));
+    o->thresh_mode = PARREP_THRESH_TIME;
+    o->precision = PARREP_FP64;
+    o->fv_group = 32;
+    o->block_threads = 0;
+    o->chunk_steps = 0;
+    o->debug_stall_barrier = -1;
+    o->T_burn = 0.0;
+    o->wait_timeout_s = 10.0;
+    o->stream = nullptr;
+}
+
+static int check_network(const parrep_network* net, const parrep_regions* reg, std::string& why) {
+    if (!net || !reg) { why = "null network or regions"; return 0; }
+    if (net->kind != PARREP_SCHLOGL && net->kind != PARREP_TOGGLE) { why = "unknown network kind"; return 0; }
+    const int nsp = net->kind == PARREP_SCHLOGL ? 1 : 2;
+    if (net->n_species != nsp) { why = "n_species does not match the kind"; return 0; }
+    if (net->hist_max[0] < 0 || net->hist_max[1] < 0 || (nsp == 1 && net->hist_max[1] != 0)) {
+        why = "bad hist_max";
+        return 0;
+    }
+    const long long nb = (long long)(net->hist_max[0] + 1) * (net->hist_max[1] + 1);
+    if (nb > (1ll << 24)) { why = "more than 2^24 histogram bins"; return 0; }
+    const int L = nsp == 1 ? 4 : 6;
+    for (int i = 0; i < L; ++i)
+        if (!std::isfinite(net->c[i])) { why = "non-finite rate constant"; return 0; }
+    if (nsp == 1) {
+        for (int i = 0; i < 4; ++i)
+            if (!(net->c[i] >= 0.0) || !(net->s[i] >= 0.0) || !std::isfinite(net->s[i])) {
+                why = "Schloegl constants must be finite and >= 0";
+                return 0;
+            }
+        if (!(net->c[2] * net->s[2] > 0.0)) { why = "Schloegl needs c3*s3 > 0 (a0 > 0 everywhere)"; return 0; }
+    } else {
+        if (!(net->c[0] > 0.0) || !(net->c[3] > 0.0) || !(net->c[2] >= 0.0) || !(net->c[5] >= 0.0)) {
+            why = "toggle rates must be positive";
+            return 0;
+        }
+    }
+    if (reg->n < 1 || reg->n > 4) { why = "regions: n must be 1..4"; return 0; }
+    if (net->x0_uniform_hi < 0) { why = "x0_uniform_hi < 0"; return 0; }
+    if (net->x0_uniform_hi > 0) {
+        if (net->x0_uniform_hi > net->hist_max[0] || (nsp == 2 && net->x0_uniform_hi > net->hist_max[1])) {
+            why = "x0_uniform_hi beyond hist_max";
+            return 0;
+        }
+    } else {
+        if (net->x0[0] < 0 || net->x0[0] > net->hist_max[0] ||
+            (nsp == 2 && (net->x0[1] < 0 || net->x0[1] > net->hist_max[1]))) {
+            why = "x0 outside [0, hist_max]";
+            return 0;
+        }
+    }
+    return 1;
+}
+
+// Host-built tables (toggle production rates, their log-derivatives in the
+// Hill exponent) and the network constants as the kernels read them.
+static void build_net(const parrep_network* net, const parrep_regions* reg, NetDev& nd,
+                      std::vector<double>& pU, std::vector<double>& pV, std::vector<double>& gU,
+                      std::vector<double>& gV) {
+    memset(&nd, 0, sizeof(nd));
+    nd.kind = net->kind;
+    nd.nsp = net->n_species;
+    nd.hist_max0 = net->hist_max[0];
+    nd.hist_max1 = net->hist_max[1];
+    nd.ystride = net->hist_max[1] + 1;
+    nd.nbins = (net->hist_max[0] + 1) * (net->hist_max[1] + 1);
+    nd.nreg = reg->n;
+    for (int i = 0; i < reg->n; ++i) {
+        nd.ra0[i] = reg->a[i][0];
+        nd.ra1[i] = net->n_species > 1 ? reg->a[i][1] : 0;
+        nd.rb[i] = reg->b[i];
+    }
+    if (net->kind == PARREP_SCHLOGL) {
+        for (int j = 0; j < 4; ++j) {
+            nd.A[j] = net->c[j] * net->s[j];
+            nd.Af[j] = (float)nd.A[j];
+        }
+    } else {
+        nd.dU = net->c[2];
+        nd.dV = net->c[5];
+        nd.dUf = (float)net->c[2];
+        nd.dVf = (float)net->c[5];
+        pU.resize(net->hist_max[1] + 1);
+        gU.resize(net->hist_max[1] + 1);
+        for (int v = 0; v <= net->hist_max[1]; ++v) {
+            const double p = pow((double)v, net->c[1]);
+            pU[v] = net->c[0] / (1.0 + p);
+            gU[v] = v > 0 ? -p * log((double)v) / (1.0 + p) : 0.0;
+        }
+        pV.resize(net->hist_max[0] + 1);
+        gV.resize(net->hist_max[0] + 1);
+        for (int u = 0; u <= net->hist_max[0]; ++u) {
+            const double p = pow((double)u, net->c[4]);
+            pV[u] = net->c[3] / (1.0 + p);
+            gV[u] = u > 0 ? -p * log((double)u) / (1.0 + p) : 0.0;
+        }
+    }
+}
+
+template <typename T>
+static cudaError_t upload(T** dst, const std::vector<T>& v) {
+    if (v.empty()) { *dst = nullptr; return cudaSuccess; }
+    cudaError_t e = cudaMalloc((void**)dst, v.size() * sizeof(T));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+static void free_all(parrep_t h) {
+    void* ptrs[] = {h->d_prodU_d, h->d_prodV_d, h->d_prodU_f, h->d_prodV_f, h->d_gradU_n, h->d_gradV_n,
+                    h->d_c, h->d_s, h->d_ctl, h->d_hist_pre, h->d_hist_post, h->d_step_sum, h->d_tau_at,
+                    h->d_log, h->d_out, h->d_out2, h->d_fim, h->d_rer, h->d_cprime};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+}
+
+extern "C" int parrep_create(const parrep_network* net, int64_t n_replicas, const parrep_regions* reg,
+                             double t_corr, double t_phase, parrep_t* out) {
+    if (!out) return fail(nullptr, PARREP_EINVAL, "out is null");
+    *out = nullptr;
+    std::string why;
+    if (!check_network(net, reg, why)) return fail(nullptr, PARREP_EINVAL, why);
+    if (n_replicas < 1 || n_replicas > (1ll << 30)) return fail(nullptr, PARREP_EINVAL, "n_replicas outside [1, 2^30]");
+    if (!(t_corr >= 0.0) || !(t_phase >= 0.0) || !(t_corr < kTEndLimit * 1024) || !(t_phase < 1e12))
+        return fail(nullptr, PARREP_EINVAL, "t_corr / t_phase must be finite and >= 0");
+    parrep_s* h = new parrep_s();
+    h->net = *net;
+    h->reg = *reg;
+    h->R = n_replicas;
+    h->t_corr = t_corr;
+    h->t_phase = t_phase;
+    parrep_default_options(&h->opt);
+    h->nbins = (net->hist_max[0] + 1) * (net->hist_max[1] + 1);
+    h->L = net->kind == PARREP_SCHLOGL ? 4 : 6;
+    std::vector<double> pU, pV, gU, gV;
+    build_net(net, reg, h->nd, pU, pV, gU, gV);
+    cudaError_t e = cudaSuccess;
+    std::vector<float> pUf(pU.begin(), pU.end()), pVf(pV.begin(), pV.end());
+    for (size_t i = 0; i < pU.size(); ++i) pUf[i] = (float)pU[i];
+    for (size_t i = 0; i < pV.size(); ++i) pVf[i] = (float)pV[i];
+    std::vector<double> cv(net->c, net->c + 6), sv(net->s, net->s + 4);
+#define TRY(x)                      \
+    do {                            \
+        e = (x);                    \
+        if (e != cudaSuccess) goto bad; \
+    } while (0)
+    TRY(upload(&h->d_prodU_d, pU));
+    TRY(upload(&h->d_prodV_d, pV));
+    TRY(upload(&h->d_prodU_f, pUf));
+    TRY(upload(&h->d_prodV_f, pVf));
+    TRY(upload(&h->d_gradU_n, gU));
+    TRY(upload(&h->d_gradV_n, gV));
+    TRY(upload(&h->d_c, cv));
+    TRY(upload(&h->d_s, sv));
+    TRY(cudaMalloc((void**)&h->d_ctl, sizeof(RunCtl)));
+    TRY(cudaMalloc((void**)&h->d_hist_pre, sizeof(unsigned long long) * h->nbins));
+    TRY(cudaMalloc((void**)&h->d_hist_post, sizeof(unsigned long long) * h->nbins));
+    TRY(cudaMalloc((void**)&h->d_step_sum, sizeof(unsigned long long) * kMaxChunk));
+    TRY(cudaMalloc((void**)&h->d_tau_at, sizeof(unsigned long long) * 2 * (size_t)n_replicas));
+    TRY(cudaMalloc((void**)&h->d_log, sizeof(CycleRecDev) * kLogCap));
+    TRY(cudaMalloc((void**)&h->d_out, sizeof(double) * h->nbins));
+    TRY(cudaMalloc((void**)&h->d_out2, sizeof(double) * h->nbins));
+    TRY(cudaMalloc((void**)&h->d_fim, sizeof(double) * 36));
+    TRY(cudaMalloc((void**)&h->d_rer, sizeof(double) * 8));
+    TRY(cudaMalloc((void**)&h->d_cprime, sizeof(double) * 8 * 6));
+    TRY(cudaEventCreate(&h->ev0));
+    TRY(cudaEventCreate(&h->ev1));
+    TRY(cudaMemset(h->d_hist_pre, 0, sizeof(unsigned long long) * h->nbins));
+    TRY(cudaMemset(h->d_hist_post, 0, sizeof(unsigned long long) * h->nbins));
+    h->nd.prodU_d = h->d_prodU_d;
+    h->nd.prodV_d = h->d_prodV_d;
+    h->nd.prodU_f = h->d_prodU_f;
+    h->nd.prodV_f = h->d_prodV_f;
+#undef TRY
+    *out = h;
+    return PARREP_OK;
+bad : {
+    std::string m = std::string("parrep_create: ") + cudaGetErrorString(e);
+    free_all(h);
+    delete h;
+    return fail(nullptr, e == cudaErrorMemoryAllocation ? PARREP_ENOMEM : PARREP_ECUDA, m);
+}
+}
+
+extern "C" int parrep_set_options(parrep_t h, const parrep_options* o) {
+    if (!h) return PARREP_EINVAL;
+    parrep_options d;
+    parrep_default_options(&d);
+    if (!o) { h->opt = d; return PARREP_OK; }
+    if (o->thresh_mode != PARREP_THRESH_TIME && o->thresh_mode != PARREP_THRESH_STEPS)
+        return fail(h, PARREP_EINVAL, "thresh_mode");
+    if (o->precision != PARREP_FP64 && o->precision != PARREP_FP32) return fail(h, PARREP_EINVAL, "precision");
+    const int g = o->fv_group;
+    if (!(g == 1 || g == 2 || g == 4 || g == 8 || g == 16 || g == 32))
+        return fail(h, PARREP_EINVAL, "fv_group must be 1, 2, 4, 8, 16 or 32");
+    if (o->block_threads < 0 || o->block_threads > 512 || (o->block_threads % 32) != 0)
+        return fail(h, PARREP_EINVAL, "block_threads must be a multiple of 32 up to 512 (0 = auto)");
+    if (o->chunk_steps < 0 || o->chunk_steps > kMaxChunk) return fail(h, PARREP_EINVAL, "chunk_steps");
+    if (!(o->T_burn >= 0.0) || !(o->T_burn < kTEndLimit)) return fail(h, PARREP_EINVAL, "T_burn");
+    if (!(o->wait_timeout_s > 0.0) || !(o->wait_timeout_s <= 3600.0)) return fail(h, PARREP_EINVAL, "wait_timeout_s");
+    if (o->thresh_mode == PARREP_THRESH_STEPS) {
+        if (h->t_corr != floor(h->t_corr) || h->t_phase != floor(h->t_phase) || h->t_phase > 4294967294.0)
+            return fail(h, PARREP_EINVAL, "STEPS mode needs integer t_corr, t_phase (t_phase < 2^32-1)");
+    } else if (!(h->t_corr < kTEndLimit)) {
+        return fail(h, PARREP_EINVAL, "TIME mode needs t_corr < 2^23");
+    }
+    h->opt = *o;
+    return PARREP_OK;
+}
+
+static void launch_shape(parrep_t h, int& threads, int& grid, int& S) {
+    threads = h->opt.block_threads > 0 ? h->opt.block_threads : 128;
+    if ((long long)threads > ((h->R + 31) / 32) * 32) threads = (int)(((h->R + 31) / 32) * 32);
+    grid = (int)((h->R + threads - 1) / threads);
+    S = h->opt.chunk_steps > 0 ? h->opt.chunk_steps : 256;
+}
+
+extern "C" int parrep_run(parrep_t h, double T_end, uint64_t seed) {
+    if (!h) return PARREP_EINVAL;
+    h->has_run = false;
+    if (!(T_end >= 0.0) || !(T_end < kTEndLimit)) return fail(h, PARREP_EINVAL, "T_end must be in [0, 2^23)");
+    if (h->opt.T_burn > T_end) return fail(h, PARREP_EINVAL, "T_burn > T_end");
+    if (h->opt.thresh_mode == PARREP_THRESH_STEPS &&
+        (h->t_corr != floor(h->t_corr) || h->t_phase != floor(h->t_phase)))
+        return fail(h, PARREP_EINVAL, "STEPS mode needs integer t_corr, t_phase");
+    int threads, grid, S;
+    launch_shape(h, threads, grid, S);
+    int smem = h->nbins * 8 <= kSmemHistLimit ? h->nbins * 8 : 0;
+    int per_sm = 0, dev = 0, nsm = 0;
+    CK(h, cudaGetDevice(&dev));
+    CK(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    int ea = kernel_attrs(h->opt.precision, &per_sm, smem, threads);
+    if (ea != 0) return cuda_fail(h, (cudaError_t)ea, "kernel attributes");
+    if ((long long)per_sm * nsm < grid && smem > 0) {
+        smem = 0;  // global-memory histogram instead of shared
+        ea = kernel_attrs(h->opt.precision, &per_sm, smem, threads);
+        if (ea != 0) return cuda_fail(h, (cudaError_t)ea, "kernel attributes");
+    }
+    if ((long long)per_sm * nsm < grid)
+        return fail(h, PARREP_ENOMEM, "n_replicas exceeds one co-resident cooperative grid");
+    RunParams p;
+    memset(&p, 0, sizeof(p));
+    p.net = h->nd;
+    p.prec = h->opt.precision;
+    p.thresh = h->opt.thresh_mode;
+    p.R = (int)h->R;
+    p.G = h->opt.fv_group;
+    p.S = S;
+    p.use_smem_hist = smem > 0;
+    if (p.thresh == PARREP_THRESH_STEPS) {
+        p.n_c = (long long)h->t_corr;
+        p.n_p = (long long)h->t_phase;
+    } else {
+        p.q_tcorr = (unsigned long long)llrint(h->t_corr * kQScale);
+        p.t_phase = h->t_phase;
+    }
+    p.q_Tend = (unsigned long long)llrint(T_end * kQScale);
+    p.q_Tburn = (unsigned long long)llrint(h->opt.T_burn * kQScale);
+    p.seed = seed;
+    p.x00 = h->net.x0[0];
+    p.x01 = h->net.n_species > 1 ? h->net.x0[1] : 0;
+    p.x0_hi = h->net.x0_uniform_hi;
+    p.ctl = h->d_ctl;
+    p.hist_pre = h->d_hist_pre;
+    p.hist_post = h->d_hist_post;
+    p.step_sum = h->d_step_sum;
+    p.tau_at = h->d_tau_at;
+    p.log = h->d_log;
+    p.log_cap = kLogCap;
+    p.timeout_ns = (long long)(h->opt.wait_timeout_s * 1e9);
+    p.stall_barrier = h->opt.debug_stall_barrier;
+    cudaStream_t st = stream_of(h);
+    CK(h, cudaMemsetAsync(h->d_ctl, 0, sizeof(RunCtl), st));
+    CK(h, cudaMemsetAsync(h->d_hist_pre, 0, sizeof(unsigned long long) * h->nbins, st));
+    CK(h, cudaMemsetAsync(h->d_hist_post, 0, sizeof(unsigned long long) * h->nbins, st));
+    CK(h, cudaEventRecord(h->ev0, st));
+    CK(h, launch_run(p, grid, threads, smem, st));
+    CK(h, cudaEventRecord(h->ev1, st));
+    CK(h, cudaMemcpyAsync(&h->h_ctl, h->d_ctl, sizeof(RunCtl), cudaMemcpyDeviceToHost, st));
+    CK(h, cudaStreamSynchronize(st));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    const RunCtl& c = h->h_ctl;
+    parrep_stats& s = h->stats;
+    memset(&s, 0, sizeof(s));
+    s.T_s = (double)c.Ts * kQInv;
+    s.events_decorr = (int64_t)c.ev_decorr;
+    s.events_dephase = (int64_t)c.ev_dephase;
+    s.events_parallel_useful = (int64_t)c.ev_useful;
+    s.events_parallel_executed = (int64_t)c.ev_par_exec;
+    s.events_replay = (int64_t)c.ev_replay;
+    s.cycles = (int64_t)c.cycles;
+    s.escapes = (int64_t)c.escapes;
+    s.chunks = (int64_t)c.chunks;
+    s.special_chunks = (int64_t)c.special;
+    s.x0[0] = c.x00;
+    s.x0[1] = c.x01;
+    s.x_final[0] = c.xt0;
+    s.x_final[1] = c.xt1;
+    s.status = c.status;
+    s.grid_blocks = grid;
+    s.block_threads = threads;
+    s.chunk_steps = S;
+    s.kernel_ms = ms;
+    h->T_end = T_end;
+    h->T_burn = h->opt.T_burn;
+    if (c.status != 0) {
+        const char* what = c.status == PARREP_ERANGE     ? "a state left [0, hist_max] or a step counter overflowed"
+                           : c.status == PARREP_ETIMEOUT ? "a device wait timed out without progress"
+                           : c.status == PARREP_EINVAL   ? "invalid initial state"
+                                                         : "device error";
+        return fail(h, c.status, what);
+    }
+    h->has_run = true;
+    return PARREP_OK;
+}
+
+extern "C" int64_t parrep_n_bins(parrep_t h) { return h ? (int64_t)h->nbins : 0; }
+
+extern "C" int parrep_histogram(parrep_t h, double* out, int64_t len) {
+    if (!h || !out) return PARREP_EINVAL;
+    if (!h->has_run) return fail(h, PARREP_ESTATE, "no completed run");
+    if (len != h->nbins) return fail(h, PARREP_EINVAL, "len != n_bins");
+    const double Ts = h->stats.T_s;
+    cudaStream_t st = stream_of(h);
+    CK(h, launch_hist_normalise(h->d_hist_pre, h->d_hist_post, h->nbins, Ts > 0 ? 1.0 / Ts : 0.0, nullptr, nullptr,
+                                h->d_out, st));
+    CK(h, cudaMemcpyAsync(out, h->d_out, sizeof(double) * h->nbins, cudaMemcpyDefault, st));
+    CK(h, cudaStreamSynchronize(st));
+    return PARREP_OK;
+}
+
+extern "C" int parrep_histogram_raw(parrep_t h, double* pre, double* post, int64_t len) {
+    if (!h) return PARREP_EINVAL;
+    if (!h->has_run) return fail(h, PARREP_ESTATE, "no completed run");
+    if (len != h->nbins) return fail(h, PARREP_EINVAL, "len != n_bins");
+    cudaStream_t st = stream_of(h);
+    CK(h, launch_hist_normalise(h->d_hist_pre, h->d_hist_post, h->nbins, 0.0, h->d_out, h->d_out2, nullptr, st));
+    if (pre) CK(h, cudaMemcpyAsync(pre, h->d_out, sizeof(double) * h->nbins, cudaMemcpyDefault, st));
+    if (post) CK(h, cudaMemcpyAsync(post, h->d_out2, sizeof(double) * h->nbins, cudaMemcpyDefault, st));
+    CK(h, cudaStreamSynchronize(st));
+    return PARREP_OK;
+}
+
+static int contract(parrep_t h, const double* cprime, int n, double* fim_host, double* rer_host) {
+    cudaStream_t st = stream_of(h);
+    CK(h, cudaMemsetAsync(h->d_fim, 0, sizeof(double) * 36, st));
+    CK(h, cudaMemsetAsync(h->d_rer, 0, sizeof(double) * 8, st));
+    if (n > 0)
+        CK(h, cudaMemcpyAsync(h->d_cprime, cprime, sizeof(double) * n * h->L, cudaMemcpyHostToDevice, st));
+    CK(h, launch_fim_rer(h->nd, h->d_c, h->d_s, h->d_hist_post, h->d_gradU_n, h->d_gradV_n, h->d_cprime, n,
+                         h->d_fim, h->d_rer, st));
+    if (fim_host) CK(h, cudaMemcpyAsync(fim_host, h->d_fim, sizeof(double) * 36, cudaMemcpyDeviceToHost, st));
+    if (rer_host) CK(h, cudaMemcpyAsync(rer_host, h->d_rer, sizeof(double) * 8, cudaMemcpyDeviceToHost, st));
+    CK(h, cudaStreamSynchronize(st));
+    return PARREP_OK;
+}
+
+extern "C" int parrep_fim(parrep_t h, double* out, int32_t len) {
+    if (!h || !out) return PARREP_EINVAL;
+    if (!h->has_run) return fail(h, PARREP_ESTATE, "no completed run");
+    if (len != h->L * h->L) return fail(h, PARREP_EINVAL, "len != l*l");
+    const double span = h->stats.T_s - h->T_burn;
+    if (!(span > 0.0)) return fail(h, PARREP_ESTATE, "empty window [T_burn, T_end]");
+    double buf[36];
+    int rc = contract(h, nullptr, 0, buf, nullptr);
+    if (rc) return rc;
+    double res[36];
+    for (int i = 0; i < h->L * h->L; ++i) res[i] = buf[i] / span;
+    CK(h, cudaMemcpy(out, res, sizeof(double) * h->L * h->L, cudaMemcpyDefault));
+    return PARREP_OK;
+}
+
+extern "C" int parrep_rer(parrep_t h, const double* c_prime, int32_t n, double* out) {
+    if (!h || !out || (n > 0 && !c_prime) || n < 0) return PARREP_EINVAL;
+    if (!h->has_run) return fail(h, PARREP_ESTATE, "no completed run");
+    const double span = h->stats.T_s - h->T_burn;
+    if (!(span > 0.0)) return fail(h, PARREP_ESTATE, "empty window [T_burn, T_end]");
+    std::vector<double> res(n);
+    for (int k0 = 0; k0 < n; k0 += 8) {
+        const int m = n - k0 < 8 ? n - k0 : 8;
+        for (int k = 0; k < m; ++k)
+            for (int i = 0; i < h->L; ++i)
+                if (!(c_prime[(k0 + k) * h->L + i] > 0.0) && i != 1 && i != 4)
+                    return fail(h, PARREP_EINVAL, "perturbed rate constants must be > 0");
+        double buf[8];
+        int rc = contract(h, c_prime + (size_t)k0 * h->L, m, nullptr, buf);
+        if (rc) return rc;
+        for (int k = 0; k < m; ++k) res[k0 + k] = buf[k] / span;
+    }
+    if (n > 0) CK(h, cudaMemcpy(out, res.data(), sizeof(double) * n, cudaMemcpyDefault));
+    return PARREP_OK;
+}
+
+extern "C" int parrep_stats_get(parrep_t h, parrep_stats* out) {
+    if (!h || !out) return PARREP_EINVAL;
+    *out = h->stats;
+    return PARREP_OK;
+}
+
+extern "C" int parrep_cycle_log(parrep_t h, parrep_cycle* out, int64_t cap, int64_t* n_out) {
+    if (!h || (!out && cap > 0) || cap < 0) return PARREP_EINVAL;
+    if (!h->has_run && h->h_ctl.log_n == 0) return fail(h, PARREP_ESTATE, "no run");
+    const long long n = h->h_ctl.log_n;
+    if (n_out) *n_out = n;
+    long long m = n < cap ? n : cap;
+    if (m > kLogCap) m = kLogCap;
+    if (m <= 0) return PARREP_OK;
+    std::vector<CycleRecDev> buf(m);
+    CK(h, cudaMemcpy(buf.data(), h->d_log, sizeof(CycleRecDev) * m, cudaMemcpyDeviceToHost));
+    for (long long i = 0; i < m; ++i) {
+        parrep_cycle& c = out[i];
+        const CycleRecDev& d = buf[i];
+        c.cycle = d.cycle;
+        c.W = d.W;
+        c.ended = d.ended;
+        c.decorr_steps = d.decorr_steps;
+        c.dephase_steps = d.dephase_steps;
+        c.n_star = d.n_star;
+        c.k = d.k;
+        c.x_tilde[0] = d.xt0;
+        c.x_tilde[1] = d.xt1;
+        c.T_s = (double)d.Ts * kQInv;
+    }
+    return PARREP_OK;
+}
+
+extern "C" int parrep_dephase(parrep_t h, const int32_t* x_tilde, int32_t W, uint32_t cycle, uint64_t seed,
+                              int32_t* out_states) {
+    if (!h || !x_tilde || !out_states) return PARREP_EINVAL;
+    const int x0 = x_tilde[0], x1 = h->net.n_species > 1 ? x_tilde[1] : 0;
+    if (x0 < 0 || x0 > h->net.hist_max[0] || x1 < 0 || x1 > h->net.hist_max[1])
+        return fail(h, PARREP_EINVAL, "x_tilde outside [0, hist_max]");
+    long long np;
+    if (h->opt.thresh_mode == PARREP_THRESH_STEPS) {
+        np = (long long)h->t_phase;
+    } else {
+        // a0 at X~ in binary64, the same expression as the kernels'
+        double l0, l1, l2, l3;
+        const NetDev& N = h->nd;
+        if (N.kind == PARREP_SCHLOGL) {
+            const double xd = (double)x0;
+            const double a = xd * (xd - 1.0);
+            const double b = a * (xd - 2.0);
+            l0 = N.A[0] * a;
+            l1 = N.A[1] * b;
+            l2 = N.A[2];
+            l3 = N.A[3] * xd;
+        } else {
+            std::vector<double> t(1);
+            CK(h, cudaMemcpy(&l0, h->d_prodU_d + x1, sizeof(double), cudaMemcpyDeviceToHost));
+            CK(h, cudaMemcpy(&l1, h->d_prodV_d + x0, sizeof(double), cudaMemcpyDeviceToHost));
+            l2 = N.dU * (double)x0;
+            l3 = N.dV * (double)x1;
+        }
+        const double a0 = ((l0 + l1) + l2) + l3;
+        const double n = ceil(h->t_phase * a0);
+        if (!(n < 4294967295.0)) return fail(h, PARREP_ERANGE, "dephasing step count >= 2^32-1");
+        np = (long long)n;
+    }
+    RunParams p;
+    memset(&p, 0, sizeof(p));
+    p.net = h->nd;
+    p.prec = h->opt.precision;
+    p.R = (int)h->R;
+    p.G = h->opt.fv_group;
+    p.seed = seed;
+    p.ctl = h->d_ctl;
+    cudaStream_t st = stream_of(h);
+    int* d_states = nullptr;
+    CK(h, cudaMalloc((void**)&d_states, sizeof(int) * 2 * h->R));
+    CK(h, cudaMemsetAsync(h->d_ctl, 0, sizeof(RunCtl), st));
+    const int threads = 128;
+    const int grid = (int)((h->R + threads - 1) / threads);
+    cudaError_t e = launch_dephase(p, x0, x1, W, cycle, np, d_states, grid, threads, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out_states, d_states, sizeof(int) * 2 * h->R, cudaMemcpyDefault, st);
+    int status = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&status, &h->d_ctl->status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d_states);
+    if (e != cudaSuccess) return cuda_fail(h, e, "dephase");
+    if (status) return fail(h, status, "a dephasing state left [0, hist_max]");
+    return PARREP_OK;
+}
+
+extern "C" void parrep_destroy(parrep_t h) {
+    if (!h) return;
+    free_all(h);
+    delete h;
+}
+
+extern "C" const char* parrep_last_error(parrep_t h) {
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+extern "C" int parrep_ssa(const parrep_network* net, int32_t precision, int64_t n_traj, double T_end, uint64_t seed,
+                          double* hist_out, int64_t len, int64_t* events_out, float* kernel_ms, void* stream) {
+    parrep_regions reg;
+    memset(&reg, 0, sizeof(reg));
+    reg.n = 1;
+    reg.b[0] = 0;
+    std::string why;
+    if (!check_network(net, &reg, why)) return fail(nullptr, PARREP_EINVAL, why);
+    if (precision != PARREP_FP64 && precision != PARREP_FP32) return fail(nullptr, PARREP_EINVAL, "precision");
+    if (n_traj < 1 || n_traj > (1ll << 31)) return fail(nullptr, PARREP_EINVAL, "n_traj");
+    if (!(T_end >= 0.0) || !(T_end < kTEndLimit)) return fail(nullptr, PARREP_EINVAL, "T_end");
+    NetDev nd;
+    std::vector<double> pU, pV, gU, gV;
+    build_net(net, &reg, nd, pU, pV, gU, gV);
+    const int nbins = nd.nbins;
+    if (hist_out && len != nbins) return fail(nullptr, PARREP_EINVAL, "len != n_bins");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<float> pUf(pU.size()), pVf(pV.size());
+    for (size_t i = 0; i < pU.size(); ++i) pUf[i] = (float)pU[i];
+    for (size_t i = 0; i < pV.size(); ++i) pVf[i] = (float)pV[i];
+    double *dpU = nullptr, *dpV = nullptr, *dout = nullptr;
+    float *dpUf = nullptr, *dpVf = nullptr;
+    unsigned long long *dh = nullptr, *dev_ev = nullptr;
+    int* dst = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = upload(&dpU, pU);
+    if (e == cudaSuccess) e = upload(&dpV, pV);
+    if (e == cudaSuccess) e = upload(&dpUf, pUf);
+    if (e == cudaSuccess) e = upload(&dpVf, pVf);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dh, sizeof(unsigned long long) * nbins);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dout, sizeof(double) * nbins);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dev_ev, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dst, sizeof(int));
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    int status = 0;
+    unsigned long long evh = 0;
+    if (e == cudaSuccess) {
+        nd.prodU_d = dpU;
+        nd.prodV_d = dpV;
+        nd.prodU_f = dpUf;
+        nd.prodV_f = dpVf;
+        e = cudaMemsetAsync(dh, 0, sizeof(unsigned long long) * nbins, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(dev_ev, 0, sizeof(unsigned long long), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(dst, 0, sizeof(int), st);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        if (e == cudaSuccess)
+            e = launch_ssa(nd, precision, n_traj, net->x0[0], net->n_species > 1 ? net->x0[1] : 0,
+                           (unsigned long long)llrint(T_end * kQScale), seed, dh, dev_ev, dst, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess && hist_out) e = launch_hist_normalise(dh, dh, nbins, 0.0, dout, nullptr, nullptr, st);
+        if (e == cudaSuccess && hist_out)
+            e = cudaMemcpyAsync(hist_out, dout, sizeof(double) * nbins, cudaMemcpyDefault, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&evh, dev_ev, sizeof(evh), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&status, dst, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess && kernel_ms) cudaEventElapsedTime(kernel_ms, e0, e1);
+    }
+    void* ptrs[] = {dpU, dpV, dpUf, dpVf, dh, dout, dev_ev, dst};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return fail(nullptr, PARREP_ECUDA, std::string("parrep_ssa: ") + cudaGetErrorString(e));
+    if (events_out) *events_out = (int64_t)evh;
+    if (status) return fail(nullptr, status, "parrep_ssa: a state left [0, hist_max]");
+    return PARREP_OK;
+}
+
+extern "C" int parrep_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out) {
+    if (!ctr || !key || !out || n < 0) return fail(nullptr, PARREP_EINVAL, "parrep_philox: bad arguments");
+    if (n == 0) return PARREP_OK;
+    uint32_t *dc = nullptr, *dk = nullptr, *dout = nullptr;
+    cudaError_t e = cudaMalloc((void**)&dc, sizeof(uint32_t) * 4 * n);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dk, sizeof(uint32_t) * 2 * n);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dout, sizeof(uint32_t) * 4 * n);
+    if (e == cudaSuccess) e = cudaMemcpy(dc, ctr, sizeof(uint32_t) * 4 * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dk, key, sizeof(uint32_t) * 2 * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_philox(dc, dk, n, dout, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, sizeof(uint32_t) * 4 * n, cudaMemcpyDeviceToHost);
+    if (dc) cudaFree(dc);
+    if (dk) cudaFree(dk);
+    if (dout) cudaFree(dout);
+    if (e != cudaSuccess) return fail(nullptr, PARREP_ECUDA, std::string("parrep_philox: ") + cudaGetErrorString(e));
+    return PARREP_OK;
+}

@@ -1,0 +1,113 @@
+// Internal declarations shared by the CUDA kernels and the host side of the
+// C ABI.  Not part of the public interface (that is include/parrep.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "parrep.h"
+
+namespace parrep {
+
+// Time sums are unsigned 64-bit fixed point with 2^-40 resolution: a holding
+// time tau is stored as round(tau * 2^40).  Addition is exact and
+// order-independent, so sums do not depend on the order in which replicas
+// finish, and a contribution added by a first pass can be taken back exactly.
+constexpr int kQBits = 40;
+constexpr double kQScale = 1099511627776.0;  // 2^40
+constexpr double kQInv = 1.0 / 1099511627776.0;
+constexpr double kTEndLimit = 8388608.0;     // 2^23: keeps every sum below 2^63
+
+// Stage tags in the last word of the Philox counter.
+enum Tag : uint32_t { kTagInit = 0, kTagDecorr = 1, kTagDephase = 2, kTagFV = 3, kTagParallel = 4, kTagSSA = 5 };
+
+constexpr unsigned long long kNone = ~0ull;
+
+// Network as the kernels see it (Sec. II.A).  Schloegl: lambda_j = A[j] h_j(x)
+// with A[j] = c_j s_j.  Toggle: production rates come from host-built tables
+// indexed by the repressor count, degradation is d * count.
+struct NetDev {
+    int kind, nsp;
+    int hist_max0, hist_max1, ystride, nbins;
+    int nreg;
+    int ra0[4], ra1[4];
+    long long rb[4];
+    double A[4];
+    float Af[4];
+    double dU, dV;
+    float dUf, dVf;
+    const double* prodU_d;  // production of U as a function of V: c0/(1+V^c1)
+    const double* prodV_d;  // production of V as a function of U: c3/(1+U^c4)
+    const float* prodU_f;
+    const float* prodV_f;
+};
+
+struct CycleRecDev {
+    long long cycle;
+    int W, ended;
+    long long decorr_steps, dephase_steps, n_star, k;
+    int xt0, xt1;
+    unsigned long long Ts;
+};
+
+// Mutable state of one run, in global memory, zeroed before the launch.
+struct RunCtl {
+    unsigned int bar_count, bar_gen;
+    unsigned long long progress;
+    int status, done;
+    int xt0, xt1, W, burn_done;
+    unsigned int cycle, pad0;
+    unsigned long long Ts;
+    long long np;
+    // first-pass vote of each chunk, rotated over three slots
+    unsigned long long minkey[3], oobkey[3], chunksum[3], chunkev[3];
+    unsigned long long inc_sum[3], inc_ev[3];
+    // cut positions of a special chunk
+    unsigned long long posT, partT, posB, partB;
+    int xe0, xe1;
+    // statistics
+    unsigned long long ev_decorr, ev_dephase, ev_par_exec, ev_useful, ev_replay;
+    unsigned long long escapes, chunks, special, cycles;
+    long long log_n;
+    int x00, x01;
+};
+
+struct RunParams {
+    NetDev net;
+    int prec, thresh;
+    int R, G, S;
+    int use_smem_hist;
+    unsigned long long q_tcorr;
+    long long n_c;
+    double t_phase;
+    long long n_p;
+    unsigned long long q_Tend, q_Tburn;
+    unsigned long long seed;
+    int x00, x01, x0_hi;
+    RunCtl* ctl;
+    unsigned long long* hist_pre;
+    unsigned long long* hist_post;
+    unsigned long long* step_sum;  // S entries
+    unsigned long long* tau_at;    // 2 x R entries
+    CycleRecDev* log;
+    long long log_cap;
+    long long timeout_ns;
+    int stall_barrier;
+};
+
+// ---- launchers (parrep_kernels.cu) ----
+int kernel_attrs(int prec, int* max_blocks_per_sm, int smem_bytes, int threads);
+cudaError_t launch_run(const RunParams& p, int grid, int threads, int smem_bytes, cudaStream_t st);
+cudaError_t launch_dephase(const RunParams& p, int xt0, int xt1, int W, unsigned cycle, long long np,
+                           int* out_states, int grid, int threads, cudaStream_t st);
+cudaError_t launch_hist_normalise(const unsigned long long* pre, const unsigned long long* post, int n, double scale,
+                                  double* out_pre, double* out_post, double* out_norm, cudaStream_t st);
+cudaError_t launch_fim_rer(const NetDev& net, const double* c, const double* s, const unsigned long long* hist,
+                           const double* gradU_n, const double* gradV_n, const double* cprime, int n_cprime,
+                           double* fim_out, double* rer_out, cudaStream_t st);
+cudaError_t launch_ssa(const NetDev& net, int prec, long long n_traj, int x0, int x1, unsigned long long q_Tend,
+                       unsigned long long seed, unsigned long long* hist, unsigned long long* events,
+                       int* status, cudaStream_t st);
+cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, long long n, uint32_t* out, cudaStream_t st);
+
+}  // namespace parrep

@@ -1,0 +1,1082 @@
+// CUDA kernels of the ParRep library (sm_103a).
+//
+// One persistent cooperative launch runs Algorithm 1 of Wang & Plechac
+// (arXiv 1705.06807, Sec. III.A) to T_end:
+//   * decorrelation: one leader thread simulates X~ (serial by definition);
+//   * dephasing: one thread per replica, lockstep jumps of the embedded chain,
+//     Fleming-Viot respawn inside groups of <= 32 lanes by warp ballot and
+//     shuffle (no memory traffic);
+//   * parallel step: one thread per replica with its integer state in
+//     registers runs S lockstep steps ahead ("a chunk"), stopping at its own
+//     escape; a warp/block/grid minimum over the packed key (step, replica)
+//     gives the paper's (N*, K).  Contributions tau and f(X) tau go straight
+//     into a block-private shared-memory histogram in 64-bit fixed point.
+//     A chunk that holds the escape, the T_end cut or the T_burn split is
+//     rolled back and replayed exactly (the counter-based generator makes a
+//     replay bit-identical), keeping only the contributions at or before the
+//     cut in the paper's (step, replica) order.
+// Every wait on another block is bounded by a no-progress timeout and turns
+// into PARREP_ETIMEOUT instead of a hang.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "parrep_internal.h"
+
+namespace parrep {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two 32x32
+// multiplies with the Weyl key schedule.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        const unsigned m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
+        unsigned hi0 = __umulhi(m0, c.x), lo0 = m0 * c.x;
+        unsigned hi1 = __umulhi(m1, c.z), lo1 = m1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// uniform in (0,1): 52 bits, (m + 1/2) 2^-52 (exact in binary64)
+__device__ __forceinline__ double u01d(unsigned a, unsigned b) {
+    unsigned long long m = ((unsigned long long)a << 20) | (unsigned long long)(b >> 12);
+    return ((double)m + 0.5) * 0x1p-52;
+}
+// uniform in (0,1): 23 bits, (m + 1/2) 2^-23 (exact in binary32)
+__device__ __forceinline__ float u01f(unsigned w) { return ((float)(w >> 9) + 0.5f) * 0x1p-23f; }
+
+// uniform integer in {0..n-1}
+__device__ __forceinline__ unsigned pick(unsigned w, unsigned n) { return __umulhi(w, n); }
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+template <typename T>
+__device__ __forceinline__ T ldv(const T* p) {
+    return *(const volatile T*)p;
+}
+
+// ---------------------------------------------------------------------------
+// network: propensities, selection, update, regions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int region_of(const NetDev& N, int x0, int x1) {
+    for (int i = 0; i < N.nreg; ++i) {
+        long long v = (long long)N.ra0[i] * x0 + (long long)N.ra1[i] * x1;
+        if (v < N.rb[i]) return i;
+    }
+    return N.nreg;
+}
+
+__device__ __forceinline__ bool out_of_range(const NetDev& N, int x0, int x1) {
+    return x0 < 0 || x0 > N.hist_max0 || x1 < 0 || x1 > N.hist_max1;
+}
+
+// eta_J: Schloegl (+1,-1,+1,-1) on x0; toggle (+U,+V,-U,-V)
+__device__ __forceinline__ void apply(const NetDev& N, int J, int& x0, int& x1) {
+    if (N.kind == PARREP_SCHLOGL) {
+        x0 += (J & 1) ? -1 : 1;
+    } else {
+        int d = (J < 2) ? 1 : -1;
+        if (J & 1) x1 += d; else x0 += d;
+    }
+}
+
+template <typename F>
+__device__ __forceinline__ int select4(F l0, F l1, F l2, F l3, F target) {
+    F cum = l0;
+    if (cum > target) return 0;
+    cum = cum + l1;
+    if (cum > target) return 1;
+    cum = cum + l2;
+    if (cum > target) return 2;
+    cum = cum + l3;
+    if (cum > target) return 3;
+    // rounding left no channel above the target: take the last positive one
+    return l3 > (F)0 ? 3 : (l2 > (F)0 ? 2 : (l1 > (F)0 ? 1 : 0));
+}
+
+__device__ __forceinline__ void props_d(const NetDev& N, int x0, int x1, double& l0, double& l1, double& l2,
+                                        double& l3) {
+    if (N.kind == PARREP_SCHLOGL) {
+        double xd = (double)x0;
+        double h1 = xd * (xd - 1.0);
+        double h2 = h1 * (xd - 2.0);
+        l0 = N.A[0] * h1;
+        l1 = N.A[1] * h2;
+        l2 = N.A[2];
+        l3 = N.A[3] * xd;
+    } else {
+        l0 = __ldg(N.prodU_d + x1);
+        l1 = __ldg(N.prodV_d + x0);
+        l2 = N.dU * (double)x0;
+        l3 = N.dV * (double)x1;
+    }
+}
+
+__device__ __forceinline__ void props_f(const NetDev& N, int x0, int x1, float& l0, float& l1, float& l2,
+                                        float& l3) {
+    if (N.kind == PARREP_SCHLOGL) {
+        float xf = (float)x0;
+        float h1 = xf * (xf - 1.0f);
+        float h2 = h1 * (xf - 2.0f);
+        l0 = N.Af[0] * h1;
+        l1 = N.Af[1] * h2;
+        l2 = N.Af[2];
+        l3 = N.Af[3] * xf;
+    } else {
+        l0 = __ldg(N.prodU_f + x1);
+        l1 = __ldg(N.prodV_f + x0);
+        l2 = N.dUf * (float)x0;
+        l3 = N.dVf * (float)x1;
+    }
+}
+
+// One Gillespie direct-method step at (x0,x1) from the Philox words w:
+// returns J and (if WANT_TAU) the holding time tau = -log(u1)/a0 in fixed point.
+template <bool F32, bool WANT_TAU>
+__device__ __forceinline__ int ssa_draw(const NetDev& N, int x0, int x1, uint4 w, unsigned long long& q) {
+    if (F32) {
+        float l0, l1, l2, l3;
+        props_f(N, x0, x1, l0, l1, l2, l3);
+        float a0 = ((l0 + l1) + l2) + l3;
+        if (WANT_TAU) {
+            float tau = -logf(u01f(w.x)) / a0;
+            q = __float2ull_rn(tau * 0x1p40f);
+        }
+        return select4<float>(l0, l1, l2, l3, u01f(w.y) * a0);
+    } else {
+        double l0, l1, l2, l3;
+        props_d(N, x0, x1, l0, l1, l2, l3);
+        double a0 = ((l0 + l1) + l2) + l3;
+        if (WANT_TAU) {
+            double tau = -log(u01d(w.x, w.y)) / a0;
+            q = __double2ull_rn(tau * 0x1p40);
+        }
+        return select4<double>(l0, l1, l2, l3, u01d(w.z, w.w) * a0);
+    }
+}
+
+__device__ __forceinline__ uint2 seed_key(unsigned long long seed) {
+    return make_uint2((unsigned)seed, (unsigned)(seed >> 32));
+}
+
+// ---------------------------------------------------------------------------
+// reductions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ unsigned long long warp_min(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
+        v = u < v ? u : v;
+    }
+    return v;
+}
+
+struct BlockScratch {
+    unsigned long long a[32], b[32], c[32], d[32];
+};
+
+// Block reduction of (min a, min b, sum c, sum d); thread 0 gets the result.
+__device__ __forceinline__ void block_reduce4(BlockScratch& s, unsigned long long& a, unsigned long long& b,
+                                              unsigned long long& c, unsigned long long& d) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    a = warp_min(a);
+    b = warp_min(b);
+    c = warp_sum(c);
+    d = warp_sum(d);
+    if (lane == 0) {
+        s.a[wid] = a;
+        s.b[wid] = b;
+        s.c[wid] = c;
+        s.d[wid] = d;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        a = lane < nw ? s.a[lane] : kNone;
+        b = lane < nw ? s.b[lane] : kNone;
+        c = lane < nw ? s.c[lane] : 0ull;
+        d = lane < nw ? s.d[lane] : 0ull;
+        a = warp_min(a);
+        b = warp_min(b);
+        c = warp_sum(c);
+        d = warp_sum(d);
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// grid barrier, bounded: a wait that sees no progress for timeout_ns sets
+// PARREP_ETIMEOUT and returns; every caller leaves the kernel on a nonzero
+// status.  The barrier counts calls so that a test can make block 0 skip one.
+// ---------------------------------------------------------------------------
+struct BarState {
+    int index;
+};
+
+__device__ bool grid_sync(const RunParams& P, BarState& bs) {
+    __shared__ int ok;
+    RunCtl* ctl = P.ctl;
+    const int idx = bs.index++;
+    __syncthreads();
+    if (P.stall_barrier >= 0 && idx == P.stall_barrier && blockIdx.x == 0) {
+        // fault injection: block 0 leaves without arriving
+        return false;
+    }
+    if (threadIdx.x == 0) {
+        const unsigned g = ldv(&ctl->bar_gen);
+        __threadfence();
+        atomicAdd(&ctl->progress, 1ull);
+        const unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(&ctl->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&ctl->bar_gen, 1u);
+        } else {
+            unsigned long long t0 = globaltimer();
+            unsigned long long p0 = ldv(&ctl->progress);
+            unsigned ns = 32;
+            while (ldv(&ctl->bar_gen) == g) {
+                if (ldv(&ctl->status) != 0) break;
+                __nanosleep(ns);
+                if (ns < 1024) ns <<= 1;
+                const unsigned long long p = ldv(&ctl->progress);
+                const unsigned long long t = globaltimer();
+                if (p != p0) {
+                    p0 = p;
+                    t0 = t;
+                } else if ((long long)(t - t0) > P.timeout_ns) {
+                    atomicCAS(&ctl->status, 0, PARREP_ETIMEOUT);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        // one read per block, so that every thread of the block takes the same branch
+        ok = ldv(&ctl->status) == 0;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// leader (block 0, thread 0): initial state and decorrelation
+// ---------------------------------------------------------------------------
+__device__ void leader_contribute(const RunParams& P, RunCtl* ctl, int x0, int x1, unsigned long long q,
+                                  unsigned long long& Ts, int& burn_done, bool& ended) {
+    const NetDev& N = P.net;
+    unsigned long long t = q;
+    const unsigned long long rem = P.q_Tend - Ts;
+    if (t >= rem) {
+        t = rem;
+        ended = true;
+    }
+    unsigned long long pre = 0, post = t;
+    if (!burn_done) {
+        const unsigned long long room = P.q_Tburn - Ts;
+        pre = t < room ? t : room;
+        post = t - pre;
+        if (t >= room) burn_done = 1;
+    }
+    const int bin = x0 * N.ystride + x1;
+    if (pre) atomicAdd(P.hist_pre + bin, pre);
+    if (post) atomicAdd(P.hist_post + bin, post);
+    Ts += t;
+}
+
+__device__ void leader_log(const RunParams& P, RunCtl* ctl, const CycleRecDev& rec) {
+    long long i = ctl->log_n;
+    if (i < P.log_cap) P.log[i] = rec;
+    ctl->log_n = i + 1;
+}
+
+template <bool F32>
+__device__ void leader_decorrelate(const RunParams& P) {
+    RunCtl* ctl = P.ctl;
+    const NetDev& N = P.net;
+    const uint2 key = seed_key(P.seed);
+    int x0 = ctl->xt0, x1 = ctl->xt1;
+    unsigned long long Ts = ctl->Ts;
+    int burn_done = ctl->burn_done;
+    const unsigned cycle = ctl->cycle;
+    int W = region_of(N, x0, x1);
+    long long Nc = 0;
+    unsigned long long inW = 0;
+    unsigned long long step = 0;
+    bool ended = false;
+    int status = 0;
+    for (;;) {
+        if (P.thresh == PARREP_THRESH_STEPS ? (Nc >= P.n_c) : (inW >= P.q_tcorr)) break;
+        uint4 w = philox10(make_uint4((unsigned)(step >> 32), (unsigned)step, cycle, kTagDecorr), key);
+        unsigned long long q = 0;
+        const int J = ssa_draw<F32, true>(N, x0, x1, w, q);
+        ++step;
+        leader_contribute(P, ctl, x0, x1, q, Ts, burn_done, ended);
+        if (ended) break;
+        apply(N, J, x0, x1);
+        if (out_of_range(N, x0, x1)) {
+            status = PARREP_ERANGE;
+            break;
+        }
+        const int Wn = region_of(N, x0, x1);
+        if (Wn == W) {
+            ++Nc;
+            inW += q;
+        } else {
+            Nc = 0;
+            inW = 0;
+            W = Wn;
+        }
+        if ((step & 4095ull) == 0) atomicAdd(&ctl->progress, 1ull);
+    }
+    ctl->ev_decorr += step;
+    long long np = 0;
+    if (!ended && status == 0) {
+        if (P.thresh == PARREP_THRESH_STEPS) {
+            np = P.n_p;
+        } else {
+            double l0, l1, l2, l3;
+            props_d(N, x0, x1, l0, l1, l2, l3);
+            const double a0 = ((l0 + l1) + l2) + l3;
+            const double n = ceil(P.t_phase * a0);
+            if (!(n < 4294967295.0)) status = PARREP_ERANGE;
+            else np = (long long)n;
+        }
+    }
+    ctl->xt0 = x0;
+    ctl->xt1 = x1;
+    ctl->W = W;
+    ctl->Ts = Ts;
+    ctl->burn_done = burn_done;
+    ctl->np = np;
+    // the cycle record is completed when the cycle ends; keep its first part
+    CycleRecDev rec;
+    rec.cycle = cycle;
+    rec.W = W;
+    rec.ended = ended ? 1 : 0;
+    rec.decorr_steps = (long long)step;
+    rec.dephase_steps = np;
+    rec.n_star = 0;
+    rec.k = -1;
+    rec.xt0 = x0;
+    rec.xt1 = x1;
+    rec.Ts = Ts;
+    if (ended || status) {
+        if (ended) leader_log(P, ctl, rec);
+        ctl->cycles += 1;
+        ctl->done = 1;
+    } else {
+        // stash for the end of the cycle
+        if (ctl->log_n < P.log_cap) P.log[ctl->log_n] = rec;
+    }
+    if (status) atomicCAS(&ctl->status, 0, status);
+    __threadfence();
+}
+
+// ---------------------------------------------------------------------------
+// dephasing (Algorithm 1): n_p lockstep jumps of the embedded chain; after
+// each, replicas that left W copy a uniformly chosen survivor of their group
+// (fv_group consecutive lanes of the warp), or X~ if the group has none.
+// All lanes of the warp execute the loop (inactive lanes carry no replica).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int kth_set_bit(unsigned m, unsigned k) {
+    for (unsigned i = 0; i < k; ++i) m &= m - 1;
+    return __ffs(m) - 1;
+}
+
+template <bool F32>
+__device__ int dephase_warp(const NetDev& N, bool active, unsigned r, int G, int W, int xt0, int xt1, long long np,
+                            unsigned cycle, uint2 key, int& x0, int& x1) {
+    const int lane = threadIdx.x & 31;
+    const unsigned act = __ballot_sync(0xffffffffu, active);
+    x0 = xt0;
+    x1 = xt1;
+    if (act == 0) return 0;
+    const unsigned gm = (G >= 32) ? 0xffffffffu : (((1u << G) - 1u) << ((lane / G) * G));
+    for (long long i = 0; i < np; ++i) {
+        int n0 = x0, n1 = x1;
+        bool ex = false, bad = false;
+        if (active) {
+            uint4 w = philox10(make_uint4(r, (unsigned)i, cycle, kTagDephase), key);
+            unsigned long long q;
+            const int J = ssa_draw<F32, false>(N, x0, x1, w, q);
+            apply(N, J, n0, n1);
+            ex = region_of(N, n0, n1) != W;
+            bad = !ex && out_of_range(N, n0, n1);
+        }
+        const unsigned exm = __ballot_sync(0xffffffffu, ex);
+        if (__ballot_sync(0xffffffffu, bad)) return PARREP_ERANGE;
+        if (exm) {
+            const unsigned sm = act & ~exm & gm;
+            int src = lane;
+            if (ex) {
+                const int ns = __popc(sm);
+                if (ns > 0) {
+                    uint4 w = philox10(make_uint4(r, (unsigned)i, cycle, kTagFV), key);
+                    src = kth_set_bit(sm, pick(w.x, (unsigned)ns));
+                } else {
+                    src = -1;
+                }
+            }
+            const int s0 = __shfl_sync(0xffffffffu, n0, src < 0 ? lane : src);
+            const int s1 = __shfl_sync(0xffffffffu, n1, src < 0 ? lane : src);
+            if (ex) {
+                n0 = src < 0 ? xt0 : s0;
+                n1 = src < 0 ? xt1 : s1;
+            }
+        }
+        x0 = n0;
+        x1 = n1;
+    }
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// parallel step helpers
+// ---------------------------------------------------------------------------
+struct HistSink {
+    unsigned long long* sh;  // shared histogram or nullptr
+    unsigned long long* g;   // global histogram of the current period
+    int ystride;
+    __device__ __forceinline__ void add(int x0, int x1, unsigned long long q) const {
+        const int b = x0 * ystride + x1;
+        if (sh) atomicAdd(sh + b, q);
+        else atomicAdd(g + b, q);
+    }
+};
+
+__device__ __forceinline__ unsigned long long pos_of(int s, unsigned r) {
+    return ((unsigned long long)(unsigned)s << 32) | (unsigned long long)r;
+}
+
+enum ReplayMode { kRollback = 0, kStepSum = 1, kTauAt = 2, kPrecise = 3 };
+
+struct Cuts {
+    unsigned long long posC;  // replica contributions after this are never included
+    unsigned long long posE;  // escape cut (N*, K), in-chunk
+    unsigned long long posT, partT;
+    unsigned long long posB, partB;
+    int nB, nT;               // steps of the T_burn / T_end crossing (-1: none)
+};
+
+// Re-simulates the chunk of replica r from (x0,x1) exactly as the first pass.
+template <bool F32, int MODE>
+__device__ void replay_chunk(const RunParams& P, const HistSink& hs, int x0, int x1, unsigned r, int W,
+                             unsigned cycle, unsigned n0, const Cuts& cut, bool to_post,
+                             unsigned long long& inc_q, unsigned long long& inc_ev, unsigned long long& ev) {
+    const NetDev& N = P.net;
+    const uint2 key = seed_key(P.seed);
+    for (int s = 0; s < P.S; ++s) {
+        const unsigned long long pos = pos_of(s, r);
+        if (MODE != kRollback && pos > cut.posC) break;
+        uint4 w = philox10(make_uint4(r, n0 + (unsigned)s, cycle, kTagParallel), key);
+        unsigned long long q = 0;
+        const int J = ssa_draw<F32, true>(N, x0, x1, w, q);
+        ++ev;
+        if (MODE == kRollback) {
+            hs.add(x0, x1, 0ull - q);
+        } else if (MODE == kStepSum) {
+            atomicAdd(P.step_sum + s, q);
+        } else if (MODE == kTauAt) {
+            if (s == cut.nB) P.tau_at[r] = q;
+            if (s == cut.nT) P.tau_at[P.R + r] = q;
+        } else {
+            if (pos > cut.posE || pos > cut.posT) break;
+            unsigned long long amt = (pos == cut.posT) ? cut.partT : q;
+            // the T_burn split: before the cut to the global pre-burn sums,
+            // after it to the (post-burn) sink
+            unsigned long long pre = 0, post = amt;
+            if (cut.posB != kNone) {
+                if (pos < cut.posB) {
+                    pre = amt;
+                    post = 0;
+                } else if (pos == cut.posB) {
+                    pre = cut.partB < amt ? cut.partB : amt;
+                    post = amt - pre;
+                }
+            }
+            const int b = x0 * P.net.ystride + x1;
+            if (pre) atomicAdd(P.hist_pre + b, pre);
+            if (post) {
+                if (hs.sh) atomicAdd(hs.sh + b, post);
+                else atomicAdd((to_post ? P.hist_post : P.hist_pre) + b, post);
+            }
+            inc_q += amt;
+            inc_ev += 1;
+            if (pos == cut.posT) break;
+        }
+        int n0_ = x0, n1_ = x1;
+        apply(N, J, n0_, n1_);
+        if (region_of(N, n0_, n1_) != W) break;
+        if (out_of_range(N, n0_, n1_)) break;
+        x0 = n0_;
+        x1 = n1_;
+    }
+}
+
+__device__ void flush_shared(unsigned long long* sh, unsigned long long* g, int nbins) {
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+        const unsigned long long v = sh[b];
+        if (v) atomicAdd(g + b, v);
+        sh[b] = 0;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// the persistent ParRep kernel
+// ---------------------------------------------------------------------------
+template <bool F32>
+__global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
+    extern __shared__ unsigned long long sh_hist[];
+    __shared__ BlockScratch red;
+    RunCtl* ctl = P.ctl;
+    const NetDev& N = P.net;
+    const unsigned r = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = (long long)r < (long long)P.R;
+    const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+    const uint2 key = seed_key(P.seed);
+    BarState bs{0};
+
+    if (P.use_smem_hist) {
+        for (int b = threadIdx.x; b < N.nbins; b += blockDim.x) sh_hist[b] = 0;
+    }
+    unsigned long long ev_replay = 0;
+
+    if (leader) {
+        int x0 = P.x00, x1 = P.x01;
+        if (P.x0_hi > 0) {
+            uint4 w = philox10(make_uint4(0u, 0u, 0u, kTagInit), key);
+            x0 = (int)pick(w.x, (unsigned)P.x0_hi + 1u);
+            x1 = N.nsp > 1 ? (int)pick(w.y, (unsigned)P.x0_hi + 1u) : 0;
+        }
+        ctl->x00 = x0;
+        ctl->x01 = x1;
+        ctl->xt0 = x0;
+        ctl->xt1 = x1;
+        ctl->Ts = 0;
+        ctl->cycle = 0;
+        ctl->burn_done = P.q_Tburn == 0 ? 1 : 0;
+        ctl->W = region_of(N, x0, x1);
+        if (out_of_range(N, x0, x1)) atomicCAS(&ctl->status, 0, PARREP_EINVAL);
+        ctl->done = P.q_Tend == 0 ? 1 : 0;
+        for (int s = 0; s < 3; ++s) {
+            ctl->minkey[s] = kNone;
+            ctl->oobkey[s] = kNone;
+            ctl->chunksum[s] = 0;
+            ctl->chunkev[s] = 0;
+            ctl->inc_sum[s] = 0;
+            ctl->inc_ev[s] = 0;
+        }
+        __threadfence();
+    }
+    int period_post = P.q_Tburn == 0 ? 1 : 0;  // which global sums this block's histogram feeds
+    HistSink hs{P.use_smem_hist ? sh_hist : nullptr, period_post ? P.hist_post : P.hist_pre, N.ystride};
+    unsigned long long chunk_c = 0;
+    if (!grid_sync(P, bs)) goto out;
+
+    for (;;) {
+        // ---------------- decorrelation (serial, leader) ----------------
+        if (leader && !ctl->done) leader_decorrelate<F32>(P);
+        if (!grid_sync(P, bs)) goto out;
+        if (ldv(&ctl->done)) break;
+        {
+            const int W = ldv(&ctl->W);
+            const int xt0 = ldv(&ctl->xt0), xt1 = ldv(&ctl->xt1);
+            const long long np = ldv(&ctl->np);
+            const unsigned cycle = ldv(&ctl->cycle);
+            unsigned long long Ts = ldv(&ctl->Ts);
+            int burn_done = ldv(&ctl->burn_done);
+            if (burn_done && !period_post) {
+                if (hs.sh) flush_shared(sh_hist, P.hist_pre, N.nbins);
+                period_post = 1;
+                hs.g = P.hist_post;
+            }
+            // ---------------- dephasing ----------------
+            int x0, x1;
+            if (dephase_warp<F32>(N, active, r, P.G, W, xt0, xt1, np, cycle, key, x0, x1)) {
+                if ((threadIdx.x & 31) == 0) atomicCAS(&ctl->status, 0, PARREP_ERANGE);
+            }
+            if (leader) ctl->ev_dephase += (unsigned long long)np * (unsigned long long)P.R;
+            // ---------------- parallel step ----------------
+            unsigned n0 = 0;
+            for (;;) {
+                if ((unsigned long long)n0 + (unsigned long long)P.S > 0xFFFFFFFFull) {
+                    if (leader) atomicCAS(&ctl->status, 0, PARREP_ERANGE);
+                }
+                if (leader) {
+                    const int s1 = (int)((chunk_c + 1) % 3);
+                    ctl->minkey[s1] = kNone;
+                    ctl->oobkey[s1] = kNone;
+                    ctl->chunksum[s1] = 0;
+                    ctl->chunkev[s1] = 0;
+                    ctl->inc_sum[s1] = 0;
+                    ctl->inc_ev[s1] = 0;
+                }
+                const int xs0 = x0, xs1 = x1;
+                unsigned long long mykey = kNone, myoob = kNone, qsum = 0, ev = 0;
+                int xe0 = 0, xe1 = 0;
+                if (active) {
+                    for (int s = 0; s < P.S; ++s) {
+                        uint4 w = philox10(make_uint4(r, n0 + (unsigned)s, cycle, kTagParallel), key);
+                        unsigned long long q = 0;
+                        const int J = ssa_draw<F32, true>(N, x0, x1, w, q);
+                        qsum += q;
+                        ++ev;
+                        hs.add(x0, x1, q);
+                        int a0 = x0, a1 = x1;
+                        apply(N, J, a0, a1);
+                        if (region_of(N, a0, a1) != W) {
+                            mykey = pos_of(s, r);
+                            xe0 = a0;
+                            xe1 = a1;
+                            break;
+                        }
+                        if (out_of_range(N, a0, a1)) {
+                            myoob = pos_of(s, r);
+                            break;
+                        }
+                        x0 = a0;
+                        x1 = a1;
+                    }
+                }
+                const int slot = (int)(chunk_c % 3);
+                {
+                    unsigned long long a = mykey, b = myoob, c = qsum, d = ev;
+                    block_reduce4(red, a, b, c, d);
+                    if (threadIdx.x == 0) {
+                        if (a != kNone) atomicMin(&ctl->minkey[slot], a);
+                        if (b != kNone) atomicMin(&ctl->oobkey[slot], b);
+                        if (c) atomicAdd(&ctl->chunksum[slot], c);
+                        if (d) atomicAdd(&ctl->chunkev[slot], d);
+                    }
+                }
+                if (!grid_sync(P, bs)) goto out;
+                ++chunk_c;
+                const unsigned long long ekey = ldv(&ctl->minkey[slot]);
+                const unsigned long long okey = ldv(&ctl->oobkey[slot]);
+                const unsigned long long csum = ldv(&ctl->chunksum[slot]);
+                const unsigned long long cev = ldv(&ctl->chunkev[slot]);
+                const unsigned long long q_next = burn_done ? P.q_Tend : P.q_Tburn;
+                if (leader) {
+                    ctl->chunks += 1;
+                    ctl->ev_par_exec += cev;
+                }
+                if (ekey == kNone && okey == kNone && Ts + csum < q_next) {
+                    Ts += csum;
+                    if (leader) {
+                        ctl->ev_useful += cev;
+                        ctl->Ts = Ts;
+                    }
+                    n0 += (unsigned)P.S;
+                    continue;
+                }
+                // ------------- special chunk: escape, range error or time cut -------------
+                if (leader) ctl->special += 1;
+                if (active) {
+                    unsigned long long d0 = 0, d1 = 0;
+                    Cuts none{kNone, kNone, kNone, 0, kNone, 0, -1, -1};
+                    replay_chunk<F32, kRollback>(P, hs, xs0, xs1, r, W, cycle, n0, none, period_post, d0, d1,
+                                                 ev_replay);
+                }
+                Cuts cut{kNone, kNone, kNone, 0, kNone, 0, -1, -1};
+                cut.posE = ekey;
+                cut.posC = ekey < okey ? ekey : okey;
+                if (Ts + csum >= q_next) {
+                    // a threshold may be crossed: find the step, then the replica
+                    if (blockIdx.x == 0) {
+                        for (int j = threadIdx.x; j < P.S; j += blockDim.x) P.step_sum[j] = 0;
+                    }
+                    if (!grid_sync(P, bs)) goto out;
+                    if (active) {
+                        unsigned long long d0 = 0, d1 = 0;
+                        replay_chunk<F32, kStepSum>(P, hs, xs0, xs1, r, W, cycle, n0, cut, period_post, d0, d1,
+                                                    ev_replay);
+                    }
+                    if (!grid_sync(P, bs)) goto out;
+                    unsigned long long baseB = 0, baseT = 0;
+                    {
+                        unsigned long long acc = Ts;
+                        for (int j = 0; j < P.S; ++j) {
+                            const unsigned long long v = __ldcg(P.step_sum + j);
+                            if (!burn_done && cut.nB < 0 && acc + v >= P.q_Tburn) {
+                                cut.nB = j;
+                                baseB = acc;
+                            }
+                            if (cut.nT < 0 && acc + v >= P.q_Tend) {
+                                cut.nT = j;
+                                baseT = acc;
+                            }
+                            acc += v;
+                        }
+                    }
+                    if (cut.nB >= 0 || cut.nT >= 0) {
+                        if (active) {
+                            P.tau_at[r] = 0;
+                            P.tau_at[P.R + r] = 0;
+                            unsigned long long d0 = 0, d1 = 0;
+                            replay_chunk<F32, kTauAt>(P, hs, xs0, xs1, r, W, cycle, n0, cut, period_post, d0, d1,
+                                                      ev_replay);
+                        }
+                        if (!grid_sync(P, bs)) goto out;
+                        if (leader) {
+                            ctl->posB = kNone;
+                            ctl->posT = kNone;
+                            if (cut.nB >= 0) {
+                                unsigned long long acc = baseB;
+                                for (int rr = 0; rr < P.R; ++rr) {
+                                    const unsigned long long v = __ldcg(P.tau_at + rr);
+                                    if (acc + v >= P.q_Tburn) {
+                                        ctl->posB = pos_of(cut.nB, (unsigned)rr);
+                                        ctl->partB = P.q_Tburn - acc;
+                                        break;
+                                    }
+                                    acc += v;
+                                }
+                            }
+                            if (cut.nT >= 0) {
+                                unsigned long long acc = baseT;
+                                for (int rr = 0; rr < P.R; ++rr) {
+                                    const unsigned long long v = __ldcg(P.tau_at + P.R + rr);
+                                    if (acc + v >= P.q_Tend) {
+                                        ctl->posT = pos_of(cut.nT, (unsigned)rr);
+                                        ctl->partT = P.q_Tend - acc;
+                                        break;
+                                    }
+                                    acc += v;
+                                }
+                            }
+                            __threadfence();
+                        }
+                        if (!grid_sync(P, bs)) goto out;
+                        cut.posB = ldv(&ctl->posB);
+                        cut.partB = ldv(&ctl->partB);
+                        cut.posT = ldv(&ctl->posT);
+                        cut.partT = ldv(&ctl->partT);
+                    }
+                }
+                // a range error stands if the replica's jump really happened
+                if (okey != kNone && okey <= cut.posE && okey < cut.posT) {
+                    if (leader) atomicCAS(&ctl->status, 0, PARREP_ERANGE);
+                    grid_sync(P, bs);
+                    goto out;
+                }
+                if (cut.posB != kNone && hs.sh) {
+                    // this block's shared sums are all before T_burn now
+                    flush_shared(sh_hist, P.hist_pre, N.nbins);
+                }
+                {
+                    unsigned long long inc_q = 0, inc_ev = 0;
+                    if (active) {
+                        replay_chunk<F32, kPrecise>(P, hs, xs0, xs1, r, W, cycle, n0, cut,
+                                                    period_post || cut.posB != kNone, inc_q, inc_ev, ev_replay);
+                    }
+                    unsigned long long a = kNone, b = kNone;
+                    block_reduce4(red, a, b, inc_q, inc_ev);
+                    if (threadIdx.x == 0) {
+                        if (inc_q) atomicAdd(&ctl->inc_sum[slot], inc_q);
+                        if (inc_ev) atomicAdd(&ctl->inc_ev[slot], inc_ev);
+                    }
+                }
+                if (cut.posB != kNone) {
+                    burn_done = 1;
+                    period_post = 1;
+                    hs.g = P.hist_post;
+                }
+                // the escaping replica publishes X^K_{N*}
+                if (ekey != kNone && (unsigned)(ekey & 0xffffffffu) == r && !(cut.posT <= cut.posE)) {
+                    ctl->xe0 = xe0;
+                    ctl->xe1 = xe1;
+                }
+                if (!grid_sync(P, bs)) goto out;
+                Ts += ldv(&ctl->inc_sum[slot]);
+                const bool t_end = cut.posT != kNone && cut.posT <= cut.posE;
+                if (leader) {
+                    ctl->ev_useful += ldv(&ctl->inc_ev[slot]);
+                    ctl->Ts = Ts;
+                    ctl->burn_done = burn_done;
+                    CycleRecDev rec{};
+                    const long long i = ctl->log_n;
+                    if (i < P.log_cap) rec = P.log[i];
+                    if (t_end || ekey != kNone) {
+                        rec.ended = t_end ? 1 : 0;
+                        rec.n_star = (long long)n0 + (long long)((t_end ? cut.posT : ekey) >> 32) + 1;
+                        rec.k = t_end ? -1 : (long long)(ekey & 0xffffffffu);
+                        if (!t_end) {
+                            ctl->xt0 = ldv(&ctl->xe0);
+                            ctl->xt1 = ldv(&ctl->xe1);
+                            ctl->escapes += 1;
+                        }
+                        rec.xt0 = ctl->xt0;
+                        rec.xt1 = ctl->xt1;
+                        rec.Ts = t_end ? P.q_Tend : Ts;
+                        if (t_end) ctl->Ts = P.q_Tend;
+                        leader_log(P, ctl, rec);
+                        ctl->cycles += 1;
+                        ctl->cycle = cycle + 1;
+                        if (t_end) ctl->done = 1;
+                    }
+                    __threadfence();
+                }
+                if (t_end) goto finished;
+                if (ekey != kNone) break;  // next cycle
+                n0 += (unsigned)P.S;  // only the T_burn split was in this chunk
+            }
+        }
+        if (!grid_sync(P, bs)) goto out;
+    }
+finished:
+out:
+    if (P.use_smem_hist) flush_shared(sh_hist, period_post ? P.hist_post : P.hist_pre, N.nbins);
+    {
+        unsigned long long a = kNone, b = kNone, c = ev_replay, d = 0;
+        block_reduce4(red, a, b, c, d);
+        if (threadIdx.x == 0 && c) atomicAdd(&ctl->ev_replay, c);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// stand-alone dephasing (for tests and diagnostics)
+// ---------------------------------------------------------------------------
+template <bool F32>
+__global__ void dephase_kernel(RunParams P, int xt0, int xt1, int W, unsigned cycle, long long np, int* out,
+                               int* status) {
+    const unsigned r = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = (long long)r < (long long)P.R;
+    int x0, x1;
+    int st = dephase_warp<F32>(P.net, active, r, P.G, W, xt0, xt1, np, cycle, seed_key(P.seed), x0, x1);
+    if (st && (threadIdx.x & 31) == 0) atomicCAS(status, 0, st);
+    if (active) {
+        out[2 * r] = x0;
+        out[2 * r + 1] = x1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// histogram normalisation, FIM and RER contractions (Sec. IV, Appendix A)
+// ---------------------------------------------------------------------------
+__global__ void hist_normalise_kernel(const unsigned long long* pre, const unsigned long long* post, int n,
+                                      double scale, double* out_pre, double* out_post, double* out_norm) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < n; b += gridDim.x * blockDim.x) {
+        const double a = (double)pre[b] * kQInv, c = (double)post[b] * kQInv;
+        if (out_pre) out_pre[b] = a;
+        if (out_post) out_post[b] = c;
+        if (out_norm) out_norm[b] = (a + c) * scale;
+    }
+}
+
+// Per bin: w = time in the bin; FIM += w sum_j lambda_j g_j g_j^T with
+// g_j = grad_c log lambda_j; RER_k += w sum_j [lambda_j log(lambda_j/lambda'_j)
+// - lambda_j + lambda'_j].
+__global__ void fim_rer_kernel(NetDev N, const double* __restrict__ c, const double* __restrict__ s,
+                               const unsigned long long* __restrict__ hist, const double* __restrict__ gradU_n,
+                               const double* __restrict__ gradV_n, const double* __restrict__ cprime, int n_cprime,
+                               double* fim_out, double* rer_out) {
+    const int L = N.kind == PARREP_SCHLOGL ? 4 : 6;
+    double acc[36];
+#pragma unroll
+    for (int i = 0; i < 36; ++i) acc[i] = 0.0;
+    double racc[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) racc[i] = 0.0;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < N.nbins; b += gridDim.x * blockDim.x) {
+        const unsigned long long hq = hist[b];
+        if (!hq) continue;
+        const double w = (double)hq * kQInv;
+        const int x0 = b / N.ystride, x1 = b % N.ystride;
+        double lam[4];
+        props_d(N, x0, x1, lam[0], lam[1], lam[2], lam[3]);
+        double g[4][6];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) g[j][k] = 0.0;
+        if (N.kind == PARREP_SCHLOGL) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) g[j][j] = 1.0 / c[j];
+        } else {
+            g[0][0] = 1.0 / c[0];
+            g[0][1] = gradU_n[x1];
+            g[1][3] = 1.0 / c[3];
+            g[1][4] = gradV_n[x0];
+            g[2][2] = 1.0 / c[2];
+            g[3][5] = 1.0 / c[5];
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (lam[j] == 0.0) continue;
+            for (int a = 0; a < L; ++a)
+                for (int bb = 0; bb < L; ++bb) acc[a * L + bb] += w * lam[j] * g[j][a] * g[j][bb];
+        }
+        for (int k = 0; k < n_cprime && k < 8; ++k) {
+            const double* cp = cprime + k * L;
+            double lp[4];
+            if (N.kind == PARREP_SCHLOGL) {
+                const double xd = (double)x0;
+                const double h1 = xd * (xd - 1.0), h2 = h1 * (xd - 2.0);
+                lp[0] = (cp[0] * s[0]) * h1;
+                lp[1] = (cp[1] * s[1]) * h2;
+                lp[2] = (cp[2] * s[2]);
+                lp[3] = (cp[3] * s[3]) * xd;
+            } else {
+                lp[0] = cp[0] / (1.0 + pow((double)x1, cp[1]));
+                lp[1] = cp[3] / (1.0 + pow((double)x0, cp[4]));
+                lp[2] = cp[2] * (double)x0;
+                lp[3] = cp[5] * (double)x1;
+            }
+            double h = 0.0;
+            for (int j = 0; j < 4; ++j) {
+                double t = lp[j] - lam[j];
+                if (lam[j] > 0.0) t += lam[j] * log(lam[j] / lp[j]);
+                h += t;
+            }
+            racc[k] += w * h;
+        }
+    }
+    for (int i = 0; i < L * L; ++i) {
+        double v = acc[i];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(fim_out + i, v);
+    }
+    for (int k = 0; k < n_cprime && k < 8; ++k) {
+        double v = racc[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(rer_out + k, v);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// plain SSA: one thread per independent trajectory
+// ---------------------------------------------------------------------------
+template <bool F32>
+__global__ void ssa_kernel(NetDev N, long long n_traj, int x00, int x01, unsigned long long q_Tend,
+                           unsigned long long seed, unsigned long long* hist, unsigned long long* events,
+                           int* status) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long ev = 0;
+    if (t < n_traj) {
+        const uint2 key = seed_key(seed);
+        int x0 = x00, x1 = x01;
+        unsigned long long T = 0, step = 0;
+        while (T < q_Tend) {
+            uint4 w = philox10(make_uint4((unsigned)t, (unsigned)step, (unsigned)(step >> 32), kTagSSA), key);
+            unsigned long long q = 0;
+            const int J = ssa_draw<F32, true>(N, x0, x1, w, q);
+            const unsigned long long rem = q_Tend - T;
+            const int b = x0 * N.ystride + x1;
+            if (q >= rem) {
+                atomicAdd(hist + b, rem);
+                break;
+            }
+            atomicAdd(hist + b, q);
+            T += q;
+            apply(N, J, x0, x1);
+            ++ev;
+            ++step;
+            if (out_of_range(N, x0, x1)) {
+                atomicCAS(status, 0, PARREP_ERANGE);
+                break;
+            }
+        }
+    }
+    ev = warp_sum(ev);
+    if ((threadIdx.x & 31) == 0 && ev) atomicAdd(events, ev);
+}
+
+__global__ void philox_kernel(const uint4* ctr, const uint2* key, long long n, uint4* out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = philox10(ctr[i], key[i]);
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+int kernel_attrs(int prec, int* max_blocks_per_sm, int smem_bytes, int threads) {
+    cudaError_t e;
+    if (prec == PARREP_FP32) {
+        e = cudaFuncSetAttribute(parrep_run_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, parrep_run_kernel<true>, threads,
+                                                              smem_bytes);
+    } else {
+        e = cudaFuncSetAttribute(parrep_run_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem_bytes);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, parrep_run_kernel<false>, threads,
+                                                              smem_bytes);
+    }
+    return (int)e;
+}
+
+cudaError_t launch_run(const RunParams& p, int grid, int threads, int smem_bytes, cudaStream_t st) {
+    void* args[] = {(void*)&p};
+    if (p.prec == PARREP_FP32)
+        return cudaLaunchCooperativeKernel((void*)parrep_run_kernel<true>, dim3(grid), dim3(threads), args,
+                                           (size_t)smem_bytes, st);
+    return cudaLaunchCooperativeKernel((void*)parrep_run_kernel<false>, dim3(grid), dim3(threads), args,
+                                       (size_t)smem_bytes, st);
+}
+
+cudaError_t launch_dephase(const RunParams& p, int xt0, int xt1, int W, unsigned cycle, long long np,
+                           int* out_states, int grid, int threads, cudaStream_t st) {
+    int* status = &p.ctl->status;
+    if (p.prec == PARREP_FP32)
+        dephase_kernel<true><<<grid, threads, 0, st>>>(p, xt0, xt1, W, cycle, np, out_states, status);
+    else
+        dephase_kernel<false><<<grid, threads, 0, st>>>(p, xt0, xt1, W, cycle, np, out_states, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hist_normalise(const unsigned long long* pre, const unsigned long long* post, int n, double scale,
+                                  double* out_pre, double* out_post, double* out_norm, cudaStream_t st) {
+    int blocks = (n + 255) / 256;
+    if (blocks > 1024) blocks = 1024;
+    if (blocks < 1) blocks = 1;
+    hist_normalise_kernel<<<blocks, 256, 0, st>>>(pre, post, n, scale, out_pre, out_post, out_norm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fim_rer(const NetDev& net, const double* c, const double* s, const unsigned long long* hist,
+                           const double* gradU_n, const double* gradV_n, const double* cprime, int n_cprime,
+                           double* fim_out, double* rer_out, cudaStream_t st) {
+    int blocks = (net.nbins + 127) / 128;
+    if (blocks > 304) blocks = 304;
+    if (blocks < 1) blocks = 1;
+    fim_rer_kernel<<<blocks, 128, 0, st>>>(net, c, s, hist, gradU_n, gradV_n, cprime, n_cprime, fim_out, rer_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ssa(const NetDev& net, int prec, long long n_traj, int x0, int x1, unsigned long long q_Tend,
+                       unsigned long long seed, unsigned long long* hist, unsigned long long* events, int* status,
+                       cudaStream_t st) {
+    const int threads = 128;
+    const long long blocks = (n_traj + threads - 1) / threads;
+    if (prec == PARREP_FP32)
+        ssa_kernel<true><<<(unsigned)blocks, threads, 0, st>>>(net, n_traj, x0, x1, q_Tend, seed, hist, events,
+                                                               status);
+    else
+        ssa_kernel<false><<<(unsigned)blocks, threads, 0, st>>>(net, n_traj, x0, x1, q_Tend, seed, hist, events,
+                                                                status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, long long n, uint32_t* out, cudaStream_t st) {
+    const int threads = 128;
+    const long long blocks = (n + threads - 1) / threads;
+    philox_kernel<<<(unsigned)blocks, threads, 0, st>>>((const uint4*)ctr, (const uint2*)key, n, (uint4*)out);
+    return cudaGetLastError();
+}
+
+}  // namespace parrep
