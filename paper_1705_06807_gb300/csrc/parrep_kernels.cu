@@ -513,8 +513,8 @@ __device__ void replay_chunk(const RunParams& P, const HistSink& hs, int x0, int
                 else atomicAdd((to_post ? P.hist_post : P.hist_pre) + b, post);
             }
             inc_q += amt;
+            if (pos == cut.posT) break;  // the run ends inside this holding time
             inc_ev += 1;
-            if (pos == cut.posT) break;
         }
         int n0_ = x0, n1_ = x1;
         apply(N, J, n0_, n1_);
