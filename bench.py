@@ -55,7 +55,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
-    ap.add_argument("--T_end", type=float, default=None, help="override T_end (testing only)")
+    ap.add_argument("--T_end", type=float, default=None, help="override T_end (small profiling cases only)")
+    ap.add_argument("--x0", type=int, default=None, help="fixed x_0 instead of the uniform draw (profiling)")
+    ap.add_argument("--t_corr", type=float, default=None, help="override t_corr (profiling)")
+    ap.add_argument("--t_phase", type=float, default=None, help="override t_phase (profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -178,8 +181,14 @@ def main():
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    c = workload()
+    c = dict(workload())
     T_end = args.T_end or c["T_end"]
+    if args.x0 is not None:
+        c["x0"], c["x0_uniform_hi"] = [args.x0], 0
+    if args.t_corr is not None:
+        c["t_corr"] = args.t_corr
+    if args.t_phase is not None:
+        c["t_phase"] = args.t_phase
     stream = torch.cuda.Stream()
     g = ParRep(c["network"], c["n_replicas"], c["t_corr"], c["t_phase"], x0=c["x0"],
                x0_uniform_hi=c["x0_uniform_hi"], thresh=c["thresh"], precision=args.precision,
