@@ -192,6 +192,34 @@ const char* parrep_last_error(parrep_t h);
 int parrep_ssa(const parrep_network* net, int32_t precision, int64_t n_traj, double T_end, uint64_t seed,
                double* hist_out, int64_t len, int64_t* events_out, float* kernel_ms, void* stream);
 
+/* Limits of parrep_ssa_noalloc's fixed scratch. */
+#define PARREP_SSA_NOALLOC_MAX_BINS 65536
+#define PARREP_SSA_NOALLOC_MAX_SPECIES_STATES 4096
+
+/* parrep_ssa for callers that cannot allocate device memory -- e.g. code
+ * inside a framework that owns the whole device memory pool and forbids side
+ * allocations, or a latency-sensitive loop in which cudaMalloc/cudaFree would
+ * synchronise the device.  The paper has no counterpart: this is an interface
+ * variant of the plain SSA above, with the same arguments, results and
+ * counters, except that hist_out (host or device, len = bins, time units) is
+ * required and no kernel time is reported.
+ *   - It calls no cudaMalloc/cudaFree and no allocating library routine.  Its
+ *     scratch (fixed-point histogram, jump counter, status, toggle tables) is
+ *     one file-scope device array of about 0.6 MB, which every GPU that loads
+ *     the library holds until the process exits.
+ *   - The first call on a device looks up that array's device address
+ *     (cudaGetSymbolAddress) with the device current; make this first call
+ *     before any stream capture on that device.
+ *   - Limits: at most PARREP_SSA_NOALLOC_MAX_BINS histogram bins and
+ *     PARREP_SSA_NOALLOC_MAX_SPECIES_STATES states per species (hist_max+1);
+ *     larger networks are rejected with PARREP_EINVAL.
+ *   - All calls share the one array and clear it at the start; calls that
+ *     overlap on the GPU (other streams, other host threads) race and must be
+ *     serialised by the caller.
+ * Returns PARREP_OK, PARREP_EINVAL, PARREP_ERANGE or PARREP_ECUDA. */
+int parrep_ssa_noalloc(const parrep_network* net, int32_t precision, int64_t n_traj, double T_end, uint64_t seed,
+                       double* hist_out, int64_t len, int64_t* events_out, void* stream);
+
 /* Device Philox4x32-10 of n counters (ctr: n x 4, key: n x 2, out: n x 4
  * uint32, all host pointers) -- exposes the generator the kernels use. */
 int parrep_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out);

@@ -60,7 +60,7 @@ class parrep_cycle(C.Structure):
 EXPORTS = ["parrep_default_options", "parrep_create", "parrep_set_options", "parrep_run", "parrep_n_bins",
            "parrep_histogram", "parrep_histogram_raw", "parrep_fim", "parrep_rer", "parrep_stats_get",
            "parrep_cycle_log", "parrep_dephase", "parrep_destroy", "parrep_last_error", "parrep_ssa",
-           "parrep_philox"]
+           "parrep_philox", "parrep_ssa_noalloc"]
 
 _lib = None
 
@@ -97,6 +97,8 @@ def load():
     L.parrep_ssa.argtypes = [P(parrep_network), C.c_int32, C.c_int64, C.c_double, C.c_uint64, vp, C.c_int64,
                              P(C.c_int64), P(C.c_float), vp]
     L.parrep_philox.argtypes = [vp, vp, C.c_int64, vp]
+    L.parrep_ssa_noalloc.argtypes = [P(parrep_network), C.c_int32, C.c_int64, C.c_double, C.c_uint64, vp,
+                                     C.c_int64, P(C.c_int64), vp]
     for name in EXPORTS:
         if name not in ("parrep_default_options", "parrep_n_bins", "parrep_destroy", "parrep_last_error"):
             getattr(L, name).restype = C.c_int

@@ -209,3 +209,17 @@ def parrep_philox(ctr, key):
     out = np.zeros_like(ctr)
     _check(lib.parrep_philox(_buf(ctr), _buf(key), len(ctr), _buf(out)))
     return out
+
+
+def parrep_ssa_noalloc(spec: dict, n_traj: int, x0, T_end: float, seed: int, hist_out, *, precision: str = "f64",
+                       stream=None):
+    """parrep_ssa without device allocation (fixed scratch in the library).
+    hist_out: float64 numpy array or torch tensor of n_bins.  Returns events."""
+    lib = L.load()
+    net = make_network(spec, x0)
+    ev = C.c_int64(0)
+    st = None if stream is None else C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+    n = hist_out.numel() if hasattr(hist_out, "numel") else hist_out.size
+    _check(lib.parrep_ssa_noalloc(C.byref(net), L.PARREP_FP32 if precision == "f32" else L.PARREP_FP64,
+                                  int(n_traj), float(T_end), int(seed), _buf(hist_out), int(n), C.byref(ev), st))
+    return int(ev.value)
