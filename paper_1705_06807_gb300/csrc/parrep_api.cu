@@ -108,6 +108,10 @@ static int check_network(const parrep_network* net, const parrep_regions* reg, s
             return 0;
         }
     }
+    if (nsp == 2 && (net->hist_max[0] > 32767 || net->hist_max[1] > 32767)) {
+        why = "toggle hist_max must be <= 32767 per species";
+        return 0;
+    }
     if (reg->n < 1 || reg->n > 4) { why = "regions: n must be 1..4"; return 0; }
     if (net->x0_uniform_hi < 0) { why = "x0_uniform_hi < 0"; return 0; }
     if (net->x0_uniform_hi > 0) {
@@ -282,11 +286,93 @@ extern "C" int parrep_set_options(parrep_t h, const parrep_options* o) {
     return PARREP_OK;
 }
 
-static void launch_shape(parrep_t h, int& threads, int& grid, int& S) {
-    threads = h->opt.block_threads > 0 ? h->opt.block_threads : 128;
-    if ((long long)threads > ((h->R + 31) / 32) * 32) threads = (int)(((h->R + 31) / 32) * 32);
-    grid = (int)((h->R + threads - 1) / threads);
-    S = h->opt.chunk_steps > 0 ? h->opt.chunk_steps : 256;
+static int align16(int x) { return (x + 15) & ~15; }
+
+// Launch plan of parrep_run.  FP64 form: one replica per thread.  FP32 form:
+// blocks of T threads of which the first RB own replicas (RB a power of two,
+// >= 32), the smallest RB whose grid is co-resident; B = 32 staged steps.
+struct Plan {
+    int threads, grid, smem, RB, log2RB, B, S, use_smem_hist;
+    int off_tab, off_buf, off_trace, off_live, off_nvalid;
+};
+
+static int fast_layout(parrep_t h, int RB, int with_hist, Plan& pl) {
+    const int B = 32;
+    int off = 0;
+    pl.use_smem_hist = with_hist;
+    if (with_hist) off += align16(h->nbins * 8);
+    pl.off_tab = -1;
+    if (h->net.kind == PARREP_SCHLOGL) {
+        const int tb = (h->net.hist_max[0] + 1) * 16;
+        if (tb <= 64 * 1024) {
+            pl.off_tab = off;
+            off += align16(tb);
+        }
+    } else {
+        pl.off_tab = off;
+        off += align16((h->net.hist_max[0] + 1 + h->net.hist_max[1] + 1) * 4);
+    }
+    pl.off_buf = off;
+    off += B * RB * 8;
+    pl.off_trace = off;
+    off += B * RB * 4;
+    pl.off_live = off;
+    off += RB * 4;
+    pl.off_nvalid = off;
+    off += RB * 4;
+    pl.B = B;
+    pl.RB = RB;
+    int l = 0;
+    while ((1 << l) < RB) ++l;
+    pl.log2RB = l;
+    return off;
+}
+
+static int plan_launch(parrep_t h, Plan& pl) {
+    int dev = 0, nsm = 0;
+    CK(h, cudaGetDevice(&dev));
+    CK(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int prec = h->opt.precision, kind = h->net.kind;
+    memset(&pl, 0, sizeof(pl));
+    int per_sm = 0;
+    if (prec == PARREP_FP64) {
+        int threads = h->opt.block_threads > 0 ? h->opt.block_threads : 128;
+        if ((long long)threads > ((h->R + 31) / 32) * 32) threads = (int)(((h->R + 31) / 32) * 32);
+        pl.threads = threads;
+        pl.RB = threads;
+        pl.grid = (int)((h->R + threads - 1) / threads);
+        pl.S = h->opt.chunk_steps > 0 ? h->opt.chunk_steps : 256;
+        pl.off_tab = pl.off_buf = pl.off_trace = pl.off_live = pl.off_nvalid = -1;
+        for (int with_hist = 1; with_hist >= 0; --with_hist) {
+            if (with_hist && h->nbins * 8 > kSmemHistLimit) continue;
+            pl.use_smem_hist = with_hist;
+            pl.smem = with_hist ? h->nbins * 8 : 0;
+            int ea = kernel_attrs(prec, kind, &per_sm, pl.smem, threads);
+            if (ea != 0) return cuda_fail(h, (cudaError_t)ea, "kernel attributes");
+            if ((long long)per_sm * nsm >= pl.grid) return PARREP_OK;
+        }
+        return fail(h, PARREP_ENOMEM, "n_replicas exceeds one co-resident cooperative grid");
+    }
+    const int T = h->opt.block_threads > 0 ? h->opt.block_threads : 256;
+    for (int RB = 32; RB <= 512; RB *= 2) {
+        const int threads = RB > T ? RB : T;
+        const long long grid = (h->R + RB - 1) / RB;
+        for (int with_hist = 1; with_hist >= 0; --with_hist) {
+            const int smem = fast_layout(h, RB, with_hist, pl);
+            if (smem > 200 * 1024) continue;
+            int ea = kernel_attrs(prec, kind, &per_sm, smem, threads);
+            if (ea != 0) return cuda_fail(h, (cudaError_t)ea, "kernel attributes");
+            if ((long long)per_sm * nsm >= grid) {
+                pl.threads = threads;
+                pl.grid = (int)grid;
+                pl.smem = smem;
+                const int S = h->opt.chunk_steps > 0 ? h->opt.chunk_steps : 1024;
+                pl.S = ((S + pl.B - 1) / pl.B) * pl.B;
+                return PARREP_OK;
+            }
+        }
+    }
+    return fail(h, PARREP_ENOMEM, "n_replicas exceeds one co-resident cooperative grid");
 }
 
 extern "C" int parrep_run(parrep_t h, double T_end, uint64_t seed) {
@@ -297,21 +383,11 @@ extern "C" int parrep_run(parrep_t h, double T_end, uint64_t seed) {
     if (h->opt.thresh_mode == PARREP_THRESH_STEPS &&
         (h->t_corr != floor(h->t_corr) || h->t_phase != floor(h->t_phase)))
         return fail(h, PARREP_EINVAL, "STEPS mode needs integer t_corr, t_phase");
-    int threads, grid, S;
-    launch_shape(h, threads, grid, S);
-    int smem = h->nbins * 8 <= kSmemHistLimit ? h->nbins * 8 : 0;
-    int per_sm = 0, dev = 0, nsm = 0;
-    CK(h, cudaGetDevice(&dev));
-    CK(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    int ea = kernel_attrs(h->opt.precision, &per_sm, smem, threads);
-    if (ea != 0) return cuda_fail(h, (cudaError_t)ea, "kernel attributes");
-    if ((long long)per_sm * nsm < grid && smem > 0) {
-        smem = 0;  // global-memory histogram instead of shared
-        ea = kernel_attrs(h->opt.precision, &per_sm, smem, threads);
-        if (ea != 0) return cuda_fail(h, (cudaError_t)ea, "kernel attributes");
-    }
-    if ((long long)per_sm * nsm < grid)
-        return fail(h, PARREP_ENOMEM, "n_replicas exceeds one co-resident cooperative grid");
+    Plan pl;
+    int prc = plan_launch(h, pl);
+    if (prc != PARREP_OK) return prc;
+    const int threads = pl.threads, grid = pl.grid, S = pl.S, smem = pl.smem;
+    if (S > kMaxChunk) return fail(h, PARREP_EINVAL, "chunk_steps too large");
     RunParams p;
     memset(&p, 0, sizeof(p));
     p.net = h->nd;
@@ -320,7 +396,15 @@ extern "C" int parrep_run(parrep_t h, double T_end, uint64_t seed) {
     p.R = (int)h->R;
     p.G = h->opt.fv_group;
     p.S = S;
-    p.use_smem_hist = smem > 0;
+    p.use_smem_hist = pl.use_smem_hist;
+    p.RB = pl.RB;
+    p.log2RB = pl.log2RB;
+    p.B = pl.B;
+    p.off_tab = pl.off_tab;
+    p.off_buf = pl.off_buf;
+    p.off_trace = pl.off_trace;
+    p.off_live = pl.off_live;
+    p.off_nvalid = pl.off_nvalid;
     if (p.thresh == PARREP_THRESH_STEPS) {
         p.n_c = (long long)h->t_corr;
         p.n_p = (long long)h->t_phase;
@@ -538,6 +622,7 @@ extern "C" int parrep_dephase(parrep_t h, const int32_t* x_tilde, int32_t W, uin
     p.prec = h->opt.precision;
     p.R = (int)h->R;
     p.G = h->opt.fv_group;
+    p.RB = 128;
     p.seed = seed;
     p.ctl = h->d_ctl;
     cudaStream_t st = stream_of(h);

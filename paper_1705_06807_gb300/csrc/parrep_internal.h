@@ -77,6 +77,11 @@ struct RunParams {
     int prec, thresh;
     int R, G, S;
     int use_smem_hist;
+    // block layout: the first RB threads of a block own replicas (RB = blockDim.x
+    // in the FP64 form); the FP32 form stages B steps at a time through shared
+    // memory (byte offsets of its arrays in the dynamic shared memory below)
+    int RB, log2RB, B;
+    int off_tab, off_buf, off_trace, off_live, off_nvalid;
     unsigned long long q_tcorr;
     long long n_c;
     double t_phase;
@@ -96,7 +101,7 @@ struct RunParams {
 };
 
 // ---- launchers (parrep_kernels.cu) ----
-int kernel_attrs(int prec, int* max_blocks_per_sm, int smem_bytes, int threads);
+int kernel_attrs(int prec, int kind, int* max_blocks_per_sm, int smem_bytes, int threads);
 cudaError_t launch_run(const RunParams& p, int grid, int threads, int smem_bytes, cudaStream_t st);
 cudaError_t launch_dephase(const RunParams& p, int xt0, int xt1, int W, unsigned cycle, long long np,
                            int* out_states, int grid, int threads, cudaStream_t st);

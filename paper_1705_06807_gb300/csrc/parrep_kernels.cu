@@ -138,6 +138,20 @@ __device__ __forceinline__ void props_f(const NetDev& N, int x0, int x1, float& 
     }
 }
 
+// round(tau * 2^40) of a finite binary32 tau >= 0 by integer operations on its
+// bits (half-way cases round up), saturated at 2^62 -- no 64-bit conversion
+// instruction, which GB300 would issue on its narrow FP64 pipe.
+__device__ __forceinline__ unsigned long long q_of_f32(float tau) {
+    const unsigned b = __float_as_uint(tau);
+    const int be = (int)(b >> 23);
+    if (be == 0) return 0ull;  // zero or subnormal
+    const unsigned long long m = (unsigned long long)((b & 0x7fffffu) | 0x800000u);
+    const int e = be - 110;  // tau * 2^40 = m * 2^(be - 127 - 23 + 40)
+    if (e >= 0) return e > 38 ? (1ull << 62) : (m << e);
+    if (e < -25) return 0ull;
+    return (m + (1ull << (-e - 1))) >> (-e);
+}
+
 // One Gillespie direct-method step at (x0,x1) from the Philox words w:
 // returns J and (if WANT_TAU) the holding time tau = -log(u1)/a0 in fixed point.
 template <bool F32, bool WANT_TAU>
@@ -146,18 +160,16 @@ __device__ __forceinline__ int ssa_draw(const NetDev& N, int x0, int x1, uint4 w
         float l0, l1, l2, l3;
         props_f(N, x0, x1, l0, l1, l2, l3);
         float a0 = ((l0 + l1) + l2) + l3;
-        if (WANT_TAU) {
-            float tau = -logf(u01f(w.x)) / a0;
-            q = __float2ull_rn(tau * 0x1p40f);
-        }
+        if (WANT_TAU) q = q_of_f32(-logf(u01f(w.x)) / a0);
         return select4<float>(l0, l1, l2, l3, u01f(w.y) * a0);
     } else {
         double l0, l1, l2, l3;
         props_d(N, x0, x1, l0, l1, l2, l3);
         double a0 = ((l0 + l1) + l2) + l3;
         if (WANT_TAU) {
-            double tau = -log(u01d(w.x, w.y)) / a0;
+            const double tau = -log(u01d(w.x, w.y)) / a0;
             q = __double2ull_rn(tau * 0x1p40);
+            if (q > (1ull << 62)) q = 1ull << 62;
         }
         return select4<double>(l0, l1, l2, l3, u01d(w.z, w.w) * a0);
     }
@@ -301,45 +313,12 @@ __device__ void leader_log(const RunParams& P, RunCtl* ctl, const CycleRecDev& r
     ctl->log_n = i + 1;
 }
 
-template <bool F32>
-__device__ void leader_decorrelate(const RunParams& P) {
+// End of a decorrelation (leader): n_p of the coming dephasing, the cycle
+// record's first half, the shared state for the other blocks.
+__device__ void leader_finish_decorr(const RunParams& P, int x0, int x1, int W, unsigned long long Ts, int burn_done,
+                                     unsigned long long step, bool ended, int status, unsigned cycle) {
     RunCtl* ctl = P.ctl;
     const NetDev& N = P.net;
-    const uint2 key = seed_key(P.seed);
-    int x0 = ctl->xt0, x1 = ctl->xt1;
-    unsigned long long Ts = ctl->Ts;
-    int burn_done = ctl->burn_done;
-    const unsigned cycle = ctl->cycle;
-    int W = region_of(N, x0, x1);
-    long long Nc = 0;
-    unsigned long long inW = 0;
-    unsigned long long step = 0;
-    bool ended = false;
-    int status = 0;
-    for (;;) {
-        if (P.thresh == PARREP_THRESH_STEPS ? (Nc >= P.n_c) : (inW >= P.q_tcorr)) break;
-        uint4 w = philox10(make_uint4((unsigned)(step >> 32), (unsigned)step, cycle, kTagDecorr), key);
-        unsigned long long q = 0;
-        const int J = ssa_draw<F32, true>(N, x0, x1, w, q);
-        ++step;
-        leader_contribute(P, ctl, x0, x1, q, Ts, burn_done, ended);
-        if (ended) break;
-        apply(N, J, x0, x1);
-        if (out_of_range(N, x0, x1)) {
-            status = PARREP_ERANGE;
-            break;
-        }
-        const int Wn = region_of(N, x0, x1);
-        if (Wn == W) {
-            ++Nc;
-            inW += q;
-        } else {
-            Nc = 0;
-            inW = 0;
-            W = Wn;
-        }
-        if ((step & 4095ull) == 0) atomicAdd(&ctl->progress, 1ull);
-    }
     ctl->ev_decorr += step;
     long long np = 0;
     if (!ended && status == 0) {
@@ -382,6 +361,49 @@ __device__ void leader_decorrelate(const RunParams& P) {
     }
     if (status) atomicCAS(&ctl->status, 0, status);
     __threadfence();
+}
+
+
+template <bool F32>
+__device__ void leader_decorrelate(const RunParams& P) {
+    RunCtl* ctl = P.ctl;
+    const NetDev& N = P.net;
+    const uint2 key = seed_key(P.seed);
+    int x0 = ctl->xt0, x1 = ctl->xt1;
+    unsigned long long Ts = ctl->Ts;
+    int burn_done = ctl->burn_done;
+    const unsigned cycle = ctl->cycle;
+    int W = region_of(N, x0, x1);
+    long long Nc = 0;
+    unsigned long long inW = 0;
+    unsigned long long step = 0;
+    bool ended = false;
+    int status = 0;
+    for (;;) {
+        if (P.thresh == PARREP_THRESH_STEPS ? (Nc >= P.n_c) : (inW >= P.q_tcorr)) break;
+        uint4 w = philox10(make_uint4((unsigned)(step >> 32), (unsigned)step, cycle, kTagDecorr), key);
+        unsigned long long q = 0;
+        const int J = ssa_draw<F32, true>(N, x0, x1, w, q);
+        ++step;
+        leader_contribute(P, ctl, x0, x1, q, Ts, burn_done, ended);
+        if (ended) break;
+        apply(N, J, x0, x1);
+        if (out_of_range(N, x0, x1)) {
+            status = PARREP_ERANGE;
+            break;
+        }
+        const int Wn = region_of(N, x0, x1);
+        if (Wn == W) {
+            ++Nc;
+            inW += q;
+        } else {
+            Nc = 0;
+            inW = 0;
+            W = Wn;
+        }
+        if ((step & 4095ull) == 0) atomicAdd(&ctl->progress, 1ull);
+    }
+    leader_finish_decorr(P, x0, x1, W, Ts, burn_done, step, ended, status, cycle);
 }
 
 // ---------------------------------------------------------------------------
@@ -536,19 +558,386 @@ __device__ void flush_shared(unsigned long long* sh, unsigned long long* g, int 
 }
 
 // ---------------------------------------------------------------------------
+// FP32 form: staged chunks.  Per sub-chunk of B steps, three phases split by
+// __syncthreads: (P) every thread of the block draws Philox words for the
+// block's replicas -- independent work with no dependency chain; (C) the
+// replica owners advance their states through the B steps, reading the
+// uniforms from shared memory and the cumulative propensities from a per-state
+// table, and write the pre-jump states to a trace; (A) every thread turns the
+// trace into holding times and accumulates them.  An owner's serial chain is
+// thus only the choice of the reaction and the update.
+// ---------------------------------------------------------------------------
+struct FastSmem {
+    const float4* tab;   // Schloegl: per state (c0, c0+c1, ..., a0); nullptr = compute
+    const float* prodU;  // toggle: production of U by V, of V by U (shared copies)
+    const float* prodV;
+    float2* buf;         // [B][RB]: (E = -log u1, u2)
+    int* trace;          // [B][RB]: pre-jump state
+    int* live;           // [RB]: replica still running in this chunk
+    int* nvalid;         // [RB]: steps of the replica in this sub-chunk
+};
+
+template <int KIND>
+__device__ __forceinline__ float4 cums_f32(const NetDev& N, const FastSmem& F, int x0, int x1) {
+    if (KIND == PARREP_SCHLOGL) {
+        if (F.tab) return F.tab[x0];
+        float l0, l1, l2, l3;
+        props_f(N, x0, 0, l0, l1, l2, l3);
+        const float c1 = l0 + l1, c2 = c1 + l2;
+        return make_float4(l0, c1, c2, c2 + l3);
+    }
+    const float l0 = F.prodU[x1], l1 = F.prodV[x0];
+    const float l2 = N.dUf * (float)x0, l3 = N.dVf * (float)x1;
+    const float c1 = l0 + l1, c2 = c1 + l2;
+    return make_float4(l0, c1, c2, c2 + l3);
+}
+
+// The direct-method choice from the cumulative sums: the number of sums <= t
+// is the first j with sum_j > t (the sums are non-decreasing).
+template <int KIND>
+__device__ __forceinline__ int pick_channel(const NetDev& N, float4 c, float u2, int x0, int x1) {
+    const float t = u2 * c.w;
+    int J = (int)(c.x <= t) + (int)(c.y <= t) + (int)(c.z <= t) + (int)(c.w <= t);
+    if (J == 4) {  // rounding left no channel above the target
+        float l0, l1, l2, l3;
+        props_f(N, x0, x1, l0, l1, l2, l3);
+        J = l3 > 0.f ? 3 : (l2 > 0.f ? 2 : (l1 > 0.f ? 1 : 0));
+    }
+    return J;
+}
+
+__device__ __forceinline__ int pack_state(int nsp, int x0, int x1) { return nsp > 1 ? (x0 | (x1 << 16)) : x0; }
+__device__ __forceinline__ void unpack_state(int nsp, int p, int& x0, int& x1) {
+    x0 = nsp > 1 ? (p & 0xffff) : p;
+    x1 = nsp > 1 ? (p >> 16) : 0;
+}
+
+__device__ void build_fast_tables(const NetDev& N, float4* tab, float* pU, float* pV) {
+    if (N.kind == PARREP_SCHLOGL) {
+        if (!tab) return;
+        for (int x = threadIdx.x; x <= N.hist_max0; x += blockDim.x) {
+            float l0, l1, l2, l3;
+            props_f(N, x, 0, l0, l1, l2, l3);
+            const float c1 = l0 + l1, c2 = c1 + l2;
+            tab[x] = make_float4(l0, c1, c2, c2 + l3);
+        }
+    } else {
+        for (int v = threadIdx.x; v <= N.hist_max1; v += blockDim.x) pU[v] = N.prodU_f[v];
+        for (int u = threadIdx.x; u <= N.hist_max0; u += blockDim.x) pV[u] = N.prodV_f[u];
+    }
+}
+
+// (P) Philox words for steps step0 .. step0+nsteps-1 of the block's live replicas.
+template <bool WANT_E>
+__device__ __forceinline__ void produce_lanes(const RunParams& P, const FastSmem& F, unsigned rbase, unsigned step0,
+                                              int nsteps, unsigned cycle, unsigned tag, uint2 key) {
+    const int total = nsteps << P.log2RB;
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+        const int lane = i & (P.RB - 1);
+        if (F.live[lane]) {
+            const int s = i >> P.log2RB;
+            const uint4 w = philox10(make_uint4(rbase + (unsigned)lane, step0 + (unsigned)s, cycle, tag), key);
+            F.buf[i] = make_float2(WANT_E ? -logf(u01f(w.x)) : 0.f, u01f(w.y));
+        }
+    }
+}
+
+// (C) one owner's B lockstep steps of the parallel step; stops at its escape
+// or at a state outside [0, hist_max].
+template <int KIND>
+__device__ __forceinline__ void consume_par(const RunParams& P, const FastSmem& F, bool& running, int& x0, int& x1,
+                                            unsigned r, int W, int sbase, unsigned long long& mykey,
+                                            unsigned long long& myoob, int& xe0, int& xe1) {
+    const NetDev& N = P.net;
+    const int lane = threadIdx.x;
+    int nv = 0;
+    if (running) {
+        nv = P.B;
+        for (int s = 0; s < P.B; ++s) {
+            const int i = (s << P.log2RB) + lane;
+            const float4 c = cums_f32<KIND>(N, F, x0, x1);
+            const int J = pick_channel<KIND>(N, c, F.buf[i].y, x0, x1);
+            F.trace[i] = pack_state(N.nsp, x0, x1);
+            int a0 = x0, a1 = x1;
+            apply(N, J, a0, a1);
+            if (region_of(N, a0, a1) != W) {
+                mykey = pos_of(sbase + s, r);
+                xe0 = a0;
+                xe1 = a1;
+                nv = s + 1;
+                running = false;
+                break;
+            }
+            if (out_of_range(N, a0, a1)) {
+                myoob = pos_of(sbase + s, r);
+                nv = s + 1;
+                running = false;
+                break;
+            }
+            x0 = a0;
+            x1 = a1;
+        }
+        if (!running) F.live[lane] = 0;
+    }
+    F.nvalid[lane] = nv;
+}
+
+enum ChunkMode { kFirst = 4 };
+
+// (A) the holding times of the sub-chunk's trace, used as the mode says:
+// first pass (add), roll-back (subtract), per-step sums, one step's
+// per-replica values, or the precise pass that keeps what precedes the cut.
+template <int KIND, int MODE>
+__device__ __forceinline__ void account(const RunParams& P, const FastSmem& F, const HistSink& hs, unsigned rbase,
+                                        int sbase, const Cuts& cut, bool to_post, unsigned long long& qs,
+                                        unsigned long long& ev, unsigned long long& ev2) {
+    const NetDev& N = P.net;
+    const int total = P.B << P.log2RB;
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+        const int lane = i & (P.RB - 1), s = i >> P.log2RB;
+        if (s >= F.nvalid[lane]) continue;
+        int x0, x1;
+        unpack_state(N.nsp, F.trace[i], x0, x1);
+        const float a0 = cums_f32<KIND>(N, F, x0, x1).w;
+        const unsigned long long q = q_of_f32(F.buf[i].x / a0);
+        const int sc = sbase + s;
+        const unsigned rr = rbase + (unsigned)lane;
+        if (MODE == kFirst) {
+            hs.add(x0, x1, q);
+            qs += q;
+            ++ev;
+        } else if (MODE == kRollback) {
+            hs.add(x0, x1, 0ull - q);
+            ++ev;
+        } else {
+            const unsigned long long pos = pos_of(sc, rr);
+            if (pos > cut.posC) continue;
+            ++ev;
+            if (MODE == kStepSum) {
+                atomicAdd(P.step_sum + sc, q);
+            } else if (MODE == kTauAt) {
+                if (sc == cut.nB) P.tau_at[rr] = q;
+                if (sc == cut.nT) P.tau_at[P.R + rr] = q;
+            } else {
+                if (pos > cut.posE || pos > cut.posT) continue;
+                const unsigned long long amt = (pos == cut.posT) ? cut.partT : q;
+                unsigned long long pre = 0, post = amt;
+                if (cut.posB != kNone) {
+                    if (pos < cut.posB) {
+                        pre = amt;
+                        post = 0;
+                    } else if (pos == cut.posB) {
+                        pre = cut.partB < amt ? cut.partB : amt;
+                        post = amt - pre;
+                    }
+                }
+                const int b = x0 * N.ystride + x1;
+                if (pre) atomicAdd(P.hist_pre + b, pre);
+                if (post) {
+                    if (hs.sh) atomicAdd(hs.sh + b, post);
+                    else atomicAdd((to_post ? P.hist_post : P.hist_pre) + b, post);
+                }
+                qs += amt;                   // included time
+                if (pos != cut.posT) ++ev2;  // included jumps (the truncated one does not jump)
+            }
+        }
+    }
+}
+
+// One chunk (S steps) of the parallel step for the whole block, in a mode.
+// Every thread of the block calls it; owners carry the replica states.
+template <int KIND, int MODE>
+__device__ void chunk_f32(const RunParams& P, const FastSmem& F, const HistSink& hs, bool active, unsigned rbase,
+                          unsigned r, int W, unsigned cycle, unsigned n0, uint2 key, int& x0, int& x1,
+                          const Cuts& cut, bool to_post, unsigned long long& mykey, unsigned long long& myoob,
+                          int& xe0, int& xe1, unsigned long long& qs, unsigned long long& ev,
+                          unsigned long long& inc_ev) {
+    const bool owner = threadIdx.x < P.RB;
+    bool running = owner && active;
+    if (owner) F.live[threadIdx.x] = running ? 1 : 0;
+    __syncthreads();
+    for (int sub = 0; sub < P.S; sub += P.B) {
+        produce_lanes<true>(P, F, rbase, n0 + (unsigned)sub, P.B, cycle, kTagParallel, key);
+        __syncthreads();
+        if (owner) consume_par<KIND>(P, F, running, x0, x1, r, W, sub, mykey, myoob, xe0, xe1);
+        __syncthreads();
+        account<KIND, MODE>(P, F, hs, rbase, sub, cut, to_post, qs, ev, inc_ev);
+        if (!__syncthreads_or(running)) break;
+    }
+}
+
+// Dephasing of the FP32 form: the uniforms of B lockstep jumps at a time come
+// from shared memory; the owner warps run the jumps and the Fleming-Viot
+// ballots exactly as dephase_warp does.
+template <int KIND>
+__device__ int dephase_f32(const RunParams& P, const FastSmem& F, bool active, unsigned rbase, unsigned r, int W,
+                           int xt0, int xt1, long long np, unsigned cycle, uint2 key, int& x0, int& x1) {
+    const NetDev& N = P.net;
+    const bool owner = threadIdx.x < P.RB;  // whole warps, RB is a multiple of 32
+    const int lane = threadIdx.x & 31;
+    const int G = P.G;
+    x0 = xt0;
+    x1 = xt1;
+    if (owner) F.live[threadIdx.x] = active ? 1 : 0;
+    __syncthreads();
+    unsigned act = 0, gm = 0;
+    if (owner) {
+        act = __ballot_sync(0xffffffffu, active);
+        gm = (G >= 32) ? 0xffffffffu : (((1u << G) - 1u) << ((lane / G) * G));
+    }
+    int err = 0;
+    for (long long i0 = 0; i0 < np; i0 += P.B) {
+        const int nb = (int)((np - i0) < (long long)P.B ? (np - i0) : (long long)P.B);
+        produce_lanes<false>(P, F, rbase, (unsigned)i0, nb, cycle, kTagDephase, key);
+        __syncthreads();
+        if (owner && act && !err) {
+            for (int s = 0; s < nb; ++s) {
+                const unsigned i = (unsigned)i0 + (unsigned)s;
+                int n0 = x0, n1 = x1;
+                bool ex = false, bad = false;
+                if (active) {
+                    const float4 c = cums_f32<KIND>(N, F, x0, x1);
+                    const int J = pick_channel<KIND>(N, c, F.buf[(s << P.log2RB) + threadIdx.x].y, x0, x1);
+                    apply(N, J, n0, n1);
+                    ex = region_of(N, n0, n1) != W;
+                    bad = !ex && out_of_range(N, n0, n1);
+                }
+                const unsigned exm = __ballot_sync(0xffffffffu, ex);
+                if (__ballot_sync(0xffffffffu, bad)) {
+                    err = PARREP_ERANGE;
+                    break;
+                }
+                if (exm) {
+                    const unsigned sm = act & ~exm & gm;
+                    int src = lane;
+                    if (ex) {
+                        const int ns = __popc(sm);
+                        if (ns > 0) {
+                            uint4 w = philox10(make_uint4(r, i, cycle, kTagFV), key);
+                            src = kth_set_bit(sm, pick(w.x, (unsigned)ns));
+                        } else {
+                            src = -1;
+                        }
+                    }
+                    const int s0 = __shfl_sync(0xffffffffu, n0, src < 0 ? lane : src);
+                    const int s1 = __shfl_sync(0xffffffffu, n1, src < 0 ? lane : src);
+                    if (ex) {
+                        n0 = src < 0 ? xt0 : s0;
+                        n1 = src < 0 ? xt1 : s1;
+                    }
+                }
+                x0 = n0;
+                x1 = n1;
+            }
+        }
+        __syncthreads();
+    }
+    return err;
+}
+
+// Decorrelation of the FP32 form: block 0 draws the leader's next B*RB
+// uniforms at once; the leader (thread 0) walks through them serially.
+template <int KIND>
+__device__ void decorrelate_f32(const RunParams& P, const FastSmem& F) {
+    __shared__ int s_more;
+    __shared__ unsigned long long s_step;
+    RunCtl* ctl = P.ctl;
+    const NetDev& N = P.net;
+    const uint2 key = seed_key(P.seed);
+    const unsigned cycle = ldv(&ctl->cycle);
+    int x0 = 0, x1 = 0, W = 0, burn_done = 0, status = 0;
+    long long Nc = 0;
+    unsigned long long inW = 0, step = 0, Ts = 0;
+    bool ended = false;
+    if (threadIdx.x == 0) {
+        x0 = ctl->xt0;
+        x1 = ctl->xt1;
+        Ts = ctl->Ts;
+        burn_done = ctl->burn_done;
+        W = region_of(N, x0, x1);
+        s_step = 0;
+        s_more = (P.thresh == PARREP_THRESH_STEPS) ? (Nc < P.n_c) : (inW < P.q_tcorr);
+    }
+    __syncthreads();
+    const int M = P.B << P.log2RB;
+    while (s_more) {
+        const unsigned long long step0 = s_step;
+        for (int i = threadIdx.x; i < M; i += blockDim.x) {
+            const unsigned long long st = step0 + (unsigned long long)i;
+            const uint4 w = philox10(make_uint4((unsigned)(st >> 32), (unsigned)st, cycle, kTagDecorr), key);
+            F.buf[i] = make_float2(-logf(u01f(w.x)), u01f(w.y));
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int more = 1;
+            for (int i = 0; i < M; ++i) {
+                if (P.thresh == PARREP_THRESH_STEPS ? (Nc >= P.n_c) : (inW >= P.q_tcorr)) {
+                    more = 0;
+                    break;
+                }
+                const float2 eu = F.buf[i];
+                const float4 c = cums_f32<KIND>(N, F, x0, x1);
+                const int J = pick_channel<KIND>(N, c, eu.y, x0, x1);
+                const unsigned long long q = q_of_f32(eu.x / c.w);
+                ++step;
+                leader_contribute(P, ctl, x0, x1, q, Ts, burn_done, ended);
+                if (ended) {
+                    more = 0;
+                    break;
+                }
+                apply(N, J, x0, x1);
+                if (out_of_range(N, x0, x1)) {
+                    status = PARREP_ERANGE;
+                    more = 0;
+                    break;
+                }
+                const int Wn = region_of(N, x0, x1);
+                if (Wn == W) {
+                    ++Nc;
+                    inW += q;
+                } else {
+                    Nc = 0;
+                    inW = 0;
+                    W = Wn;
+                }
+                if ((step & 4095ull) == 0) atomicAdd(&ctl->progress, 1ull);
+            }
+            s_step = step;
+            s_more = more;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) leader_finish_decorr(P, x0, x1, W, Ts, burn_done, step, ended, status, cycle);
+}
+
+// ---------------------------------------------------------------------------
 // the persistent ParRep kernel
 // ---------------------------------------------------------------------------
-template <bool F32>
+template <bool F32, int KIND>
 __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
-    extern __shared__ unsigned long long sh_hist[];
+    extern __shared__ __align__(16) unsigned char smem[];
     __shared__ BlockScratch red;
     RunCtl* ctl = P.ctl;
     const NetDev& N = P.net;
-    const unsigned r = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = (long long)r < (long long)P.R;
+    const bool owner = (int)threadIdx.x < P.RB;
+    const unsigned rbase = blockIdx.x * (unsigned)P.RB;
+    const unsigned r = rbase + threadIdx.x;
+    const bool active = owner && (long long)r < (long long)P.R;
     const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
     const uint2 key = seed_key(P.seed);
+    unsigned long long* sh_hist = (unsigned long long*)smem;
     BarState bs{0};
+    FastSmem F{};
+    if (F32) {
+        F.tab = P.off_tab >= 0 && KIND == PARREP_SCHLOGL ? (const float4*)(smem + P.off_tab) : nullptr;
+        F.prodU = KIND == PARREP_TOGGLE ? (const float*)(smem + P.off_tab) : nullptr;
+        F.prodV = KIND == PARREP_TOGGLE ? (const float*)(smem + P.off_tab) + (N.hist_max1 + 1) : nullptr;
+        F.buf = (float2*)(smem + P.off_buf);
+        F.trace = (int*)(smem + P.off_trace);
+        F.live = (int*)(smem + P.off_live);
+        F.nvalid = (int*)(smem + P.off_nvalid);
+        build_fast_tables(N, (float4*)F.tab, (float*)F.prodU, (float*)F.prodV);
+    }
 
     if (P.use_smem_hist) {
         for (int b = threadIdx.x; b < N.nbins; b += blockDim.x) sh_hist[b] = 0;
@@ -588,8 +977,12 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
     if (!grid_sync(P, bs)) goto out;
 
     for (;;) {
-        // ---------------- decorrelation (serial, leader) ----------------
-        if (leader && !ctl->done) leader_decorrelate<F32>(P);
+        // ---------------- decorrelation (serial) ----------------
+        if (F32) {
+            if (blockIdx.x == 0 && !ldv(&ctl->done)) decorrelate_f32<KIND>(P, F);
+        } else {
+            if (leader && !ctl->done) leader_decorrelate<F32>(P);
+        }
         if (!grid_sync(P, bs)) goto out;
         if (ldv(&ctl->done)) break;
         {
@@ -605,10 +998,10 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
                 hs.g = P.hist_post;
             }
             // ---------------- dephasing ----------------
-            int x0, x1;
-            if (dephase_warp<F32>(N, active, r, P.G, W, xt0, xt1, np, cycle, key, x0, x1)) {
-                if ((threadIdx.x & 31) == 0) atomicCAS(&ctl->status, 0, PARREP_ERANGE);
-            }
+            int x0, x1, derr;
+            if (F32) derr = dephase_f32<KIND>(P, F, active, rbase, r, W, xt0, xt1, np, cycle, key, x0, x1);
+            else derr = dephase_warp<F32>(N, active, r, P.G, W, xt0, xt1, np, cycle, key, x0, x1);
+            if (derr && (threadIdx.x & 31) == 0) atomicCAS(&ctl->status, 0, PARREP_ERANGE);
             if (leader) ctl->ev_dephase += (unsigned long long)np * (unsigned long long)P.R;
             // ---------------- parallel step ----------------
             unsigned n0 = 0;
@@ -628,7 +1021,12 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
                 const int xs0 = x0, xs1 = x1;
                 unsigned long long mykey = kNone, myoob = kNone, qsum = 0, ev = 0;
                 int xe0 = 0, xe1 = 0;
-                if (active) {
+                Cuts none{kNone, kNone, kNone, 0, kNone, 0, -1, -1};
+                if (F32) {
+                    unsigned long long dummy = 0;
+                    chunk_f32<KIND, kFirst>(P, F, hs, active, rbase, r, W, cycle, n0, key, x0, x1, none, period_post,
+                                            mykey, myoob, xe0, xe1, qsum, ev, dummy);
+                } else if (active) {
                     for (int s = 0; s < P.S; ++s) {
                         uint4 w = philox10(make_uint4(r, n0 + (unsigned)s, cycle, kTagParallel), key);
                         unsigned long long q = 0;
@@ -685,11 +1083,15 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
                 }
                 // ------------- special chunk: escape, range error or time cut -------------
                 if (leader) ctl->special += 1;
-                if (active) {
-                    unsigned long long d0 = 0, d1 = 0;
-                    Cuts none{kNone, kNone, kNone, 0, kNone, 0, -1, -1};
-                    replay_chunk<F32, kRollback>(P, hs, xs0, xs1, r, W, cycle, n0, none, period_post, d0, d1,
-                                                 ev_replay);
+                {
+                    unsigned long long d0 = 0, d1 = 0, k0 = kNone, k1 = kNone;
+                    int y0 = xs0, y1 = xs1, e0 = 0, e1 = 0;
+                    if (F32)
+                        chunk_f32<KIND, kRollback>(P, F, hs, active, rbase, r, W, cycle, n0, key, y0, y1, none,
+                                                   period_post, k0, k1, e0, e1, d0, ev_replay, d1);
+                    else if (active)
+                        replay_chunk<F32, kRollback>(P, hs, xs0, xs1, r, W, cycle, n0, none, period_post, d0, d1,
+                                                     ev_replay);
                 }
                 Cuts cut{kNone, kNone, kNone, 0, kNone, 0, -1, -1};
                 cut.posE = ekey;
@@ -700,10 +1102,15 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
                         for (int j = threadIdx.x; j < P.S; j += blockDim.x) P.step_sum[j] = 0;
                     }
                     if (!grid_sync(P, bs)) goto out;
-                    if (active) {
-                        unsigned long long d0 = 0, d1 = 0;
-                        replay_chunk<F32, kStepSum>(P, hs, xs0, xs1, r, W, cycle, n0, cut, period_post, d0, d1,
-                                                    ev_replay);
+                    {
+                        unsigned long long d0 = 0, d1 = 0, k0 = kNone, k1 = kNone;
+                        int y0 = xs0, y1 = xs1, e0 = 0, e1 = 0;
+                        if (F32)
+                            chunk_f32<KIND, kStepSum>(P, F, hs, active, rbase, r, W, cycle, n0, key, y0, y1, cut,
+                                                      period_post, k0, k1, e0, e1, d0, ev_replay, d1);
+                        else if (active)
+                            replay_chunk<F32, kStepSum>(P, hs, xs0, xs1, r, W, cycle, n0, cut, period_post, d0, d1,
+                                                        ev_replay);
                     }
                     if (!grid_sync(P, bs)) goto out;
                     unsigned long long baseB = 0, baseT = 0;
@@ -726,9 +1133,16 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
                         if (active) {
                             P.tau_at[r] = 0;
                             P.tau_at[P.R + r] = 0;
-                            unsigned long long d0 = 0, d1 = 0;
-                            replay_chunk<F32, kTauAt>(P, hs, xs0, xs1, r, W, cycle, n0, cut, period_post, d0, d1,
-                                                      ev_replay);
+                        }
+                        {
+                            unsigned long long d0 = 0, d1 = 0, k0 = kNone, k1 = kNone;
+                            int y0 = xs0, y1 = xs1, e0 = 0, e1 = 0;
+                            if (F32)
+                                chunk_f32<KIND, kTauAt>(P, F, hs, active, rbase, r, W, cycle, n0, key, y0, y1, cut,
+                                                        period_post, k0, k1, e0, e1, d0, ev_replay, d1);
+                            else if (active)
+                                replay_chunk<F32, kTauAt>(P, hs, xs0, xs1, r, W, cycle, n0, cut, period_post, d0,
+                                                          d1, ev_replay);
                         }
                         if (!grid_sync(P, bs)) goto out;
                         if (leader) {
@@ -779,9 +1193,15 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
                 }
                 {
                     unsigned long long inc_q = 0, inc_ev = 0;
-                    if (active) {
-                        replay_chunk<F32, kPrecise>(P, hs, xs0, xs1, r, W, cycle, n0, cut,
-                                                    period_post || cut.posB != kNone, inc_q, inc_ev, ev_replay);
+                    const bool tp = period_post || cut.posB != kNone;
+                    if (F32) {
+                        unsigned long long k0 = kNone, k1 = kNone;
+                        int y0 = xs0, y1 = xs1, e0 = 0, e1 = 0;
+                        chunk_f32<KIND, kPrecise>(P, F, hs, active, rbase, r, W, cycle, n0, key, y0, y1, cut, tp, k0,
+                                                  k1, e0, e1, inc_q, ev_replay, inc_ev);
+                    } else if (active) {
+                        replay_chunk<F32, kPrecise>(P, hs, xs0, xs1, r, W, cycle, n0, cut, tp, inc_q, inc_ev,
+                                                    ev_replay);
                     }
                     unsigned long long a = kNone, b = kNone;
                     block_reduce4(red, a, b, inc_q, inc_ev);
@@ -796,7 +1216,7 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
                     hs.g = P.hist_post;
                 }
                 // the escaping replica publishes X^K_{N*}
-                if (ekey != kNone && (unsigned)(ekey & 0xffffffffu) == r && !(cut.posT <= cut.posE)) {
+                if (active && ekey != kNone && (unsigned)(ekey & 0xffffffffu) == r && !(cut.posT <= cut.posE)) {
                     ctl->xe0 = xe0;
                     ctl->xe1 = xe1;
                 }
@@ -832,7 +1252,7 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
                 }
                 if (t_end) goto finished;
                 if (ekey != kNone) break;  // next cycle
-                n0 += (unsigned)P.S;  // only the T_burn split was in this chunk
+                n0 += (unsigned)P.S;       // only the T_burn split was in this chunk
             }
         }
         if (!grid_sync(P, bs)) goto out;
@@ -1003,30 +1423,34 @@ __global__ void philox_kernel(const uint4* ctr, const uint2* key, long long n, u
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-int kernel_attrs(int prec, int* max_blocks_per_sm, int smem_bytes, int threads) {
-    cudaError_t e;
-    if (prec == PARREP_FP32) {
-        e = cudaFuncSetAttribute(parrep_run_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, parrep_run_kernel<true>, threads,
-                                                              smem_bytes);
-    } else {
-        e = cudaFuncSetAttribute(parrep_run_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 smem_bytes);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, parrep_run_kernel<false>, threads,
-                                                              smem_bytes);
-    }
+template <bool F32, int KIND>
+static int attrs_one(int* max_blocks_per_sm, int smem_bytes, int threads) {
+    cudaError_t e = cudaFuncSetAttribute(parrep_run_kernel<F32, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem_bytes);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, parrep_run_kernel<F32, KIND>, threads,
+                                                          smem_bytes);
     return (int)e;
+}
+
+int kernel_attrs(int prec, int kind, int* max_blocks_per_sm, int smem_bytes, int threads) {
+    if (prec == PARREP_FP32)
+        return kind == PARREP_SCHLOGL ? attrs_one<true, PARREP_SCHLOGL>(max_blocks_per_sm, smem_bytes, threads)
+                                      : attrs_one<true, PARREP_TOGGLE>(max_blocks_per_sm, smem_bytes, threads);
+    return kind == PARREP_SCHLOGL ? attrs_one<false, PARREP_SCHLOGL>(max_blocks_per_sm, smem_bytes, threads)
+                                  : attrs_one<false, PARREP_TOGGLE>(max_blocks_per_sm, smem_bytes, threads);
 }
 
 cudaError_t launch_run(const RunParams& p, int grid, int threads, int smem_bytes, cudaStream_t st) {
     void* args[] = {(void*)&p};
+    void* fn;
     if (p.prec == PARREP_FP32)
-        return cudaLaunchCooperativeKernel((void*)parrep_run_kernel<true>, dim3(grid), dim3(threads), args,
-                                           (size_t)smem_bytes, st);
-    return cudaLaunchCooperativeKernel((void*)parrep_run_kernel<false>, dim3(grid), dim3(threads), args,
-                                       (size_t)smem_bytes, st);
+        fn = p.net.kind == PARREP_SCHLOGL ? (void*)parrep_run_kernel<true, PARREP_SCHLOGL>
+                                          : (void*)parrep_run_kernel<true, PARREP_TOGGLE>;
+    else
+        fn = p.net.kind == PARREP_SCHLOGL ? (void*)parrep_run_kernel<false, PARREP_SCHLOGL>
+                                          : (void*)parrep_run_kernel<false, PARREP_TOGGLE>;
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(threads), args, (size_t)smem_bytes, st);
 }
 
 cudaError_t launch_dephase(const RunParams& p, int xt0, int xt1, int W, unsigned cycle, long long np,
