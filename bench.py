@@ -226,6 +226,12 @@ def main():
                    for s in stats)
     dephase = sum(s["events_dephase"] for s in stats)
     kernel_s = sum(s["kernel_ms"] for s in stats) / 1e3
+    ph = {}
+    for s_ in stats:
+        for k, v in s_["phase_cycles"].items():
+            ph[k] = ph.get(k, 0.0) + v
+    ph_tot = sum(ph.values()) or 1.0
+    phase_share = {k: round(v / ph_tot, 4) for k, v in ph.items()}
     if dist:
         t = torch.tensor([t_total, float(useful), float(executed)], device="cuda", dtype=torch.float64)
         tmax = t.clone()
@@ -275,6 +281,7 @@ def main():
                      "frac": achieved / peak_ops if achieved else None, "traffic": None,
                      "note": "thread-instructions at 120 per event (107 per dephasing jump) over the run kernel "
                              "time; peak = 152 SM x 4 schedulers x 32 lanes x 2.07 GHz"},
+        "phase_share": phase_share,
         "gpu_launches": args.steps,
         "clocks": clocks,
         "e2e": e2e,

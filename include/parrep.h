@@ -107,6 +107,11 @@ typedef struct {
     int32_t chunk_steps;
     float kernel_ms;               /* device time of the run (CUDA events) */
     float pad;
+    /* device cycles per phase, summed over blocks (thread 0 of each block):
+     * decorrelation, dephasing, Philox draws, owner chains, accounting, grid
+     * barriers, special-chunk work, vote reduction (FP32 form; the FP64 form
+     * fills decorrelation, dephasing, barriers, special and vote) */
+    double phase_cycles[8];
 } parrep_stats;
 
 typedef struct {

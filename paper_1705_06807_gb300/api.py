@@ -151,6 +151,7 @@ class ParRep:
         d = {k: getattr(s, k) for k, _ in L.parrep_stats._fields_ if k != "pad"}
         d["x0"] = (s.x0[0], s.x0[1])
         d["x_final"] = (s.x_final[0], s.x_final[1])
+        d["phase_cycles"] = {n: float(s.phase_cycles[i]) for i, n in enumerate(L.PHASES)}
         return d
 
     def cycle_log(self, cap: int = 65536):

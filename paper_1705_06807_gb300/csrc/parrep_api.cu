@@ -147,6 +147,22 @@ static void build_net(const parrep_network* net, const parrep_regions* reg, NetD
         nd.ra1[i] = net->n_species > 1 ? reg->a[i][1] : 0;
         nd.rb[i] = reg->b[i];
     }
+    for (int i = 0; i < 5; ++i) {
+        nd.wlo[i] = 1;
+        nd.whi[i] = 0;
+    }
+    if (net->n_species == 1) {
+        for (int x = 0; x <= net->hist_max[0]; ++x) {
+            int rg = reg->n;
+            for (int i = 0; i < reg->n; ++i)
+                if ((long long)reg->a[i][0] * x < reg->b[i]) {
+                    rg = i;
+                    break;
+                }
+            if (nd.wlo[rg] > nd.whi[rg]) nd.wlo[rg] = x;
+            nd.whi[rg] = x;
+        }
+    }
     if (net->kind == PARREP_SCHLOGL) {
         for (int j = 0; j < 4; ++j) {
             nd.A[j] = net->c[j] * net->s[j];
@@ -294,19 +310,28 @@ static int align16(int x) { return (x + 15) & ~15; }
 struct Plan {
     int threads, grid, smem, RB, log2RB, B, S, use_smem_hist;
     int off_tab, off_buf, off_trace, off_live, off_nvalid;
+    int off_limbs, off_inv, off_rng;
 };
 
 static int fast_layout(parrep_t h, int RB, int with_hist, Plan& pl) {
     const int B = 32;
     int off = 0;
     pl.use_smem_hist = with_hist;
-    if (with_hist) off += align16(h->nbins * 8);
+    pl.off_limbs = -1;
+    if (with_hist) {
+        off += align16(h->nbins * 8);
+        pl.off_limbs = off;
+        off += align16(h->nbins * 8);  // two 32-bit limbs per bin
+    }
     pl.off_tab = -1;
+    pl.off_inv = -1;
     if (h->net.kind == PARREP_SCHLOGL) {
         const int tb = (h->net.hist_max[0] + 1) * 16;
         if (tb <= 64 * 1024) {
             pl.off_tab = off;
             off += align16(tb);
+            pl.off_inv = off;
+            off += align16((h->net.hist_max[0] + 1) * 4);
         }
     } else {
         pl.off_tab = off;
@@ -320,6 +345,8 @@ static int fast_layout(parrep_t h, int RB, int with_hist, Plan& pl) {
     off += RB * 4;
     pl.off_nvalid = off;
     off += RB * 4;
+    pl.off_rng = off;
+    off += 16;
     pl.B = B;
     pl.RB = RB;
     int l = 0;
@@ -343,6 +370,7 @@ static int plan_launch(parrep_t h, Plan& pl) {
         pl.grid = (int)((h->R + threads - 1) / threads);
         pl.S = h->opt.chunk_steps > 0 ? h->opt.chunk_steps : 256;
         pl.off_tab = pl.off_buf = pl.off_trace = pl.off_live = pl.off_nvalid = -1;
+        pl.off_limbs = pl.off_inv = pl.off_rng = -1;
         for (int with_hist = 1; with_hist >= 0; --with_hist) {
             if (with_hist && h->nbins * 8 > kSmemHistLimit) continue;
             pl.use_smem_hist = with_hist;
@@ -405,6 +433,9 @@ extern "C" int parrep_run(parrep_t h, double T_end, uint64_t seed) {
     p.off_trace = pl.off_trace;
     p.off_live = pl.off_live;
     p.off_nvalid = pl.off_nvalid;
+    p.off_limbs = pl.off_limbs;
+    p.off_inv = pl.off_inv;
+    p.off_rng = pl.off_rng;
     if (p.thresh == PARREP_THRESH_STEPS) {
         p.n_c = (long long)h->t_corr;
         p.n_p = (long long)h->t_phase;
@@ -460,6 +491,7 @@ extern "C" int parrep_run(parrep_t h, double T_end, uint64_t seed) {
     s.block_threads = threads;
     s.chunk_steps = S;
     s.kernel_ms = ms;
+    for (int i = 0; i < 8; ++i) s.phase_cycles[i] = (double)c.phase_cycles[i];
     h->T_end = T_end;
     h->T_burn = h->opt.T_burn;
     if (c.status != 0) {

@@ -32,6 +32,9 @@ struct NetDev {
     int nreg;
     int ra0[4], ra1[4];
     long long rb[4];
+    // one species: region i is the interval [wlo[i], whi[i]] of [0, hist_max]
+    // (an intersection of half-lines); empty when wlo > whi
+    int wlo[5], whi[5];
     double A[4];
     float Af[4];
     double dU, dV;
@@ -70,6 +73,10 @@ struct RunCtl {
     unsigned long long escapes, chunks, special, cycles;
     long long log_n;
     int x00, x01;
+    // per-phase device cycles summed over blocks (thread 0 of each block):
+    // decorrelation, dephasing, draw (P), owner chain (C), accounting (A),
+    // grid barriers, special-chunk work, first-pass vote reduction
+    unsigned long long phase_cycles[8];
 };
 
 struct RunParams {
@@ -82,6 +89,7 @@ struct RunParams {
     // memory (byte offsets of its arrays in the dynamic shared memory below)
     int RB, log2RB, B;
     int off_tab, off_buf, off_trace, off_live, off_nvalid;
+    int off_limbs, off_inv, off_rng;
     unsigned long long q_tcorr;
     long long n_c;
     double t_phase;

@@ -58,6 +58,24 @@ __device__ __forceinline__ unsigned long long globaltimer() {
     return t;
 }
 
+// Phase timer of a block: thread 0 adds clock64 deltas per phase.
+struct PhaseClock {
+    unsigned long long acc[8];
+    long long t;
+    __device__ __forceinline__ void start() {
+        if (threadIdx.x == 0) t = clock64();
+    }
+    __device__ __forceinline__ void lap(int phase) {
+        if (threadIdx.x == 0) {
+            const long long n = clock64();
+            acc[phase] += (unsigned long long)(n - t);
+            t = n;
+        }
+    }
+};
+enum { kPhDecorr = 0, kPhDephase = 1, kPhDraw = 2, kPhChain = 3, kPhAccount = 4, kPhBarrier = 5, kPhSpecial = 6,
+       kPhVote = 7 };
+
 template <typename T>
 __device__ __forceinline__ T ldv(const T* p) {
     return *(const volatile T*)p;
@@ -160,7 +178,7 @@ __device__ __forceinline__ int ssa_draw(const NetDev& N, int x0, int x1, uint4 w
         float l0, l1, l2, l3;
         props_f(N, x0, x1, l0, l1, l2, l3);
         float a0 = ((l0 + l1) + l2) + l3;
-        if (WANT_TAU) q = q_of_f32(-logf(u01f(w.x)) / a0);
+        if (WANT_TAU) q = q_of_f32(-logf(u01f(w.x)) * __frcp_rn(a0));
         return select4<float>(l0, l1, l2, l3, u01f(w.y) * a0);
     } else {
         double l0, l1, l2, l3;
@@ -286,7 +304,8 @@ __device__ bool grid_sync(const RunParams& P, BarState& bs) {
 // leader (block 0, thread 0): initial state and decorrelation
 // ---------------------------------------------------------------------------
 __device__ void leader_contribute(const RunParams& P, RunCtl* ctl, int x0, int x1, unsigned long long q,
-                                  unsigned long long& Ts, int& burn_done, bool& ended) {
+                                  unsigned long long& Ts, int& burn_done, bool& ended,
+                                  unsigned long long* sh = nullptr, int sh_post = 0) {
     const NetDev& N = P.net;
     unsigned long long t = q;
     const unsigned long long rem = P.q_Tend - Ts;
@@ -302,8 +321,16 @@ __device__ void leader_contribute(const RunParams& P, RunCtl* ctl, int x0, int x
         if (t >= room) burn_done = 1;
     }
     const int bin = x0 * N.ystride + x1;
-    if (pre) atomicAdd(P.hist_pre + bin, pre);
-    if (post) atomicAdd(P.hist_post + bin, post);
+    // block 0's shared histogram feeds the period sh_post says (the leader is
+    // its only writer during the decorrelation); else the global sums
+    if (pre) {
+        if (sh && !sh_post) sh[bin] += pre;
+        else atomicAdd(P.hist_pre + bin, pre);
+    }
+    if (post) {
+        if (sh && sh_post) sh[bin] += post;
+        else atomicAdd(P.hist_post + bin, post);
+    }
     Ts += t;
 }
 
@@ -467,16 +494,62 @@ __device__ int dephase_warp(const NetDev& N, bool active, unsigned r, int G, int
 // ---------------------------------------------------------------------------
 // parallel step helpers
 // ---------------------------------------------------------------------------
+// Where a block's holding times go.  GB300 has no native 64-bit shared-memory
+// atomic add (it is emulated and serialises under contention), so the FP32
+// form splits q into two 32-bit limbs -- the low 16 bits and the rest -- added
+// with native 32-bit atomics and folded exactly into the 64-bit shared sums
+// after every staged sub-chunk.  A sub-chunk adds at most B*RB values to a
+// bin, so with q < qmax = 2^47 / (B*RB) the high-limb sum stays inside a
+// signed 32-bit range (roll-backs included) and the low-limb sum below 2^30.
+// Holding times too large for the limbs go straight to the global sums.
 struct HistSink {
     unsigned long long* sh;  // shared histogram or nullptr
     unsigned long long* g;   // global histogram of the current period
+    unsigned* lo;            // FP32 form: limbs of the shared histogram
+    unsigned* hi;
     int ystride;
+    unsigned long long qmax;
     __device__ __forceinline__ void add(int x0, int x1, unsigned long long q) const {
         const int b = x0 * ystride + x1;
-        if (sh) atomicAdd(sh + b, q);
-        else atomicAdd(g + b, q);
+        if (lo && q < qmax) {
+            atomicAdd(lo + b, (unsigned)(q & 0xffffu));
+            atomicAdd(hi + b, (unsigned)(q >> 16));
+        } else if (sh && !lo) {
+            atomicAdd(sh + b, q);
+        } else {
+            atomicAdd(g + b, q);
+        }
+    }
+    __device__ __forceinline__ void sub(int x0, int x1, unsigned long long q) const {
+        const int b = x0 * ystride + x1;
+        if (lo && q < qmax) {
+            atomicAdd(lo + b, 0u - (unsigned)(q & 0xffffu));
+            atomicAdd(hi + b, 0u - (unsigned)(q >> 16));
+        } else if (sh && !lo) {
+            atomicAdd(sh + b, 0ull - q);
+        } else {
+            atomicAdd(g + b, 0ull - q);
+        }
     }
 };
+
+// Folds the limbs of bins [b0, b1] into the 64-bit shared sums (signed, so a
+// roll-back's negative limb sums are exact) and clears them.
+__device__ __forceinline__ void fold_limbs(const HistSink& hs, int b0, int b1, int ystride, int c0, int c1) {
+    // bins of the rectangle rows [b0, b1] x columns [c0, c1]
+    const int w = c1 - c0 + 1;
+    const int n = (b1 - b0 + 1) * w;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int row = b0 + k / w, col = c0 + k % w;
+        const int b = row * ystride + col;
+        const int vl = (int)hs.lo[b], vh = (int)hs.hi[b];
+        if (vl | vh) {
+            hs.sh[b] += (unsigned long long)(((long long)vh << 16) + (long long)vl);
+            hs.lo[b] = 0;
+            hs.hi[b] = 0;
+        }
+    }
+}
 
 __device__ __forceinline__ unsigned long long pos_of(int s, unsigned r) {
     return ((unsigned long long)(unsigned)s << 32) | (unsigned long long)r;
@@ -507,7 +580,7 @@ __device__ void replay_chunk(const RunParams& P, const HistSink& hs, int x0, int
         const int J = ssa_draw<F32, true>(N, x0, x1, w, q);
         ++ev;
         if (MODE == kRollback) {
-            hs.add(x0, x1, 0ull - q);
+            hs.sub(x0, x1, q);
         } else if (MODE == kStepSum) {
             atomicAdd(P.step_sum + s, q);
         } else if (MODE == kTauAt) {
@@ -569,6 +642,8 @@ __device__ void flush_shared(unsigned long long* sh, unsigned long long* g, int 
 // ---------------------------------------------------------------------------
 struct FastSmem {
     const float4* tab;   // Schloegl: per state (c0, c0+c1, ..., a0); nullptr = compute
+    const float* inv;    // Schloegl with tab: per state RN(1/a0)
+    int* rng;            // [4]: min/max of x0 and x1 touched in the sub-chunk
     const float* prodU;  // toggle: production of U by V, of V by U (shared copies)
     const float* prodV;
     float2* buf;         // [B][RB]: (E = -log u1, u2)
@@ -612,7 +687,7 @@ __device__ __forceinline__ void unpack_state(int nsp, int p, int& x0, int& x1) {
     x1 = nsp > 1 ? (p >> 16) : 0;
 }
 
-__device__ void build_fast_tables(const NetDev& N, float4* tab, float* pU, float* pV) {
+__device__ void build_fast_tables(const NetDev& N, float4* tab, float* inv, float* pU, float* pV) {
     if (N.kind == PARREP_SCHLOGL) {
         if (!tab) return;
         for (int x = threadIdx.x; x <= N.hist_max0; x += blockDim.x) {
@@ -620,6 +695,7 @@ __device__ void build_fast_tables(const NetDev& N, float4* tab, float* pU, float
             props_f(N, x, 0, l0, l1, l2, l3);
             const float c1 = l0 + l1, c2 = c1 + l2;
             tab[x] = make_float4(l0, c1, c2, c2 + l3);
+            inv[x] = __frcp_rn(c2 + l3);
         }
     } else {
         for (int v = threadIdx.x; v <= N.hist_max1; v += blockDim.x) pU[v] = N.prodU_f[v];
@@ -642,44 +718,178 @@ __device__ __forceinline__ void produce_lanes(const RunParams& P, const FastSmem
     }
 }
 
-// (C) one owner's B lockstep steps of the parallel step; stops at its escape
-// or at a state outside [0, hist_max].
+// Region test of the owners' chains.  One species: W is the interval
+// [lo, hi]; a state outside it left W or left [0, hist_max], which the rare
+// branch tells apart.  Two species: the half-plane tests with coefficients
+// held in registers.
+struct RegionTest {
+    int lo, hi;           // one species
+    int n;                // two species: number of tests
+    int a0[4], a1[4];
+    long long b[4];
+    int W;
+    __device__ __forceinline__ void init(const NetDev& N, int W_) {
+        W = W_;
+        n = N.nreg;
+        lo = N.wlo[W_];
+        hi = N.whi[W_];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            a0[i] = N.ra0[i];
+            a1[i] = N.ra1[i];
+            b[i] = N.rb[i];
+        }
+    }
+    __device__ __forceinline__ int region2(int x0, int x1) const {
+        int r = n;
+#pragma unroll
+        for (int i = 3; i >= 0; --i)
+            if (i < n && (long long)a0[i] * x0 + (long long)a1[i] * x1 < b[i]) r = i;
+        return r;
+    }
+};
+
+// Outcome of a jump to (a0, a1): 0 = stays in W, 1 = escape, 2 = outside [0, hist_max].
 template <int KIND>
-__device__ __forceinline__ void consume_par(const RunParams& P, const FastSmem& F, bool& running, int& x0, int& x1,
-                                            unsigned r, int W, int sbase, unsigned long long& mykey,
-                                            unsigned long long& myoob, int& xe0, int& xe1) {
+__device__ __forceinline__ int jump_outcome(const NetDev& N, const RegionTest& rt, int a0, int a1) {
+    if (KIND == PARREP_SCHLOGL) {
+        if (a0 >= rt.lo && a0 <= rt.hi) return 0;
+        return region_of(N, a0, 0) != rt.W ? 1 : 2;
+    }
+    if (rt.region2(a0, a1) != rt.W) return 1;
+    return out_of_range(N, a0, a1) ? 2 : 0;
+}
+
+__device__ __forceinline__ int count_le(float4 c, float t) {
+    return (int)(c.x <= t) + (int)(c.y <= t) + (int)(c.z <= t) + (int)(c.w <= t);
+}
+
+// J == 4: rounding left no cumulative sum above the target; the direct
+// method then takes the last channel with positive propensity.
+__device__ __noinline__ int last_positive(const NetDev& N, int x0, int x1) {
+    float l0, l1, l2, l3;
+    props_f(N, x0, x1, l0, l1, l2, l3);
+    return l3 > 0.f ? 3 : (l2 > 0.f ? 2 : (l1 > 0.f ? 1 : 0));
+}
+
+// (C) one owner's B lockstep steps of the parallel step; stops at its escape
+// or at a state outside [0, hist_max].  Schloegl with its table: two steps
+// per iteration -- the sums at x-1, x, x+1 are loaded together and the second
+// choice is made for both outcomes of the first.
+template <int KIND>
+__device__ __forceinline__ void consume_par(const RunParams& P, const FastSmem& F, const RegionTest& rt,
+                                            bool& running, int& x0, int& x1, unsigned r, int sbase,
+                                            unsigned long long& mykey, unsigned long long& myoob, int& xe0,
+                                            int& xe1) {
     const NetDev& N = P.net;
     const int lane = threadIdx.x;
     int nv = 0;
+    int lo0 = 0x7fffffff, hi0 = -1, lo1 = 0x7fffffff, hi1 = -1;
     if (running) {
         nv = P.B;
-        for (int s = 0; s < P.B; ++s) {
-            const int i = (s << P.log2RB) + lane;
-            const float4 c = cums_f32<KIND>(N, F, x0, x1);
-            const int J = pick_channel<KIND>(N, c, F.buf[i].y, x0, x1);
-            F.trace[i] = pack_state(N.nsp, x0, x1);
-            int a0 = x0, a1 = x1;
-            apply(N, J, a0, a1);
-            if (region_of(N, a0, a1) != W) {
-                mykey = pos_of(sbase + s, r);
-                xe0 = a0;
-                xe1 = a1;
-                nv = s + 1;
-                running = false;
-                break;
+        if (KIND == PARREP_SCHLOGL && F.tab) {
+            const int hm = N.hist_max0;
+            int x = x0;
+            for (int s = 0; s < P.B; s += 2) {
+                const int i1 = (s << P.log2RB) + lane, i2 = i1 + P.RB;
+                const float4 C = F.tab[x];
+                const float4 L = F.tab[x > 0 ? x - 1 : 0];
+                const float4 R = F.tab[x < hm ? x + 1 : hm];
+                const float ua = F.buf[i1].y, ub = F.buf[i2].y;
+                int J1 = count_le(C, ua * C.w);
+                const int JR = count_le(R, ub * R.w), JL = count_le(L, ub * L.w);
+                if (J1 == 4) J1 = last_positive(N, x, 0);
+                const int xa = x + ((J1 & 1) ? -1 : 1);
+                F.trace[i1] = x;
+                lo0 = min(lo0, x);
+                hi0 = max(hi0, x);
+                int o = jump_outcome<KIND>(N, rt, xa, 0);
+                if (o) {
+                    if (o == 1) {
+                        mykey = pos_of(sbase + s, r);
+                        xe0 = xa;
+                        xe1 = 0;
+                    } else {
+                        myoob = pos_of(sbase + s, r);
+                    }
+                    nv = s + 1;
+                    running = false;
+                    break;
+                }
+                int J2 = (J1 & 1) ? JL : JR;
+                if (J2 == 4) J2 = last_positive(N, xa, 0);
+                const int xb = xa + ((J2 & 1) ? -1 : 1);
+                F.trace[i2] = xa;
+                lo0 = min(lo0, xa);
+                hi0 = max(hi0, xa);
+                o = jump_outcome<KIND>(N, rt, xb, 0);
+                if (o) {
+                    if (o == 1) {
+                        mykey = pos_of(sbase + s + 1, r);
+                        xe0 = xb;
+                        xe1 = 0;
+                    } else {
+                        myoob = pos_of(sbase + s + 1, r);
+                    }
+                    x = xa;
+                    nv = s + 2;
+                    running = false;
+                    break;
+                }
+                x = xb;
             }
-            if (out_of_range(N, a0, a1)) {
-                myoob = pos_of(sbase + s, r);
-                nv = s + 1;
-                running = false;
-                break;
+            x0 = x;
+        } else {
+            for (int s = 0; s < P.B; ++s) {
+                const int i = (s << P.log2RB) + lane;
+                const float4 c = cums_f32<KIND>(N, F, x0, x1);
+                int J = count_le(c, F.buf[i].y * c.w);
+                if (J == 4) J = last_positive(N, x0, x1);
+                F.trace[i] = pack_state(N.nsp, x0, x1);
+                lo0 = min(lo0, x0);
+                hi0 = max(hi0, x0);
+                lo1 = min(lo1, x1);
+                hi1 = max(hi1, x1);
+                int a0 = x0, a1 = x1;
+                apply(N, J, a0, a1);
+                const int o = jump_outcome<KIND>(N, rt, a0, a1);
+                if (o) {
+                    if (o == 1) {
+                        mykey = pos_of(sbase + s, r);
+                        xe0 = a0;
+                        xe1 = a1;
+                    } else {
+                        myoob = pos_of(sbase + s, r);
+                    }
+                    nv = s + 1;
+                    running = false;
+                    break;
+                }
+                x0 = a0;
+                x1 = a1;
             }
-            x0 = a0;
-            x1 = a1;
         }
         if (!running) F.live[lane] = 0;
     }
     F.nvalid[lane] = nv;
+    // the rectangle of states this warp touched, for folding the limbs
+    if (KIND == PARREP_SCHLOGL) {
+        lo1 = 0;
+        hi1 = 0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo0 = min(lo0, __shfl_xor_sync(0xffffffffu, lo0, o));
+        hi0 = max(hi0, __shfl_xor_sync(0xffffffffu, hi0, o));
+        lo1 = min(lo1, __shfl_xor_sync(0xffffffffu, lo1, o));
+        hi1 = max(hi1, __shfl_xor_sync(0xffffffffu, hi1, o));
+    }
+    if ((lane & 31) == 0 && hi0 >= 0) {
+        atomicMin(F.rng + 0, lo0);
+        atomicMax(F.rng + 1, hi0);
+        atomicMin(F.rng + 2, lo1);
+        atomicMax(F.rng + 3, hi1);
+    }
 }
 
 enum ChunkMode { kFirst = 4 };
@@ -698,8 +908,8 @@ __device__ __forceinline__ void account(const RunParams& P, const FastSmem& F, c
         if (s >= F.nvalid[lane]) continue;
         int x0, x1;
         unpack_state(N.nsp, F.trace[i], x0, x1);
-        const float a0 = cums_f32<KIND>(N, F, x0, x1).w;
-        const unsigned long long q = q_of_f32(F.buf[i].x / a0);
+        const float ia0 = (KIND == PARREP_SCHLOGL && F.tab) ? F.inv[x0] : __frcp_rn(cums_f32<KIND>(N, F, x0, x1).w);
+        const unsigned long long q = q_of_f32(F.buf[i].x * ia0);
         const int sc = sbase + s;
         const unsigned rr = rbase + (unsigned)lane;
         if (MODE == kFirst) {
@@ -707,7 +917,7 @@ __device__ __forceinline__ void account(const RunParams& P, const FastSmem& F, c
             qs += q;
             ++ev;
         } else if (MODE == kRollback) {
-            hs.add(x0, x1, 0ull - q);
+            hs.sub(x0, x1, q);
             ++ev;
         } else {
             const unsigned long long pos = pos_of(sc, rr);
@@ -734,7 +944,7 @@ __device__ __forceinline__ void account(const RunParams& P, const FastSmem& F, c
                 const int b = x0 * N.ystride + x1;
                 if (pre) atomicAdd(P.hist_pre + b, pre);
                 if (post) {
-                    if (hs.sh) atomicAdd(hs.sh + b, post);
+                    if (hs.sh) hs.add(x0, x1, post);
                     else atomicAdd((to_post ? P.hist_post : P.hist_pre) + b, post);
                 }
                 qs += amt;                   // included time
@@ -748,21 +958,45 @@ __device__ __forceinline__ void account(const RunParams& P, const FastSmem& F, c
 // Every thread of the block calls it; owners carry the replica states.
 template <int KIND, int MODE>
 __device__ void chunk_f32(const RunParams& P, const FastSmem& F, const HistSink& hs, bool active, unsigned rbase,
-                          unsigned r, int W, unsigned cycle, unsigned n0, uint2 key, int& x0, int& x1,
+                          unsigned r, const RegionTest& rt, unsigned cycle, unsigned n0, uint2 key, int& x0, int& x1,
                           const Cuts& cut, bool to_post, unsigned long long& mykey, unsigned long long& myoob,
                           int& xe0, int& xe1, unsigned long long& qs, unsigned long long& ev,
-                          unsigned long long& inc_ev) {
+                          unsigned long long& inc_ev, PhaseClock& pc) {
     const bool owner = threadIdx.x < P.RB;
     bool running = owner && active;
     if (owner) F.live[threadIdx.x] = running ? 1 : 0;
+    if (threadIdx.x == 0) {
+        F.rng[0] = 0x7fffffff;
+        F.rng[1] = -1;
+        F.rng[2] = 0x7fffffff;
+        F.rng[3] = -1;
+    }
     __syncthreads();
+    const bool limbs = hs.lo != nullptr && MODE != kStepSum && MODE != kTauAt;
     for (int sub = 0; sub < P.S; sub += P.B) {
+        pc.start();
         produce_lanes<true>(P, F, rbase, n0 + (unsigned)sub, P.B, cycle, kTagParallel, key);
         __syncthreads();
-        if (owner) consume_par<KIND>(P, F, running, x0, x1, r, W, sub, mykey, myoob, xe0, xe1);
+        pc.lap(kPhDraw);
+        if (owner) consume_par<KIND>(P, F, rt, running, x0, x1, r, sub, mykey, myoob, xe0, xe1);
         __syncthreads();
+        pc.lap(kPhChain);
         account<KIND, MODE>(P, F, hs, rbase, sub, cut, to_post, qs, ev, inc_ev);
-        if (!__syncthreads_or(running)) break;
+        const bool any = __syncthreads_or(running);
+        if (limbs) {
+            const int r0 = F.rng[0], r1 = F.rng[1], c0 = F.rng[2], c1 = F.rng[3];
+            if (r1 >= r0) fold_limbs(hs, r0, r1, P.net.ystride, c0, c1);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                F.rng[0] = 0x7fffffff;
+                F.rng[1] = -1;
+                F.rng[2] = 0x7fffffff;
+                F.rng[3] = -1;
+            }
+            __syncthreads();
+        }
+        pc.lap(kPhAccount);
+        if (!any) break;
     }
 }
 
@@ -770,8 +1004,8 @@ __device__ void chunk_f32(const RunParams& P, const FastSmem& F, const HistSink&
 // from shared memory; the owner warps run the jumps and the Fleming-Viot
 // ballots exactly as dephase_warp does.
 template <int KIND>
-__device__ int dephase_f32(const RunParams& P, const FastSmem& F, bool active, unsigned rbase, unsigned r, int W,
-                           int xt0, int xt1, long long np, unsigned cycle, uint2 key, int& x0, int& x1) {
+__device__ int dephase_f32(const RunParams& P, const FastSmem& F, const RegionTest& rt, bool active, unsigned rbase,
+                           unsigned r, int xt0, int xt1, long long np, unsigned cycle, uint2 key, int& x0, int& x1) {
     const NetDev& N = P.net;
     const bool owner = threadIdx.x < P.RB;  // whole warps, RB is a multiple of 32
     const int lane = threadIdx.x & 31;
@@ -797,10 +1031,12 @@ __device__ int dephase_f32(const RunParams& P, const FastSmem& F, bool active, u
                 bool ex = false, bad = false;
                 if (active) {
                     const float4 c = cums_f32<KIND>(N, F, x0, x1);
-                    const int J = pick_channel<KIND>(N, c, F.buf[(s << P.log2RB) + threadIdx.x].y, x0, x1);
+                    int J = count_le(c, F.buf[(s << P.log2RB) + threadIdx.x].y * c.w);
+                    if (J == 4) J = last_positive(N, x0, x1);
                     apply(N, J, n0, n1);
-                    ex = region_of(N, n0, n1) != W;
-                    bad = !ex && out_of_range(N, n0, n1);
+                    const int o = jump_outcome<KIND>(N, rt, n0, n1);
+                    ex = o == 1;
+                    bad = o == 2;
                 }
                 const unsigned exm = __ballot_sync(0xffffffffu, ex);
                 if (__ballot_sync(0xffffffffu, bad)) {
@@ -838,7 +1074,7 @@ __device__ int dephase_f32(const RunParams& P, const FastSmem& F, bool active, u
 // Decorrelation of the FP32 form: block 0 draws the leader's next B*RB
 // uniforms at once; the leader (thread 0) walks through them serially.
 template <int KIND>
-__device__ void decorrelate_f32(const RunParams& P, const FastSmem& F) {
+__device__ void decorrelate_f32(const RunParams& P, const FastSmem& F, unsigned long long* sh, int sh_post) {
     __shared__ int s_more;
     __shared__ unsigned long long s_step;
     RunCtl* ctl = P.ctl;
@@ -849,12 +1085,14 @@ __device__ void decorrelate_f32(const RunParams& P, const FastSmem& F) {
     long long Nc = 0;
     unsigned long long inW = 0, step = 0, Ts = 0;
     bool ended = false;
+    RegionTest rt;
     if (threadIdx.x == 0) {
         x0 = ctl->xt0;
         x1 = ctl->xt1;
         Ts = ctl->Ts;
         burn_done = ctl->burn_done;
         W = region_of(N, x0, x1);
+        rt.init(N, W);
         s_step = 0;
         s_more = (P.thresh == PARREP_THRESH_STEPS) ? (Nc < P.n_c) : (inW < P.q_tcorr);
     }
@@ -877,21 +1115,25 @@ __device__ void decorrelate_f32(const RunParams& P, const FastSmem& F) {
                 }
                 const float2 eu = F.buf[i];
                 const float4 c = cums_f32<KIND>(N, F, x0, x1);
-                const int J = pick_channel<KIND>(N, c, eu.y, x0, x1);
-                const unsigned long long q = q_of_f32(eu.x / c.w);
+                int J = count_le(c, eu.y * c.w);
+                if (J == 4) J = last_positive(N, x0, x1);
+                const float ia0 = (KIND == PARREP_SCHLOGL && F.tab) ? F.inv[x0] : __frcp_rn(c.w);
+                const unsigned long long q = q_of_f32(eu.x * ia0);
                 ++step;
-                leader_contribute(P, ctl, x0, x1, q, Ts, burn_done, ended);
+                leader_contribute(P, ctl, x0, x1, q, Ts, burn_done, ended, sh, sh_post);
                 if (ended) {
                     more = 0;
                     break;
                 }
                 apply(N, J, x0, x1);
-                if (out_of_range(N, x0, x1)) {
+                const int o = jump_outcome<KIND>(N, rt, x0, x1);
+                if (o == 2) {
                     status = PARREP_ERANGE;
                     more = 0;
                     break;
                 }
-                const int Wn = region_of(N, x0, x1);
+                const int Wn = o == 0 ? W : region_of(N, x0, x1);
+                if (Wn != W) rt.init(N, Wn);
                 if (Wn == W) {
                     ++Nc;
                     inW += q;
@@ -927,16 +1169,26 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
     const uint2 key = seed_key(P.seed);
     unsigned long long* sh_hist = (unsigned long long*)smem;
     BarState bs{0};
+    PhaseClock pc{};
     FastSmem F{};
+    unsigned* limb_lo = nullptr;
+    unsigned* limb_hi = nullptr;
     if (F32) {
+        if (P.use_smem_hist) {
+            limb_lo = (unsigned*)(smem + P.off_limbs);
+            limb_hi = limb_lo + N.nbins;
+            for (int b = threadIdx.x; b < 2 * N.nbins; b += blockDim.x) limb_lo[b] = 0;
+        }
         F.tab = P.off_tab >= 0 && KIND == PARREP_SCHLOGL ? (const float4*)(smem + P.off_tab) : nullptr;
+        F.inv = F.tab ? (const float*)(smem + P.off_inv) : nullptr;
+        F.rng = (int*)(smem + P.off_rng);
         F.prodU = KIND == PARREP_TOGGLE ? (const float*)(smem + P.off_tab) : nullptr;
         F.prodV = KIND == PARREP_TOGGLE ? (const float*)(smem + P.off_tab) + (N.hist_max1 + 1) : nullptr;
         F.buf = (float2*)(smem + P.off_buf);
         F.trace = (int*)(smem + P.off_trace);
         F.live = (int*)(smem + P.off_live);
         F.nvalid = (int*)(smem + P.off_nvalid);
-        build_fast_tables(N, (float4*)F.tab, (float*)F.prodU, (float*)F.prodV);
+        build_fast_tables(N, (float4*)F.tab, (float*)F.inv, (float*)F.prodU, (float*)F.prodV);
     }
 
     if (P.use_smem_hist) {
@@ -972,21 +1224,28 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
         __threadfence();
     }
     int period_post = P.q_Tburn == 0 ? 1 : 0;  // which global sums this block's histogram feeds
-    HistSink hs{P.use_smem_hist ? sh_hist : nullptr, period_post ? P.hist_post : P.hist_pre, N.ystride};
+    HistSink hs{P.use_smem_hist ? sh_hist : nullptr, period_post ? P.hist_post : P.hist_pre, limb_lo, limb_hi,
+                N.ystride, F32 ? ((1ull << 47) >> (P.log2RB + 5)) : 0ull};
     unsigned long long chunk_c = 0;
     if (!grid_sync(P, bs)) goto out;
 
     for (;;) {
         // ---------------- decorrelation (serial) ----------------
+        pc.start();
         if (F32) {
-            if (blockIdx.x == 0 && !ldv(&ctl->done)) decorrelate_f32<KIND>(P, F);
+            if (blockIdx.x == 0 && !ldv(&ctl->done))
+                decorrelate_f32<KIND>(P, F, P.use_smem_hist ? sh_hist : nullptr, period_post);
         } else {
             if (leader && !ctl->done) leader_decorrelate<F32>(P);
         }
+        pc.lap(kPhDecorr);
         if (!grid_sync(P, bs)) goto out;
+        pc.lap(kPhBarrier);
         if (ldv(&ctl->done)) break;
         {
             const int W = ldv(&ctl->W);
+            RegionTest rt;
+            rt.init(N, W);
             const int xt0 = ldv(&ctl->xt0), xt1 = ldv(&ctl->xt1);
             const long long np = ldv(&ctl->np);
             const unsigned cycle = ldv(&ctl->cycle);
@@ -999,8 +1258,11 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
             }
             // ---------------- dephasing ----------------
             int x0, x1, derr;
-            if (F32) derr = dephase_f32<KIND>(P, F, active, rbase, r, W, xt0, xt1, np, cycle, key, x0, x1);
+            pc.start();
+            if (F32) derr = dephase_f32<KIND>(P, F, rt, active, rbase, r, xt0, xt1, np, cycle, key, x0, x1);
             else derr = dephase_warp<F32>(N, active, r, P.G, W, xt0, xt1, np, cycle, key, x0, x1);
+            __syncthreads();
+            pc.lap(kPhDephase);
             if (derr && (threadIdx.x & 31) == 0) atomicCAS(&ctl->status, 0, PARREP_ERANGE);
             if (leader) ctl->ev_dephase += (unsigned long long)np * (unsigned long long)P.R;
             // ---------------- parallel step ----------------
@@ -1024,8 +1286,8 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
                 Cuts none{kNone, kNone, kNone, 0, kNone, 0, -1, -1};
                 if (F32) {
                     unsigned long long dummy = 0;
-                    chunk_f32<KIND, kFirst>(P, F, hs, active, rbase, r, W, cycle, n0, key, x0, x1, none, period_post,
-                                            mykey, myoob, xe0, xe1, qsum, ev, dummy);
+                    chunk_f32<KIND, kFirst>(P, F, hs, active, rbase, r, rt, cycle, n0, key, x0, x1, none, period_post,
+                                            mykey, myoob, xe0, xe1, qsum, ev, dummy, pc);
                 } else if (active) {
                     for (int s = 0; s < P.S; ++s) {
                         uint4 w = philox10(make_uint4(r, n0 + (unsigned)s, cycle, kTagParallel), key);
@@ -1051,6 +1313,7 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
                     }
                 }
                 const int slot = (int)(chunk_c % 3);
+                pc.start();
                 {
                     unsigned long long a = mykey, b = myoob, c = qsum, d = ev;
                     block_reduce4(red, a, b, c, d);
@@ -1061,7 +1324,9 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
                         if (d) atomicAdd(&ctl->chunkev[slot], d);
                     }
                 }
+                pc.lap(kPhVote);
                 if (!grid_sync(P, bs)) goto out;
+                pc.lap(kPhBarrier);
                 ++chunk_c;
                 const unsigned long long ekey = ldv(&ctl->minkey[slot]);
                 const unsigned long long okey = ldv(&ctl->oobkey[slot]);
@@ -1083,12 +1348,13 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
                 }
                 // ------------- special chunk: escape, range error or time cut -------------
                 if (leader) ctl->special += 1;
+                pc.start();
                 {
                     unsigned long long d0 = 0, d1 = 0, k0 = kNone, k1 = kNone;
                     int y0 = xs0, y1 = xs1, e0 = 0, e1 = 0;
                     if (F32)
-                        chunk_f32<KIND, kRollback>(P, F, hs, active, rbase, r, W, cycle, n0, key, y0, y1, none,
-                                                   period_post, k0, k1, e0, e1, d0, ev_replay, d1);
+                        chunk_f32<KIND, kRollback>(P, F, hs, active, rbase, r, rt, cycle, n0, key, y0, y1, none,
+                                                   period_post, k0, k1, e0, e1, d0, ev_replay, d1, pc);
                     else if (active)
                         replay_chunk<F32, kRollback>(P, hs, xs0, xs1, r, W, cycle, n0, none, period_post, d0, d1,
                                                      ev_replay);
@@ -1106,8 +1372,8 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
                         unsigned long long d0 = 0, d1 = 0, k0 = kNone, k1 = kNone;
                         int y0 = xs0, y1 = xs1, e0 = 0, e1 = 0;
                         if (F32)
-                            chunk_f32<KIND, kStepSum>(P, F, hs, active, rbase, r, W, cycle, n0, key, y0, y1, cut,
-                                                      period_post, k0, k1, e0, e1, d0, ev_replay, d1);
+                            chunk_f32<KIND, kStepSum>(P, F, hs, active, rbase, r, rt, cycle, n0, key, y0, y1, cut,
+                                                      period_post, k0, k1, e0, e1, d0, ev_replay, d1, pc);
                         else if (active)
                             replay_chunk<F32, kStepSum>(P, hs, xs0, xs1, r, W, cycle, n0, cut, period_post, d0, d1,
                                                         ev_replay);
@@ -1138,8 +1404,8 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
                             unsigned long long d0 = 0, d1 = 0, k0 = kNone, k1 = kNone;
                             int y0 = xs0, y1 = xs1, e0 = 0, e1 = 0;
                             if (F32)
-                                chunk_f32<KIND, kTauAt>(P, F, hs, active, rbase, r, W, cycle, n0, key, y0, y1, cut,
-                                                        period_post, k0, k1, e0, e1, d0, ev_replay, d1);
+                                chunk_f32<KIND, kTauAt>(P, F, hs, active, rbase, r, rt, cycle, n0, key, y0, y1, cut,
+                                                        period_post, k0, k1, e0, e1, d0, ev_replay, d1, pc);
                             else if (active)
                                 replay_chunk<F32, kTauAt>(P, hs, xs0, xs1, r, W, cycle, n0, cut, period_post, d0,
                                                           d1, ev_replay);
@@ -1187,9 +1453,11 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
                     grid_sync(P, bs);
                     goto out;
                 }
-                if (cut.posB != kNone && hs.sh) {
-                    // this block's shared sums are all before T_burn now
-                    flush_shared(sh_hist, P.hist_pre, N.nbins);
+                if (cut.posB != kNone) {
+                    // this block's shared sums are all before T_burn now; what
+                    // the precise pass adds to the sink is after it
+                    if (hs.sh) flush_shared(sh_hist, P.hist_pre, N.nbins);
+                    hs.g = P.hist_post;
                 }
                 {
                     unsigned long long inc_q = 0, inc_ev = 0;
@@ -1197,8 +1465,8 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
                     if (F32) {
                         unsigned long long k0 = kNone, k1 = kNone;
                         int y0 = xs0, y1 = xs1, e0 = 0, e1 = 0;
-                        chunk_f32<KIND, kPrecise>(P, F, hs, active, rbase, r, W, cycle, n0, key, y0, y1, cut, tp, k0,
-                                                  k1, e0, e1, inc_q, ev_replay, inc_ev);
+                        chunk_f32<KIND, kPrecise>(P, F, hs, active, rbase, r, rt, cycle, n0, key, y0, y1, cut, tp, k0,
+                                                  k1, e0, e1, inc_q, ev_replay, inc_ev, pc);
                     } else if (active) {
                         replay_chunk<F32, kPrecise>(P, hs, xs0, xs1, r, W, cycle, n0, cut, tp, inc_q, inc_ev,
                                                     ev_replay);
@@ -1220,7 +1488,9 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
                     ctl->xe0 = xe0;
                     ctl->xe1 = xe1;
                 }
+                pc.lap(kPhSpecial);
                 if (!grid_sync(P, bs)) goto out;
+                pc.lap(kPhBarrier);
                 Ts += ldv(&ctl->inc_sum[slot]);
                 const bool t_end = cut.posT != kNone && cut.posT <= cut.posE;
                 if (leader) {
@@ -1265,6 +1535,9 @@ out:
         block_reduce4(red, a, b, c, d);
         if (threadIdx.x == 0 && c) atomicAdd(&ctl->ev_replay, c);
     }
+    if (threadIdx.x == 0)
+        for (int i = 0; i < 8; ++i)
+            if (pc.acc[i]) atomicAdd(&ctl->phase_cycles[i], pc.acc[i]);
 }
 
 // ---------------------------------------------------------------------------

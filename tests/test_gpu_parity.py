@@ -9,10 +9,12 @@ binary64 summation error (about n * 2^-53 relative); the tolerance used is
 atol = 4e-12 * (events in the run) + 1e-12 * T_end, rtol = 1e-12.
 
 In the FP32 form the reaction choice is taken in binary32 on both sides, so
-every integer result is still identical; the holding time -logf(u)/a0 differs
-where CUDA's and the C library's logf round differently (at most 1 ulp of
-the logarithm, relative 2^-23), which bounds every time sum by
-rtol = 2^-23 on top of the fixed-point term.
+every integer result is still identical.  The holding time differs: the
+kernel computes -logf(u) * RN(1/a0), the oracle -logf(u) / a0.  CUDA's and
+the C library's logf may differ by 1 ulp, and the reciprocal-multiply rounds
+twice where the division rounds once, so each tau agrees to within 3 ulp of
+binary32 (relative 3 * 2^-24 < 2^-22); every time sum is bounded by
+rtol = 2^-22 on top of the fixed-point term.
 """
 import numpy as np
 import pytest
@@ -24,7 +26,7 @@ from paper_1705_06807_gb300.api import ParRepError
 pytestmark = pytest.mark.gpu
 
 
-F32_RTOL = 2.0**-23
+F32_RTOL = 2.0**-22
 
 
 def _tol(events, T_end, precision="f64"):
@@ -244,3 +246,21 @@ def test_bounded_wait_times_out_and_context_survives():
     g.set_options(block_threads=64)
     g.run(5.0, 1)
     assert g.stats()["T_s"] == 5.0
+
+
+@pytest.mark.parametrize("spec,x0", [(V10, [2]), (K.toggle(alpha=20.0, n=2.5, hist_max=(63, 63)), [15, 2])])
+def test_fp32_staged_path_is_shape_invariant(spec, x0):
+    """The FP32 form stages 32 steps at a time and splits holding times into
+    32-bit limbs; none of that may change a bit of the fixed-point sums, the
+    cycle log or the event counts across chunk lengths and block sizes."""
+    thresh, tc = ("steps", 200) if spec["kind"] == "schlogl" else ("time", 0.5)
+    res = []
+    for S, B in [(32, 64), (256, 256), (1024, 128)]:
+        g = ParRep(spec, 77, tc, tc, x0=x0, thresh=thresh, precision="f32", fv_group=16, T_burn=30.0,
+                   chunk_steps=S, block_threads=B)
+        g.run(90.0, 99)
+        pre, post = g.histogram_raw()
+        res.append((pre, post, g.cycle_log(), g.stats()["events_parallel_useful"]))
+    for r in res[1:]:
+        assert np.array_equal(r[0], res[0][0]) and np.array_equal(r[1], res[0][1])
+        assert r[2] == res[0][2] and r[3] == res[0][3]
