@@ -326,7 +326,7 @@ static int fast_layout(parrep_t h, int RB, int with_hist, Plan& pl) {
     pl.off_tab = -1;
     pl.off_inv = -1;
     if (h->net.kind == PARREP_SCHLOGL) {
-        const int tb = (h->net.hist_max[0] + 1) * 16;
+        const int tb = (h->net.hist_max[0] + 5) * 16;  // padded by two entries on each side
         if (tb <= 64 * 1024) {
             pl.off_tab = off;
             off += align16(tb);

@@ -613,8 +613,8 @@ __device__ void replay_chunk(const RunParams& P, const HistSink& hs, int x0, int
         }
         int n0_ = x0, n1_ = x1;
         apply(N, J, n0_, n1_);
-        if (region_of(N, n0_, n1_) != W) break;
         if (out_of_range(N, n0_, n1_)) break;
+        if (region_of(N, n0_, n1_) != W) break;
         x0 = n0_;
         x1 = n1_;
     }
@@ -690,12 +690,15 @@ __device__ __forceinline__ void unpack_state(int nsp, int p, int& x0, int& x1) {
 __device__ void build_fast_tables(const NetDev& N, float4* tab, float* inv, float* pU, float* pV) {
     if (N.kind == PARREP_SCHLOGL) {
         if (!tab) return;
-        for (int x = threadIdx.x; x <= N.hist_max0; x += blockDim.x) {
+        // entries -2..hist_max+2: the two on each side are copies of the
+        // edge states (never used for a decision, only loaded speculatively)
+        for (int k = threadIdx.x; k <= N.hist_max0 + 4; k += blockDim.x) {
+            const int x = min(max(k - 2, 0), N.hist_max0);
             float l0, l1, l2, l3;
             props_f(N, x, 0, l0, l1, l2, l3);
             const float c1 = l0 + l1, c2 = c1 + l2;
-            tab[x] = make_float4(l0, c1, c2, c2 + l3);
-            inv[x] = __frcp_rn(c2 + l3);
+            tab[k - 2] = make_float4(l0, c1, c2, c2 + l3);
+            if (k >= 2 && k - 2 <= N.hist_max0) inv[k - 2] = __frcp_rn(c2 + l3);
         }
     } else {
         for (int v = threadIdx.x; v <= N.hist_max1; v += blockDim.x) pU[v] = N.prodU_f[v];
@@ -707,13 +710,23 @@ __device__ void build_fast_tables(const NetDev& N, float4* tab, float* inv, floa
 template <bool WANT_E>
 __device__ __forceinline__ void produce_lanes(const RunParams& P, const FastSmem& F, unsigned rbase, unsigned step0,
                                               int nsteps, unsigned cycle, unsigned tag, uint2 key) {
-    const int total = nsteps << P.log2RB;
-    for (int i = threadIdx.x; i < total; i += blockDim.x) {
-        const int lane = i & (P.RB - 1);
-        if (F.live[lane]) {
-            const int s = i >> P.log2RB;
-            const uint4 w = philox10(make_uint4(rbase + (unsigned)lane, step0 + (unsigned)s, cycle, tag), key);
-            F.buf[i] = make_float2(WANT_E ? -logf(u01f(w.x)) : 0.f, u01f(w.y));
+    const int lg = P.log2RB, mask = P.RB - 1, T = blockDim.x;
+    const int total = nsteps << lg;
+    const int* live = F.live;
+    float2* buf = F.buf;
+    // four independent draws per thread and pass, so that their Philox rounds interleave
+    for (int base = threadIdx.x; base < total; base += 4 * T) {
+        uint4 w[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int i = base + k * T < total ? base + k * T : base;
+            w[k] = philox10(make_uint4(rbase + (unsigned)(i & mask), step0 + (unsigned)(i >> lg), cycle, tag), key);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int i = base + k * T;
+            if (i < total && live[i & mask])
+                buf[i] = make_float2(WANT_E ? -logf(u01f(w[k].x)) : 0.f, u01f(w[k].y));
         }
     }
 }
@@ -749,13 +762,19 @@ struct RegionTest {
     }
 };
 
-// Outcome of a jump to (a0, a1): 0 = stays in W, 1 = escape, 2 = outside [0, hist_max].
-template <int KIND>
+// Outcome of a jump to (a0, a1): 0 = stays in W, 1 = escape, 2 = outside
+// [0, hist_max].  In the parallel step and the decorrelation a jump outside
+// the range is an error even if it also leaves W (OOB_FIRST); in the
+// dephasing a replica that left W is replaced, whatever its state.
+template <int KIND, bool OOB_FIRST>
 __device__ __forceinline__ int jump_outcome(const NetDev& N, const RegionTest& rt, int a0, int a1) {
     if (KIND == PARREP_SCHLOGL) {
         if (a0 >= rt.lo && a0 <= rt.hi) return 0;
+        const bool oob = a0 < 0 || a0 > N.hist_max0;
+        if (OOB_FIRST) return oob ? 2 : 1;
         return region_of(N, a0, 0) != rt.W ? 1 : 2;
     }
+    if (OOB_FIRST && out_of_range(N, a0, a1)) return 2;
     if (rt.region2(a0, a1) != rt.W) return 1;
     return out_of_range(N, a0, a1) ? 2 : 0;
 }
@@ -788,26 +807,46 @@ __device__ __forceinline__ void consume_par(const RunParams& P, const FastSmem& 
     if (running) {
         nv = P.B;
         if (KIND == PARREP_SCHLOGL && F.tab) {
-            const int hm = N.hist_max0;
+            // The table is padded by two entries on each side, so x-1 and x+1
+            // need no clamping.  For a +-1 chain the direct-method choice is
+            // "up" iff t < c0 or c1 <= t < c2, three independent comparisons;
+            // rounding (t >= a0), escapes and range errors share one rare
+            // branch that redoes the two steps with the general code.
+            const float4* tabp = F.tab;
+            const float2* buf = F.buf;
+            int* trace = F.trace;
+            const int lo = rt.lo, hi = rt.hi, RBl = P.RB, lg = P.log2RB, B = P.B;
             int x = x0;
-            for (int s = 0; s < P.B; s += 2) {
-                const int i1 = (s << P.log2RB) + lane, i2 = i1 + P.RB;
-                const float4 C = F.tab[x];
-                const float4 L = F.tab[x > 0 ? x - 1 : 0];
-                const float4 R = F.tab[x < hm ? x + 1 : hm];
-                const float ua = F.buf[i1].y, ub = F.buf[i2].y;
-                int J1 = count_le(C, ua * C.w);
-                const int JR = count_le(R, ub * R.w), JL = count_le(L, ub * L.w);
+            for (int s = 0; s < B; s += 2) {
+                const int i1 = (s << lg) + lane, i2 = i1 + RBl;
+                const float ua = buf[i1].y, ub = buf[i2].y;
+                const float4 C = tabp[x], L = tabp[x - 1], R = tabp[x + 1];
+                const float t1 = ua * C.w, tR = ub * R.w, tL = ub * L.w;
+                const bool up1 = (t1 < C.x) | ((C.y <= t1) & (t1 < C.z));
+                const bool upR = (tR < R.x) | ((R.y <= tR) & (tR < R.z));
+                const bool upL = (tL < L.x) | ((L.y <= tL) & (tL < L.z));
+                const int xa = up1 ? x + 1 : x - 1;
+                const bool up2 = up1 ? upR : upL;
+                const int xb = up2 ? xa + 1 : xa - 1;
+                const float t2 = up1 ? tR : tL, a2 = up1 ? R.w : L.w;
+                const bool rare = (t1 >= C.w) | (t2 >= a2) | (xa < lo) | (xa > hi) | (xb < lo) | (xb > hi);
+                trace[i1] = x;
+                trace[i2] = xa;
+                lo0 = min(lo0, min(x, xa));
+                hi0 = max(hi0, max(x, xa));
+                if (!rare) {
+                    x = xb;
+                    continue;
+                }
+                // exact handling of the two steps
+                int J1 = count_le(C, t1);
                 if (J1 == 4) J1 = last_positive(N, x, 0);
-                const int xa = x + ((J1 & 1) ? -1 : 1);
-                F.trace[i1] = x;
-                lo0 = min(lo0, x);
-                hi0 = max(hi0, x);
-                int o = jump_outcome<KIND>(N, rt, xa, 0);
+                const int ya = x + ((J1 & 1) ? -1 : 1);
+                int o = jump_outcome<KIND, true>(N, rt, ya, 0);
                 if (o) {
                     if (o == 1) {
                         mykey = pos_of(sbase + s, r);
-                        xe0 = xa;
+                        xe0 = ya;
                         xe1 = 0;
                     } else {
                         myoob = pos_of(sbase + s, r);
@@ -816,27 +855,28 @@ __device__ __forceinline__ void consume_par(const RunParams& P, const FastSmem& 
                     running = false;
                     break;
                 }
-                int J2 = (J1 & 1) ? JL : JR;
-                if (J2 == 4) J2 = last_positive(N, xa, 0);
-                const int xb = xa + ((J2 & 1) ? -1 : 1);
-                F.trace[i2] = xa;
-                lo0 = min(lo0, xa);
-                hi0 = max(hi0, xa);
-                o = jump_outcome<KIND>(N, rt, xb, 0);
+                trace[i2] = ya;
+                lo0 = min(lo0, ya);
+                hi0 = max(hi0, ya);
+                const float4 C2 = tabp[ya];
+                int J2 = count_le(C2, ub * C2.w);
+                if (J2 == 4) J2 = last_positive(N, ya, 0);
+                const int yb = ya + ((J2 & 1) ? -1 : 1);
+                o = jump_outcome<KIND, true>(N, rt, yb, 0);
                 if (o) {
                     if (o == 1) {
                         mykey = pos_of(sbase + s + 1, r);
-                        xe0 = xb;
+                        xe0 = yb;
                         xe1 = 0;
                     } else {
                         myoob = pos_of(sbase + s + 1, r);
                     }
-                    x = xa;
+                    x = ya;
                     nv = s + 2;
                     running = false;
                     break;
                 }
-                x = xb;
+                x = yb;
             }
             x0 = x;
         } else {
@@ -852,7 +892,7 @@ __device__ __forceinline__ void consume_par(const RunParams& P, const FastSmem& 
                 hi1 = max(hi1, x1);
                 int a0 = x0, a1 = x1;
                 apply(N, J, a0, a1);
-                const int o = jump_outcome<KIND>(N, rt, a0, a1);
+                const int o = jump_outcome<KIND, true>(N, rt, a0, a1);
                 if (o) {
                     if (o == 1) {
                         mykey = pos_of(sbase + s, r);
@@ -902,53 +942,71 @@ __device__ __forceinline__ void account(const RunParams& P, const FastSmem& F, c
                                         int sbase, const Cuts& cut, bool to_post, unsigned long long& qs,
                                         unsigned long long& ev, unsigned long long& ev2) {
     const NetDev& N = P.net;
-    const int total = P.B << P.log2RB;
-    for (int i = threadIdx.x; i < total; i += blockDim.x) {
-        const int lane = i & (P.RB - 1), s = i >> P.log2RB;
-        if (s >= F.nvalid[lane]) continue;
-        int x0, x1;
-        unpack_state(N.nsp, F.trace[i], x0, x1);
-        const float ia0 = (KIND == PARREP_SCHLOGL && F.tab) ? F.inv[x0] : __frcp_rn(cums_f32<KIND>(N, F, x0, x1).w);
-        const unsigned long long q = q_of_f32(F.buf[i].x * ia0);
-        const int sc = sbase + s;
-        const unsigned rr = rbase + (unsigned)lane;
-        if (MODE == kFirst) {
-            hs.add(x0, x1, q);
-            qs += q;
-            ++ev;
-        } else if (MODE == kRollback) {
-            hs.sub(x0, x1, q);
-            ++ev;
-        } else {
-            const unsigned long long pos = pos_of(sc, rr);
-            if (pos > cut.posC) continue;
-            ++ev;
-            if (MODE == kStepSum) {
-                atomicAdd(P.step_sum + sc, q);
-            } else if (MODE == kTauAt) {
-                if (sc == cut.nB) P.tau_at[rr] = q;
-                if (sc == cut.nT) P.tau_at[P.R + rr] = q;
+    const int lg = P.log2RB, mask = P.RB - 1, T = blockDim.x;
+    const int total = P.B << lg;
+    const bool tabbed = KIND == PARREP_SCHLOGL && F.tab;
+    for (int base = threadIdx.x; base < total; base += 4 * T) {
+        int xa[4], xb[4];
+        unsigned long long qv[4];
+        bool ok[4];
+        // four independent items per pass: loads and conversions interleave
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int i = base + k * T;
+            const int ic = i < total ? i : base;
+            const int lane = ic & mask, s = ic >> lg;
+            ok[k] = i < total && s < F.nvalid[lane];
+            unpack_state(N.nsp, ok[k] ? F.trace[ic] : 0, xa[k], xb[k]);
+            const float ia0 = tabbed ? F.inv[xa[k]] : __frcp_rn(cums_f32<KIND>(N, F, xa[k], xb[k]).w);
+            qv[k] = q_of_f32(F.buf[ic].x * ia0);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (!ok[k]) continue;
+            const int i = base + k * T;
+            const int lane = i & mask, s = i >> lg;
+            const int x0 = xa[k], x1 = xb[k];
+            const unsigned long long q = qv[k];
+            const int sc = sbase + s;
+            const unsigned rr = rbase + (unsigned)lane;
+            if (MODE == kFirst) {
+                hs.add(x0, x1, q);
+                qs += q;
+                ++ev;
+            } else if (MODE == kRollback) {
+                hs.sub(x0, x1, q);
+                ++ev;
             } else {
-                if (pos > cut.posE || pos > cut.posT) continue;
-                const unsigned long long amt = (pos == cut.posT) ? cut.partT : q;
-                unsigned long long pre = 0, post = amt;
-                if (cut.posB != kNone) {
-                    if (pos < cut.posB) {
-                        pre = amt;
-                        post = 0;
-                    } else if (pos == cut.posB) {
-                        pre = cut.partB < amt ? cut.partB : amt;
-                        post = amt - pre;
+                const unsigned long long pos = pos_of(sc, rr);
+                if (pos > cut.posC) continue;
+                ++ev;
+                if (MODE == kStepSum) {
+                    atomicAdd(P.step_sum + sc, q);
+                } else if (MODE == kTauAt) {
+                    if (sc == cut.nB) P.tau_at[rr] = q;
+                    if (sc == cut.nT) P.tau_at[P.R + rr] = q;
+                } else {
+                    if (pos > cut.posE || pos > cut.posT) continue;
+                    const unsigned long long amt = (pos == cut.posT) ? cut.partT : q;
+                    unsigned long long pre = 0, post = amt;
+                    if (cut.posB != kNone) {
+                        if (pos < cut.posB) {
+                            pre = amt;
+                            post = 0;
+                        } else if (pos == cut.posB) {
+                            pre = cut.partB < amt ? cut.partB : amt;
+                            post = amt - pre;
+                        }
                     }
+                    const int b = x0 * N.ystride + x1;
+                    if (pre) atomicAdd(P.hist_pre + b, pre);
+                    if (post) {
+                        if (hs.sh) hs.add(x0, x1, post);
+                        else atomicAdd((to_post ? P.hist_post : P.hist_pre) + b, post);
+                    }
+                    qs += amt;                   // included time
+                    if (pos != cut.posT) ++ev2;  // included jumps (the truncated one does not jump)
                 }
-                const int b = x0 * N.ystride + x1;
-                if (pre) atomicAdd(P.hist_pre + b, pre);
-                if (post) {
-                    if (hs.sh) hs.add(x0, x1, post);
-                    else atomicAdd((to_post ? P.hist_post : P.hist_pre) + b, post);
-                }
-                qs += amt;                   // included time
-                if (pos != cut.posT) ++ev2;  // included jumps (the truncated one does not jump)
             }
         }
     }
@@ -1024,7 +1082,72 @@ __device__ int dephase_f32(const RunParams& P, const FastSmem& F, const RegionTe
         const int nb = (int)((np - i0) < (long long)P.B ? (np - i0) : (long long)P.B);
         produce_lanes<false>(P, F, rbase, (unsigned)i0, nb, cycle, kTagDephase, key);
         __syncthreads();
-        if (owner && act && !err) {
+        if (owner && act && !err && KIND == PARREP_SCHLOGL && F.tab) {
+            // window (x-1, x, x+1) in registers; the common step is three
+            // comparisons and a shift, the far neighbour loaded ahead
+            const float4* tabp = F.tab;
+            const int lo = rt.lo, hi = rt.hi, lg = P.log2RB;
+            float4 Lw = tabp[x0 - 1], Cw = tabp[x0], Rw = tabp[x0 + 1];
+            for (int s = 0; s < nb; ++s) {
+                const unsigned i = (unsigned)i0 + (unsigned)s;
+                const float u = F.buf[(s << lg) + threadIdx.x].y;
+                const float t = u * Cw.w;
+                const bool up = (t < Cw.x) | ((Cw.y <= t) & (t < Cw.z));
+                const int xn = up ? x0 + 1 : x0 - 1;
+                const bool odd = active && ((t >= Cw.w) | (xn < lo) | (xn > hi));
+                if (!__any_sync(0xffffffffu, odd)) {
+                    if (active) {
+                        const float4 far = tabp[up ? x0 + 2 : x0 - 2];
+                        const float4 oldC = Cw;
+                        Cw = up ? Rw : Lw;
+                        Lw = up ? oldC : far;
+                        Rw = up ? far : oldC;
+                        x0 = xn;
+                    }
+                    continue;
+                }
+                // exact step for the warp: choice, escapes, range, Fleming-Viot
+                int n0 = x0, n1 = x1;
+                bool ex = false, bad = false;
+                if (active) {
+                    int J = count_le(Cw, t);
+                    if (J == 4) J = last_positive(N, x0, x1);
+                    apply(N, J, n0, n1);
+                    const int o = jump_outcome<KIND, false>(N, rt, n0, n1);
+                    ex = o == 1;
+                    bad = o == 2;
+                }
+                const unsigned exm = __ballot_sync(0xffffffffu, ex);
+                if (__ballot_sync(0xffffffffu, bad)) {
+                    err = PARREP_ERANGE;
+                    break;
+                }
+                if (exm) {
+                    const unsigned sm = act & ~exm & gm;
+                    int src = lane;
+                    if (ex) {
+                        const int ns = __popc(sm);
+                        if (ns > 0) {
+                            uint4 w = philox10(make_uint4(r, i, cycle, kTagFV), key);
+                            src = kth_set_bit(sm, pick(w.x, (unsigned)ns));
+                        } else {
+                            src = -1;
+                        }
+                    }
+                    const int s0 = __shfl_sync(0xffffffffu, n0, src < 0 ? lane : src);
+                    const int s1 = __shfl_sync(0xffffffffu, n1, src < 0 ? lane : src);
+                    if (ex) {
+                        n0 = src < 0 ? xt0 : s0;
+                        n1 = src < 0 ? xt1 : s1;
+                    }
+                }
+                x0 = n0;
+                x1 = n1;
+                Lw = tabp[x0 - 1];
+                Cw = tabp[x0];
+                Rw = tabp[x0 + 1];
+            }
+        } else if (owner && act && !err) {
             for (int s = 0; s < nb; ++s) {
                 const unsigned i = (unsigned)i0 + (unsigned)s;
                 int n0 = x0, n1 = x1;
@@ -1034,7 +1157,7 @@ __device__ int dephase_f32(const RunParams& P, const FastSmem& F, const RegionTe
                     int J = count_le(c, F.buf[(s << P.log2RB) + threadIdx.x].y * c.w);
                     if (J == 4) J = last_positive(N, x0, x1);
                     apply(N, J, n0, n1);
-                    const int o = jump_outcome<KIND>(N, rt, n0, n1);
+                    const int o = jump_outcome<KIND, false>(N, rt, n0, n1);
                     ex = o == 1;
                     bad = o == 2;
                 }
@@ -1071,11 +1194,79 @@ __device__ int dephase_f32(const RunParams& P, const FastSmem& F, const RegionTe
     return err;
 }
 
-// Decorrelation of the FP32 form: block 0 draws the leader's next B*RB
-// uniforms at once; the leader (thread 0) walks through them serially.
+// Decorrelation of the FP32 form.  Block 0 works in rounds of M = B*RB
+// steps: (1) all threads draw the M uniforms; (2) the leader walks the jump
+// chain alone -- the states do not depend on the stopping rule, so this
+// serial loop carries only the state; (3) all threads turn the states into
+// holding times; (4) the leader replays the round in order, applying the
+// stopping rule (n_c jumps or t_corr time in W), T_end, T_burn and the
+// histogram, and stops where Algorithm 1 stops.  Draws beyond the stop are
+// discarded; the next round starts at the step where this one stopped.
+template <int KIND>
+__device__ int decorr_chain(const NetDev& N, const FastSmem& F, int x0, int x1, int M, int& last0, int& last1) {
+    // (2): states before each of the M jumps; returns the number of jumps
+    // made (a jump that leaves [0, hist_max] ends the round, its state is
+    // returned in last0/last1)
+    const float2* buf = F.buf;
+    int* trace = F.trace;
+    if (KIND == PARREP_SCHLOGL && F.tab) {
+        const float4* tabp = F.tab;
+        const int hm = N.hist_max0;
+        float4 Lw = tabp[x0 - 1], Cw = tabp[x0], Rw = tabp[x0 + 1];
+        for (int k = 0; k < M; ++k) {
+            trace[k] = x0;
+            const float t = buf[k].y * Cw.w;
+            const bool up = (t < Cw.x) | ((Cw.y <= t) & (t < Cw.z));
+            int xn = up ? x0 + 1 : x0 - 1;
+            if ((t >= Cw.w) | (xn < 0) | (xn > hm)) {
+                int J = count_le(Cw, t);
+                if (J == 4) J = last_positive(N, x0, 0);
+                xn = x0 + ((J & 1) ? -1 : 1);
+                if (xn < 0 || xn > hm) {
+                    last0 = xn;
+                    last1 = 0;
+                    return k + 1;
+                }
+                x0 = xn;
+                Lw = tabp[x0 - 1];
+                Cw = tabp[x0];
+                Rw = tabp[x0 + 1];
+                continue;
+            }
+            const float4 far = tabp[up ? x0 + 2 : x0 - 2];
+            const float4 oldC = Cw;
+            Cw = up ? Rw : Lw;
+            Lw = up ? oldC : far;
+            Rw = up ? far : oldC;
+            x0 = xn;
+        }
+        last0 = x0;
+        last1 = 0;
+        return M;
+    }
+    for (int k = 0; k < M; ++k) {
+        trace[k] = pack_state(N.nsp, x0, x1);
+        const float4 c = cums_f32<KIND>(N, F, x0, x1);
+        int J = count_le(c, buf[k].y * c.w);
+        if (J == 4) J = last_positive(N, x0, x1);
+        int a0 = x0, a1 = x1;
+        apply(N, J, a0, a1);
+        if (out_of_range(N, a0, a1)) {
+            last0 = a0;
+            last1 = a1;
+            return k + 1;
+        }
+        x0 = a0;
+        x1 = a1;
+    }
+    last0 = x0;
+    last1 = x1;
+    return M;
+}
+
 template <int KIND>
 __device__ void decorrelate_f32(const RunParams& P, const FastSmem& F, unsigned long long* sh, int sh_post) {
-    __shared__ int s_more;
+    __shared__ int s_more, s_n, s_l0, s_l1;
     __shared__ unsigned long long s_step;
     RunCtl* ctl = P.ctl;
     const NetDev& N = P.net;
@@ -1086,6 +1277,9 @@ __device__ void decorrelate_f32(const RunParams& P, const FastSmem& F, unsigned 
     unsigned long long inW = 0, step = 0, Ts = 0;
     bool ended = false;
     RegionTest rt;
+    const bool steps_mode = P.thresh == PARREP_THRESH_STEPS;
+    const long long n_c = P.n_c;
+    const unsigned long long q_tcorr = P.q_tcorr;
     if (threadIdx.x == 0) {
         x0 = ctl->xt0;
         x1 = ctl->xt1;
@@ -1094,62 +1288,106 @@ __device__ void decorrelate_f32(const RunParams& P, const FastSmem& F, unsigned 
         W = region_of(N, x0, x1);
         rt.init(N, W);
         s_step = 0;
-        s_more = (P.thresh == PARREP_THRESH_STEPS) ? (Nc < P.n_c) : (inW < P.q_tcorr);
+        s_more = steps_mode ? (Nc < n_c) : (inW < q_tcorr);
     }
     __syncthreads();
-    const int M = P.B << P.log2RB;
+    const int M = P.B << P.log2RB, T = blockDim.x;
+    float2* buf = F.buf;
+    unsigned long long* qbuf = (unsigned long long*)F.buf;  // (3) overwrites the draws in place
+    const int* trace = F.trace;
+    const bool tabbed = KIND == PARREP_SCHLOGL && F.tab;
     while (s_more) {
         const unsigned long long step0 = s_step;
-        for (int i = threadIdx.x; i < M; i += blockDim.x) {
-            const unsigned long long st = step0 + (unsigned long long)i;
-            const uint4 w = philox10(make_uint4((unsigned)(st >> 32), (unsigned)st, cycle, kTagDecorr), key);
-            F.buf[i] = make_float2(-logf(u01f(w.x)), u01f(w.y));
+        // (1) draws
+        for (int base = threadIdx.x; base < M; base += 4 * T) {
+            uint4 w[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const unsigned long long st = step0 + (unsigned long long)(base + k * T);
+                w[k] = philox10(make_uint4((unsigned)(st >> 32), (unsigned)st, cycle, kTagDecorr), key);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (base + k * T < M) buf[base + k * T] = make_float2(-logf(u01f(w[k].x)), u01f(w[k].y));
         }
         __syncthreads();
+        // (2) the jump chain
+        if (threadIdx.x == 0) {
+            int l0, l1;
+            s_n = decorr_chain<KIND>(N, F, x0, x1, M, l0, l1);
+            s_l0 = l0;
+            s_l1 = l1;
+        }
+        __syncthreads();
+        const int n = s_n;
+        // (3) holding times
+        for (int k = threadIdx.x; k < n; k += T) {
+            int a0, a1;
+            unpack_state(N.nsp, trace[k], a0, a1);
+            const float E = buf[k].x;
+            const float ia0 = tabbed ? F.inv[a0] : __frcp_rn(cums_f32<KIND>(N, F, a0, a1).w);
+            qbuf[k] = q_of_f32(E * ia0);  // same thread read buf[k] just before
+        }
+        __syncthreads();
+        // (4) the stopping rule, in order
         if (threadIdx.x == 0) {
             int more = 1;
-            for (int i = 0; i < M; ++i) {
-                if (P.thresh == PARREP_THRESH_STEPS ? (Nc >= P.n_c) : (inW >= P.q_tcorr)) {
+            int k = 0;
+            for (; k < n; ++k) {
+                if (steps_mode ? (Nc >= n_c) : (inW >= q_tcorr)) {
                     more = 0;
                     break;
                 }
-                const float2 eu = F.buf[i];
-                const float4 c = cums_f32<KIND>(N, F, x0, x1);
-                int J = count_le(c, eu.y * c.w);
-                if (J == 4) J = last_positive(N, x0, x1);
-                const float ia0 = (KIND == PARREP_SCHLOGL && F.tab) ? F.inv[x0] : __frcp_rn(c.w);
-                const unsigned long long q = q_of_f32(eu.x * ia0);
+                int a0, a1;
+                unpack_state(N.nsp, trace[k], a0, a1);
+                const unsigned long long q = qbuf[k];
                 ++step;
-                leader_contribute(P, ctl, x0, x1, q, Ts, burn_done, ended, sh, sh_post);
+                leader_contribute(P, ctl, a0, a1, q, Ts, burn_done, ended, sh, sh_post);
                 if (ended) {
                     more = 0;
                     break;
                 }
-                apply(N, J, x0, x1);
-                const int o = jump_outcome<KIND>(N, rt, x0, x1);
+                int y0, y1;
+                if (k + 1 < n) {
+                    unpack_state(N.nsp, trace[k + 1], y0, y1);
+                } else {
+                    y0 = s_l0;
+                    y1 = s_l1;
+                }
+                const int o = jump_outcome<KIND, true>(N, rt, y0, y1);
                 if (o == 2) {
                     status = PARREP_ERANGE;
                     more = 0;
+                    x0 = y0;
+                    x1 = y1;
                     break;
                 }
-                const int Wn = o == 0 ? W : region_of(N, x0, x1);
-                if (Wn != W) rt.init(N, Wn);
-                if (Wn == W) {
+                x0 = y0;
+                x1 = y1;
+                if (o == 0) {
                     ++Nc;
                     inW += q;
                 } else {
                     Nc = 0;
                     inW = 0;
-                    W = Wn;
+                    W = region_of(N, x0, x1);
+                    rt.init(N, W);
                 }
-                if ((step & 4095ull) == 0) atomicAdd(&ctl->progress, 1ull);
             }
+            atomicAdd(&ctl->progress, 1ull);
             s_step = step;
-            s_more = more;
+            s_more = more && status == 0;
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) leader_finish_decorr(P, x0, x1, W, Ts, burn_done, step, ended, status, cycle);
+    if (threadIdx.x == 0) {
+        // the state after an out-of-range jump is not kept
+        if (status == PARREP_ERANGE) {
+            x0 = min(max(x0, 0), N.hist_max0);
+            x1 = min(max(x1, 0), N.hist_max1);
+        }
+        leader_finish_decorr(P, x0, x1, W, Ts, burn_done, step, ended, status, cycle);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1179,7 +1417,7 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
             limb_hi = limb_lo + N.nbins;
             for (int b = threadIdx.x; b < 2 * N.nbins; b += blockDim.x) limb_lo[b] = 0;
         }
-        F.tab = P.off_tab >= 0 && KIND == PARREP_SCHLOGL ? (const float4*)(smem + P.off_tab) : nullptr;
+        F.tab = P.off_tab >= 0 && KIND == PARREP_SCHLOGL ? (const float4*)(smem + P.off_tab) + 2 : nullptr;
         F.inv = F.tab ? (const float*)(smem + P.off_inv) : nullptr;
         F.rng = (int*)(smem + P.off_rng);
         F.prodU = KIND == PARREP_TOGGLE ? (const float*)(smem + P.off_tab) : nullptr;
@@ -1298,14 +1536,14 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
                         hs.add(x0, x1, q);
                         int a0 = x0, a1 = x1;
                         apply(N, J, a0, a1);
+                        if (out_of_range(N, a0, a1)) {
+                            myoob = pos_of(s, r);
+                            break;
+                        }
                         if (region_of(N, a0, a1) != W) {
                             mykey = pos_of(s, r);
                             xe0 = a0;
                             xe1 = a1;
-                            break;
-                        }
-                        if (out_of_range(N, a0, a1)) {
-                            myoob = pos_of(s, r);
                             break;
                         }
                         x0 = a0;
