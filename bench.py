@@ -230,8 +230,12 @@ def main():
     for s_ in stats:
         for k, v in s_["phase_cycles"].items():
             ph[k] = ph.get(k, 0.0) + v
-    ph_tot = sum(ph.values()) or 1.0
+    main_phases = [k for k in ph if not k.startswith("dec_")]
+    ph_tot = sum(ph[k] for k in main_phases) or 1.0
     phase_share = {k: round(v / ph_tot, 4) for k, v in ph.items()}
+    events = {k: sum(s_[k] for s_ in stats) // max(1, len(stats)) for k in
+              ("events_decorr", "events_dephase", "events_parallel_useful", "events_parallel_executed",
+               "events_replay", "cycles", "escapes")}
     if dist:
         t = torch.tensor([t_total, float(useful), float(executed)], device="cuda", dtype=torch.float64)
         tmax = t.clone()
@@ -282,6 +286,7 @@ def main():
                      "note": "thread-instructions at 120 per event (107 per dephasing jump) over the run kernel "
                              "time; peak = 152 SM x 4 schedulers x 32 lanes x 2.07 GHz"},
         "phase_share": phase_share,
+        "events_per_step": events,
         "gpu_launches": args.steps,
         "clocks": clocks,
         "e2e": e2e,

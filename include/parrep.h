@@ -109,9 +109,11 @@ typedef struct {
     float pad;
     /* device cycles per phase, summed over blocks (thread 0 of each block):
      * decorrelation, dephasing, Philox draws, owner chains, accounting, grid
-     * barriers, special-chunk work, vote reduction (FP32 form; the FP64 form
-     * fills decorrelation, dephasing, barriers, special and vote) */
-    double phase_cycles[8];
+     * barriers, special-chunk work, vote reduction; then, inside block 0's
+     * decorrelation, its draws, jump chain, holding times and ordered commit
+     * (FP32 form; the FP64 form fills decorrelation, dephasing, barriers,
+     * special and vote) */
+    double phase_cycles[12];
 } parrep_stats;
 
 typedef struct {

@@ -48,9 +48,10 @@ class parrep_stats(C.Structure):
                 ("chunks", C.c_int64), ("special_chunks", C.c_int64), ("x0", C.c_int32 * 2),
                 ("x_final", C.c_int32 * 2), ("status", C.c_int32), ("grid_blocks", C.c_int32),
                 ("block_threads", C.c_int32), ("chunk_steps", C.c_int32), ("kernel_ms", C.c_float),
-                ("pad", C.c_float), ("phase_cycles", C.c_double * 8)]
+                ("pad", C.c_float), ("phase_cycles", C.c_double * 12)]
 
-PHASES = ["decorrelation", "dephasing", "draw", "chain", "account", "barrier", "special", "vote"]
+PHASES = ["decorrelation", "dephasing", "draw", "chain", "account", "barrier", "special", "vote", "dec_draw",
+          "dec_chain", "dec_times", "dec_commit"]
 
 
 class parrep_cycle(C.Structure):

@@ -491,7 +491,7 @@ extern "C" int parrep_run(parrep_t h, double T_end, uint64_t seed) {
     s.block_threads = threads;
     s.chunk_steps = S;
     s.kernel_ms = ms;
-    for (int i = 0; i < 8; ++i) s.phase_cycles[i] = (double)c.phase_cycles[i];
+    for (int i = 0; i < 12; ++i) s.phase_cycles[i] = (double)c.phase_cycles[i];
     h->T_end = T_end;
     h->T_burn = h->opt.T_burn;
     if (c.status != 0) {

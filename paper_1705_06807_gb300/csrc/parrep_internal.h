@@ -76,7 +76,7 @@ struct RunCtl {
     // per-phase device cycles summed over blocks (thread 0 of each block):
     // decorrelation, dephasing, draw (P), owner chain (C), accounting (A),
     // grid barriers, special-chunk work, first-pass vote reduction
-    unsigned long long phase_cycles[8];
+    unsigned long long phase_cycles[12];
 };
 
 struct RunParams {

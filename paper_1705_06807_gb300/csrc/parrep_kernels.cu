@@ -60,7 +60,7 @@ __device__ __forceinline__ unsigned long long globaltimer() {
 
 // Phase timer of a block: thread 0 adds clock64 deltas per phase.
 struct PhaseClock {
-    unsigned long long acc[8];
+    unsigned long long acc[12];
     long long t;
     __device__ __forceinline__ void start() {
         if (threadIdx.x == 0) t = clock64();
@@ -74,7 +74,7 @@ struct PhaseClock {
     }
 };
 enum { kPhDecorr = 0, kPhDephase = 1, kPhDraw = 2, kPhChain = 3, kPhAccount = 4, kPhBarrier = 5, kPhSpecial = 6,
-       kPhVote = 7 };
+       kPhVote = 7, kPhDecDraw = 8, kPhDecChain = 9, kPhDecTimes = 10, kPhDecCommit = 11 };
 
 template <typename T>
 __device__ __forceinline__ T ldv(const T* p) {
@@ -791,6 +791,54 @@ __device__ __noinline__ int last_positive(const NetDev& N, int x0, int x1) {
     return l3 > 0.f ? 3 : (l2 > 0.f ? 2 : (l1 > 0.f ? 1 : 0));
 }
 
+// Cumulative propensities of the Schloegl network at x in binary32, the same
+// operations as props_f (so the same bits as the oracle's binary32 mode).
+__device__ __forceinline__ float4 cums_schlogl(float A0, float A1, float A2, float A3, int x) {
+    const float xf = (float)x;
+    const float h1 = xf * (xf - 1.0f);
+    const float h2 = h1 * (xf - 2.0f);
+    const float l0 = A0 * h1, l1 = A1 * h2, l3 = A3 * xf;
+    const float c1 = l0 + l1, c2 = c1 + A2;
+    return make_float4(l0, c1, c2, c2 + l3);
+}
+
+__device__ __forceinline__ bool goes_up(float4 C, float t) { return (t < C.x) | ((C.y <= t) & (t < C.z)); }
+
+// Speculative pass of a Schloegl jump chain over n steps (n even) from x, two
+// steps per iteration, with no branch: the propensities at x-1, x, x+1 are
+// computed together, the direct-method choice of a +-1 chain is "up" iff
+// t < c0 or c1 <= t < c2, and the state is kept inside [lo, hi] so that it
+// stays a valid table index.  trace[s*stride + off] receives the state before
+// step s.  Returns the first step whose choice needed the rounding rule or
+// whose target left [lo, hi] (n if none): every state up to and including
+// that step's pre-jump state is exact.
+__device__ __forceinline__ int spec_pass_schlogl(const NetDev& N, const float2* buf, int* trace, int stride, int off,
+                                                 int n, int lo, int hi, int& x, int& mn, int& mx) {
+    const float A0 = N.Af[0], A1 = N.Af[1], A2 = N.Af[2], A3 = N.Af[3];
+    int first = n;
+    for (int s = 0; s < n; s += 2) {
+        const int i1 = s * stride + off, i2 = i1 + stride;
+        const float ua = buf[i1].y, ub = buf[i2].y;
+        const float4 C = cums_schlogl(A0, A1, A2, A3, x);
+        const float4 L = cums_schlogl(A0, A1, A2, A3, x - 1);
+        const float4 R = cums_schlogl(A0, A1, A2, A3, x + 1);
+        const float t1 = ua * C.w, tR = ub * R.w, tL = ub * L.w;
+        const bool up1 = goes_up(C, t1);
+        const int xa = up1 ? x + 1 : x - 1;
+        const bool up2 = up1 ? goes_up(R, tR) : goes_up(L, tL);
+        const int xb = up2 ? xa + 1 : xa - 1;
+        const bool r1 = (t1 >= C.w) | (xa < lo) | (xa > hi);
+        const bool r2 = ((up1 ? tR : tL) >= (up1 ? R.w : L.w)) | (xb < lo) | (xb > hi);
+        first = min(first, r1 ? s : (r2 ? s + 1 : n));
+        trace[i1] = x;
+        trace[i2] = xa;
+        mn = min(mn, min(x, xa));
+        mx = max(mx, max(x, xa));
+        x = min(max(xb, lo), hi);
+    }
+    return first;
+}
+
 // (C) one owner's B lockstep steps of the parallel step; stops at its escape
 // or at a state outside [0, hist_max].  Schloegl with its table: two steps
 // per iteration -- the sums at x-1, x, x+1 are loaded together and the second
@@ -806,77 +854,38 @@ __device__ __forceinline__ void consume_par(const RunParams& P, const FastSmem& 
     int lo0 = 0x7fffffff, hi0 = -1, lo1 = 0x7fffffff, hi1 = -1;
     if (running) {
         nv = P.B;
-        if (KIND == PARREP_SCHLOGL && F.tab) {
-            // The table is padded by two entries on each side, so x-1 and x+1
-            // need no clamping.  For a +-1 chain the direct-method choice is
-            // "up" iff t < c0 or c1 <= t < c2, three independent comparisons;
-            // rounding (t >= a0), escapes and range errors share one rare
-            // branch that redoes the two steps with the general code.
-            const float4* tabp = F.tab;
-            const float2* buf = F.buf;
-            int* trace = F.trace;
-            const int lo = rt.lo, hi = rt.hi, RBl = P.RB, lg = P.log2RB, B = P.B;
+        if (KIND == PARREP_SCHLOGL) {
+            // speculative pass, then the exact rule from the first rare step on
+            const int B = P.B, lg = P.log2RB;
             int x = x0;
-            for (int s = 0; s < B; s += 2) {
-                const int i1 = (s << lg) + lane, i2 = i1 + RBl;
-                const float ua = buf[i1].y, ub = buf[i2].y;
-                const float4 C = tabp[x], L = tabp[x - 1], R = tabp[x + 1];
-                const float t1 = ua * C.w, tR = ub * R.w, tL = ub * L.w;
-                const bool up1 = (t1 < C.x) | ((C.y <= t1) & (t1 < C.z));
-                const bool upR = (tR < R.x) | ((R.y <= tR) & (tR < R.z));
-                const bool upL = (tL < L.x) | ((L.y <= tL) & (tL < L.z));
-                const int xa = up1 ? x + 1 : x - 1;
-                const bool up2 = up1 ? upR : upL;
-                const int xb = up2 ? xa + 1 : xa - 1;
-                const float t2 = up1 ? tR : tL, a2 = up1 ? R.w : L.w;
-                const bool rare = (t1 >= C.w) | (t2 >= a2) | (xa < lo) | (xa > hi) | (xb < lo) | (xb > hi);
-                trace[i1] = x;
-                trace[i2] = xa;
-                lo0 = min(lo0, min(x, xa));
-                hi0 = max(hi0, max(x, xa));
-                if (!rare) {
-                    x = xb;
-                    continue;
-                }
-                // exact handling of the two steps
-                int J1 = count_le(C, t1);
-                if (J1 == 4) J1 = last_positive(N, x, 0);
-                const int ya = x + ((J1 & 1) ? -1 : 1);
-                int o = jump_outcome<KIND, true>(N, rt, ya, 0);
-                if (o) {
-                    if (o == 1) {
-                        mykey = pos_of(sbase + s, r);
-                        xe0 = ya;
-                        xe1 = 0;
-                    } else {
-                        myoob = pos_of(sbase + s, r);
+            const int first = spec_pass_schlogl(N, F.buf, F.trace, P.RB, lane, B, rt.lo, rt.hi, x, lo0, hi0);
+            if (first < B) {
+                int y = F.trace[(first << lg) + lane];
+                for (int s = first; s < B; ++s) {
+                    const int i = (s << lg) + lane;
+                    F.trace[i] = y;
+                    lo0 = min(lo0, y);
+                    hi0 = max(hi0, y);
+                    const float4 c = cums_schlogl(N.Af[0], N.Af[1], N.Af[2], N.Af[3], y);
+                    int J = count_le(c, F.buf[i].y * c.w);
+                    if (J == 4) J = last_positive(N, y, 0);
+                    const int yn = y + ((J & 1) ? -1 : 1);
+                    const int o = jump_outcome<KIND, true>(N, rt, yn, 0);
+                    if (o) {
+                        if (o == 1) {
+                            mykey = pos_of(sbase + s, r);
+                            xe0 = yn;
+                            xe1 = 0;
+                        } else {
+                            myoob = pos_of(sbase + s, r);
+                        }
+                        nv = s + 1;
+                        running = false;
+                        break;
                     }
-                    nv = s + 1;
-                    running = false;
-                    break;
+                    y = yn;
                 }
-                trace[i2] = ya;
-                lo0 = min(lo0, ya);
-                hi0 = max(hi0, ya);
-                const float4 C2 = tabp[ya];
-                int J2 = count_le(C2, ub * C2.w);
-                if (J2 == 4) J2 = last_positive(N, ya, 0);
-                const int yb = ya + ((J2 & 1) ? -1 : 1);
-                o = jump_outcome<KIND, true>(N, rt, yb, 0);
-                if (o) {
-                    if (o == 1) {
-                        mykey = pos_of(sbase + s + 1, r);
-                        xe0 = yb;
-                        xe1 = 0;
-                    } else {
-                        myoob = pos_of(sbase + s + 1, r);
-                    }
-                    x = ya;
-                    nv = s + 2;
-                    running = false;
-                    break;
-                }
-                x = yb;
+                x = y;
             }
             x0 = x;
         } else {
@@ -1209,38 +1218,32 @@ __device__ int decorr_chain(const NetDev& N, const FastSmem& F, int x0, int x1, 
     // returned in last0/last1)
     const float2* buf = F.buf;
     int* trace = F.trace;
-    if (KIND == PARREP_SCHLOGL && F.tab) {
-        const float4* tabp = F.tab;
+    if (KIND == PARREP_SCHLOGL) {
+        // region changes do not stop this chain, only the range does
         const int hm = N.hist_max0;
-        float4 Lw = tabp[x0 - 1], Cw = tabp[x0], Rw = tabp[x0 + 1];
-        for (int k = 0; k < M; ++k) {
-            trace[k] = x0;
-            const float t = buf[k].y * Cw.w;
-            const bool up = (t < Cw.x) | ((Cw.y <= t) & (t < Cw.z));
-            int xn = up ? x0 + 1 : x0 - 1;
-            if ((t >= Cw.w) | (xn < 0) | (xn > hm)) {
-                int J = count_le(Cw, t);
-                if (J == 4) J = last_positive(N, x0, 0);
-                xn = x0 + ((J & 1) ? -1 : 1);
-                if (xn < 0 || xn > hm) {
-                    last0 = xn;
-                    last1 = 0;
-                    return k + 1;
-                }
-                x0 = xn;
-                Lw = tabp[x0 - 1];
-                Cw = tabp[x0];
-                Rw = tabp[x0 + 1];
-                continue;
-            }
-            const float4 far = tabp[up ? x0 + 2 : x0 - 2];
-            const float4 oldC = Cw;
-            Cw = up ? Rw : Lw;
-            Lw = up ? oldC : far;
-            Rw = up ? far : oldC;
-            x0 = xn;
+        int mn = 0, mx = 0;
+        int x = x0;
+        const int first = spec_pass_schlogl(N, buf, trace, 1, 0, M, 0, hm, x, mn, mx);
+        if (first == M) {
+            last0 = x;
+            last1 = 0;
+            return M;
         }
-        last0 = x0;
+        int y = trace[first];
+        for (int k = first; k < M; ++k) {
+            trace[k] = y;
+            const float4 c = cums_schlogl(N.Af[0], N.Af[1], N.Af[2], N.Af[3], y);
+            int J = count_le(c, buf[k].y * c.w);
+            if (J == 4) J = last_positive(N, y, 0);
+            const int yn = y + ((J & 1) ? -1 : 1);
+            if (yn < 0 || yn > hm) {
+                last0 = yn;
+                last1 = 0;
+                return k + 1;
+            }
+            y = yn;
+        }
+        last0 = y;
         last1 = 0;
         return M;
     }
@@ -1265,7 +1268,8 @@ __device__ int decorr_chain(const NetDev& N, const FastSmem& F, int x0, int x1, 
 }
 
 template <int KIND>
-__device__ void decorrelate_f32(const RunParams& P, const FastSmem& F, unsigned long long* sh, int sh_post) {
+__device__ void decorrelate_f32(const RunParams& P, const FastSmem& F, unsigned long long* sh, int sh_post,
+                                PhaseClock& pc) {
     __shared__ int s_more, s_n, s_l0, s_l1;
     __shared__ unsigned long long s_step;
     RunCtl* ctl = P.ctl;
@@ -1296,6 +1300,8 @@ __device__ void decorrelate_f32(const RunParams& P, const FastSmem& F, unsigned 
     unsigned long long* qbuf = (unsigned long long*)F.buf;  // (3) overwrites the draws in place
     const int* trace = F.trace;
     const bool tabbed = KIND == PARREP_SCHLOGL && F.tab;
+    PhaseClock dc{};
+    dc.start();
     while (s_more) {
         const unsigned long long step0 = s_step;
         // (1) draws
@@ -1311,6 +1317,7 @@ __device__ void decorrelate_f32(const RunParams& P, const FastSmem& F, unsigned 
                 if (base + k * T < M) buf[base + k * T] = make_float2(-logf(u01f(w[k].x)), u01f(w[k].y));
         }
         __syncthreads();
+        dc.lap(kPhDecDraw);
         // (2) the jump chain
         if (threadIdx.x == 0) {
             int l0, l1;
@@ -1319,6 +1326,7 @@ __device__ void decorrelate_f32(const RunParams& P, const FastSmem& F, unsigned 
             s_l1 = l1;
         }
         __syncthreads();
+        dc.lap(kPhDecChain);
         const int n = s_n;
         // (3) holding times
         for (int k = threadIdx.x; k < n; k += T) {
@@ -1329,6 +1337,7 @@ __device__ void decorrelate_f32(const RunParams& P, const FastSmem& F, unsigned 
             qbuf[k] = q_of_f32(E * ia0);  // same thread read buf[k] just before
         }
         __syncthreads();
+        dc.lap(kPhDecTimes);
         // (4) the stopping rule, in order
         if (threadIdx.x == 0) {
             int more = 1;
@@ -1379,7 +1388,10 @@ __device__ void decorrelate_f32(const RunParams& P, const FastSmem& F, unsigned 
             s_more = more && status == 0;
         }
         __syncthreads();
+        dc.lap(kPhDecCommit);
     }
+    if (threadIdx.x == 0)
+        for (int i = 8; i < 12; ++i) pc.acc[i] += dc.acc[i];
     if (threadIdx.x == 0) {
         // the state after an out-of-range jump is not kept
         if (status == PARREP_ERANGE) {
@@ -1472,7 +1484,7 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
         pc.start();
         if (F32) {
             if (blockIdx.x == 0 && !ldv(&ctl->done))
-                decorrelate_f32<KIND>(P, F, P.use_smem_hist ? sh_hist : nullptr, period_post);
+                decorrelate_f32<KIND>(P, F, P.use_smem_hist ? sh_hist : nullptr, period_post, pc);
         } else {
             if (leader && !ctl->done) leader_decorrelate<F32>(P);
         }
@@ -1774,7 +1786,7 @@ out:
         if (threadIdx.x == 0 && c) atomicAdd(&ctl->ev_replay, c);
     }
     if (threadIdx.x == 0)
-        for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < 12; ++i)
             if (pc.acc[i]) atomicAdd(&ctl->phase_cycles[i], pc.acc[i]);
 }
 
