@@ -736,22 +736,50 @@ __device__ __forceinline__ void produce_lanes(const RunParams& P, const FastSmem
 // branch tells apart.  Two species: the half-plane tests with coefficients
 // held in registers.
 struct RegionTest {
-    int lo, hi;           // one species
-    int n;                // two species: number of tests
+    int lo, hi;           // one species: the interval of W
+    int n;                // number of half-plane tests
     int a0[4], a1[4];
     long long b[4];
+    int ilo[5], ihi[5];   // one species: all region intervals
     int W;
-    __device__ __forceinline__ void init(const NetDev& N, int W_) {
-        W = W_;
+    // all loads with constant indices: a runtime index into the kernel
+    // parameters would turn into a slow generic load
+    __device__ __forceinline__ void load(const NetDev& N) {
         n = N.nreg;
-        lo = N.wlo[W_];
-        hi = N.whi[W_];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             a0[i] = N.ra0[i];
             a1[i] = N.ra1[i];
             b[i] = N.rb[i];
         }
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            ilo[i] = N.wlo[i];
+            ihi[i] = N.whi[i];
+        }
+    }
+    __device__ __forceinline__ void set(int W_) {
+        W = W_;
+        lo = 1;
+        hi = 0;
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+            if (i == W_) {
+                lo = ilo[i];
+                hi = ihi[i];
+            }
+    }
+    __device__ __forceinline__ void init(const NetDev& N, int W_) {
+        load(N);
+        set(W_);
+    }
+    // region of a one-species state inside [0, hist_max]
+    __device__ __forceinline__ int region1(int x) const {
+        int r = 0;
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+            if (x >= ilo[i] && x <= ihi[i]) r = i;
+        return r;
     }
     __device__ __forceinline__ int region2(int x0, int x1) const {
         int r = n;
@@ -759,6 +787,9 @@ struct RegionTest {
         for (int i = 3; i >= 0; --i)
             if (i < n && (long long)a0[i] * x0 + (long long)a1[i] * x1 < b[i]) r = i;
         return r;
+    }
+    __device__ __forceinline__ int region(int nsp, int x0, int x1) const {
+        return nsp == 1 ? region1(x0) : region2(x0, x1);
     }
 };
 
@@ -772,7 +803,7 @@ __device__ __forceinline__ int jump_outcome(const NetDev& N, const RegionTest& r
         if (a0 >= rt.lo && a0 <= rt.hi) return 0;
         const bool oob = a0 < 0 || a0 > N.hist_max0;
         if (OOB_FIRST) return oob ? 2 : 1;
-        return region_of(N, a0, 0) != rt.W ? 1 : 2;
+        return oob ? (region_of(N, a0, 0) != rt.W ? 1 : 2) : 1;
     }
     if (OOB_FIRST && out_of_range(N, a0, a1)) return 2;
     if (rt.region2(a0, a1) != rt.W) return 1;
@@ -813,10 +844,11 @@ __device__ __forceinline__ bool goes_up(float4 C, float t) { return (t < C.x) | 
 // whose target left [lo, hi] (n if none): every state up to and including
 // that step's pre-jump state is exact.
 __device__ __forceinline__ int spec_pass_schlogl(const NetDev& N, const float2* buf, int* trace, int stride, int off,
-                                                 int n, int lo, int hi, int& x, int& mn, int& mx) {
+                                                 int n, int lo, int hi, int& x, int& mn, int& mx, int s0 = 0) {
     const float A0 = N.Af[0], A1 = N.Af[1], A2 = N.Af[2], A3 = N.Af[3];
     int first = n;
-    for (int s = 0; s < n; s += 2) {
+    const int npair = s0 + ((n - s0) & ~1);
+    for (int s = s0; s < npair; s += 2) {
         const int i1 = s * stride + off, i2 = i1 + stride;
         const float ua = buf[i1].y, ub = buf[i2].y;
         const float4 C = cums_schlogl(A0, A1, A2, A3, x);
@@ -835,6 +867,17 @@ __device__ __forceinline__ int spec_pass_schlogl(const NetDev& N, const float2* 
         mn = min(mn, min(x, xa));
         mx = max(mx, max(x, xa));
         x = min(max(xb, lo), hi);
+    }
+    if (npair < n) {  // odd tail: one step
+        const int i = npair * stride + off;
+        const float4 C = cums_schlogl(A0, A1, A2, A3, x);
+        const float t = buf[i].y * C.w;
+        const int xa = goes_up(C, t) ? x + 1 : x - 1;
+        first = min(first, ((t >= C.w) | (xa < lo) | (xa > hi)) ? npair : n);
+        trace[i] = x;
+        mn = min(mn, x);
+        mx = max(mx, x);
+        x = min(max(xa, lo), hi);
     }
     return first;
 }
@@ -1091,35 +1134,31 @@ __device__ int dephase_f32(const RunParams& P, const FastSmem& F, const RegionTe
         const int nb = (int)((np - i0) < (long long)P.B ? (np - i0) : (long long)P.B);
         produce_lanes<false>(P, F, rbase, (unsigned)i0, nb, cycle, kTagDephase, key);
         __syncthreads();
-        if (owner && act && !err && KIND == PARREP_SCHLOGL && F.tab) {
-            // window (x-1, x, x+1) in registers; the common step is three
-            // comparisons and a shift, the far neighbour loaded ahead
-            const float4* tabp = F.tab;
-            const int lo = rt.lo, hi = rt.hi, lg = P.log2RB;
-            float4 Lw = tabp[x0 - 1], Cw = tabp[x0], Rw = tabp[x0 + 1];
-            for (int s = 0; s < nb; ++s) {
-                const unsigned i = (unsigned)i0 + (unsigned)s;
-                const float u = F.buf[(s << lg) + threadIdx.x].y;
-                const float t = u * Cw.w;
-                const bool up = (t < Cw.x) | ((Cw.y <= t) & (t < Cw.z));
-                const int xn = up ? x0 + 1 : x0 - 1;
-                const bool odd = active && ((t >= Cw.w) | (xn < lo) | (xn > hi));
-                if (!__any_sync(0xffffffffu, odd)) {
-                    if (active) {
-                        const float4 far = tabp[up ? x0 + 2 : x0 - 2];
-                        const float4 oldC = Cw;
-                        Cw = up ? Rw : Lw;
-                        Lw = up ? oldC : far;
-                        Rw = up ? far : oldC;
-                        x0 = xn;
-                    }
-                    continue;
+        if (owner && act && !err && KIND == PARREP_SCHLOGL) {
+            // every lane speculates through the sub-chunk; the warp goes back
+            // to the first step at which any lane met an escape or the
+            // rounding rule, takes that step exactly (with Fleming-Viot), and
+            // speculates again from the next one
+            const int lg = P.log2RB;
+            int sb = 0;
+            while (sb < nb) {
+                int x = x0, mn = 0, mx = 0;
+                int first = spec_pass_schlogl(N, F.buf, F.trace, P.RB, threadIdx.x, nb, rt.lo, rt.hi, x, mn, mx, sb);
+                if (!active) first = nb;
+                int fw = first;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) fw = min(fw, __shfl_xor_sync(0xffffffffu, fw, o));
+                if (fw == nb) {
+                    if (active) x0 = x;
+                    break;
                 }
-                // exact step for the warp: choice, escapes, range, Fleming-Viot
+                if (active) x0 = F.trace[(fw << lg) + threadIdx.x];
+                const unsigned i = (unsigned)i0 + (unsigned)fw;
                 int n0 = x0, n1 = x1;
                 bool ex = false, bad = false;
                 if (active) {
-                    int J = count_le(Cw, t);
+                    const float4 c = cums_schlogl(N.Af[0], N.Af[1], N.Af[2], N.Af[3], x0);
+                    int J = count_le(c, F.buf[(fw << lg) + threadIdx.x].y * c.w);
                     if (J == 4) J = last_positive(N, x0, x1);
                     apply(N, J, n0, n1);
                     const int o = jump_outcome<KIND, false>(N, rt, n0, n1);
@@ -1152,9 +1191,7 @@ __device__ int dephase_f32(const RunParams& P, const FastSmem& F, const RegionTe
                 }
                 x0 = n0;
                 x1 = n1;
-                Lw = tabp[x0 - 1];
-                Cw = tabp[x0];
-                Rw = tabp[x0 + 1];
+                sb = fw + 1;
             }
         } else if (owner && act && !err) {
             for (int s = 0; s < nb; ++s) {
@@ -1268,7 +1305,7 @@ __device__ int decorr_chain(const NetDev& N, const FastSmem& F, int x0, int x1, 
 }
 
 template <int KIND>
-__device__ void decorrelate_f32(const RunParams& P, const FastSmem& F, unsigned long long* sh, int sh_post,
+__device__ void decorrelate_f32(const RunParams& P, const FastSmem& F, const HistSink& hs, int sh_post,
                                 PhaseClock& pc) {
     __shared__ int s_more, s_n, s_l0, s_l1;
     __shared__ unsigned long long s_step;
@@ -1338,54 +1375,91 @@ __device__ void decorrelate_f32(const RunParams& P, const FastSmem& F, unsigned 
         }
         __syncthreads();
         dc.lap(kPhDecTimes);
-        // (4) the stopping rule, in order
+        // (4) the stopping rule, in order (the leader); the holding times go
+        // to block 0's limbs with fire-and-forget adds, folded afterwards
         if (threadIdx.x == 0) {
             int more = 1;
-            int k = 0;
-            for (; k < n; ++k) {
+            int a = x0, a1 = x1;
+            unsigned long long qn = n > 0 ? qbuf[0] : 0ull;
+            int yn = n > 1 ? trace[1] : s_l0 | (N.nsp > 1 ? (s_l1 << 16) : 0);
+            int bmin = 0x7fffffff, bmax = -1;
+            for (int k = 0; k < n; ++k) {
                 if (steps_mode ? (Nc >= n_c) : (inW >= q_tcorr)) {
                     more = 0;
                     break;
                 }
-                int a0, a1;
-                unpack_state(N.nsp, trace[k], a0, a1);
-                const unsigned long long q = qbuf[k];
-                ++step;
-                leader_contribute(P, ctl, a0, a1, q, Ts, burn_done, ended, sh, sh_post);
-                if (ended) {
-                    more = 0;
-                    break;
-                }
+                const unsigned long long q = qn;
                 int y0, y1;
                 if (k + 1 < n) {
-                    unpack_state(N.nsp, trace[k + 1], y0, y1);
+                    unpack_state(N.nsp, yn, y0, y1);
                 } else {
                     y0 = s_l0;
                     y1 = s_l1;
+                }
+                if (k + 1 < n) {
+                    qn = qbuf[k + 1];
+                    yn = k + 2 < n ? trace[k + 2] : 0;
+                }
+                ++step;
+                // T_end truncation and the T_burn split
+                unsigned long long t = q;
+                const unsigned long long rem = P.q_Tend - Ts;
+                if (t >= rem) {
+                    t = rem;
+                    ended = true;
+                }
+                unsigned long long pre = 0, post = t;
+                if (!burn_done) {
+                    const unsigned long long room = P.q_Tburn - Ts;
+                    pre = t < room ? t : room;
+                    post = t - pre;
+                    if (t >= room) burn_done = 1;
+                }
+                Ts += t;
+                if (pre) {
+                    if (hs.sh && !sh_post) hs.add(a, a1, pre);
+                    else atomicAdd(P.hist_pre + a * N.ystride + a1, pre);
+                }
+                if (post) {
+                    if (hs.sh && sh_post) hs.add(a, a1, post);
+                    else atomicAdd(P.hist_post + a * N.ystride + a1, post);
+                }
+                bmin = min(bmin, a);
+                bmax = max(bmax, a);
+                if (ended) {
+                    more = 0;
+                    break;
                 }
                 const int o = jump_outcome<KIND, true>(N, rt, y0, y1);
                 if (o == 2) {
                     status = PARREP_ERANGE;
                     more = 0;
-                    x0 = y0;
-                    x1 = y1;
                     break;
                 }
                 x0 = y0;
                 x1 = y1;
+                a = y0;
+                a1 = y1;
                 if (o == 0) {
                     ++Nc;
                     inW += q;
                 } else {
                     Nc = 0;
                     inW = 0;
-                    W = region_of(N, x0, x1);
-                    rt.init(N, W);
+                    W = rt.region(N.nsp, x0, x1);
+                    rt.set(W);
                 }
             }
             atomicAdd(&ctl->progress, 1ull);
+            F.rng[0] = bmin;
+            F.rng[1] = bmax;
             s_step = step;
             s_more = more && status == 0;
+        }
+        __syncthreads();
+        if (hs.lo && F.rng[1] >= F.rng[0]) {
+            // one species: rows = states; two species: all columns of the rows
+            fold_limbs(hs, F.rng[0], F.rng[1], N.ystride, 0, N.nsp > 1 ? N.hist_max1 : 0);
         }
         __syncthreads();
         dc.lap(kPhDecCommit);
@@ -1484,7 +1558,7 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
         pc.start();
         if (F32) {
             if (blockIdx.x == 0 && !ldv(&ctl->done))
-                decorrelate_f32<KIND>(P, F, P.use_smem_hist ? sh_hist : nullptr, period_post, pc);
+                decorrelate_f32<KIND>(P, F, hs, period_post, pc);
         } else {
             if (leader && !ctl->done) leader_decorrelate<F32>(P);
         }
