@@ -310,10 +310,10 @@ static int align16(int x) { return (x + 15) & ~15; }
 struct Plan {
     int threads, grid, smem, RB, log2RB, B, S, use_smem_hist;
     int off_tab, off_buf, off_trace, off_live, off_nvalid;
-    int off_limbs, off_inv, off_rng;
+    int off_limbs, off_inv, off_rng, off_decp;
 };
 
-static int fast_layout(parrep_t h, int RB, int with_hist, Plan& pl) {
+static int fast_layout(parrep_t h, int RB, int threads, int with_hist, Plan& pl) {
     const int B = 32;
     int off = 0;
     pl.use_smem_hist = with_hist;
@@ -347,6 +347,8 @@ static int fast_layout(parrep_t h, int RB, int with_hist, Plan& pl) {
     off += RB * 4;
     pl.off_rng = off;
     off += 16;
+    pl.off_decp = off;  // decorrelation rounds of min(4 x threads, B x RB) steps
+    off += (4 * threads < B * RB ? 4 * threads : B * RB) * 8;
     pl.B = B;
     pl.RB = RB;
     int l = 0;
@@ -370,7 +372,7 @@ static int plan_launch(parrep_t h, Plan& pl) {
         pl.grid = (int)((h->R + threads - 1) / threads);
         pl.S = h->opt.chunk_steps > 0 ? h->opt.chunk_steps : 256;
         pl.off_tab = pl.off_buf = pl.off_trace = pl.off_live = pl.off_nvalid = -1;
-        pl.off_limbs = pl.off_inv = pl.off_rng = -1;
+        pl.off_limbs = pl.off_inv = pl.off_rng = pl.off_decp = -1;
         for (int with_hist = 1; with_hist >= 0; --with_hist) {
             if (with_hist && h->nbins * 8 > kSmemHistLimit) continue;
             pl.use_smem_hist = with_hist;
@@ -386,7 +388,7 @@ static int plan_launch(parrep_t h, Plan& pl) {
         const int threads = RB > T ? RB : T;
         const long long grid = (h->R + RB - 1) / RB;
         for (int with_hist = 1; with_hist >= 0; --with_hist) {
-            const int smem = fast_layout(h, RB, with_hist, pl);
+            const int smem = fast_layout(h, RB, threads, with_hist, pl);
             if (smem > 200 * 1024) continue;
             int ea = kernel_attrs(prec, kind, &per_sm, smem, threads);
             if (ea != 0) return cuda_fail(h, (cudaError_t)ea, "kernel attributes");
@@ -436,6 +438,7 @@ extern "C" int parrep_run(parrep_t h, double T_end, uint64_t seed) {
     p.off_limbs = pl.off_limbs;
     p.off_inv = pl.off_inv;
     p.off_rng = pl.off_rng;
+    p.off_decp = pl.off_decp;
     if (p.thresh == PARREP_THRESH_STEPS) {
         p.n_c = (long long)h->t_corr;
         p.n_p = (long long)h->t_phase;

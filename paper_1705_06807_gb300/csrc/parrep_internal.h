@@ -89,7 +89,7 @@ struct RunParams {
     // memory (byte offsets of its arrays in the dynamic shared memory below)
     int RB, log2RB, B;
     int off_tab, off_buf, off_trace, off_live, off_nvalid;
-    int off_limbs, off_inv, off_rng;
+    int off_limbs, off_inv, off_rng, off_decp;
     unsigned long long q_tcorr;
     long long n_c;
     double t_phase;

@@ -644,6 +644,7 @@ struct FastSmem {
     const float4* tab;   // Schloegl: per state (c0, c0+c1, ..., a0); nullptr = compute
     const float* inv;    // Schloegl with tab: per state RN(1/a0)
     int* rng;            // [4]: min/max of x0 and x1 touched in the sub-chunk
+    unsigned long long* decp;  // decorrelation rounds: prefix sums of the holding times
     const float* prodU;  // toggle: production of U by V, of V by U (shared copies)
     const float* prodV;
     float2* buf;         // [B][RB]: (E = -log u1, u2)
@@ -1304,39 +1305,87 @@ __device__ int decorr_chain(const NetDev& N, const FastSmem& F, int x0, int x1, 
     return M;
 }
 
+// Block-wide exclusive scan of (sum, max) over the threads, in thread order.
+__device__ __forceinline__ void block_scan_sum_max(unsigned long long v, int m, unsigned long long* wsum, int* wmax,
+                                                   unsigned long long& ex_sum, int& ex_max) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned long long sv = v;
+    int mv = m;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long su = __shfl_up_sync(0xffffffffu, sv, o);
+        const int mu = __shfl_up_sync(0xffffffffu, mv, o);
+        if (lane >= o) {
+            sv += su;
+            mv = max(mv, mu);
+        }
+    }
+    if (lane == 31) {
+        wsum[wid] = sv;
+        wmax[wid] = mv;
+    }
+    __syncthreads();
+    unsigned long long ws = 0;
+    int wm = -1;
+    for (int w = 0; w < nw && w < wid; ++w) {
+        ws += wsum[w];
+        wm = max(wm, wmax[w]);
+    }
+    const int mprev = __shfl_up_sync(0xffffffffu, mv, 1);
+    ex_sum = ws + sv - v;
+    ex_max = lane >= 1 ? max(wm, mprev) : wm;
+    __syncthreads();
+}
+
+// Decorrelation of the FP32 form.  Block 0 works in rounds of M = 4T steps:
+// (1) all threads draw the M uniforms; (2) the leader walks the jump chain
+// alone -- the only serial part, as the states do not depend on the
+// stopping rule; (3) all threads turn the states into holding times; (4) the
+// stopping rule (n_c jumps, or t_corr time, of consecutive stay in W), the
+// T_end and T_burn crossings are found with block scans -- the in-W counters
+// after step k follow from the prefix sums of the holding times and the last
+// region change at or before k -- and the committed steps are accumulated in
+// parallel.  Draws beyond the stop are discarded; the next round starts at
+// the step where this one stopped.
 template <int KIND>
 __device__ void decorrelate_f32(const RunParams& P, const FastSmem& F, const HistSink& hs, int sh_post,
                                 PhaseClock& pc) {
-    __shared__ int s_more, s_n, s_l0, s_l1;
-    __shared__ unsigned long long s_step;
+    __shared__ int s_more, s_n, s_l0, s_l1, s_x0, s_x1, s_W, s_burn, s_status, s_ended;
+    __shared__ int s_stop, s_end, s_bcross, s_c;
+    __shared__ long long s_Nc, s_Nc_last;
+    __shared__ unsigned long long s_step, s_Ts, s_inW, s_inW_last;
+    __shared__ unsigned long long s_wsum[32];
+    __shared__ int s_wmax[32];
+    __shared__ int s_bmin, s_bmax;
     RunCtl* ctl = P.ctl;
     const NetDev& N = P.net;
     const uint2 key = seed_key(P.seed);
     const unsigned cycle = ldv(&ctl->cycle);
-    int x0 = 0, x1 = 0, W = 0, burn_done = 0, status = 0;
-    long long Nc = 0;
-    unsigned long long inW = 0, step = 0, Ts = 0;
-    bool ended = false;
-    RegionTest rt;
     const bool steps_mode = P.thresh == PARREP_THRESH_STEPS;
     const long long n_c = P.n_c;
-    const unsigned long long q_tcorr = P.q_tcorr;
-    if (threadIdx.x == 0) {
-        x0 = ctl->xt0;
-        x1 = ctl->xt1;
-        Ts = ctl->Ts;
-        burn_done = ctl->burn_done;
-        W = region_of(N, x0, x1);
-        rt.init(N, W);
-        s_step = 0;
-        s_more = steps_mode ? (Nc < n_c) : (inW < q_tcorr);
-    }
-    __syncthreads();
-    const int M = P.B << P.log2RB, T = blockDim.x;
+    const unsigned long long q_tcorr = P.q_tcorr, q_Tend = P.q_Tend, q_Tburn = P.q_Tburn;
+    RegionTest rt0;
+    rt0.load(N);
+    const int T = blockDim.x, M = min(4 * T, P.B << P.log2RB);  // within buf, trace and decp
     float2* buf = F.buf;
     unsigned long long* qbuf = (unsigned long long*)F.buf;  // (3) overwrites the draws in place
-    const int* trace = F.trace;
+    unsigned long long* Pk = F.decp;                        // inclusive prefix sums of the round
+    int* trace = F.trace;
     const bool tabbed = KIND == PARREP_SCHLOGL && F.tab;
+    if (threadIdx.x == 0) {
+        s_x0 = ctl->xt0;
+        s_x1 = ctl->xt1;
+        s_Ts = ctl->Ts;
+        s_burn = ctl->burn_done;
+        s_W = rt0.region(N.nsp, s_x0, s_x1);
+        s_Nc = 0;
+        s_inW = 0;
+        s_step = 0;
+        s_status = 0;
+        s_ended = 0;
+        s_more = steps_mode ? (0 < n_c) : (0ull < q_tcorr);
+    }
+    __syncthreads();
     PhaseClock dc{};
     dc.start();
     while (s_more) {
@@ -1358,9 +1407,14 @@ __device__ void decorrelate_f32(const RunParams& P, const FastSmem& F, const His
         // (2) the jump chain
         if (threadIdx.x == 0) {
             int l0, l1;
-            s_n = decorr_chain<KIND>(N, F, x0, x1, M, l0, l1);
+            s_n = decorr_chain<KIND>(N, F, s_x0, s_x1, M, l0, l1);
             s_l0 = l0;
             s_l1 = l1;
+            s_stop = 0x7fffffff;
+            s_end = 0x7fffffff;
+            s_bcross = 0x7fffffff;
+            s_bmin = 0x7fffffff;
+            s_bmax = -1;
         }
         __syncthreads();
         dc.lap(kPhDecChain);
@@ -1371,108 +1425,177 @@ __device__ void decorrelate_f32(const RunParams& P, const FastSmem& F, const His
             unpack_state(N.nsp, trace[k], a0, a1);
             const float E = buf[k].x;
             const float ia0 = tabbed ? F.inv[a0] : __frcp_rn(cums_f32<KIND>(N, F, a0, a1).w);
-            qbuf[k] = q_of_f32(E * ia0);  // same thread read buf[k] just before
+            qbuf[k] = q_of_f32(E * ia0);  // the same thread read buf[k] just before
         }
         __syncthreads();
         dc.lap(kPhDecTimes);
-        // (4) the stopping rule, in order (the leader); the holding times go
-        // to block 0's limbs with fire-and-forget adds, folded afterwards
-        if (threadIdx.x == 0) {
-            int more = 1;
-            int a = x0, a1 = x1;
-            unsigned long long qn = n > 0 ? qbuf[0] : 0ull;
-            int yn = n > 1 ? trace[1] : s_l0 | (N.nsp > 1 ? (s_l1 << 16) : 0);
-            int bmin = 0x7fffffff, bmax = -1;
-            for (int k = 0; k < n; ++k) {
-                if (steps_mode ? (Nc >= n_c) : (inW >= q_tcorr)) {
-                    more = 0;
-                    break;
-                }
-                const unsigned long long q = qn;
-                int y0, y1;
-                if (k + 1 < n) {
-                    unpack_state(N.nsp, yn, y0, y1);
-                } else {
-                    y0 = s_l0;
-                    y1 = s_l1;
-                }
-                if (k + 1 < n) {
-                    qn = qbuf[k + 1];
-                    yn = k + 2 < n ? trace[k + 2] : 0;
-                }
-                ++step;
-                // T_end truncation and the T_burn split
-                unsigned long long t = q;
-                const unsigned long long rem = P.q_Tend - Ts;
-                if (t >= rem) {
-                    t = rem;
-                    ended = true;
-                }
-                unsigned long long pre = 0, post = t;
-                if (!burn_done) {
-                    const unsigned long long room = P.q_Tburn - Ts;
+        // (4a) scans: inclusive prefix of q and the last region change
+        const int k0 = 4 * threadIdx.x;
+        unsigned long long qk[4], lp[4];
+        int lc[4], yst[4];
+        unsigned long long run = 0;
+        int lastc = -1;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int k = k0 + e;
+            int a0, a1, y0, y1;
+            unpack_state(N.nsp, k < n ? trace[k] : 0, a0, a1);
+            if (k + 1 < n) {
+                unpack_state(N.nsp, trace[k + 1], y0, y1);
+            } else {
+                y0 = s_l0;
+                y1 = s_l1;
+            }
+            yst[e] = pack_state(N.nsp, y0, y1);
+            qk[e] = k < n ? qbuf[k] : 0ull;
+            const bool chg = k < n && !out_of_range(N, y0, y1) &&
+                             rt0.region(N.nsp, y0, y1) != rt0.region(N.nsp, a0, a1);
+            run += qk[e];
+            lp[e] = run;
+            if (chg) lastc = k;
+            lc[e] = lastc;
+        }
+        unsigned long long tpre;
+        int tmax;
+        block_scan_sum_max(run, lastc, s_wsum, s_wmax, tpre, tmax);
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (k0 + e < n) Pk[k0 + e] = tpre + lp[e];
+        __syncthreads();
+        // (4b) the rule before each step, the T_end and T_burn steps
+        const unsigned long long Ts0 = s_Ts, inW0 = s_inW;
+        const long long Nc0 = s_Nc;
+        const int bd0 = s_burn;
+        int my_stop = 0x7fffffff, my_end = 0x7fffffff, my_b = 0x7fffffff;
+        if (threadIdx.x == 0 && (steps_mode ? (Nc0 >= n_c) : (inW0 >= q_tcorr))) my_stop = 0;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int k = k0 + e;
+            if (k >= n) continue;
+            const unsigned long long Pe = tpre + lp[e];
+            const int L = max(tmax, lc[e]);
+            long long Nc;
+            unsigned long long inW;
+            if (L == k) {
+                Nc = 0;
+                inW = 0;
+            } else if (L < 0) {
+                Nc = Nc0 + (long long)(k + 1);
+                inW = inW0 + Pe;
+            } else {
+                Nc = (long long)(k - L);
+                inW = Pe - Pk[L];
+            }
+            if (steps_mode ? (Nc >= n_c) : (inW >= q_tcorr)) my_stop = min(my_stop, k + 1);
+            if (Ts0 + Pe >= q_Tend) my_end = min(my_end, k);
+            if (!bd0 && Ts0 + Pe >= q_Tburn) my_b = min(my_b, k);
+        }
+        if (my_stop != 0x7fffffff) atomicMin(&s_stop, my_stop);
+        if (my_end != 0x7fffffff) atomicMin(&s_end, my_end);
+        if (my_b != 0x7fffffff) atomicMin(&s_bcross, my_b);
+        __syncthreads();
+        // (4c) commit steps [0, c): c = min(rule stop, T_end step + 1, n)
+        const int stop = s_stop, endk = s_end, bk = s_bcross;
+        int c = n;
+        if (stop < c) c = stop;
+        if (endk < c) c = endk + 1;
+        const bool ended = endk < n && endk + 1 == c && endk < stop;
+        for (int k = threadIdx.x; k < c; k += T) {
+            int a0, a1;
+            unpack_state(N.nsp, trace[k], a0, a1);
+            const unsigned long long Pb = k > 0 ? Pk[k - 1] : 0ull;  // before step k
+            const unsigned long long q = Pk[k] - Pb;
+            unsigned long long t = q;
+            if (ended && k == endk) t = q_Tend - (Ts0 + Pb);
+            unsigned long long pre = 0, post = t;
+            if (!bd0) {
+                if (k < bk) {
+                    pre = t;
+                    post = 0;
+                } else if (k == bk) {
+                    const unsigned long long room = q_Tburn - (Ts0 + Pb);
                     pre = t < room ? t : room;
                     post = t - pre;
-                    if (t >= room) burn_done = 1;
-                }
-                Ts += t;
-                if (pre) {
-                    if (hs.sh && !sh_post) hs.add(a, a1, pre);
-                    else atomicAdd(P.hist_pre + a * N.ystride + a1, pre);
-                }
-                if (post) {
-                    if (hs.sh && sh_post) hs.add(a, a1, post);
-                    else atomicAdd(P.hist_post + a * N.ystride + a1, post);
-                }
-                bmin = min(bmin, a);
-                bmax = max(bmax, a);
-                if (ended) {
-                    more = 0;
-                    break;
-                }
-                const int o = jump_outcome<KIND, true>(N, rt, y0, y1);
-                if (o == 2) {
-                    status = PARREP_ERANGE;
-                    more = 0;
-                    break;
-                }
-                x0 = y0;
-                x1 = y1;
-                a = y0;
-                a1 = y1;
-                if (o == 0) {
-                    ++Nc;
-                    inW += q;
-                } else {
-                    Nc = 0;
-                    inW = 0;
-                    W = rt.region(N.nsp, x0, x1);
-                    rt.set(W);
                 }
             }
-            atomicAdd(&ctl->progress, 1ull);
-            F.rng[0] = bmin;
-            F.rng[1] = bmax;
-            s_step = step;
-            s_more = more && status == 0;
+            if (pre) {
+                if (hs.sh && !sh_post) hs.add(a0, a1, pre);
+                else atomicAdd(P.hist_pre + a0 * N.ystride + a1, pre);
+            }
+            if (post) {
+                if (hs.sh && sh_post) hs.add(a0, a1, post);
+                else atomicAdd(P.hist_post + a0 * N.ystride + a1, post);
+            }
+            atomicMin(&s_bmin, a0);
+            atomicMax(&s_bmax, a0);
+        }
+        // the carried state after step c-1 (its owner thread writes it)
+        if (c > 0 && (c - 1) >= k0 && (c - 1) < k0 + 4) {
+            const int e = c - 1 - k0;
+            const int k = c - 1;
+            const unsigned long long Pe = tpre + lp[e];
+            const int L = max(tmax, lc[e]);
+            if (L == k) {
+                s_Nc_last = 0;
+                s_inW_last = 0;
+            } else if (L < 0) {
+                s_Nc_last = Nc0 + (long long)(k + 1);
+                s_inW_last = inW0 + Pe;
+            } else {
+                s_Nc_last = (long long)(k - L);
+                s_inW_last = Pe - Pk[L];
+            }
+            int y0, y1;
+            unpack_state(N.nsp, yst[e], y0, y1);
+            s_x0 = y0;
+            s_x1 = y1;
+            s_c = c;
         }
         __syncthreads();
-        if (hs.lo && F.rng[1] >= F.rng[0]) {
-            // one species: rows = states; two species: all columns of the rows
-            fold_limbs(hs, F.rng[0], F.rng[1], N.ystride, 0, N.nsp > 1 ? N.hist_max1 : 0);
+        if (threadIdx.x == 0) {
+            int more = 1;
+            if (c > 0) {
+                s_step = step0 + (unsigned long long)c;
+                s_Ts = ended ? q_Tend : Ts0 + Pk[c - 1];
+                if (!bd0 && bk < c) s_burn = 1;
+                if (ended) {
+                    s_ended = 1;
+                    more = 0;
+                    // the state stays the pre-jump state of the truncated step
+                    int a0, a1;
+                    unpack_state(N.nsp, trace[endk], a0, a1);
+                    s_x0 = a0;
+                    s_x1 = a1;
+                    s_W = rt0.region(N.nsp, a0, a1);
+                } else if (out_of_range(N, s_x0, s_x1)) {
+                    // the chain's jump out of range is committed: range error
+                    s_status = PARREP_ERANGE;
+                    more = 0;
+                    int a0, a1;
+                    unpack_state(N.nsp, trace[c - 1], a0, a1);
+                    s_x0 = a0;
+                    s_x1 = a1;
+                } else {
+                    s_Nc = s_Nc_last;
+                    s_inW = s_inW_last;
+                    s_W = rt0.region(N.nsp, s_x0, s_x1);
+                }
+            }
+            if (stop <= c) more = 0;  // the rule holds before step c
+            if (c < n) more = 0;
+            if (n < M && c == n && !s_ended && s_status == 0) more = 0;
+            atomicAdd(&ctl->progress, 1ull);
+            s_more = more;
         }
+        __syncthreads();
+        if (hs.lo && s_bmax >= s_bmin)
+            fold_limbs(hs, s_bmin, s_bmax, N.ystride, 0, N.nsp > 1 ? N.hist_max1 : 0);
         __syncthreads();
         dc.lap(kPhDecCommit);
     }
-    if (threadIdx.x == 0)
-        for (int i = 8; i < 12; ++i) pc.acc[i] += dc.acc[i];
     if (threadIdx.x == 0) {
-        // the state after an out-of-range jump is not kept
-        if (status == PARREP_ERANGE) {
-            x0 = min(max(x0, 0), N.hist_max0);
-            x1 = min(max(x1, 0), N.hist_max1);
-        }
-        leader_finish_decorr(P, x0, x1, W, Ts, burn_done, step, ended, status, cycle);
+        for (int i = 8; i < 12; ++i) pc.acc[i] += dc.acc[i];
+        leader_finish_decorr(P, s_x0, s_x1, s_W, s_Ts, s_burn, s_step, s_ended != 0, s_status, cycle);
     }
 }
 
@@ -1506,6 +1629,7 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
         F.tab = P.off_tab >= 0 && KIND == PARREP_SCHLOGL ? (const float4*)(smem + P.off_tab) + 2 : nullptr;
         F.inv = F.tab ? (const float*)(smem + P.off_inv) : nullptr;
         F.rng = (int*)(smem + P.off_rng);
+        F.decp = (unsigned long long*)(smem + P.off_decp);
         F.prodU = KIND == PARREP_TOGGLE ? (const float*)(smem + P.off_tab) : nullptr;
         F.prodV = KIND == PARREP_TOGGLE ? (const float*)(smem + P.off_tab) + (N.hist_max1 + 1) : nullptr;
         F.buf = (float2*)(smem + P.off_buf);
