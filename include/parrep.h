@@ -83,6 +83,9 @@ typedef struct {
     int32_t chunk_steps;   /* lockstep steps between escape votes (0 = auto) */
     int32_t debug_stall_barrier; /* fault injection: >= 0 makes block 0 leave at that
                                     grid barrier so the others time out; -1 = off */
+    int32_t serial_stages; /* FP32 form: 1 runs the staged chunks without the owner /
+                              helper overlap (same results; for tests), 0 = auto */
+    int32_t reserved;
     double T_burn;         /* FIM / RER integrate over [T_burn, T_end] (default 0) */
     double wait_timeout_s; /* device wait limit without progress (default 10 s) */
     void* stream;          /* cudaStream_t to run on (NULL = legacy default stream) */

@@ -76,6 +76,8 @@ extern "C" void parrep_default_options(parrep_options* o) {
     o->block_threads = 0;
     o->chunk_steps = 0;
     o->debug_stall_barrier = -1;
+    o->serial_stages = 0;
+    o->reserved = 0;
     o->T_burn = 0.0;
     o->wait_timeout_s = 10.0;
     o->stream = nullptr;
@@ -311,10 +313,13 @@ struct Plan {
     int threads, grid, smem, RB, log2RB, B, S, use_smem_hist;
     int off_tab, off_buf, off_trace, off_live, off_nvalid;
     int off_limbs, off_inv, off_rng, off_decp;
+    int pipelined;
 };
 
-static int fast_layout(parrep_t h, int RB, int threads, int with_hist, Plan& pl) {
+static int fast_layout(parrep_t h, int RB, int threads, int with_hist, int pipelined, Plan& pl) {
     const int B = 32;
+    const int nbuf = pipelined ? 3 : 1, ntr = pipelined ? 2 : 1;
+    pl.pipelined = pipelined;
     int off = 0;
     pl.use_smem_hist = with_hist;
     pl.off_limbs = -1;
@@ -338,15 +343,15 @@ static int fast_layout(parrep_t h, int RB, int threads, int with_hist, Plan& pl)
         off += align16((h->net.hist_max[0] + 1 + h->net.hist_max[1] + 1) * 4);
     }
     pl.off_buf = off;
-    off += B * RB * 8;
+    off += nbuf * B * RB * 8;
     pl.off_trace = off;
-    off += B * RB * 4;
+    off += ntr * B * RB * 4;
     pl.off_live = off;
     off += RB * 4;
     pl.off_nvalid = off;
-    off += RB * 4;
+    off += ntr * RB * 4;
     pl.off_rng = off;
-    off += 16;
+    off += 32;
     pl.off_decp = off;  // decorrelation rounds of min(4 x threads, B x RB) steps
     off += (4 * threads < B * RB ? 4 * threads : B * RB) * 8;
     pl.B = B;
@@ -373,6 +378,7 @@ static int plan_launch(parrep_t h, Plan& pl) {
         pl.S = h->opt.chunk_steps > 0 ? h->opt.chunk_steps : 256;
         pl.off_tab = pl.off_buf = pl.off_trace = pl.off_live = pl.off_nvalid = -1;
         pl.off_limbs = pl.off_inv = pl.off_rng = pl.off_decp = -1;
+        pl.pipelined = 0;
         for (int with_hist = 1; with_hist >= 0; --with_hist) {
             if (with_hist && h->nbins * 8 > kSmemHistLimit) continue;
             pl.use_smem_hist = with_hist;
@@ -387,8 +393,13 @@ static int plan_launch(parrep_t h, Plan& pl) {
     for (int RB = 32; RB <= 512; RB *= 2) {
         const int threads = RB > T ? RB : T;
         const long long grid = (h->R + RB - 1) / RB;
-        for (int with_hist = 1; with_hist >= 0; --with_hist) {
-            const int smem = fast_layout(h, RB, threads, with_hist, pl);
+        for (int cfg = 3; cfg >= 0; --cfg) {
+            // prefer the warp-specialised pipeline (needs >= 2 helper warps),
+            // then the shared-memory histogram
+            const int pipe = (cfg & 2) && threads - RB >= 64 && !h->opt.serial_stages;
+            const int with_hist = cfg & 1;
+            if ((cfg & 2) && !pipe) continue;
+            const int smem = fast_layout(h, RB, threads, with_hist, pipe, pl);
             if (smem > 200 * 1024) continue;
             int ea = kernel_attrs(prec, kind, &per_sm, smem, threads);
             if (ea != 0) return cuda_fail(h, (cudaError_t)ea, "kernel attributes");
@@ -439,6 +450,7 @@ extern "C" int parrep_run(parrep_t h, double T_end, uint64_t seed) {
     p.off_inv = pl.off_inv;
     p.off_rng = pl.off_rng;
     p.off_decp = pl.off_decp;
+    p.pipelined = pl.pipelined;
     if (p.thresh == PARREP_THRESH_STEPS) {
         p.n_c = (long long)h->t_corr;
         p.n_p = (long long)h->t_phase;

@@ -90,6 +90,7 @@ struct RunParams {
     int RB, log2RB, B;
     int off_tab, off_buf, off_trace, off_live, off_nvalid;
     int off_limbs, off_inv, off_rng, off_decp;
+    int pipelined;  // FP32: owner warps and helper warps overlap (three draw slots, two trace slots)
     unsigned long long q_tcorr;
     long long n_c;
     double t_phase;

@@ -535,11 +535,16 @@ struct HistSink {
 
 // Folds the limbs of bins [b0, b1] into the 64-bit shared sums (signed, so a
 // roll-back's negative limb sums are exact) and clears them.
-__device__ __forceinline__ void fold_limbs(const HistSink& hs, int b0, int b1, int ystride, int c0, int c1) {
+__device__ __forceinline__ void fold_limbs(const HistSink& hs, int b0, int b1, int ystride, int c0, int c1,
+                                           int tid = -1, int T = 0) {
+    if (tid < 0) {
+        tid = threadIdx.x;
+        T = blockDim.x;
+    }
     // bins of the rectangle rows [b0, b1] x columns [c0, c1]
     const int w = c1 - c0 + 1;
     const int n = (b1 - b0 + 1) * w;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    for (int k = tid; k < n; k += T) {
         const int row = b0 + k / w, col = c0 + k % w;
         const int b = row * ystride + col;
         const int vl = (int)hs.lo[b], vh = (int)hs.hi[b];
@@ -710,13 +715,18 @@ __device__ void build_fast_tables(const NetDev& N, float4* tab, float* inv, floa
 // (P) Philox words for steps step0 .. step0+nsteps-1 of the block's live replicas.
 template <bool WANT_E>
 __device__ __forceinline__ void produce_lanes(const RunParams& P, const FastSmem& F, unsigned rbase, unsigned step0,
-                                              int nsteps, unsigned cycle, unsigned tag, uint2 key) {
-    const int lg = P.log2RB, mask = P.RB - 1, T = blockDim.x;
+                                              int nsteps, unsigned cycle, unsigned tag, uint2 key,
+                                              int tid = -1, int T = 0) {
+    if (tid < 0) {
+        tid = threadIdx.x;
+        T = blockDim.x;
+    }
+    const int lg = P.log2RB, mask = P.RB - 1;
     const int total = nsteps << lg;
     const int* live = F.live;
     float2* buf = F.buf;
     // four independent draws per thread and pass, so that their Philox rounds interleave
-    for (int base = threadIdx.x; base < total; base += 4 * T) {
+    for (int base = tid; base < total; base += 4 * T) {
         uint4 w[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -993,12 +1003,16 @@ enum ChunkMode { kFirst = 4 };
 template <int KIND, int MODE>
 __device__ __forceinline__ void account(const RunParams& P, const FastSmem& F, const HistSink& hs, unsigned rbase,
                                         int sbase, const Cuts& cut, bool to_post, unsigned long long& qs,
-                                        unsigned long long& ev, unsigned long long& ev2) {
+                                        unsigned long long& ev, unsigned long long& ev2, int tid = -1, int T = 0) {
+    if (tid < 0) {
+        tid = threadIdx.x;
+        T = blockDim.x;
+    }
     const NetDev& N = P.net;
-    const int lg = P.log2RB, mask = P.RB - 1, T = blockDim.x;
+    const int lg = P.log2RB, mask = P.RB - 1;
     const int total = P.B << lg;
     const bool tabbed = KIND == PARREP_SCHLOGL && F.tab;
-    for (int base = threadIdx.x; base < total; base += 4 * T) {
+    for (int base = tid; base < total; base += 4 * T) {
         int xa[4], xb[4];
         unsigned long long qv[4];
         bool ok[4];
@@ -1075,6 +1089,70 @@ __device__ void chunk_f32(const RunParams& P, const FastSmem& F, const HistSink&
                           unsigned long long& inc_ev, PhaseClock& pc) {
     const bool owner = threadIdx.x < P.RB;
     bool running = owner && active;
+    const bool limbs = hs.lo != nullptr && MODE != kStepSum && MODE != kTauAt;
+    if (P.pipelined) {
+        // Warp-specialised pipeline: in stage j the owner warps walk
+        // sub-chunk j while the helper warps draw sub-chunk j+1 and account
+        // for sub-chunk j-1 (draws in three slots, traces in two), so the
+        // owners' serial chains overlap the helpers' parallel work.  One
+        // block barrier per stage; the helpers fold the limbs of j-1 behind a
+        // named barrier of their own before the stage ends.
+        const int RB = P.RB, B = P.B;
+        const int nh = blockDim.x - RB, h = threadIdx.x - RB;
+        const int slotsz = B << P.log2RB;
+        if (owner) F.live[threadIdx.x] = running ? 1 : 0;
+        if (threadIdx.x < 8) F.rng[threadIdx.x] = (threadIdx.x & 1) ? -1 : 0x7fffffff;
+        __syncthreads();
+        pc.start();
+        const int nsub = P.S / B;
+        if (!owner) {
+            FastSmem Fp = F;
+            produce_lanes<true>(P, Fp, rbase, n0, B, cycle, kTagParallel, key, h, nh);
+        }
+        __syncthreads();
+        pc.lap(kPhDraw);
+        bool any = true;
+        for (int j = 0;; ++j) {
+            const bool consume = any && j < nsub;
+            if (owner) {
+                if (consume) {
+                    FastSmem Fj = F;
+                    Fj.buf = F.buf + (j % 3) * slotsz;
+                    Fj.trace = F.trace + (j & 1) * slotsz;
+                    Fj.nvalid = F.nvalid + (j & 1) * RB;
+                    Fj.rng = F.rng + (j & 1) * 4;
+                    consume_par<KIND>(P, Fj, rt, running, x0, x1, r, j * B, mykey, myoob, xe0, xe1);
+                } else {
+                    F.nvalid[(j & 1) * RB + threadIdx.x] = 0;
+                }
+            } else {
+                if (consume && j + 1 < nsub) {
+                    FastSmem Fp = F;
+                    Fp.buf = F.buf + ((j + 1) % 3) * slotsz;
+                    produce_lanes<true>(P, Fp, rbase, n0 + (unsigned)((j + 1) * B), B, cycle, kTagParallel, key,
+                                        h, nh);
+                }
+                if (j >= 1) {
+                    const int jp = j - 1;
+                    FastSmem Fa = F;
+                    Fa.buf = F.buf + (jp % 3) * slotsz;
+                    Fa.trace = F.trace + (jp & 1) * slotsz;
+                    Fa.nvalid = F.nvalid + (jp & 1) * RB;
+                    account<KIND, MODE>(P, Fa, hs, rbase, jp * B, cut, to_post, qs, ev, inc_ev, h, nh);
+                    asm volatile("bar.sync 1, %0;" ::"r"(nh) : "memory");
+                    int* rg = F.rng + (jp & 1) * 4;
+                    if (limbs && rg[1] >= rg[0]) fold_limbs(hs, rg[0], rg[1], P.net.ystride, rg[2], rg[3], h, nh);
+                    asm volatile("bar.sync 1, %0;" ::"r"(nh) : "memory");
+                    if (h < 4) rg[h] = (h & 1) ? -1 : 0x7fffffff;
+                }
+            }
+            const bool any_next = __syncthreads_or(running);
+            pc.lap(kPhChain);
+            if (!consume) break;
+            any = any_next;
+        }
+        return;
+    }
     if (owner) F.live[threadIdx.x] = running ? 1 : 0;
     if (threadIdx.x == 0) {
         F.rng[0] = 0x7fffffff;
@@ -1083,7 +1161,6 @@ __device__ void chunk_f32(const RunParams& P, const FastSmem& F, const HistSink&
         F.rng[3] = -1;
     }
     __syncthreads();
-    const bool limbs = hs.lo != nullptr && MODE != kStepSum && MODE != kTauAt;
     for (int sub = 0; sub < P.S; sub += P.B) {
         pc.start();
         produce_lanes<true>(P, F, rbase, n0 + (unsigned)sub, P.B, cycle, kTagParallel, key);

@@ -264,3 +264,19 @@ def test_fp32_staged_path_is_shape_invariant(spec, x0):
     for r in res[1:]:
         assert np.array_equal(r[0], res[0][0]) and np.array_equal(r[1], res[0][1])
         assert r[2] == res[0][2] and r[3] == res[0][3]
+
+
+@pytest.mark.parametrize("spec,x0", [(V10, [2]), (K.toggle(alpha=20.0, n=2.5, hist_max=(63, 63)), [15, 2])])
+def test_fp32_pipelined_equals_serial_stages(spec, x0):
+    """The owner/helper overlap only reorders work between warps: the results
+    must equal those of the unpipelined stages bit for bit."""
+    thresh, tc = ("steps", 200) if spec["kind"] == "schlogl" else ("time", 0.5)
+    out = []
+    for serial in (0, 1):
+        g = ParRep(spec, 100, tc, tc, x0=x0, thresh=thresh, precision="f32", fv_group=16, T_burn=25.0,
+                   serial_stages=serial)
+        g.run(80.0, 5)
+        pre, post = g.histogram_raw()
+        out.append((pre, post, g.cycle_log(), g.stats()["events_parallel_useful"]))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2] and out[0][3] == out[1][3]
