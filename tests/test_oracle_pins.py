@@ -301,6 +301,41 @@ def test_parrep_clock_and_burn_in_split_are_exact():
     assert abs(r["rer"][1] - F[0, 0] * net["c"][0] ** 2 * (eps - np.log1p(eps))) < 1e-6 * abs(r["rer"][1])
 
 
+@pytest.mark.parametrize("which", ["schlogl", "toggle"])
+def test_parrep_fim_rer_are_histogram_contractions(which):
+    """The per-jump sums of the RER and FIM integrands (Appendix A) equal the
+    post-burn occupation times contracted with
+    the closed-form per-state rates (sum_j lambda_j grad log lambda_j^2, and
+    sum_j lambda_j log(lambda_j / lambda'_j) - lambda_j + lambda'_j)."""
+    if which == "schlogl":
+        net = K.schlogl_paper(V=10, hist_max=200, split=11)
+        xs = np.arange(201)
+        lam = E.schlogl_props(net["c"], net["s"], xs)
+        grad = E.schlogl_grad_log(net["c"], xs)
+        props = lambda c: E.schlogl_props(c, net["s"], xs)
+        run = dict(t_corr=300, t_phase=300, T_end=800.0, x0=[2], thresh="steps")
+    else:
+        net = K.toggle(alpha=20, n=2.5, hist_max=(63, 63))
+        U, V = np.meshgrid(np.arange(64.0), np.arange(64.0), indexing="ij")
+        U, V = U.ravel(), V.ravel()
+        lam = E.toggle_props(net["c"], U, V)
+        grad = E.toggle_grad_log(net["c"], U, V)
+        props = lambda c: E.toggle_props(c, U, V)
+        run = dict(t_corr=1.0, t_phase=1.0, T_end=60.0, x0=[15, 2], thresh="time")
+    cp = np.array([net["c"]] * 2, dtype=float)
+    cp[0, 0] *= 1.2
+    cp[1, 2] *= 0.7
+    r = O.parrep_run(net, 16, run["t_corr"], run["t_phase"], run["T_end"], 9, run["x0"], thresh=run["thresh"],
+                     T_burn=20.0, rer_cprime=cp)
+    assert r["status"] == 0
+    w = r["hist_post"]
+    F = E.fim_exact(lam, grad, w)
+    assert np.allclose(r["fim"], F, rtol=1e-12, atol=1e-12 * np.abs(F).max())
+    for k in range(2):
+        Rk = E.rer_exact(lam, props(cp[k]), w)
+        assert abs(r["rer"][k] - Rk) <= 1e-12 * abs(Rk)
+
+
 def test_parrep_without_escapes_is_stationary_poisson():
     """A single region: after decorrelation and dephasing the parallel step
     runs R replicas to T_end; the pooled histogram is Poisson and the FIM of
