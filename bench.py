@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--x0", type=int, default=None, help="fixed x_0 instead of the uniform draw (profiling)")
     ap.add_argument("--t_corr", type=float, default=None, help="override t_corr (profiling)")
     ap.add_argument("--t_phase", type=float, default=None, help="override t_phase (profiling)")
+    ap.add_argument("--block_threads", type=int, default=0, help="CUDA block size (0 = library default)")
+    ap.add_argument("--chunk_steps", type=int, default=0, help="steps between escape votes (0 = default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -192,7 +194,8 @@ def main():
     stream = torch.cuda.Stream()
     g = ParRep(c["network"], c["n_replicas"], c["t_corr"], c["t_phase"], x0=c["x0"],
                x0_uniform_hi=c["x0_uniform_hi"], thresh=c["thresh"], precision=args.precision,
-               T_burn=c["T_burn"] * T_end / c["T_end"], stream=stream)
+               T_burn=c["T_burn"] * T_end / c["T_end"], stream=stream, block_threads=args.block_threads,
+               chunk_steps=args.chunk_steps)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     seed0 = 1_000_003 * (rank + 1)
 
@@ -255,7 +258,8 @@ def main():
             t0 = time.perf_counter()
             h = ParRep(c["network"], c["n_replicas"], c["t_corr"], c["t_phase"], x0=c["x0"],
                        x0_uniform_hi=c["x0_uniform_hi"], thresh=c["thresh"], precision=args.precision,
-                       T_burn=c["T_burn"] * T_end / c["T_end"])
+                       T_burn=c["T_burn"] * T_end / c["T_end"], block_threads=args.block_threads,
+                       chunk_steps=args.chunk_steps)
             st = h.run(T_end, seed0 + 777 + i)
             hist = h.histogram()
             fim = h.fim()

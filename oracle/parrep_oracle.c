@@ -24,7 +24,12 @@
  *   - Holding time tau = -log(u1)/a0 and the direct-method selection "first j
  *     with lambda_1+...+lambda_j > u2*a0" (Gillespie direct method, Sec. II.A).
  *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11) keyed by the 64-bit
- *     seed, counter = (replica, step, cycle, stage tag).
+ *     seed, counter = (replica, step, cycle, stage tag).  binary64 mode: one
+ *     call per step (words 0,1 -> u1 and 2,3 -> u2).  binary32 mode: a step
+ *     needs two 23-bit uniforms, so one call serves two steps -- counter step
+ *     field = step/2, words (0,1) for even and (2,3) for odd steps -- and in
+ *     the dephasing, which only needs the choice uniform, four steps: counter
+ *     step/4, word step%4.
  *   - Thresholds: STEPS mode = the paper's counts n_c, n_p; TIME mode = the
  *     decorrelation ends after t_corr units of consecutive in-W time, and the
  *     dephasing makes n_p = ceil(t_phase * a0(X~)) lockstep jumps of the
@@ -131,6 +136,22 @@ static void draw(uint64_t seed, uint32_t a, uint32_t b, uint32_t cyc, uint32_t t
     or_philox4x32_10(ctr, key, w);
 }
 
+/* The four Philox words a step reads, and where u1 (and u2) sit in them:
+ * binary64 mode: counter field `step`, words 0..3; binary32 mode: counter
+ * field step/2, the pair (2*(step%2), 2*(step%2)+1).  `hi` is the counter
+ * word above the step (replica, or the high step bits). */
+static const uint32_t* step_words(uint64_t seed, uint32_t hi, uint64_t step, uint32_t cyc, uint32_t tag, int prec,
+                                  uint32_t w[4])
+{
+    if (prec == 1) {
+        uint64_t pair = step >> 1;
+        draw(seed, hi, (uint32_t)pair, cyc, tag, w);
+        return w + 2 * (int)(step & 1);
+    }
+    draw(seed, hi, (uint32_t)step, cyc, tag, w);
+    return w;
+}
+
 /* Uniform in (0,1) from 52 random bits: (m + 1/2) 2^-52, exact in binary64. */
 double or_u01_f64(uint32_t wa, uint32_t wb)
 {
@@ -234,7 +255,7 @@ static int select_f32(const float lam[4], float target)
 
 /* One SSA step at state x from the four Philox words: the holding time tau
  * (needs_tau) and the reaction J.  Returns J, or -1 if a0 <= 0. */
-static int ssa_step(const or_network* N, int prec, const int32_t* x, const uint32_t w[4], double* tau)
+static int ssa_step(const or_network* N, int prec, const int32_t* x, const uint32_t* w, double* tau)
 {
     if (prec == OR_F64) {
         double lam[4];
@@ -421,9 +442,19 @@ int64_t or_dephase(const or_network* N, const or_config* C, const int32_t* x_til
         /* every replica makes one jump of the embedded chain */
         for (int64_t r = 0; r < R; ++r) {
             uint32_t w[4];
-            draw(C->seed, (uint32_t)r, (uint32_t)i, cycle, TAG_DEPHASE, w);
-            double tau = 0.0;
-            int J = ssa_step(N, C->precision, xs + 2 * r, w, &tau);
+            int J;
+            if (C->precision == OR_F32) {
+                /* the choice uniform only: word i%4 of counter (r, i/4, cycle, DEPHASE) */
+                draw(C->seed, (uint32_t)r, (uint32_t)(i >> 2), cycle, TAG_DEPHASE, w);
+                float lam[4];
+                props_f32(N, xs + 2 * r, lam);
+                float a0 = ((lam[0] + lam[1]) + lam[2]) + lam[3];
+                J = a0 > 0.0f ? select_f32(lam, or_u01_f32(w[i & 3]) * a0) : -1;
+            } else {
+                draw(C->seed, (uint32_t)r, (uint32_t)i, cycle, TAG_DEPHASE, w);
+                double tau = 0.0;
+                J = ssa_step(N, C->precision, xs + 2 * r, w, &tau);
+            }
             if (J < 0) { status = OR_ERANGE; goto done; }
             ++ev;
             xn[2 * r] = xs[2 * r] + ETA[N->kind][J][0];
@@ -484,8 +515,8 @@ static int parallel_step(const or_network* N, const or_config* C, acc_t* A, int3
         int64_t K = -1;
         for (int64_t r = 0; r < R; ++r) {
             uint32_t w[4];
-            draw(C->seed, (uint32_t)r, (uint32_t)n, cycle, TAG_PARALLEL, w);
-            int J = ssa_step(N, C->precision, xs + 2 * r, w, &tau[r]);
+            const uint32_t* ws = step_words(C->seed, (uint32_t)r, (uint64_t)n, cycle, TAG_PARALLEL, C->precision, w);
+            int J = ssa_step(N, C->precision, xs + 2 * r, ws, &tau[r]);
             if (J < 0) { rc = OR_ERANGE; goto out; }
             xn[2 * r] = xs[2 * r] + ETA[N->kind][J][0];
             xn[2 * r + 1] = xs[2 * r + 1] + ETA[N->kind][J][1];
@@ -589,9 +620,11 @@ int or_parrep_run(const or_network* N, const or_config* C, double* hist_pre, dou
         for (;;) {
             if (steps_mode ? (Nc >= (int64_t)C->t_corr) : (inW >= C->t_corr)) break;
             uint32_t w[4];
-            draw(C->seed, (uint32_t)(step >> 32), (uint32_t)step, cycle, TAG_DECORR, w);
+            const uint64_t cs = C->precision == OR_F32 ? (uint64_t)step >> 1 : (uint64_t)step;
+            draw(C->seed, (uint32_t)(cs >> 32), (uint32_t)cs, cycle, TAG_DECORR, w);
+            const uint32_t* ws = C->precision == OR_F32 ? w + 2 * (int)(step & 1) : w;
             double tau = 0.0;
-            int J = ssa_step(N, C->precision, xt, w, &tau);
+            int J = ssa_step(N, C->precision, xt, ws, &tau);
             if (J < 0) { status = OR_ERANGE; goto finish; }
             ++res->events_decorr;
             ++step;
@@ -667,9 +700,11 @@ int or_ssa_run(const or_network* N, int32_t precision, int64_t n_traj, const int
         if (!in_range(N, x)) return OR_EINVAL;
         while (T < T_end) {
             uint32_t w[4];
-            draw(seed, (uint32_t)t, (uint32_t)step, (uint32_t)(step >> 32), TAG_SSA, w);
+            const uint64_t cs = precision == OR_F32 ? step >> 1 : step;
+            draw(seed, (uint32_t)t, (uint32_t)cs, (uint32_t)(cs >> 32), TAG_SSA, w);
+            const uint32_t* ws = precision == OR_F32 ? w + 2 * (int)(step & 1) : w;
             double tau = 0.0;
-            int J = ssa_step(N, precision, x, w, &tau);
+            int J = ssa_step(N, precision, x, ws, &tau);
             if (J < 0) return OR_ERANGE;
             double rem = T_end - T;
             int64_t b = bin_of(N, x);
@@ -701,9 +736,11 @@ int or_ssa_trace(const or_network* N, int32_t precision, const int32_t* x0, uint
     int32_t x[2] = {x0[0], N->n_species > 1 ? x0[1] : 0};
     for (int64_t s = 0; s < n_max; ++s) {
         uint32_t w[4];
-        draw(seed, traj, (uint32_t)s, (uint32_t)((uint64_t)s >> 32), TAG_SSA, w);
+        const uint64_t cs = precision == OR_F32 ? (uint64_t)s >> 1 : (uint64_t)s;
+        draw(seed, traj, (uint32_t)cs, (uint32_t)(cs >> 32), TAG_SSA, w);
+        const uint32_t* ws = precision == OR_F32 ? w + 2 * (int)(s & 1) : w;
         double tau = 0.0;
-        int J = ssa_step(N, precision, x, w, &tau);
+        int J = ssa_step(N, precision, x, ws, &tau);
         if (J < 0) return OR_ERANGE;
         x[0] += ETA[N->kind][J][0];
         x[1] += ETA[N->kind][J][1];

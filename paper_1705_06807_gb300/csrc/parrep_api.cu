@@ -389,7 +389,7 @@ static int plan_launch(parrep_t h, Plan& pl) {
         }
         return fail(h, PARREP_ENOMEM, "n_replicas exceeds one co-resident cooperative grid");
     }
-    const int T = h->opt.block_threads > 0 ? h->opt.block_threads : 256;
+    const int T = h->opt.block_threads > 0 ? h->opt.block_threads : 384;
     for (int RB = 32; RB <= 512; RB *= 2) {
         const int threads = RB > T ? RB : T;
         const long long grid = (h->R + RB - 1) / RB;
@@ -407,7 +407,7 @@ static int plan_launch(parrep_t h, Plan& pl) {
                 pl.threads = threads;
                 pl.grid = (int)grid;
                 pl.smem = smem;
-                const int S = h->opt.chunk_steps > 0 ? h->opt.chunk_steps : 1024;
+                const int S = h->opt.chunk_steps > 0 ? h->opt.chunk_steps : 512;
                 pl.S = ((S + pl.B - 1) / pl.B) * pl.B;
                 return PARREP_OK;
             }

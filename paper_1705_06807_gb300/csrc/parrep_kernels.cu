@@ -172,6 +172,24 @@ __device__ __forceinline__ unsigned long long q_of_f32(float tau) {
 
 // One Gillespie direct-method step at (x0,x1) from the Philox words w:
 // returns J and (if WANT_TAU) the holding time tau = -log(u1)/a0 in fixed point.
+// Words of parallel step n of replica r, and of decorrelation step `step`.
+// The FP32 form needs two 23-bit uniforms per step, so one Philox call serves
+// the step pair (2p, 2p+1): words 0,1 for the even step, 2,3 for the odd one.
+template <bool F32>
+__device__ __forceinline__ uint4 par_words(unsigned r, unsigned n, unsigned cycle, uint2 key) {
+    if (!F32) return philox10(make_uint4(r, n, cycle, kTagParallel), key);
+    const uint4 w = philox10(make_uint4(r, n >> 1, cycle, kTagParallel), key);
+    return (n & 1) ? make_uint4(w.z, w.w, 0u, 0u) : w;
+}
+template <bool F32>
+__device__ __forceinline__ uint4 decorr_words(unsigned long long step, unsigned cycle, uint2 key) {
+    const unsigned long long c = F32 ? step >> 1 : step;
+    const uint4 w = philox10(make_uint4((unsigned)(c >> 32), (unsigned)c, cycle, kTagDecorr), key);
+    return (F32 && (step & 1)) ? make_uint4(w.z, w.w, 0u, 0u) : w;
+}
+
+// FP32 form: w.x and w.y are the step's two words (a Philox call serves two
+// steps: words 0,1 for the even and 2,3 for the odd step).
 template <bool F32, bool WANT_TAU>
 __device__ __forceinline__ int ssa_draw(const NetDev& N, int x0, int x1, uint4 w, unsigned long long& q) {
     if (F32) {
@@ -408,7 +426,7 @@ __device__ void leader_decorrelate(const RunParams& P) {
     int status = 0;
     for (;;) {
         if (P.thresh == PARREP_THRESH_STEPS ? (Nc >= P.n_c) : (inW >= P.q_tcorr)) break;
-        uint4 w = philox10(make_uint4((unsigned)(step >> 32), (unsigned)step, cycle, kTagDecorr), key);
+        const uint4 w = decorr_words<F32>(step, cycle, key);
         unsigned long long q = 0;
         const int J = ssa_draw<F32, true>(N, x0, x1, w, q);
         ++step;
@@ -457,7 +475,11 @@ __device__ int dephase_warp(const NetDev& N, bool active, unsigned r, int G, int
         int n0 = x0, n1 = x1;
         bool ex = false, bad = false;
         if (active) {
-            uint4 w = philox10(make_uint4(r, (unsigned)i, cycle, kTagDephase), key);
+            uint4 w = philox10(make_uint4(r, F32 ? (unsigned)(i >> 2) : (unsigned)i, cycle, kTagDephase), key);
+            if (F32) {
+                const unsigned wi = (i & 3) == 0 ? w.x : (i & 3) == 1 ? w.y : (i & 3) == 2 ? w.z : w.w;
+                w = make_uint4(0u, wi, 0u, 0u);
+            }
             unsigned long long q;
             const int J = ssa_draw<F32, false>(N, x0, x1, w, q);
             apply(N, J, n0, n1);
@@ -580,7 +602,7 @@ __device__ void replay_chunk(const RunParams& P, const HistSink& hs, int x0, int
     for (int s = 0; s < P.S; ++s) {
         const unsigned long long pos = pos_of(s, r);
         if (MODE != kRollback && pos > cut.posC) break;
-        uint4 w = philox10(make_uint4(r, n0 + (unsigned)s, cycle, kTagParallel), key);
+        const uint4 w = par_words<F32>(r, n0 + (unsigned)s, cycle, key);
         unsigned long long q = 0;
         const int J = ssa_draw<F32, true>(N, x0, x1, w, q);
         ++ev;
@@ -717,27 +739,44 @@ template <bool WANT_E>
 __device__ __forceinline__ void produce_lanes(const RunParams& P, const FastSmem& F, unsigned rbase, unsigned step0,
                                               int nsteps, unsigned cycle, unsigned tag, uint2 key,
                                               int tid = -1, int T = 0) {
+    // A Philox call serves PER consecutive steps of one replica: two in the
+    // parallel step (u1, u2 each), four in the dephasing (u2 only).  step0 is
+    // a multiple of PER.
     if (tid < 0) {
         tid = threadIdx.x;
         T = blockDim.x;
     }
+    constexpr int PER = WANT_E ? 2 : 4;
     const int lg = P.log2RB, mask = P.RB - 1;
-    const int total = nsteps << lg;
+    const int ngroups = (nsteps + PER - 1) / PER;
+    const int total = ngroups << lg;
     const int* live = F.live;
     float2* buf = F.buf;
-    // four independent draws per thread and pass, so that their Philox rounds interleave
+    const unsigned g0 = step0 / PER;
+    // four independent calls per thread and pass, so that their rounds interleave
     for (int base = tid; base < total; base += 4 * T) {
         uint4 w[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int i = base + k * T < total ? base + k * T : base;
-            w[k] = philox10(make_uint4(rbase + (unsigned)(i & mask), step0 + (unsigned)(i >> lg), cycle, tag), key);
+            w[k] = philox10(make_uint4(rbase + (unsigned)(i & mask), g0 + (unsigned)(i >> lg), cycle, tag), key);
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int i = base + k * T;
-            if (i < total && live[i & mask])
-                buf[i] = make_float2(WANT_E ? -logf(u01f(w[k].x)) : 0.f, u01f(w[k].y));
+            const int lane = i & mask, g = i >> lg;
+            if (i < total && live[lane]) {
+                const int s = g * PER;
+                if (WANT_E) {
+                    buf[(s << lg) + lane] = make_float2(-logf(u01f(w[k].x)), u01f(w[k].y));
+                    if (s + 1 < nsteps) buf[((s + 1) << lg) + lane] = make_float2(-logf(u01f(w[k].z)), u01f(w[k].w));
+                } else {
+                    buf[(s << lg) + lane].y = u01f(w[k].x);
+                    if (s + 1 < nsteps) buf[((s + 1) << lg) + lane].y = u01f(w[k].y);
+                    if (s + 2 < nsteps) buf[((s + 2) << lg) + lane].y = u01f(w[k].z);
+                    if (s + 3 < nsteps) buf[((s + 3) << lg) + lane].y = u01f(w[k].w);
+                }
+            }
         }
     }
 }
@@ -1467,17 +1506,25 @@ __device__ void decorrelate_f32(const RunParams& P, const FastSmem& F, const His
     dc.start();
     while (s_more) {
         const unsigned long long step0 = s_step;
-        // (1) draws
-        for (int base = threadIdx.x; base < M; base += 4 * T) {
-            uint4 w[4];
+        // (1) draws: one Philox call per pair of steps (2p, 2p+1)
+        {
+            const unsigned long long p0 = step0 >> 1;
+            const int npairs = (int)(((step0 + (unsigned long long)M - 1) >> 1) - p0) + 1;
+            for (int base = threadIdx.x; base < npairs; base += 4 * T) {
+                uint4 w[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const unsigned long long st = step0 + (unsigned long long)(base + k * T);
-                w[k] = philox10(make_uint4((unsigned)(st >> 32), (unsigned)st, cycle, kTagDecorr), key);
+                for (int k = 0; k < 4; ++k) {
+                    const unsigned long long pr = p0 + (unsigned long long)(base + k * T);
+                    w[k] = philox10(make_uint4((unsigned)(pr >> 32), (unsigned)pr, cycle, kTagDecorr), key);
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (base + k * T >= npairs) continue;
+                    const long long ke = (long long)((p0 + (unsigned long long)(base + k * T)) << 1) - (long long)step0;
+                    if (ke >= 0 && ke < M) buf[ke] = make_float2(-logf(u01f(w[k].x)), u01f(w[k].y));
+                    if (ke + 1 >= 0 && ke + 1 < M) buf[ke + 1] = make_float2(-logf(u01f(w[k].z)), u01f(w[k].w));
+                }
             }
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (base + k * T < M) buf[base + k * T] = make_float2(-logf(u01f(w[k].x)), u01f(w[k].y));
         }
         __syncthreads();
         dc.lap(kPhDecDraw);
@@ -1815,7 +1862,7 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
                                             mykey, myoob, xe0, xe1, qsum, ev, dummy, pc);
                 } else if (active) {
                     for (int s = 0; s < P.S; ++s) {
-                        uint4 w = philox10(make_uint4(r, n0 + (unsigned)s, cycle, kTagParallel), key);
+                        const uint4 w = par_words<F32>(r, n0 + (unsigned)s, cycle, key);
                         unsigned long long q = 0;
                         const int J = ssa_draw<F32, true>(N, x0, x1, w, q);
                         qsum += q;
@@ -2189,7 +2236,9 @@ __global__ void ssa_kernel(NetDev N, long long n_traj, int x00, int x01, unsigne
         int x0 = x00, x1 = x01;
         unsigned long long T = 0, step = 0;
         while (T < q_Tend) {
-            uint4 w = philox10(make_uint4((unsigned)t, (unsigned)step, (unsigned)(step >> 32), kTagSSA), key);
+            const unsigned long long cs = F32 ? step >> 1 : step;
+            uint4 w = philox10(make_uint4((unsigned)t, (unsigned)cs, (unsigned)(cs >> 32), kTagSSA), key);
+            if (F32 && (step & 1)) w = make_uint4(w.z, w.w, 0u, 0u);
             unsigned long long q = 0;
             const int J = ssa_draw<F32, true>(N, x0, x1, w, q);
             const unsigned long long rem = q_Tend - T;
