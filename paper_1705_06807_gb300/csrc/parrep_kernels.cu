@@ -736,48 +736,51 @@ __device__ void build_fast_tables(const NetDev& N, float4* tab, float* inv, floa
 
 // (P) Philox words for steps step0 .. step0+nsteps-1 of the block's live replicas.
 template <bool WANT_E>
+__device__ __forceinline__ void produce_store(const FastSmem& F, int lg, int mask, int nsteps, int i, uint4 w) {
+    constexpr int PER = WANT_E ? 2 : 4;
+    const int lane = i & mask, s = (i >> lg) * PER;
+    if (!F.live[lane]) return;
+    float2* buf = F.buf;
+    if (WANT_E) {
+        buf[(s << lg) + lane] = make_float2(-logf(u01f(w.x)), u01f(w.y));
+        if (s + 1 < nsteps) buf[((s + 1) << lg) + lane] = make_float2(-logf(u01f(w.z)), u01f(w.w));
+    } else {
+        buf[(s << lg) + lane].y = u01f(w.x);
+        if (s + 1 < nsteps) buf[((s + 1) << lg) + lane].y = u01f(w.y);
+        if (s + 2 < nsteps) buf[((s + 2) << lg) + lane].y = u01f(w.z);
+        if (s + 3 < nsteps) buf[((s + 3) << lg) + lane].y = u01f(w.w);
+    }
+}
+
+template <bool WANT_E>
 __device__ __forceinline__ void produce_lanes(const RunParams& P, const FastSmem& F, unsigned rbase, unsigned step0,
                                               int nsteps, unsigned cycle, unsigned tag, uint2 key,
                                               int tid = -1, int T = 0) {
     // A Philox call serves PER consecutive steps of one replica: two in the
     // parallel step (u1, u2 each), four in the dephasing (u2 only).  step0 is
-    // a multiple of PER.
+    // a multiple of PER.  Item i is (lane i % RB, call i / RB); T and the item
+    // count are multiples of 32, so whether an item exists is warp-uniform and
+    // no thread computes a call that is not needed.
     if (tid < 0) {
         tid = threadIdx.x;
         T = blockDim.x;
     }
     constexpr int PER = WANT_E ? 2 : 4;
     const int lg = P.log2RB, mask = P.RB - 1;
-    const int ngroups = (nsteps + PER - 1) / PER;
-    const int total = ngroups << lg;
-    const int* live = F.live;
-    float2* buf = F.buf;
+    const int total = ((nsteps + PER - 1) / PER) << lg;
     const unsigned g0 = step0 / PER;
-    // four independent calls per thread and pass, so that their rounds interleave
-    for (int base = tid; base < total; base += 4 * T) {
-        uint4 w[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int i = base + k * T < total ? base + k * T : base;
-            w[k] = philox10(make_uint4(rbase + (unsigned)(i & mask), g0 + (unsigned)(i >> lg), cycle, tag), key);
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int i = base + k * T;
-            const int lane = i & mask, g = i >> lg;
-            if (i < total && live[lane]) {
-                const int s = g * PER;
-                if (WANT_E) {
-                    buf[(s << lg) + lane] = make_float2(-logf(u01f(w[k].x)), u01f(w[k].y));
-                    if (s + 1 < nsteps) buf[((s + 1) << lg) + lane] = make_float2(-logf(u01f(w[k].z)), u01f(w[k].w));
-                } else {
-                    buf[(s << lg) + lane].y = u01f(w[k].x);
-                    if (s + 1 < nsteps) buf[((s + 1) << lg) + lane].y = u01f(w[k].y);
-                    if (s + 2 < nsteps) buf[((s + 2) << lg) + lane].y = u01f(w[k].z);
-                    if (s + 3 < nsteps) buf[((s + 3) << lg) + lane].y = u01f(w[k].w);
-                }
-            }
-        }
+    int i = tid;
+    // two independent calls per pass while both exist, so that their rounds interleave
+    for (; i + T < total; i += 2 * T) {
+        const int j = i + T;
+        const uint4 wa = philox10(make_uint4(rbase + (unsigned)(i & mask), g0 + (unsigned)(i >> lg), cycle, tag), key);
+        const uint4 wb = philox10(make_uint4(rbase + (unsigned)(j & mask), g0 + (unsigned)(j >> lg), cycle, tag), key);
+        produce_store<WANT_E>(F, lg, mask, nsteps, i, wa);
+        produce_store<WANT_E>(F, lg, mask, nsteps, j, wb);
+    }
+    if (i < total) {
+        const uint4 wa = philox10(make_uint4(rbase + (unsigned)(i & mask), g0 + (unsigned)(i >> lg), cycle, tag), key);
+        produce_store<WANT_E>(F, lg, mask, nsteps, i, wa);
     }
 }
 
@@ -1039,6 +1042,77 @@ enum ChunkMode { kFirst = 4 };
 // (A) the holding times of the sub-chunk's trace, used as the mode says:
 // first pass (add), roll-back (subtract), per-step sums, one step's
 // per-replica values, or the precise pass that keeps what precedes the cut.
+// Accounts for K items base, base + T, ... (all of which exist).
+template <int KIND, int MODE, int K>
+__device__ __forceinline__ void account_items(const RunParams& P, const FastSmem& F, const HistSink& hs,
+                                              unsigned rbase, int sbase, const Cuts& cut, bool to_post,
+                                              unsigned long long& qs, unsigned long long& ev,
+                                              unsigned long long& ev2, int base, int T, bool tabbed) {
+    const NetDev& N = P.net;
+    const int lg = P.log2RB, mask = P.RB - 1;
+    int xa[K], xb[K];
+    unsigned long long qv[K];
+    bool ok[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int i = base + k * T;
+        const int lane = i & mask, s = i >> lg;
+        ok[k] = s < F.nvalid[lane];
+        unpack_state(N.nsp, ok[k] ? F.trace[i] : 0, xa[k], xb[k]);
+        const float ia0 = tabbed ? F.inv[xa[k]] : __frcp_rn(cums_f32<KIND>(N, F, xa[k], xb[k]).w);
+        qv[k] = q_of_f32(F.buf[i].x * ia0);
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        if (!ok[k]) continue;
+        const int i = base + k * T;
+        const int lane = i & mask, s = i >> lg;
+        const int x0 = xa[k], x1 = xb[k];
+        const unsigned long long q = qv[k];
+        const int sc = sbase + s;
+        const unsigned rr = rbase + (unsigned)lane;
+        if (MODE == kFirst) {
+            hs.add(x0, x1, q);
+            qs += q;
+            ++ev;
+        } else if (MODE == kRollback) {
+            hs.sub(x0, x1, q);
+            ++ev;
+        } else {
+            const unsigned long long pos = pos_of(sc, rr);
+            if (pos > cut.posC) continue;
+            ++ev;
+            if (MODE == kStepSum) {
+                atomicAdd(P.step_sum + sc, q);
+            } else if (MODE == kTauAt) {
+                if (sc == cut.nB) P.tau_at[rr] = q;
+                if (sc == cut.nT) P.tau_at[P.R + rr] = q;
+            } else {
+                if (pos > cut.posE || pos > cut.posT) continue;
+                const unsigned long long amt = (pos == cut.posT) ? cut.partT : q;
+                unsigned long long pre = 0, post = amt;
+                if (cut.posB != kNone) {
+                    if (pos < cut.posB) {
+                        pre = amt;
+                        post = 0;
+                    } else if (pos == cut.posB) {
+                        pre = cut.partB < amt ? cut.partB : amt;
+                        post = amt - pre;
+                    }
+                }
+                const int b = x0 * N.ystride + x1;
+                if (pre) atomicAdd(P.hist_pre + b, pre);
+                if (post) {
+                    if (hs.sh) hs.add(x0, x1, post);
+                    else atomicAdd((to_post ? P.hist_post : P.hist_pre) + b, post);
+                }
+                qs += amt;                   // included time
+                if (pos != cut.posT) ++ev2;  // included jumps (the truncated one does not jump)
+            }
+        }
+    }
+}
+
 template <int KIND, int MODE>
 __device__ __forceinline__ void account(const RunParams& P, const FastSmem& F, const HistSink& hs, unsigned rbase,
                                         int sbase, const Cuts& cut, bool to_post, unsigned long long& qs,
@@ -1047,75 +1121,19 @@ __device__ __forceinline__ void account(const RunParams& P, const FastSmem& F, c
         tid = threadIdx.x;
         T = blockDim.x;
     }
-    const NetDev& N = P.net;
-    const int lg = P.log2RB, mask = P.RB - 1;
-    const int total = P.B << lg;
+    const int total = P.B << P.log2RB;
     const bool tabbed = KIND == PARREP_SCHLOGL && F.tab;
-    for (int base = tid; base < total; base += 4 * T) {
-        int xa[4], xb[4];
-        unsigned long long qv[4];
-        bool ok[4];
-        // four independent items per pass: loads and conversions interleave
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int i = base + k * T;
-            const int ic = i < total ? i : base;
-            const int lane = ic & mask, s = ic >> lg;
-            ok[k] = i < total && s < F.nvalid[lane];
-            unpack_state(N.nsp, ok[k] ? F.trace[ic] : 0, xa[k], xb[k]);
-            const float ia0 = tabbed ? F.inv[xa[k]] : __frcp_rn(cums_f32<KIND>(N, F, xa[k], xb[k]).w);
-            qv[k] = q_of_f32(F.buf[ic].x * ia0);
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (!ok[k]) continue;
-            const int i = base + k * T;
-            const int lane = i & mask, s = i >> lg;
-            const int x0 = xa[k], x1 = xb[k];
-            const unsigned long long q = qv[k];
-            const int sc = sbase + s;
-            const unsigned rr = rbase + (unsigned)lane;
-            if (MODE == kFirst) {
-                hs.add(x0, x1, q);
-                qs += q;
-                ++ev;
-            } else if (MODE == kRollback) {
-                hs.sub(x0, x1, q);
-                ++ev;
-            } else {
-                const unsigned long long pos = pos_of(sc, rr);
-                if (pos > cut.posC) continue;
-                ++ev;
-                if (MODE == kStepSum) {
-                    atomicAdd(P.step_sum + sc, q);
-                } else if (MODE == kTauAt) {
-                    if (sc == cut.nB) P.tau_at[rr] = q;
-                    if (sc == cut.nT) P.tau_at[P.R + rr] = q;
-                } else {
-                    if (pos > cut.posE || pos > cut.posT) continue;
-                    const unsigned long long amt = (pos == cut.posT) ? cut.partT : q;
-                    unsigned long long pre = 0, post = amt;
-                    if (cut.posB != kNone) {
-                        if (pos < cut.posB) {
-                            pre = amt;
-                            post = 0;
-                        } else if (pos == cut.posB) {
-                            pre = cut.partB < amt ? cut.partB : amt;
-                            post = amt - pre;
-                        }
-                    }
-                    const int b = x0 * N.ystride + x1;
-                    if (pre) atomicAdd(P.hist_pre + b, pre);
-                    if (post) {
-                        if (hs.sh) hs.add(x0, x1, post);
-                        else atomicAdd((to_post ? P.hist_post : P.hist_pre) + b, post);
-                    }
-                    qs += amt;                   // included time
-                    if (pos != cut.posT) ++ev2;  // included jumps (the truncated one does not jump)
-                }
-            }
-        }
+    // Items i = step * RB + lane.  T and total are multiples of 32, so the
+    // bounds below are warp-uniform: up to four items per pass while four
+    // exist (their loads and conversions interleave), then one at a time.
+    int base = tid;
+    for (; base + 3 * T < total; base += 4 * T)
+        account_items<KIND, MODE, 4>(P, F, hs, rbase, sbase, cut, to_post, qs, ev, ev2, base, T, tabbed);
+    if (base + T < total) {
+        account_items<KIND, MODE, 2>(P, F, hs, rbase, sbase, cut, to_post, qs, ev, ev2, base, T, tabbed);
+        base += 2 * T;
     }
+    if (base < total) account_items<KIND, MODE, 1>(P, F, hs, rbase, sbase, cut, to_post, qs, ev, ev2, base, T, tabbed);
 }
 
 // One chunk (S steps) of the parallel step for the whole block, in a mode.
@@ -1510,20 +1528,12 @@ __device__ void decorrelate_f32(const RunParams& P, const FastSmem& F, const His
         {
             const unsigned long long p0 = step0 >> 1;
             const int npairs = (int)(((step0 + (unsigned long long)M - 1) >> 1) - p0) + 1;
-            for (int base = threadIdx.x; base < npairs; base += 4 * T) {
-                uint4 w[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const unsigned long long pr = p0 + (unsigned long long)(base + k * T);
-                    w[k] = philox10(make_uint4((unsigned)(pr >> 32), (unsigned)pr, cycle, kTagDecorr), key);
-                }
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    if (base + k * T >= npairs) continue;
-                    const long long ke = (long long)((p0 + (unsigned long long)(base + k * T)) << 1) - (long long)step0;
-                    if (ke >= 0 && ke < M) buf[ke] = make_float2(-logf(u01f(w[k].x)), u01f(w[k].y));
-                    if (ke + 1 >= 0 && ke + 1 < M) buf[ke + 1] = make_float2(-logf(u01f(w[k].z)), u01f(w[k].w));
-                }
+            for (int i = threadIdx.x; i < npairs; i += T) {
+                const unsigned long long pr = p0 + (unsigned long long)i;
+                const uint4 w = philox10(make_uint4((unsigned)(pr >> 32), (unsigned)pr, cycle, kTagDecorr), key);
+                const long long ke = (long long)(pr << 1) - (long long)step0;
+                if (ke >= 0 && ke < M) buf[ke] = make_float2(-logf(u01f(w.x)), u01f(w.y));
+                if (ke + 1 >= 0 && ke + 1 < M) buf[ke + 1] = make_float2(-logf(u01f(w.z)), u01f(w.w));
             }
         }
         __syncthreads();
