@@ -260,7 +260,7 @@ def main():
                        x0_uniform_hi=c["x0_uniform_hi"], thresh=c["thresh"], precision=args.precision,
                        T_burn=c["T_burn"] * T_end / c["T_end"], block_threads=args.block_threads,
                        chunk_steps=args.chunk_steps)
-            st = h.run(T_end, seed0 + 777 + i)
+            st = h.run(T_end, seed0 + args.warmup + i)  # the timed steps' seeds: the same work
             hist = h.histogram()
             fim = h.fim()
             h.close()

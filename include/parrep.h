@@ -79,13 +79,16 @@ typedef struct {
     int32_t thresh_mode;   /* PARREP_THRESH_TIME (default) or _STEPS */
     int32_t precision;     /* PARREP_FP64 (default) or PARREP_FP32 propensities */
     int32_t fv_group;      /* Fleming-Viot group size: 1,2,4,8,16 or 32 (default 32) */
-    int32_t block_threads; /* CUDA block size, multiple of 32 up to 512 (0 = auto) */
+    int32_t block_threads; /* CUDA block size, multiple of 32 up to 384 (0 = auto) */
     int32_t chunk_steps;   /* lockstep steps between escape votes (0 = auto) */
     int32_t debug_stall_barrier; /* fault injection: >= 0 makes block 0 leave at that
                                     grid barrier so the others time out; -1 = off */
     int32_t serial_stages; /* FP32 form: 1 runs the staged chunks without the owner /
                               helper overlap (same results; for tests), 0 = auto */
-    int32_t reserved;
+    int32_t max_blocks;    /* cap on the blocks of the run kernel (0 = auto: all groups of
+                              replicas at once when the grid fits, else a full co-resident
+                              grid); fewer blocks than groups run several groups per
+                              block with the same results */
     double T_burn;         /* FIM / RER integrate over [T_burn, T_end] (default 0) */
     double wait_timeout_s; /* device wait limit without progress (default 10 s) */
     void* stream;          /* cudaStream_t to run on (NULL = legacy default stream) */

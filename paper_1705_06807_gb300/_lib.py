@@ -38,7 +38,7 @@ class parrep_regions(C.Structure):
 class parrep_options(C.Structure):
     _fields_ = [("thresh_mode", C.c_int32), ("precision", C.c_int32), ("fv_group", C.c_int32),
                 ("block_threads", C.c_int32), ("chunk_steps", C.c_int32), ("debug_stall_barrier", C.c_int32),
-                ("serial_stages", C.c_int32), ("reserved", C.c_int32),
+                ("serial_stages", C.c_int32), ("max_blocks", C.c_int32),
                 ("T_burn", C.c_double), ("wait_timeout_s", C.c_double), ("stream", C.c_void_p)]
 
 

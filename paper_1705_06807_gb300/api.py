@@ -75,7 +75,8 @@ class ParRep:
     def __init__(self, spec: dict, n_replicas: int, t_corr: float, t_phase: float, *, x0=None,
                  x0_uniform_hi: int = 0, thresh: str = "time", precision: str = "f64", fv_group: int = 32,
                  T_burn: float = 0.0, block_threads: int = 0, chunk_steps: int = 0, stream=None,
-                 wait_timeout_s: float = 10.0, debug_stall_barrier: int = -1, serial_stages: int = 0):
+                 wait_timeout_s: float = 10.0, debug_stall_barrier: int = -1, serial_stages: int = 0,
+                 max_blocks: int = 0):
         self._lib = L.load()
         self.spec = spec
         self.L = 4 if spec["kind"] == "schlogl" else 6
@@ -89,10 +90,11 @@ class ParRep:
         self.set_options(thresh=thresh, precision=precision, fv_group=fv_group, T_burn=T_burn,
                          block_threads=block_threads, chunk_steps=chunk_steps, stream=stream,
                          wait_timeout_s=wait_timeout_s, debug_stall_barrier=debug_stall_barrier,
-                         serial_stages=serial_stages)
+                         serial_stages=serial_stages, max_blocks=max_blocks)
 
     def set_options(self, *, thresh="time", precision="f64", fv_group=32, T_burn=0.0, block_threads=0,
-                    chunk_steps=0, stream=None, wait_timeout_s=10.0, debug_stall_barrier=-1, serial_stages=0):
+                    chunk_steps=0, stream=None, wait_timeout_s=10.0, debug_stall_barrier=-1, serial_stages=0,
+                    max_blocks=0):
         o = L.parrep_options()
         self._lib.parrep_default_options(C.byref(o))
         o.thresh_mode = L.PARREP_THRESH_STEPS if thresh == "steps" else L.PARREP_THRESH_TIME
@@ -104,6 +106,7 @@ class ParRep:
         o.wait_timeout_s = float(wait_timeout_s)
         o.debug_stall_barrier = int(debug_stall_barrier)
         o.serial_stages = int(serial_stages)
+        o.max_blocks = int(max_blocks)
         if stream is not None:
             o.stream = C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
         _check(self._lib.parrep_set_options(self.h, C.byref(o)), self.h)

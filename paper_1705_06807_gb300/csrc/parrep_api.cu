@@ -38,6 +38,7 @@ struct parrep_s {
     double *d_gradU_n = nullptr, *d_gradV_n = nullptr, *d_c = nullptr, *d_s = nullptr;
     RunCtl* d_ctl = nullptr;
     unsigned long long *d_hist_pre = nullptr, *d_hist_post = nullptr, *d_step_sum = nullptr, *d_tau_at = nullptr;
+    int2* d_xstate = nullptr;  // [3 R]: replica state, chunk-start state, exit state
     CycleRecDev* d_log = nullptr;
     double *d_out = nullptr, *d_out2 = nullptr, *d_fim = nullptr, *d_rer = nullptr, *d_cprime = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -77,7 +78,7 @@ extern "C" void parrep_default_options(parrep_options* o) {
     o->chunk_steps = 0;
     o->debug_stall_barrier = -1;
     o->serial_stages = 0;
-    o->reserved = 0;
+    o->max_blocks = 0;
     o->T_burn = 0.0;
     o->wait_timeout_s = 10.0;
     o->stream = nullptr;
@@ -203,7 +204,7 @@ static cudaError_t upload(T** dst, const std::vector<T>& v) {
 static void free_all(parrep_t h) {
     void* ptrs[] = {h->d_prodU_d, h->d_prodV_d, h->d_prodU_f, h->d_prodV_f, h->d_gradU_n, h->d_gradV_n,
                     h->d_c, h->d_s, h->d_ctl, h->d_hist_pre, h->d_hist_post, h->d_step_sum, h->d_tau_at,
-                    h->d_log, h->d_out, h->d_out2, h->d_fim, h->d_rer, h->d_cprime};
+                    h->d_log, h->d_out, h->d_out2, h->d_fim, h->d_rer, h->d_cprime, h->d_xstate};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->ev0) cudaEventDestroy(h->ev0);
@@ -254,6 +255,7 @@ extern "C" int parrep_create(const parrep_network* net, int64_t n_replicas, cons
     TRY(cudaMalloc((void**)&h->d_step_sum, sizeof(unsigned long long) * kMaxChunk));
     TRY(cudaMalloc((void**)&h->d_tau_at, sizeof(unsigned long long) * 2 * (size_t)n_replicas));
     TRY(cudaMalloc((void**)&h->d_log, sizeof(CycleRecDev) * kLogCap));
+    TRY(cudaMalloc((void**)&h->d_xstate, sizeof(int2) * 3 * (size_t)n_replicas));
     TRY(cudaMalloc((void**)&h->d_out, sizeof(double) * h->nbins));
     TRY(cudaMalloc((void**)&h->d_out2, sizeof(double) * h->nbins));
     TRY(cudaMalloc((void**)&h->d_fim, sizeof(double) * 36));
@@ -289,9 +291,10 @@ extern "C" int parrep_set_options(parrep_t h, const parrep_options* o) {
     const int g = o->fv_group;
     if (!(g == 1 || g == 2 || g == 4 || g == 8 || g == 16 || g == 32))
         return fail(h, PARREP_EINVAL, "fv_group must be 1, 2, 4, 8, 16 or 32");
-    if (o->block_threads < 0 || o->block_threads > 512 || (o->block_threads % 32) != 0)
-        return fail(h, PARREP_EINVAL, "block_threads must be a multiple of 32 up to 512 (0 = auto)");
+    if (o->block_threads < 0 || o->block_threads > kMaxThreads || (o->block_threads % 32) != 0)
+        return fail(h, PARREP_EINVAL, "block_threads must be a multiple of 32 up to 384 (0 = auto)");
     if (o->chunk_steps < 0 || o->chunk_steps > kMaxChunk) return fail(h, PARREP_EINVAL, "chunk_steps");
+    if (o->max_blocks < 0) return fail(h, PARREP_EINVAL, "max_blocks must be >= 0");
     if (!(o->T_burn >= 0.0) || !(o->T_burn < kTEndLimit)) return fail(h, PARREP_EINVAL, "T_burn");
     if (!(o->wait_timeout_s > 0.0) || !(o->wait_timeout_s <= 3600.0)) return fail(h, PARREP_EINVAL, "wait_timeout_s");
     if (o->thresh_mode == PARREP_THRESH_STEPS) {
@@ -385,12 +388,19 @@ static int plan_launch(parrep_t h, Plan& pl) {
             pl.smem = with_hist ? h->nbins * 8 : 0;
             int ea = kernel_attrs(prec, kind, &per_sm, pl.smem, threads);
             if (ea != 0) return cuda_fail(h, (cudaError_t)ea, "kernel attributes");
-            if ((long long)per_sm * nsm >= pl.grid) return PARREP_OK;
+            if (per_sm < 1) continue;
+            // more replica groups than co-resident blocks: blocks take several
+            if ((long long)per_sm * nsm < pl.grid) pl.grid = per_sm * nsm;
+            if (h->opt.max_blocks > 0 && pl.grid > h->opt.max_blocks) pl.grid = h->opt.max_blocks;
+            return PARREP_OK;
         }
-        return fail(h, PARREP_ENOMEM, "n_replicas exceeds one co-resident cooperative grid");
+        return fail(h, PARREP_ENOMEM, "the run kernel does not fit on one SM");
     }
     const int T = h->opt.block_threads > 0 ? h->opt.block_threads : 384;
-    for (int RB = 32; RB <= 512; RB *= 2) {
+    // the smallest RB whose grid is co-resident; if none is, RB = 32 on a
+    // full co-resident grid, each block taking several groups of replicas
+    for (int pass = 0; pass < 2; ++pass)
+    for (int RB = 32; RB <= (pass ? 32 : 256); RB *= 2) {  // RB <= 256 keeps threads <= kMaxThreads
         const int threads = RB > T ? RB : T;
         const long long grid = (h->R + RB - 1) / RB;
         for (int cfg = 3; cfg >= 0; --cfg) {
@@ -403,9 +413,11 @@ static int plan_launch(parrep_t h, Plan& pl) {
             if (smem > 200 * 1024) continue;
             int ea = kernel_attrs(prec, kind, &per_sm, smem, threads);
             if (ea != 0) return cuda_fail(h, (cudaError_t)ea, "kernel attributes");
-            if ((long long)per_sm * nsm >= grid) {
+            if (per_sm < 1) continue;
+            if ((long long)per_sm * nsm >= grid || pass == 1) {
                 pl.threads = threads;
-                pl.grid = (int)grid;
+                pl.grid = (long long)per_sm * nsm >= grid ? (int)grid : per_sm * nsm;
+                if (h->opt.max_blocks > 0 && pl.grid > h->opt.max_blocks) pl.grid = h->opt.max_blocks;
                 pl.smem = smem;
                 const int S = h->opt.chunk_steps > 0 ? h->opt.chunk_steps : 512;
                 pl.S = ((S + pl.B - 1) / pl.B) * pl.B;
@@ -413,7 +425,7 @@ static int plan_launch(parrep_t h, Plan& pl) {
             }
         }
     }
-    return fail(h, PARREP_ENOMEM, "n_replicas exceeds one co-resident cooperative grid");
+    return fail(h, PARREP_ENOMEM, "the run kernel does not fit on one SM");
 }
 
 extern "C" int parrep_run(parrep_t h, double T_end, uint64_t seed) {
@@ -469,6 +481,10 @@ extern "C" int parrep_run(parrep_t h, double T_end, uint64_t seed) {
     p.hist_post = h->d_hist_post;
     p.step_sum = h->d_step_sum;
     p.tau_at = h->d_tau_at;
+    p.nblk = grid;
+    p.xs = h->d_xstate;
+    p.xk = h->d_xstate + h->R;
+    p.xe = h->d_xstate + 2 * h->R;
     p.log = h->d_log;
     p.log_cap = kLogCap;
     p.timeout_ns = (long long)(h->opt.wait_timeout_s * 1e9);

@@ -23,6 +23,9 @@ enum Tag : uint32_t { kTagInit = 0, kTagDecorr = 1, kTagDephase = 2, kTagFV = 3,
 
 constexpr unsigned long long kNone = ~0ull;
 
+// Largest block of the run kernels (their register budget is set for it).
+constexpr int kMaxThreads = 384;
+
 // Network as the kernels see it (Sec. II.A).  Schloegl: lambda_j = A[j] h_j(x)
 // with A[j] = c_j s_j.  Toggle: production rates come from host-built tables
 // indexed by the repressor count, degradation is d * count.
@@ -98,6 +101,10 @@ struct RunParams {
     unsigned long long q_Tend, q_Tburn;
     unsigned long long seed;
     int x00, x01, x0_hi;
+    int nblk;      // blocks serving this instance (the grid, or a gang of a batch)
+    int2* xs;      // [R] replica state between phases
+    int2* xk;      // [R] replica state at the start of the current chunk
+    int2* xe;      // [R] state a replica escaped to in the current chunk
     RunCtl* ctl;
     unsigned long long* hist_pre;
     unsigned long long* hist_post;

@@ -271,6 +271,7 @@ __device__ __forceinline__ void block_reduce4(BlockScratch& s, unsigned long lon
 // ---------------------------------------------------------------------------
 struct BarState {
     int index;
+    int lb, nblk;  // this block's index among the blocks serving the instance, and their number
 };
 
 __device__ bool grid_sync(const RunParams& P, BarState& bs) {
@@ -278,7 +279,7 @@ __device__ bool grid_sync(const RunParams& P, BarState& bs) {
     RunCtl* ctl = P.ctl;
     const int idx = bs.index++;
     __syncthreads();
-    if (P.stall_barrier >= 0 && idx == P.stall_barrier && blockIdx.x == 0) {
+    if (P.stall_barrier >= 0 && idx == P.stall_barrier && bs.lb == 0) {
         // fault injection: block 0 leaves without arriving
         return false;
     }
@@ -287,7 +288,7 @@ __device__ bool grid_sync(const RunParams& P, BarState& bs) {
         __threadfence();
         atomicAdd(&ctl->progress, 1ull);
         const unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
-        if (arrived == gridDim.x - 1) {
+        if (arrived == (unsigned)bs.nblk - 1) {
             atomicExch(&ctl->bar_count, 0u);
             __threadfence();
             atomicAdd(&ctl->bar_gen, 1u);
@@ -1736,20 +1737,57 @@ __device__ void decorrelate_f32(const RunParams& P, const FastSmem& F, const His
 // ---------------------------------------------------------------------------
 // the persistent ParRep kernel
 // ---------------------------------------------------------------------------
+// A replay pass (MODE) of the current chunk over this block's virtual
+// blocks, each replica from its chunk-start state P.xk.
+template <bool F32, int KIND, int MODE>
+__device__ __forceinline__ void replay_vblocks(const RunParams& P, const FastSmem& F, const HistSink& hs, int lb,
+                                               int nvb, const RegionTest& rt, unsigned cycle, unsigned n0, uint2 key,
+                                               const Cuts& cut, bool to_post, unsigned long long& ev_replay,
+                                               PhaseClock& pc, unsigned long long* inc_q = nullptr,
+                                               unsigned long long* inc_ev = nullptr) {
+    const bool owner = (int)threadIdx.x < P.RB;
+    for (int vb = lb; vb < nvb; vb += P.nblk) {
+        const unsigned rbase = (unsigned)vb * (unsigned)P.RB, r = rbase + threadIdx.x;
+        const bool active = owner && (long long)r < (long long)P.R;
+        int y0 = 0, y1 = 0;
+        if (active) {
+            const int2 xv = P.xk[r];
+            y0 = xv.x;
+            y1 = xv.y;
+        }
+        unsigned long long d0 = 0, d1 = 0;
+        unsigned long long& q = MODE == kPrecise ? *inc_q : d0;
+        unsigned long long& e = MODE == kPrecise ? *inc_ev : d1;
+        if (F32) {
+            unsigned long long k0 = kNone, k1 = kNone;
+            int e0 = 0, e1 = 0;
+            chunk_f32<KIND, MODE>(P, F, hs, active, rbase, r, rt, cycle, n0, key, y0, y1, cut, to_post, k0, k1, e0,
+                                  e1, q, ev_replay, e, pc);
+        } else if (active) {
+            replay_chunk<F32, MODE>(P, hs, y0, y1, r, rt.W, cycle, n0, cut, to_post, q, e, ev_replay);
+        }
+    }
+}
+
+// One ParRep run (Algorithm 1) of the instance P by the P.nblk blocks that
+// serve it; lb is this block's index among them.  Replicas come in virtual
+// blocks of RB (vb = 0 .. ceil(R / RB) - 1); block lb takes vb = lb,
+// lb + nblk, ...  A replica's state lives in P.xs between the phases (and
+// its chunk-start state in P.xk, its exit state in P.xe), so an instance can
+// have more replicas than its blocks have owner threads.  Lockstep is logical:
+// each replica takes the same steps whatever block takes it and in whatever
+// order, so every result is independent of nblk.
 template <bool F32, int KIND>
-__global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ BlockScratch red;
+__device__ __forceinline__ void run_instance(const RunParams& P, int lb, unsigned char* smem, BlockScratch& red) {
     RunCtl* ctl = P.ctl;
     const NetDev& N = P.net;
+    const int nblk = P.nblk;
+    const int nvb = (P.R + P.RB - 1) / P.RB;
     const bool owner = (int)threadIdx.x < P.RB;
-    const unsigned rbase = blockIdx.x * (unsigned)P.RB;
-    const unsigned r = rbase + threadIdx.x;
-    const bool active = owner && (long long)r < (long long)P.R;
-    const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+    const bool leader = lb == 0 && threadIdx.x == 0;
     const uint2 key = seed_key(P.seed);
     unsigned long long* sh_hist = (unsigned long long*)smem;
-    BarState bs{0};
+    BarState bs{0, lb, nblk};
     PhaseClock pc{};
     FastSmem F{};
     unsigned* limb_lo = nullptr;
@@ -1815,7 +1853,7 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
         // ---------------- decorrelation (serial) ----------------
         pc.start();
         if (F32) {
-            if (blockIdx.x == 0 && !ldv(&ctl->done))
+            if (lb == 0 && !ldv(&ctl->done))
                 decorrelate_f32<KIND>(P, F, hs, period_post, pc);
         } else {
             if (leader && !ctl->done) leader_decorrelate<F32>(P);
@@ -1839,13 +1877,21 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
                 hs.g = P.hist_post;
             }
             // ---------------- dephasing ----------------
-            int x0, x1, derr;
             pc.start();
-            if (F32) derr = dephase_f32<KIND>(P, F, rt, active, rbase, r, xt0, xt1, np, cycle, key, x0, x1);
-            else derr = dephase_warp<F32>(N, active, r, P.G, W, xt0, xt1, np, cycle, key, x0, x1);
-            __syncthreads();
+            {
+                int derr = 0;
+                for (int vb = lb; vb < nvb; vb += nblk) {
+                    const unsigned rbase = (unsigned)vb * (unsigned)P.RB, r = rbase + threadIdx.x;
+                    const bool active = owner && (long long)r < (long long)P.R;
+                    int x0, x1;
+                    if (F32) derr |= dephase_f32<KIND>(P, F, rt, active, rbase, r, xt0, xt1, np, cycle, key, x0, x1);
+                    else derr |= dephase_warp<F32>(N, active, r, P.G, W, xt0, xt1, np, cycle, key, x0, x1);
+                    if (active) P.xs[r] = make_int2(x0, x1);
+                    __syncthreads();
+                }
+                if (derr && (threadIdx.x & 31) == 0) atomicCAS(&ctl->status, 0, PARREP_ERANGE);
+            }
             pc.lap(kPhDephase);
-            if (derr && (threadIdx.x & 31) == 0) atomicCAS(&ctl->status, 0, PARREP_ERANGE);
             if (leader) ctl->ev_dephase += (unsigned long long)np * (unsigned long long)P.R;
             // ---------------- parallel step ----------------
             unsigned n0 = 0;
@@ -1862,37 +1908,53 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
                     ctl->inc_sum[s1] = 0;
                     ctl->inc_ev[s1] = 0;
                 }
-                const int xs0 = x0, xs1 = x1;
                 unsigned long long mykey = kNone, myoob = kNone, qsum = 0, ev = 0;
-                int xe0 = 0, xe1 = 0;
                 Cuts none{kNone, kNone, kNone, 0, kNone, 0, -1, -1};
-                if (F32) {
-                    unsigned long long dummy = 0;
-                    chunk_f32<KIND, kFirst>(P, F, hs, active, rbase, r, rt, cycle, n0, key, x0, x1, none, period_post,
-                                            mykey, myoob, xe0, xe1, qsum, ev, dummy, pc);
-                } else if (active) {
-                    for (int s = 0; s < P.S; ++s) {
-                        const uint4 w = par_words<F32>(r, n0 + (unsigned)s, cycle, key);
-                        unsigned long long q = 0;
-                        const int J = ssa_draw<F32, true>(N, x0, x1, w, q);
-                        qsum += q;
-                        ++ev;
-                        hs.add(x0, x1, q);
-                        int a0 = x0, a1 = x1;
-                        apply(N, J, a0, a1);
-                        if (out_of_range(N, a0, a1)) {
-                            myoob = pos_of(s, r);
-                            break;
-                        }
-                        if (region_of(N, a0, a1) != W) {
-                            mykey = pos_of(s, r);
-                            xe0 = a0;
-                            xe1 = a1;
-                            break;
-                        }
-                        x0 = a0;
-                        x1 = a1;
+                for (int vb = lb; vb < nvb; vb += nblk) {
+                    const unsigned rbase = (unsigned)vb * (unsigned)P.RB, r = rbase + threadIdx.x;
+                    const bool active = owner && (long long)r < (long long)P.R;
+                    int x0 = 0, x1 = 0, xe0 = 0, xe1 = 0;
+                    if (active) {
+                        const int2 xv = P.xs[r];
+                        x0 = xv.x;
+                        x1 = xv.y;
+                        P.xk[r] = xv;
                     }
+                    unsigned long long k0 = kNone, k1 = kNone;
+                    if (F32) {
+                        unsigned long long dummy = 0;
+                        chunk_f32<KIND, kFirst>(P, F, hs, active, rbase, r, rt, cycle, n0, key, x0, x1, none,
+                                                period_post, k0, k1, xe0, xe1, qsum, ev, dummy, pc);
+                    } else if (active) {
+                        for (int s = 0; s < P.S; ++s) {
+                            const uint4 w = par_words<F32>(r, n0 + (unsigned)s, cycle, key);
+                            unsigned long long q = 0;
+                            const int J = ssa_draw<F32, true>(N, x0, x1, w, q);
+                            qsum += q;
+                            ++ev;
+                            hs.add(x0, x1, q);
+                            int a0 = x0, a1 = x1;
+                            apply(N, J, a0, a1);
+                            if (out_of_range(N, a0, a1)) {
+                                k1 = pos_of(s, r);
+                                break;
+                            }
+                            if (region_of(N, a0, a1) != W) {
+                                k0 = pos_of(s, r);
+                                xe0 = a0;
+                                xe1 = a1;
+                                break;
+                            }
+                            x0 = a0;
+                            x1 = a1;
+                        }
+                    }
+                    if (active) {
+                        P.xs[r] = make_int2(x0, x1);
+                        if (k0 != kNone) P.xe[r] = make_int2(xe0, xe1);
+                    }
+                    mykey = k0 < mykey ? k0 : mykey;
+                    myoob = k1 < myoob ? k1 : myoob;
                 }
                 const int slot = (int)(chunk_c % 3);
                 pc.start();
@@ -1931,35 +1993,19 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
                 // ------------- special chunk: escape, range error or time cut -------------
                 if (leader) ctl->special += 1;
                 pc.start();
-                {
-                    unsigned long long d0 = 0, d1 = 0, k0 = kNone, k1 = kNone;
-                    int y0 = xs0, y1 = xs1, e0 = 0, e1 = 0;
-                    if (F32)
-                        chunk_f32<KIND, kRollback>(P, F, hs, active, rbase, r, rt, cycle, n0, key, y0, y1, none,
-                                                   period_post, k0, k1, e0, e1, d0, ev_replay, d1, pc);
-                    else if (active)
-                        replay_chunk<F32, kRollback>(P, hs, xs0, xs1, r, W, cycle, n0, none, period_post, d0, d1,
-                                                     ev_replay);
-                }
+                replay_vblocks<F32, KIND, kRollback>(P, F, hs, lb, nvb, rt, cycle, n0, key, none, period_post,
+                                                     ev_replay, pc);
                 Cuts cut{kNone, kNone, kNone, 0, kNone, 0, -1, -1};
                 cut.posE = ekey;
                 cut.posC = ekey < okey ? ekey : okey;
                 if (Ts + csum >= q_next) {
                     // a threshold may be crossed: find the step, then the replica
-                    if (blockIdx.x == 0) {
+                    if (lb == 0) {
                         for (int j = threadIdx.x; j < P.S; j += blockDim.x) P.step_sum[j] = 0;
                     }
                     if (!grid_sync(P, bs)) goto out;
-                    {
-                        unsigned long long d0 = 0, d1 = 0, k0 = kNone, k1 = kNone;
-                        int y0 = xs0, y1 = xs1, e0 = 0, e1 = 0;
-                        if (F32)
-                            chunk_f32<KIND, kStepSum>(P, F, hs, active, rbase, r, rt, cycle, n0, key, y0, y1, cut,
-                                                      period_post, k0, k1, e0, e1, d0, ev_replay, d1, pc);
-                        else if (active)
-                            replay_chunk<F32, kStepSum>(P, hs, xs0, xs1, r, W, cycle, n0, cut, period_post, d0, d1,
-                                                        ev_replay);
-                    }
+                    replay_vblocks<F32, KIND, kStepSum>(P, F, hs, lb, nvb, rt, cycle, n0, key, cut, period_post,
+                                                        ev_replay, pc);
                     if (!grid_sync(P, bs)) goto out;
                     unsigned long long baseB = 0, baseT = 0;
                     {
@@ -1978,20 +2024,15 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
                         }
                     }
                     if (cut.nB >= 0 || cut.nT >= 0) {
-                        if (active) {
-                            P.tau_at[r] = 0;
-                            P.tau_at[P.R + r] = 0;
+                        for (int vb = lb; vb < nvb; vb += nblk) {
+                            const unsigned r = (unsigned)vb * (unsigned)P.RB + threadIdx.x;
+                            if (owner && (long long)r < (long long)P.R) {
+                                P.tau_at[r] = 0;
+                                P.tau_at[P.R + r] = 0;
+                            }
                         }
-                        {
-                            unsigned long long d0 = 0, d1 = 0, k0 = kNone, k1 = kNone;
-                            int y0 = xs0, y1 = xs1, e0 = 0, e1 = 0;
-                            if (F32)
-                                chunk_f32<KIND, kTauAt>(P, F, hs, active, rbase, r, rt, cycle, n0, key, y0, y1, cut,
-                                                        period_post, k0, k1, e0, e1, d0, ev_replay, d1, pc);
-                            else if (active)
-                                replay_chunk<F32, kTauAt>(P, hs, xs0, xs1, r, W, cycle, n0, cut, period_post, d0,
-                                                          d1, ev_replay);
-                        }
+                        replay_vblocks<F32, KIND, kTauAt>(P, F, hs, lb, nvb, rt, cycle, n0, key, cut, period_post,
+                                                          ev_replay, pc);
                         if (!grid_sync(P, bs)) goto out;
                         if (leader) {
                             ctl->posB = kNone;
@@ -2044,15 +2085,8 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
                 {
                     unsigned long long inc_q = 0, inc_ev = 0;
                     const bool tp = period_post || cut.posB != kNone;
-                    if (F32) {
-                        unsigned long long k0 = kNone, k1 = kNone;
-                        int y0 = xs0, y1 = xs1, e0 = 0, e1 = 0;
-                        chunk_f32<KIND, kPrecise>(P, F, hs, active, rbase, r, rt, cycle, n0, key, y0, y1, cut, tp, k0,
-                                                  k1, e0, e1, inc_q, ev_replay, inc_ev, pc);
-                    } else if (active) {
-                        replay_chunk<F32, kPrecise>(P, hs, xs0, xs1, r, W, cycle, n0, cut, tp, inc_q, inc_ev,
-                                                    ev_replay);
-                    }
+                    replay_vblocks<F32, KIND, kPrecise>(P, F, hs, lb, nvb, rt, cycle, n0, key, cut, tp, ev_replay,
+                                                        pc, &inc_q, &inc_ev);
                     unsigned long long a = kNone, b = kNone;
                     block_reduce4(red, a, b, inc_q, inc_ev);
                     if (threadIdx.x == 0) {
@@ -2064,11 +2098,6 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
                     burn_done = 1;
                     period_post = 1;
                     hs.g = P.hist_post;
-                }
-                // the escaping replica publishes X^K_{N*}
-                if (active && ekey != kNone && (unsigned)(ekey & 0xffffffffu) == r && !(cut.posT <= cut.posE)) {
-                    ctl->xe0 = xe0;
-                    ctl->xe1 = xe1;
                 }
                 pc.lap(kPhSpecial);
                 if (!grid_sync(P, bs)) goto out;
@@ -2087,8 +2116,10 @@ __global__ void __launch_bounds__(512) parrep_run_kernel(RunParams P) {
                         rec.n_star = (long long)n0 + (long long)((t_end ? cut.posT : ekey) >> 32) + 1;
                         rec.k = t_end ? -1 : (long long)(ekey & 0xffffffffu);
                         if (!t_end) {
-                            ctl->xt0 = ldv(&ctl->xe0);
-                            ctl->xt1 = ldv(&ctl->xe1);
+                            // the escaping replica's X^K_{N*}, written in the first pass
+                            const int2 xe = __ldcg(P.xe + (ekey & 0xffffffffu));
+                            ctl->xt0 = xe.x;
+                            ctl->xt1 = xe.y;
                             ctl->escapes += 1;
                         }
                         rec.xt0 = ctl->xt0;
@@ -2120,6 +2151,14 @@ out:
     if (threadIdx.x == 0)
         for (int i = 0; i < 12; ++i)
             if (pc.acc[i]) atomicAdd(&ctl->phase_cycles[i], pc.acc[i]);
+}
+
+// One instance on the whole grid.
+template <bool F32, int KIND>
+__global__ void __launch_bounds__(kMaxThreads) parrep_run_kernel(RunParams P) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ BlockScratch red;
+    run_instance<F32, KIND>(P, (int)blockIdx.x, smem, red);
 }
 
 // ---------------------------------------------------------------------------

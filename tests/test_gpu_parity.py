@@ -234,9 +234,10 @@ def test_chunk_and_block_shape_do_not_change_results():
     """The cut is exact, so the chunk length and the block size are invisible:
     all fixed-point sums agree to the last bit."""
     res = []
-    for S, B in [(5, 32), (64, 128), (512, 64)]:
+    # max_blocks = 1: one block takes all three groups of 32 replicas in turn
+    for S, B, M in [(5, 32, 0), (64, 128, 0), (512, 64, 0), (64, 32, 1), (37, 32, 2)]:
         g = ParRep(V10, 77, 200, 200, x0=[2], thresh="steps", fv_group=16, T_burn=50.0, chunk_steps=S,
-                   block_threads=B)
+                   block_threads=B, max_blocks=M)
         g.run(150.0, 99)
         pre, post = g.histogram_raw()
         res.append((pre, post, g.cycle_log(), g.stats()["events_parallel_useful"]))
@@ -302,9 +303,9 @@ def test_fp32_staged_path_is_shape_invariant(spec, x0):
     cycle log or the event counts across chunk lengths and block sizes."""
     thresh, tc = ("steps", 200) if spec["kind"] == "schlogl" else ("time", 0.5)
     res = []
-    for S, B in [(32, 64), (256, 256), (1024, 128)]:
+    for S, B, M in [(32, 64, 0), (256, 256, 0), (1024, 128, 0), (64, 128, 1), (96, 384, 2)]:
         g = ParRep(spec, 77, tc, tc, x0=x0, thresh=thresh, precision="f32", fv_group=16, T_burn=30.0,
-                   chunk_steps=S, block_threads=B)
+                   chunk_steps=S, block_threads=B, max_blocks=M)
         g.run(90.0, 99)
         pre, post = g.histogram_raw()
         res.append((pre, post, g.cycle_log(), g.stats()["events_parallel_useful"]))
