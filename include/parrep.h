@@ -233,6 +233,81 @@ int parrep_ssa(const parrep_network* net, int32_t precision, int64_t n_traj, dou
 int parrep_ssa_noalloc(const parrep_network* net, int32_t precision, int64_t n_traj, double T_end, uint64_t seed,
                        double* hist_out, int64_t len, int64_t* events_out, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Batches: many independent ParRep instances (different networks, system
+ * sizes, replica counts, thresholds, T_end and seeds) in one persistent
+ * cooperative launch.  Each instance is an ordinary handle made with
+ * parrep_create / parrep_set_options; a batch groups n of them (it does not
+ * own them) and runs Algorithm 1 for all at once.  After parrep_batch_run
+ * every handle holds exactly the results parrep_run(h, T_end[i], seed[i])
+ * would have given it (histograms, FIM, RER, statistics, cycle log -- read
+ * with the single-run calls), bit for bit: an instance's arithmetic does not
+ * depend on the blocks that run it.
+ *
+ * Scheduling: each instance gets a gang of blocks sized to its estimated
+ * work (holding-time events ~ T_end * a0(x_0) plus the dephasing jumps) and
+ * capped by its groups of replicas; gangs are placed longest-first on the
+ * co-resident grid, every block working through its list of (instance,
+ * block index) in the schedule's start order.  A gang smaller than an
+ * instance's replica groups takes several groups per block.
+ * --------------------------------------------------------------------------- */
+typedef struct parrep_batch_s* parrep_batch_t;
+
+typedef struct {
+    int32_t block_threads;      /* threads per block; 0 = chosen by the autotuner */
+    int32_t replicas_per_block; /* FP32 form: owner threads per block (32, 64, 128 or 256);
+                                   0 = chosen by the autotuner.  FP64 form: = block_threads */
+    int32_t autotune;           /* 1 (default): the first run times candidate block shapes on a
+                                   shortened copy of the batch (T_end scaled by tune_fraction)
+                                   and keeps the fastest; 0: defaults (384 x 32 / 128) */
+    int32_t use_graph;          /* 1 (default): capture the launch sequence (parameter upload,
+                                   reset, batch kernel, read-back) in a CUDA graph and replay it
+                                   while the shape stays the same */
+    double tune_fraction;       /* default 0.05 */
+    double wait_timeout_s;      /* device wait limit without progress anywhere (default 10 s) */
+    void* stream;               /* cudaStream_t (NULL = legacy default stream) */
+} parrep_batch_options;
+
+typedef struct {
+    int32_t block_threads, replicas_per_block;
+    int32_t grid_blocks;        /* co-resident blocks of the launch */
+    int32_t n_items;            /* (instance, block) pairs of the schedule */
+    int32_t graph;              /* 1: the last run replayed a CUDA graph */
+    int32_t tuned_trials;       /* shapes timed by the autotuner so far */
+    float kernel_ms;            /* last run: device time of the launch sequence (parameter
+                                   upload, reset, batch kernel, read-back) */
+    float tune_ms;              /* wall time spent autotuning */
+    double est_makespan;        /* schedule's makespan in estimated events per block */
+    double est_balance;         /* sum of estimated work / (grid_blocks x makespan) */
+} parrep_batch_info;
+
+void parrep_batch_default_options(parrep_batch_options* opt);
+
+/* Groups n handles (all with the same precision option) into a batch.
+ * The handles must outlive the batch and must not run on their own while
+ * the batch runs.  Errors: EINVAL (n < 1, null or repeated handle, mixed
+ * precision), ENOMEM, ECUDA. */
+int parrep_batch_create(const parrep_t* instances, int32_t n, const parrep_batch_options* opt,
+                        parrep_batch_t* out);
+
+/* Runs every instance i to T_end[i] with seed[i] (host arrays of n) in one
+ * launch and waits.  Returns PARREP_OK when all instances succeeded, else
+ * the first instance's error code in batch order (see parrep_batch_status).
+ * Argument errors (T_end out of range, ...) are reported before anything
+ * runs. */
+int parrep_batch_run(parrep_batch_t b, const double* T_end, const uint64_t* seed);
+
+/* Per-instance status of the last run (host array of n). */
+int parrep_batch_status(parrep_batch_t b, int32_t* status_out);
+
+int parrep_batch_info_get(parrep_batch_t b, parrep_batch_info* out);
+
+void parrep_batch_destroy(parrep_batch_t b);
+
+/* Message of the last error on b (or of the last failed parrep_batch_create
+ * when b is NULL). */
+const char* parrep_batch_last_error(parrep_batch_t b);
+
 /* Device Philox4x32-10 of n counters (ctr: n x 4, key: n x 2, out: n x 4
  * uint32, all host pointers) -- exposes the generator the kernels use. */
 int parrep_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out);

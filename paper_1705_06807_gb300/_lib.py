@@ -51,6 +51,19 @@ class parrep_stats(C.Structure):
                 ("block_threads", C.c_int32), ("chunk_steps", C.c_int32), ("kernel_ms", C.c_float),
                 ("pad", C.c_float), ("phase_cycles", C.c_double * 12)]
 
+class parrep_batch_options(C.Structure):
+    _fields_ = [("block_threads", C.c_int32), ("replicas_per_block", C.c_int32), ("autotune", C.c_int32),
+                ("use_graph", C.c_int32), ("tune_fraction", C.c_double), ("wait_timeout_s", C.c_double),
+                ("stream", C.c_void_p)]
+
+
+class parrep_batch_info(C.Structure):
+    _fields_ = [("block_threads", C.c_int32), ("replicas_per_block", C.c_int32), ("grid_blocks", C.c_int32),
+                ("n_items", C.c_int32), ("graph", C.c_int32), ("tuned_trials", C.c_int32),
+                ("kernel_ms", C.c_float), ("tune_ms", C.c_float), ("est_makespan", C.c_double),
+                ("est_balance", C.c_double)]
+
+
 PHASES = ["decorrelation", "dephasing", "draw", "chain", "account", "barrier", "special", "vote", "dec_draw",
           "dec_chain", "dec_times", "dec_commit"]
 
@@ -64,7 +77,9 @@ class parrep_cycle(C.Structure):
 EXPORTS = ["parrep_default_options", "parrep_create", "parrep_set_options", "parrep_run", "parrep_n_bins",
            "parrep_histogram", "parrep_histogram_raw", "parrep_fim", "parrep_rer", "parrep_stats_get",
            "parrep_cycle_log", "parrep_dephase", "parrep_destroy", "parrep_last_error", "parrep_ssa",
-           "parrep_philox", "parrep_ssa_noalloc"]
+           "parrep_philox", "parrep_ssa_noalloc", "parrep_batch_default_options", "parrep_batch_create",
+           "parrep_batch_run", "parrep_batch_status", "parrep_batch_info_get", "parrep_batch_destroy",
+           "parrep_batch_last_error"]
 
 _lib = None
 
@@ -103,8 +118,19 @@ def load():
     L.parrep_philox.argtypes = [vp, vp, C.c_int64, vp]
     L.parrep_ssa_noalloc.argtypes = [P(parrep_network), C.c_int32, C.c_int64, C.c_double, C.c_uint64, vp,
                                      C.c_int64, P(C.c_int64), vp]
+    L.parrep_batch_default_options.argtypes = [P(parrep_batch_options)]
+    L.parrep_batch_default_options.restype = None
+    L.parrep_batch_create.argtypes = [P(vp), C.c_int32, P(parrep_batch_options), P(vp)]
+    L.parrep_batch_run.argtypes = [vp, P(C.c_double), P(C.c_uint64)]
+    L.parrep_batch_status.argtypes = [vp, P(C.c_int32)]
+    L.parrep_batch_info_get.argtypes = [vp, P(parrep_batch_info)]
+    L.parrep_batch_destroy.argtypes = [vp]
+    L.parrep_batch_destroy.restype = None
+    L.parrep_batch_last_error.argtypes = [vp]
+    L.parrep_batch_last_error.restype = C.c_char_p
     for name in EXPORTS:
-        if name not in ("parrep_default_options", "parrep_n_bins", "parrep_destroy", "parrep_last_error"):
+        if name not in ("parrep_default_options", "parrep_n_bins", "parrep_destroy", "parrep_last_error",
+                        "parrep_batch_default_options", "parrep_batch_destroy", "parrep_batch_last_error"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L

@@ -192,6 +192,72 @@ class ParRep:
         self.close()
 
 
+class ParRepBatch:
+    """parrep_batch_create / run / destroy over ParRep handles.  After run()
+    every handle holds its own results (read them with its methods)."""
+
+    def __init__(self, instances, *, block_threads: int = 0, replicas_per_block: int = 0, autotune: bool = True,
+                 use_graph: bool = True, tune_fraction: float = 0.05, wait_timeout_s: float = 10.0, stream=None):
+        self._lib = L.load()
+        self.instances = list(instances)
+        o = L.parrep_batch_options()
+        self._lib.parrep_batch_default_options(C.byref(o))
+        o.block_threads = int(block_threads)
+        o.replicas_per_block = int(replicas_per_block)
+        o.autotune = 1 if autotune else 0
+        o.use_graph = 1 if use_graph else 0
+        o.tune_fraction = float(tune_fraction)
+        o.wait_timeout_s = float(wait_timeout_s)
+        if stream is not None:
+            o.stream = C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+        hs = (C.c_void_p * len(self.instances))(*[g.h for g in self.instances])
+        b = C.c_void_p()
+        rc = self._lib.parrep_batch_create(hs, len(self.instances), C.byref(o), C.byref(b))
+        if rc != L.PARREP_OK:
+            msg = self._lib.parrep_batch_last_error(None)
+            raise ParRepError(rc, msg.decode() if msg else "")
+        self.b = b
+
+    def _check(self, rc):
+        if rc != L.PARREP_OK:
+            msg = self._lib.parrep_batch_last_error(self.b)
+            raise ParRepError(rc, msg.decode() if msg else "")
+
+    def run(self, T_end, seeds):
+        n = len(self.instances)
+        T = (C.c_double * n)(*[float(t) for t in (T_end if np.ndim(T_end) else [T_end] * n)])
+        S = (C.c_uint64 * n)(*[int(s) & 0xFFFFFFFFFFFFFFFF for s in seeds])
+        self._check(self._lib.parrep_batch_run(self.b, T, S))
+        return self.info()
+
+    def run_status(self, T_end, seeds) -> int:
+        n = len(self.instances)
+        T = (C.c_double * n)(*[float(t) for t in (T_end if np.ndim(T_end) else [T_end] * n)])
+        S = (C.c_uint64 * n)(*[int(s) & 0xFFFFFFFFFFFFFFFF for s in seeds])
+        return self._lib.parrep_batch_run(self.b, T, S)
+
+    def status(self):
+        out = (C.c_int32 * len(self.instances))()
+        self._check(self._lib.parrep_batch_status(self.b, out))
+        return list(out)
+
+    def info(self) -> dict:
+        i = L.parrep_batch_info()
+        self._check(self._lib.parrep_batch_info_get(self.b, C.byref(i)))
+        return {k: getattr(i, k) for k, _ in i._fields_}
+
+    def close(self):
+        if getattr(self, "b", None):
+            self._lib.parrep_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def parrep_ssa(spec: dict, n_traj: int, x0, T_end: float, seed: int, *, precision: str = "f64", stream=None,
                hist_out=None):
     """Plain SSA on the GPU.  Returns (histogram in time units, events, kernel ms)."""

@@ -11,6 +11,7 @@
 
 #include "parrep.h"
 #include "parrep_internal.h"
+#include "parrep_handle.h"
 
 using namespace parrep;
 
@@ -18,45 +19,15 @@ namespace {
 
 thread_local std::string g_create_error;
 
-constexpr long long kLogCap = 1 << 16;
-constexpr int kMaxChunk = 1 << 16;
-constexpr int kSmemHistLimit = 160 * 1024;
-
 }  // namespace
 
-struct parrep_s {
-    parrep_network net;
-    parrep_regions reg;
-    int64_t R = 0;
-    double t_corr = 0, t_phase = 0;
-    parrep_options opt;
-    int nbins = 0, L = 4;
-    NetDev nd{};
-    // device buffers
-    double *d_prodU_d = nullptr, *d_prodV_d = nullptr;
-    float *d_prodU_f = nullptr, *d_prodV_f = nullptr;
-    double *d_gradU_n = nullptr, *d_gradV_n = nullptr, *d_c = nullptr, *d_s = nullptr;
-    RunCtl* d_ctl = nullptr;
-    unsigned long long *d_hist_pre = nullptr, *d_hist_post = nullptr, *d_step_sum = nullptr, *d_tau_at = nullptr;
-    int2* d_xstate = nullptr;  // [3 R]: replica state, chunk-start state, exit state
-    CycleRecDev* d_log = nullptr;
-    double *d_out = nullptr, *d_out2 = nullptr, *d_fim = nullptr, *d_rer = nullptr, *d_cprime = nullptr;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    // last run
-    bool has_run = false;
-    RunCtl h_ctl{};
-    double T_end = 0, T_burn = 0;
-    parrep_stats stats{};
-    std::string err;
-};
-
-static int fail(parrep_t h, int code, const std::string& msg) {
+int parrep::fail(parrep_t h, int code, const std::string& msg) {
     if (h) h->err = msg;
     else g_create_error = msg;
     return code;
 }
 
-static int cuda_fail(parrep_t h, cudaError_t e, const char* what) {
+int parrep::cuda_fail(parrep_t h, cudaError_t e, const char* what) {
     std::string m = std::string(what) + ": " + cudaGetErrorString(e);
     return fail(h, PARREP_ECUDA, m);
 }
@@ -307,19 +278,9 @@ extern "C" int parrep_set_options(parrep_t h, const parrep_options* o) {
     return PARREP_OK;
 }
 
-static int align16(int x) { return (x + 15) & ~15; }
+int parrep::align16(int x) { return (x + 15) & ~15; }
 
-// Launch plan of parrep_run.  FP64 form: one replica per thread.  FP32 form:
-// blocks of T threads of which the first RB own replicas (RB a power of two,
-// >= 32), the smallest RB whose grid is co-resident; B = 32 staged steps.
-struct Plan {
-    int threads, grid, smem, RB, log2RB, B, S, use_smem_hist;
-    int off_tab, off_buf, off_trace, off_live, off_nvalid;
-    int off_limbs, off_inv, off_rng, off_decp;
-    int pipelined;
-};
-
-static int fast_layout(parrep_t h, int RB, int threads, int with_hist, int pipelined, Plan& pl) {
+int parrep::fast_layout(parrep_t h, int RB, int threads, int with_hist, int pipelined, Plan& pl) {
     const int B = 32;
     const int nbuf = pipelined ? 3 : 1, ntr = pipelined ? 2 : 1;
     pl.pipelined = pipelined;
@@ -428,20 +389,21 @@ static int plan_launch(parrep_t h, Plan& pl) {
     return fail(h, PARREP_ENOMEM, "the run kernel does not fit on one SM");
 }
 
-extern "C" int parrep_run(parrep_t h, double T_end, uint64_t seed) {
-    if (!h) return PARREP_EINVAL;
+// Checks of parrep_run's arguments against the handle's options.
+int parrep::run_checks(parrep_t h, double T_end) {
     h->has_run = false;
     if (!(T_end >= 0.0) || !(T_end < kTEndLimit)) return fail(h, PARREP_EINVAL, "T_end must be in [0, 2^23)");
     if (h->opt.T_burn > T_end) return fail(h, PARREP_EINVAL, "T_burn > T_end");
     if (h->opt.thresh_mode == PARREP_THRESH_STEPS &&
         (h->t_corr != floor(h->t_corr) || h->t_phase != floor(h->t_phase)))
         return fail(h, PARREP_EINVAL, "STEPS mode needs integer t_corr, t_phase");
-    Plan pl;
-    int prc = plan_launch(h, pl);
-    if (prc != PARREP_OK) return prc;
-    const int threads = pl.threads, grid = pl.grid, S = pl.S, smem = pl.smem;
+    return PARREP_OK;
+}
+
+// The kernel parameters of one run of h with launch plan pl.
+int parrep::run_params(parrep_t h, double T_end, uint64_t seed, const Plan& pl, RunParams& p) {
+    const int grid = pl.grid, S = pl.S;
     if (S > kMaxChunk) return fail(h, PARREP_EINVAL, "chunk_steps too large");
-    RunParams p;
     memset(&p, 0, sizeof(p));
     p.net = h->nd;
     p.prec = h->opt.precision;
@@ -489,18 +451,13 @@ extern "C" int parrep_run(parrep_t h, double T_end, uint64_t seed) {
     p.log_cap = kLogCap;
     p.timeout_ns = (long long)(h->opt.wait_timeout_s * 1e9);
     p.stall_barrier = h->opt.debug_stall_barrier;
-    cudaStream_t st = stream_of(h);
-    CK(h, cudaMemsetAsync(h->d_ctl, 0, sizeof(RunCtl), st));
-    CK(h, cudaMemsetAsync(h->d_hist_pre, 0, sizeof(unsigned long long) * h->nbins, st));
-    CK(h, cudaMemsetAsync(h->d_hist_post, 0, sizeof(unsigned long long) * h->nbins, st));
-    CK(h, cudaEventRecord(h->ev0, st));
-    CK(h, launch_run(p, grid, threads, smem, st));
-    CK(h, cudaEventRecord(h->ev1, st));
-    CK(h, cudaMemcpyAsync(&h->h_ctl, h->d_ctl, sizeof(RunCtl), cudaMemcpyDeviceToHost, st));
-    CK(h, cudaStreamSynchronize(st));
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
-    const RunCtl& c = h->h_ctl;
+    p.progress = &h->d_ctl->progress;
+    return PARREP_OK;
+}
+
+// Statistics of a finished run from its control block c.
+int parrep::run_finish(parrep_t h, const RunCtl& c, double T_end, const Plan& pl, float ms) {
+    h->h_ctl = c;
     parrep_stats& s = h->stats;
     memset(&s, 0, sizeof(s));
     s.T_s = (double)c.Ts * kQInv;
@@ -518,9 +475,9 @@ extern "C" int parrep_run(parrep_t h, double T_end, uint64_t seed) {
     s.x_final[0] = c.xt0;
     s.x_final[1] = c.xt1;
     s.status = c.status;
-    s.grid_blocks = grid;
-    s.block_threads = threads;
-    s.chunk_steps = S;
+    s.grid_blocks = pl.grid;
+    s.block_threads = pl.threads;
+    s.chunk_steps = pl.S;
     s.kernel_ms = ms;
     for (int i = 0; i < 12; ++i) s.phase_cycles[i] = (double)c.phase_cycles[i];
     h->T_end = T_end;
@@ -534,6 +491,31 @@ extern "C" int parrep_run(parrep_t h, double T_end, uint64_t seed) {
     }
     h->has_run = true;
     return PARREP_OK;
+}
+
+extern "C" int parrep_run(parrep_t h, double T_end, uint64_t seed) {
+    if (!h) return PARREP_EINVAL;
+    int rc = run_checks(h, T_end);
+    if (rc != PARREP_OK) return rc;
+    Plan pl;
+    rc = plan_launch(h, pl);
+    if (rc != PARREP_OK) return rc;
+    RunParams p;
+    rc = run_params(h, T_end, seed, pl, p);
+    if (rc != PARREP_OK) return rc;
+    cudaStream_t st = stream_of(h);
+    CK(h, cudaMemsetAsync(h->d_ctl, 0, sizeof(RunCtl), st));
+    CK(h, cudaMemsetAsync(h->d_hist_pre, 0, sizeof(unsigned long long) * h->nbins, st));
+    CK(h, cudaMemsetAsync(h->d_hist_post, 0, sizeof(unsigned long long) * h->nbins, st));
+    CK(h, cudaEventRecord(h->ev0, st));
+    CK(h, launch_run(p, pl.grid, pl.threads, pl.smem, st));
+    CK(h, cudaEventRecord(h->ev1, st));
+    RunCtl c;
+    CK(h, cudaMemcpyAsync(&c, h->d_ctl, sizeof(RunCtl), cudaMemcpyDeviceToHost, st));
+    CK(h, cudaStreamSynchronize(st));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    return run_finish(h, c, T_end, pl, ms);
 }
 
 extern "C" int64_t parrep_n_bins(parrep_t h) { return h ? (int64_t)h->nbins : 0; }

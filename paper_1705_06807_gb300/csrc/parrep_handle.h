@@ -1,0 +1,67 @@
+// Host-side internals shared by the single-run (parrep_api.cu) and the batch
+// (parrep_batch.cu) halves of the C ABI.  Not part of the public interface.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "parrep.h"
+#include "parrep_internal.h"
+
+namespace parrep {
+
+constexpr long long kLogCap = 1 << 16;
+constexpr int kMaxChunk = 1 << 16;
+constexpr int kSmemHistLimit = 160 * 1024;
+
+}  // namespace parrep
+
+struct parrep_s {
+    parrep_network net;
+    parrep_regions reg;
+    int64_t R = 0;
+    double t_corr = 0, t_phase = 0;
+    parrep_options opt;
+    int nbins = 0, L = 4;
+    parrep::NetDev nd{};
+    // device buffers
+    double *d_prodU_d = nullptr, *d_prodV_d = nullptr;
+    float *d_prodU_f = nullptr, *d_prodV_f = nullptr;
+    double *d_gradU_n = nullptr, *d_gradV_n = nullptr, *d_c = nullptr, *d_s = nullptr;
+    parrep::RunCtl* d_ctl = nullptr;
+    unsigned long long *d_hist_pre = nullptr, *d_hist_post = nullptr, *d_step_sum = nullptr, *d_tau_at = nullptr;
+    int2* d_xstate = nullptr;  // [3 R]: replica state, chunk-start state, exit state
+    parrep::CycleRecDev* d_log = nullptr;
+    double *d_out = nullptr, *d_out2 = nullptr, *d_fim = nullptr, *d_rer = nullptr, *d_cprime = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // last run
+    bool has_run = false;
+    parrep::RunCtl h_ctl{};
+    double T_end = 0, T_burn = 0;
+    parrep_stats stats{};
+    std::string err;
+};
+
+namespace parrep {
+
+// Launch plan of parrep_run.  FP64 form: one replica per thread.  FP32 form:
+// blocks of T threads of which the first RB own replicas (RB a power of two,
+// >= 32), the smallest RB whose grid is co-resident; B = 32 staged steps.
+struct Plan {
+    int threads, grid, smem, RB, log2RB, B, S, use_smem_hist;
+    int off_tab, off_buf, off_trace, off_live, off_nvalid;
+    int off_limbs, off_inv, off_rng, off_decp;
+    int pipelined;
+};
+
+int fail(parrep_t h, int code, const std::string& msg);
+int cuda_fail(parrep_t h, cudaError_t e, const char* what);
+int align16(int x);
+// shared-memory layout of the FP32 form for RB owners in blocks of `threads`
+int fast_layout(parrep_t h, int RB, int threads, int with_hist, int pipelined, Plan& pl);
+int run_checks(parrep_t h, double T_end);
+int run_params(parrep_t h, double T_end, uint64_t seed, const Plan& pl, RunParams& p);
+int run_finish(parrep_t h, const RunCtl& c, double T_end, const Plan& pl, float ms);
+
+}  // namespace parrep

@@ -106,6 +106,7 @@ struct RunParams {
     int2* xk;      // [R] replica state at the start of the current chunk
     int2* xe;      // [R] state a replica escaped to in the current chunk
     RunCtl* ctl;
+    unsigned long long* progress;  // heartbeat of the barriers: the run's own, or a whole batch's
     unsigned long long* hist_pre;
     unsigned long long* hist_post;
     unsigned long long* step_sum;  // S entries
@@ -119,6 +120,11 @@ struct RunParams {
 // ---- launchers (parrep_kernels.cu) ----
 int kernel_attrs(int prec, int kind, int* max_blocks_per_sm, int smem_bytes, int threads);
 cudaError_t launch_run(const RunParams& p, int grid, int threads, int smem_bytes, cudaStream_t st);
+int batch_kernel_attrs(int prec, int* max_blocks_per_sm, int smem_bytes, int threads);
+// zeroes the instances' control blocks and histograms, then launches the batch kernel
+cudaError_t launch_batch(int prec, const RunParams* d_params, int n, const int* d_off, const int2* d_items, int grid,
+                         int threads, int smem_bytes, cudaStream_t st);
+cudaError_t launch_batch_gather(const RunParams* d_params, int n, RunCtl* out, cudaStream_t st);
 cudaError_t launch_dephase(const RunParams& p, int xt0, int xt1, int W, unsigned cycle, long long np,
                            int* out_states, int grid, int threads, cudaStream_t st);
 cudaError_t launch_hist_normalise(const unsigned long long* pre, const unsigned long long* post, int n, double scale,

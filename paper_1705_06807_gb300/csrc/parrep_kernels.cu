@@ -286,7 +286,7 @@ __device__ bool grid_sync(const RunParams& P, BarState& bs) {
     if (threadIdx.x == 0) {
         const unsigned g = ldv(&ctl->bar_gen);
         __threadfence();
-        atomicAdd(&ctl->progress, 1ull);
+        atomicAdd(P.progress, 1ull);
         const unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
         if (arrived == (unsigned)bs.nblk - 1) {
             atomicExch(&ctl->bar_count, 0u);
@@ -294,13 +294,13 @@ __device__ bool grid_sync(const RunParams& P, BarState& bs) {
             atomicAdd(&ctl->bar_gen, 1u);
         } else {
             unsigned long long t0 = globaltimer();
-            unsigned long long p0 = ldv(&ctl->progress);
+            unsigned long long p0 = ldv(P.progress);
             unsigned ns = 32;
             while (ldv(&ctl->bar_gen) == g) {
                 if (ldv(&ctl->status) != 0) break;
                 __nanosleep(ns);
                 if (ns < 1024) ns <<= 1;
-                const unsigned long long p = ldv(&ctl->progress);
+                const unsigned long long p = ldv(P.progress);
                 const unsigned long long t = globaltimer();
                 if (p != p0) {
                     p0 = p;
@@ -1719,7 +1719,7 @@ __device__ void decorrelate_f32(const RunParams& P, const FastSmem& F, const His
             if (stop <= c) more = 0;  // the rule holds before step c
             if (c < n) more = 0;
             if (n < M && c == n && !s_ended && s_status == 0) more = 0;
-            atomicAdd(&ctl->progress, 1ull);
+            atomicAdd(P.progress, 1ull);
             s_more = more;
         }
         __syncthreads();
@@ -2161,6 +2161,51 @@ __global__ void __launch_bounds__(kMaxThreads) parrep_run_kernel(RunParams P) {
     run_instance<F32, KIND>(P, (int)blockIdx.x, smem, red);
 }
 
+// Many instances in one persistent launch.  Block b works through its list
+// items[off[b] .. off[b+1]) of (instance, local block index); the blocks that
+// serve an instance (its gang, P.nblk of them) meet at its barriers.  The
+// host orders every list by the instances' start times in one schedule, so
+// any two blocks meet their shared instances in the same order and no wait
+// is circular.  Both network kinds run in the same launch.
+template <bool F32>
+__global__ void __launch_bounds__(kMaxThreads)
+    parrep_batch_kernel(const RunParams* __restrict__ Ps, const int* __restrict__ off,
+                        const int2* __restrict__ items) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ BlockScratch red;
+    __shared__ RunParams sP;
+    const int k1 = off[blockIdx.x + 1];
+    for (int k = off[blockIdx.x]; k < k1; ++k) {
+        const int2 it = items[k];
+        const int* src = (const int*)(Ps + it.x);
+        int* dst = (int*)&sP;
+        for (int w = threadIdx.x; w < (int)(sizeof(RunParams) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
+        __syncthreads();
+        if (sP.net.kind == PARREP_SCHLOGL) run_instance<F32, PARREP_SCHLOGL>(sP, it.y, smem, red);
+        else run_instance<F32, PARREP_TOGGLE>(sP, it.y, smem, red);
+        __syncthreads();
+    }
+}
+
+// Zeroes the control block and the histograms of every instance of a batch
+// (one block per instance).
+__global__ void batch_reset_kernel(const RunParams* __restrict__ Ps, int n) {
+    const RunParams& P = Ps[blockIdx.x];
+    unsigned long long* c = (unsigned long long*)P.ctl;
+    for (int i = threadIdx.x; i < (int)(sizeof(RunCtl) / 8); i += blockDim.x) c[i] = 0;
+    for (int b = threadIdx.x; b < P.net.nbins; b += blockDim.x) {
+        P.hist_pre[b] = 0;
+        P.hist_post[b] = 0;
+    }
+}
+
+// Copies every instance's control block into one array for the host.
+__global__ void batch_gather_kernel(const RunParams* __restrict__ Ps, int n, RunCtl* out) {
+    const unsigned long long* c = (const unsigned long long*)Ps[blockIdx.x].ctl;
+    unsigned long long* o = (unsigned long long*)(out + blockIdx.x);
+    for (int i = threadIdx.x; i < (int)(sizeof(RunCtl) / 8); i += blockDim.x) o[i] = c[i];
+}
+
 // ---------------------------------------------------------------------------
 // stand-alone dephasing (for tests and diagnostics)
 // ---------------------------------------------------------------------------
@@ -2347,6 +2392,47 @@ cudaError_t launch_run(const RunParams& p, int grid, int threads, int smem_bytes
         fn = p.net.kind == PARREP_SCHLOGL ? (void*)parrep_run_kernel<false, PARREP_SCHLOGL>
                                           : (void*)parrep_run_kernel<false, PARREP_TOGGLE>;
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(threads), args, (size_t)smem_bytes, st);
+}
+
+template <bool F32>
+static int batch_attrs_one(int* max_blocks_per_sm, int smem_bytes, int threads) {
+    cudaError_t e = cudaFuncSetAttribute(parrep_batch_kernel<F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem_bytes);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, parrep_batch_kernel<F32>, threads,
+                                                          smem_bytes);
+    return (int)e;
+}
+
+int batch_kernel_attrs(int prec, int* max_blocks_per_sm, int smem_bytes, int threads) {
+    return prec == PARREP_FP32 ? batch_attrs_one<true>(max_blocks_per_sm, smem_bytes, threads)
+                               : batch_attrs_one<false>(max_blocks_per_sm, smem_bytes, threads);
+}
+
+cudaError_t launch_batch(int prec, const RunParams* d_params, int n, const int* d_off, const int2* d_items, int grid,
+                         int threads, int smem_bytes, cudaStream_t st) {
+    if (n < 1) return cudaSuccess;
+    batch_reset_kernel<<<n, 256, 0, st>>>(d_params, n);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = (size_t)smem_bytes;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (prec == PARREP_FP32) return cudaLaunchKernelEx(&cfg, parrep_batch_kernel<true>, d_params, d_off, d_items);
+    return cudaLaunchKernelEx(&cfg, parrep_batch_kernel<false>, d_params, d_off, d_items);
+}
+
+cudaError_t launch_batch_gather(const RunParams* d_params, int n, RunCtl* out, cudaStream_t st) {
+    if (n < 1) return cudaSuccess;
+    batch_gather_kernel<<<n, 64, 0, st>>>(d_params, n, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_dephase(const RunParams& p, int xt0, int xt1, int W, unsigned cycle, long long np,
