@@ -244,12 +244,14 @@ int parrep_ssa_noalloc(const parrep_network* net, int32_t precision, int64_t n_t
  * with the single-run calls), bit for bit: an instance's arithmetic does not
  * depend on the blocks that run it.
  *
- * Scheduling: each instance gets a gang of blocks sized to its estimated
- * work (holding-time events ~ T_end * a0(x_0) plus the dephasing jumps) and
- * capped by its groups of replicas; gangs are placed longest-first on the
- * co-resident grid, every block working through its list of (instance,
- * block index) in the schedule's start order.  A gang smaller than an
- * instance's replica groups takes several groups per block.
+ * Scheduling: an instance's work is the block-cycles it took in the batch's
+ * previous run (per unit of T_end; before any run, an estimate from
+ * T_end * a0(x_0) plus one dephasing of every replica).  An instance whose
+ * work exceeds the ideal makespan (total work / co-resident blocks) gets a
+ * gang of blocks big enough to fit in it, capped by its groups of replicas;
+ * gangs are placed longest-first on the grid, every block working through
+ * its list of (instance, block index) in the schedule's start order.  A gang
+ * smaller than an instance's replica groups takes several groups per block.
  * --------------------------------------------------------------------------- */
 typedef struct parrep_batch_s* parrep_batch_t;
 
@@ -277,8 +279,9 @@ typedef struct {
     float kernel_ms;            /* last run: device time of the launch sequence (parameter
                                    upload, reset, batch kernel, read-back) */
     float tune_ms;              /* wall time spent autotuning */
-    double est_makespan;        /* schedule's makespan in estimated events per block */
-    double est_balance;         /* sum of estimated work / (grid_blocks x makespan) */
+    double est_makespan;        /* the schedule's makespan in its work units (block-cycles
+                                   measured in the previous run, else estimated events) */
+    double est_balance;         /* total work / (grid_blocks x makespan) */
 } parrep_batch_info;
 
 void parrep_batch_default_options(parrep_batch_options* opt);

@@ -82,7 +82,8 @@ def batch_instances(n: int = 256, seed: int = 0, T_end: float = 1e4, n_min: int 
         else:
             hill = float(rng.uniform(2.0, 3.0))
             alpha = float(rng.uniform(30.0, 80.0))
-            hm = int(min(255, max(63, np.ceil(alpha * 2.0))))
+            # alpha + 10 sd of Poisson(alpha) + 20: no excursion reaches it
+            hm = int(max(63, np.ceil(alpha + 10.0 * np.sqrt(alpha) + 20.0)))
             net = toggle(alpha=alpha, n=hill, hist_max=(hm, hm))
             x0 = [int(alpha), 0]
         out.append(dict(network=net, n_replicas=R, t_corr=1.0, t_phase=1.0, T_end=T_end, x0=x0,

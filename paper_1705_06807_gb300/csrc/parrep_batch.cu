@@ -37,6 +37,9 @@ struct parrep_batch_s {
     bool tuned = false;
     std::vector<Plan> plans;
     std::vector<int> gang;
+    // measured cost of every instance in the last run: block-cycles per unit of T_end
+    std::vector<double> cost;
+    bool have_cost = false;
     // device buffers
     RunParams* d_params = nullptr;
     int* d_off = nullptr;
@@ -111,19 +114,36 @@ static double est_work(parrep_t h, double T_end) {
     return T_end * a0 + (double)h->R * per_replica + 1.0;
 }
 
+// Block-cycles each instance took in the last run (the kernel's per-phase
+// clocks summed over its blocks), per unit of T_end.
+static void record_costs(parrep_batch_t b, const double* T_end) {
+    const int n = (int)b->inst.size();
+    b->cost.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        double c = 0.0;
+        for (int k = 0; k < 8; ++k) c += (double)b->h_ctl_out[i].phase_cycles[k];  // 8..11 are parts of 0
+        b->cost[i] = c / std::max(T_end[i], 1e-9);
+    }
+    b->have_cost = true;
+}
+
 // Gang sizes and the ordered (instance, local block) lists of every block.
+// Work: the last run's measured cost, else an estimate.  An instance whose
+// work exceeds the ideal makespan (total work / blocks) gets enough blocks to
+// fit in it, up to one block per group of replicas.
 static void make_schedule(parrep_batch_t b, const double* T_end) {
     const int n = (int)b->inst.size(), G = b->grid;
     std::vector<double> w(n), dur(n);
     double W = 0.0;
     for (int i = 0; i < n; ++i) {
-        w[i] = est_work(b->inst[i], T_end[i]);
+        w[i] = b->have_cost ? std::max(b->cost[i] * T_end[i], 1.0) : est_work(b->inst[i], T_end[i]);
         W += w[i];
     }
+    const double M = W / (double)G;
     b->gang.assign(n, 1);
     for (int i = 0; i < n; ++i) {
         const long long nvb = (b->inst[i]->R + b->plans[i].RB - 1) / b->plans[i].RB;
-        long long g = llround((double)G * w[i] / W);
+        long long g = (long long)ceil(w[i] / M - 1e-9);
         g = std::max(1LL, std::min(g, std::min(nvb, (long long)G)));
         b->gang[i] = (int)g;
         dur[i] = w[i] / (double)g;
@@ -345,12 +365,26 @@ static int autotune(parrep_batch_t b, const double* T_end, const uint64_t* seed)
         }
         float best = 0.f;
         int best_k = -1, rc = PARREP_OK;
+        if (!b->have_cost) {
+            // one unscored run to measure the instances' costs, so that every
+            // candidate is timed with a measured schedule
+            rc = set_shape(b, cand[0].first, cand[0].second);
+            float ms = 0.f;
+            if (rc == PARREP_OK) rc = run_once(b, Tt.data(), seed, false, &ms);
+            if (rc == PARREP_OK) record_costs(b, Tt.data());
+            if (rc == PARREP_ENOMEM) rc = PARREP_OK;
+        }
         for (size_t k = 0; k < cand.size() && rc == PARREP_OK; ++k) {
             rc = set_shape(b, cand[k].first, cand[k].second);
+            if (rc == PARREP_ENOMEM) {  // this shape does not fit some instance: skip it
+                rc = PARREP_OK;
+                continue;
+            }
             if (rc != PARREP_OK) break;
             float ms = 0.f;
             rc = run_once(b, Tt.data(), seed, false, &ms);
             if (rc != PARREP_OK) break;
+            record_costs(b, Tt.data());
             b->info.tuned_trials += 1;
             if (best_k < 0 || ms < best) {
                 best = ms;
@@ -359,6 +393,7 @@ static int autotune(parrep_batch_t b, const double* T_end, const uint64_t* seed)
         }
         for (int i = 0; i < n; ++i) b->inst[i]->opt.T_burn = burn[i];
         if (rc != PARREP_OK) return rc;
+        if (best_k < 0) return bfail(b, PARREP_ENOMEM, "no candidate block shape fits every instance");
         int rc2 = set_shape(b, cand[best_k].first, cand[best_k].second);
         if (rc2 != PARREP_OK) return rc2;
     } else {
@@ -463,6 +498,7 @@ extern "C" int parrep_batch_run(parrep_batch_t b, const double* T_end, const uin
     int rc = run_once(b, T_end, seed, b->opt.use_graph != 0, &ms);
     if (rc != PARREP_OK) return rc;
     b->info.kernel_ms = ms;
+    record_costs(b, T_end);
     int first = PARREP_OK;
     for (int i = 0; i < n; ++i) {
         Plan pl = b->plans[i];

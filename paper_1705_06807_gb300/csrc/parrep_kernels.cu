@@ -596,11 +596,11 @@ struct Cuts {
 // Re-simulates the chunk of replica r from (x0,x1) exactly as the first pass.
 template <bool F32, int MODE>
 __device__ void replay_chunk(const RunParams& P, const HistSink& hs, int x0, int x1, unsigned r, int W,
-                             unsigned cycle, unsigned n0, const Cuts& cut, bool to_post,
+                             unsigned cycle, unsigned n0, int S, const Cuts& cut, bool to_post,
                              unsigned long long& inc_q, unsigned long long& inc_ev, unsigned long long& ev) {
     const NetDev& N = P.net;
     const uint2 key = seed_key(P.seed);
-    for (int s = 0; s < P.S; ++s) {
+    for (int s = 0; s < S; ++s) {
         const unsigned long long pos = pos_of(s, r);
         if (MODE != kRollback && pos > cut.posC) break;
         const uint4 w = par_words<F32>(r, n0 + (unsigned)s, cycle, key);
@@ -1141,8 +1141,8 @@ __device__ __forceinline__ void account(const RunParams& P, const FastSmem& F, c
 // Every thread of the block calls it; owners carry the replica states.
 template <int KIND, int MODE>
 __device__ void chunk_f32(const RunParams& P, const FastSmem& F, const HistSink& hs, bool active, unsigned rbase,
-                          unsigned r, const RegionTest& rt, unsigned cycle, unsigned n0, uint2 key, int& x0, int& x1,
-                          const Cuts& cut, bool to_post, unsigned long long& mykey, unsigned long long& myoob,
+                          unsigned r, const RegionTest& rt, unsigned cycle, unsigned n0, int S, uint2 key, int& x0,
+                          int& x1, const Cuts& cut, bool to_post, unsigned long long& mykey, unsigned long long& myoob,
                           int& xe0, int& xe1, unsigned long long& qs, unsigned long long& ev,
                           unsigned long long& inc_ev, PhaseClock& pc) {
     const bool owner = threadIdx.x < P.RB;
@@ -1162,7 +1162,7 @@ __device__ void chunk_f32(const RunParams& P, const FastSmem& F, const HistSink&
         if (threadIdx.x < 8) F.rng[threadIdx.x] = (threadIdx.x & 1) ? -1 : 0x7fffffff;
         __syncthreads();
         pc.start();
-        const int nsub = P.S / B;
+        const int nsub = S / B;
         if (!owner) {
             FastSmem Fp = F;
             produce_lanes<true>(P, Fp, rbase, n0, B, cycle, kTagParallel, key, h, nh);
@@ -1219,7 +1219,7 @@ __device__ void chunk_f32(const RunParams& P, const FastSmem& F, const HistSink&
         F.rng[3] = -1;
     }
     __syncthreads();
-    for (int sub = 0; sub < P.S; sub += P.B) {
+    for (int sub = 0; sub < S; sub += P.B) {
         pc.start();
         produce_lanes<true>(P, F, rbase, n0 + (unsigned)sub, P.B, cycle, kTagParallel, key);
         __syncthreads();
@@ -1741,7 +1741,8 @@ __device__ void decorrelate_f32(const RunParams& P, const FastSmem& F, const His
 // blocks, each replica from its chunk-start state P.xk.
 template <bool F32, int KIND, int MODE>
 __device__ __forceinline__ void replay_vblocks(const RunParams& P, const FastSmem& F, const HistSink& hs, int lb,
-                                               int nvb, const RegionTest& rt, unsigned cycle, unsigned n0, uint2 key,
+                                               int nvb, const RegionTest& rt, unsigned cycle, unsigned n0, int S,
+                                               uint2 key,
                                                const Cuts& cut, bool to_post, unsigned long long& ev_replay,
                                                PhaseClock& pc, unsigned long long* inc_q = nullptr,
                                                unsigned long long* inc_ev = nullptr) {
@@ -1761,10 +1762,10 @@ __device__ __forceinline__ void replay_vblocks(const RunParams& P, const FastSme
         if (F32) {
             unsigned long long k0 = kNone, k1 = kNone;
             int e0 = 0, e1 = 0;
-            chunk_f32<KIND, MODE>(P, F, hs, active, rbase, r, rt, cycle, n0, key, y0, y1, cut, to_post, k0, k1, e0,
+            chunk_f32<KIND, MODE>(P, F, hs, active, rbase, r, rt, cycle, n0, S, key, y0, y1, cut, to_post, k0, k1, e0,
                                   e1, q, ev_replay, e, pc);
         } else if (active) {
-            replay_chunk<F32, MODE>(P, hs, y0, y1, r, rt.W, cycle, n0, cut, to_post, q, e, ev_replay);
+            replay_chunk<F32, MODE>(P, hs, y0, y1, r, rt.W, cycle, n0, S, cut, to_post, q, e, ev_replay);
         }
     }
 }
@@ -1847,6 +1848,7 @@ __device__ __forceinline__ void run_instance(const RunParams& P, int lb, unsigne
     HistSink hs{P.use_smem_hist ? sh_hist : nullptr, period_post ? P.hist_post : P.hist_pre, limb_lo, limb_hi,
                 N.ystride, F32 ? ((1ull << 47) >> (P.log2RB + 5)) : 0ull};
     unsigned long long chunk_c = 0;
+    unsigned long long est_q = 0, est_ev = 0;  // time and jumps of the last chunk
     if (!grid_sync(P, bs)) goto out;
 
     for (;;) {
@@ -1895,8 +1897,29 @@ __device__ __forceinline__ void run_instance(const RunParams& P, int lb, unsigne
             if (leader) ctl->ev_dephase += (unsigned long long)np * (unsigned long long)P.R;
             // ---------------- parallel step ----------------
             unsigned n0 = 0;
+            int grow = 0;
             for (;;) {
-                if ((unsigned long long)n0 + (unsigned long long)P.S > 0xFFFFFFFFull) {
+                // chunk length: doubling from one sub-chunk at the start of a
+                // cycle up to P.S, and no longer than the steps the last chunk's
+                // time per lockstep step says are left to the next threshold.
+                // Every block computes it from the same values; results do
+                // not depend on where chunks end.
+                int Sc = P.S;
+                {
+                    const int unit = F32 ? P.B : 32;
+                    if (grow < 30 && ((long long)unit << grow) < (long long)Sc) Sc = unit << grow;
+                    const unsigned long long q_lim = burn_done ? P.q_Tend : P.q_Tburn;
+                    if (est_ev > 0 && est_q > 0 && q_lim > Ts) {
+                        const double step_q = (double)est_q * (double)P.R / (double)est_ev;
+                        const double need = ceil((double)(q_lim - Ts) / step_q * 1.25) + 1.0;
+                        if (need < (double)Sc) {
+                            int nd = ((int)need + unit - 1) / unit * unit;
+                            Sc = nd < unit ? unit : nd;
+                        }
+                    }
+                    ++grow;
+                }
+                if ((unsigned long long)n0 + (unsigned long long)Sc > 0xFFFFFFFFull) {
                     if (leader) atomicCAS(&ctl->status, 0, PARREP_ERANGE);
                 }
                 if (leader) {
@@ -1923,10 +1946,10 @@ __device__ __forceinline__ void run_instance(const RunParams& P, int lb, unsigne
                     unsigned long long k0 = kNone, k1 = kNone;
                     if (F32) {
                         unsigned long long dummy = 0;
-                        chunk_f32<KIND, kFirst>(P, F, hs, active, rbase, r, rt, cycle, n0, key, x0, x1, none,
+                        chunk_f32<KIND, kFirst>(P, F, hs, active, rbase, r, rt, cycle, n0, Sc, key, x0, x1, none,
                                                 period_post, k0, k1, xe0, xe1, qsum, ev, dummy, pc);
                     } else if (active) {
-                        for (int s = 0; s < P.S; ++s) {
+                        for (int s = 0; s < Sc; ++s) {
                             const uint4 w = par_words<F32>(r, n0 + (unsigned)s, cycle, key);
                             unsigned long long q = 0;
                             const int J = ssa_draw<F32, true>(N, x0, x1, w, q);
@@ -1977,6 +2000,10 @@ __device__ __forceinline__ void run_instance(const RunParams& P, int lb, unsigne
                 const unsigned long long csum = ldv(&ctl->chunksum[slot]);
                 const unsigned long long cev = ldv(&ctl->chunkev[slot]);
                 const unsigned long long q_next = burn_done ? P.q_Tend : P.q_Tburn;
+                if (cev > 0 && csum > 0) {
+                    est_q = csum;
+                    est_ev = cev;
+                }
                 if (leader) {
                     ctl->chunks += 1;
                     ctl->ev_par_exec += cev;
@@ -1987,13 +2014,13 @@ __device__ __forceinline__ void run_instance(const RunParams& P, int lb, unsigne
                         ctl->ev_useful += cev;
                         ctl->Ts = Ts;
                     }
-                    n0 += (unsigned)P.S;
+                    n0 += (unsigned)Sc;
                     continue;
                 }
                 // ------------- special chunk: escape, range error or time cut -------------
                 if (leader) ctl->special += 1;
                 pc.start();
-                replay_vblocks<F32, KIND, kRollback>(P, F, hs, lb, nvb, rt, cycle, n0, key, none, period_post,
+                replay_vblocks<F32, KIND, kRollback>(P, F, hs, lb, nvb, rt, cycle, n0, Sc, key, none, period_post,
                                                      ev_replay, pc);
                 Cuts cut{kNone, kNone, kNone, 0, kNone, 0, -1, -1};
                 cut.posE = ekey;
@@ -2001,16 +2028,16 @@ __device__ __forceinline__ void run_instance(const RunParams& P, int lb, unsigne
                 if (Ts + csum >= q_next) {
                     // a threshold may be crossed: find the step, then the replica
                     if (lb == 0) {
-                        for (int j = threadIdx.x; j < P.S; j += blockDim.x) P.step_sum[j] = 0;
+                        for (int j = threadIdx.x; j < Sc; j += blockDim.x) P.step_sum[j] = 0;
                     }
                     if (!grid_sync(P, bs)) goto out;
-                    replay_vblocks<F32, KIND, kStepSum>(P, F, hs, lb, nvb, rt, cycle, n0, key, cut, period_post,
+                    replay_vblocks<F32, KIND, kStepSum>(P, F, hs, lb, nvb, rt, cycle, n0, Sc, key, cut, period_post,
                                                         ev_replay, pc);
                     if (!grid_sync(P, bs)) goto out;
                     unsigned long long baseB = 0, baseT = 0;
                     {
                         unsigned long long acc = Ts;
-                        for (int j = 0; j < P.S; ++j) {
+                        for (int j = 0; j < Sc; ++j) {
                             const unsigned long long v = __ldcg(P.step_sum + j);
                             if (!burn_done && cut.nB < 0 && acc + v >= P.q_Tburn) {
                                 cut.nB = j;
@@ -2031,7 +2058,7 @@ __device__ __forceinline__ void run_instance(const RunParams& P, int lb, unsigne
                                 P.tau_at[P.R + r] = 0;
                             }
                         }
-                        replay_vblocks<F32, KIND, kTauAt>(P, F, hs, lb, nvb, rt, cycle, n0, key, cut, period_post,
+                        replay_vblocks<F32, KIND, kTauAt>(P, F, hs, lb, nvb, rt, cycle, n0, Sc, key, cut, period_post,
                                                           ev_replay, pc);
                         if (!grid_sync(P, bs)) goto out;
                         if (leader) {
@@ -2085,7 +2112,7 @@ __device__ __forceinline__ void run_instance(const RunParams& P, int lb, unsigne
                 {
                     unsigned long long inc_q = 0, inc_ev = 0;
                     const bool tp = period_post || cut.posB != kNone;
-                    replay_vblocks<F32, KIND, kPrecise>(P, F, hs, lb, nvb, rt, cycle, n0, key, cut, tp, ev_replay,
+                    replay_vblocks<F32, KIND, kPrecise>(P, F, hs, lb, nvb, rt, cycle, n0, Sc, key, cut, tp, ev_replay,
                                                         pc, &inc_q, &inc_ev);
                     unsigned long long a = kNone, b = kNone;
                     block_reduce4(red, a, b, inc_q, inc_ev);
@@ -2135,7 +2162,7 @@ __device__ __forceinline__ void run_instance(const RunParams& P, int lb, unsigne
                 }
                 if (t_end) goto finished;
                 if (ekey != kNone) break;  // next cycle
-                n0 += (unsigned)P.S;       // only the T_burn split was in this chunk
+                n0 += (unsigned)Sc;        // only the T_burn split was in this chunk
             }
         }
         if (!grid_sync(P, bs)) goto out;
