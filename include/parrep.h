@@ -244,9 +244,11 @@ int parrep_ssa_noalloc(const parrep_network* net, int32_t precision, int64_t n_t
  * with the single-run calls), bit for bit: an instance's arithmetic does not
  * depend on the blocks that run it.
  *
- * Scheduling: an instance's work is the block-cycles it took in the batch's
- * previous run (per unit of T_end; before any run, an estimate from
- * T_end * a0(x_0) plus one dephasing of every replica).  An instance whose
+ * Scheduling: an instance's work is predicted from the block-cycles it took
+ * in the batch's earlier runs, pooled: the parallel and decorrelation part
+ * per unit of T_end, plus one dephasing of all replicas per cycle for a
+ * cycle count two Poisson standard deviations above its measured mean
+ * (before any run, an estimate from T_end * a0(x_0) plus one dephasing).  An instance whose
  * work exceeds the ideal makespan (total work / co-resident blocks) gets a
  * gang of blocks big enough to fit in it, capped by its groups of replicas;
  * gangs are placed longest-first on the grid, every block working through

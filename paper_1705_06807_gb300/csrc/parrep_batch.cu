@@ -37,8 +37,9 @@ struct parrep_batch_s {
     bool tuned = false;
     std::vector<Plan> plans;
     std::vector<int> gang;
-    // measured cost of every instance in the last run: block-cycles per unit of T_end
-    std::vector<double> cost;
+    // measured costs of every instance, pooled over the batch's runs:
+    // simulated time, cycles, dephasing block-cycles and the other block-cycles
+    std::vector<double> m_T, m_cycles, m_deph, m_rest;
     bool have_cost = false;
     // device buffers
     RunParams* d_params = nullptr;
@@ -46,6 +47,9 @@ struct parrep_batch_s {
     int2* d_items = nullptr;
     RunCtl* d_ctl_out = nullptr;
     unsigned long long* d_progress = nullptr;
+    int* d_remaining = nullptr;
+    unsigned* d_idle = nullptr;
+    int4* d_mail = nullptr;
     int off_cap = 0, items_cap = 0;
     // pinned host mirrors (the graph's copy nodes read and write these)
     RunParams* h_params = nullptr;
@@ -114,17 +118,38 @@ static double est_work(parrep_t h, double T_end) {
     return T_end * a0 + (double)h->R * per_replica + 1.0;
 }
 
-// Block-cycles each instance took in the last run (the kernel's per-phase
-// clocks summed over its blocks), per unit of T_end.
+// Adds the last run's block-cycles of every instance (the kernel's per-phase
+// clocks summed over its blocks) to the pooled measurements.
 static void record_costs(parrep_batch_t b, const double* T_end) {
     const int n = (int)b->inst.size();
-    b->cost.assign(n, 0.0);
+    if (!b->have_cost) {
+        b->m_T.assign(n, 0.0);
+        b->m_cycles.assign(n, 0.0);
+        b->m_deph.assign(n, 0.0);
+        b->m_rest.assign(n, 0.0);
+    }
     for (int i = 0; i < n; ++i) {
-        double c = 0.0;
-        for (int k = 0; k < 8; ++k) c += (double)b->h_ctl_out[i].phase_cycles[k];  // 8..11 are parts of 0
-        b->cost[i] = c / std::max(T_end[i], 1e-9);
+        const RunCtl& c = b->h_ctl_out[i];
+        double tot = 0.0;
+        for (int k = 0; k < 8; ++k) tot += (double)c.phase_cycles[k];  // 8..11 are parts of 0
+        const double deph = (double)c.phase_cycles[1];
+        b->m_T[i] += T_end[i];
+        b->m_cycles[i] += (double)c.cycles;
+        b->m_deph[i] += deph;
+        b->m_rest[i] += tot - deph;
     }
     b->have_cost = true;
+}
+
+// Expected block-cycles of instance i to T_end, with room for the spread of
+// its escape count: the other phases scale with T_end; every cycle adds one
+// dephasing of all replicas, and the cycle count of a run is taken two
+// standard deviations (Poisson) above its mean.
+static double measured_work(parrep_batch_t b, int i, double T_end) {
+    const double T = std::max(b->m_T[i], 1e-9);
+    const double E = b->m_cycles[i] / T * T_end;
+    const double per_cycle = b->m_cycles[i] > 0.0 ? b->m_deph[i] / b->m_cycles[i] : 0.0;
+    return b->m_rest[i] / T * T_end + per_cycle * (E + 2.0 * sqrt(E) + 1.0);
 }
 
 // Gang sizes and the ordered (instance, local block) lists of every block.
@@ -136,7 +161,7 @@ static void make_schedule(parrep_batch_t b, const double* T_end) {
     std::vector<double> w(n), dur(n);
     double W = 0.0;
     for (int i = 0; i < n; ++i) {
-        w[i] = b->have_cost ? std::max(b->cost[i] * T_end[i], 1.0) : est_work(b->inst[i], T_end[i]);
+        w[i] = b->have_cost ? std::max(measured_work(b, i, T_end[i]), 1.0) : est_work(b->inst[i], T_end[i]);
         W += w[i];
     }
     const double M = W / (double)G;
@@ -249,10 +274,16 @@ static int set_shape(parrep_batch_t b, int threads, int RB) {
     if (off_cap > b->off_cap) {
         if (b->d_off) cudaFree(b->d_off);
         if (b->h_off) cudaFreeHost(b->h_off);
+        if (b->d_idle) cudaFree(b->d_idle);
+        if (b->d_mail) cudaFree(b->d_mail);
         b->d_off = nullptr;
         b->h_off = nullptr;
+        b->d_idle = nullptr;
+        b->d_mail = nullptr;
         BCK(b, cudaMalloc((void**)&b->d_off, sizeof(int) * off_cap));
         BCK(b, cudaMallocHost((void**)&b->h_off, sizeof(int) * off_cap));
+        BCK(b, cudaMalloc((void**)&b->d_idle, sizeof(unsigned) * ((off_cap + 31) / 32)));
+        BCK(b, cudaMalloc((void**)&b->d_mail, sizeof(int4) * off_cap));
         b->off_cap = off_cap;
     }
     return PARREP_OK;
@@ -269,7 +300,8 @@ static int enqueue(parrep_batch_t b) {
     BCK(b, cudaMemcpyAsync(b->d_off, b->h_off, sizeof(int) * b->off_cap, cudaMemcpyHostToDevice, b->st));
     BCK(b, cudaMemcpyAsync(b->d_items, b->h_items, sizeof(int2) * b->items_cap, cudaMemcpyHostToDevice, b->st));
     BCK(b, cudaMemsetAsync(b->d_progress, 0, sizeof(unsigned long long), b->st));
-    BCK(b, launch_batch(b->prec, b->d_params, n, b->d_off, b->d_items, b->grid, b->threads, b->smem, b->st));
+    BatchDev bd{b->d_remaining, b->d_idle, b->d_mail};
+    BCK(b, launch_batch(b->prec, b->d_params, n, b->d_off, b->d_items, bd, b->grid, b->threads, b->smem, b->st));
     BCK(b, launch_batch_gather(b->d_params, n, b->d_ctl_out, b->st));
     BCK(b, cudaMemcpyAsync(b->h_ctl_out, b->d_ctl_out, sizeof(RunCtl) * n, cudaMemcpyDeviceToHost, b->st));
     return PARREP_OK;
@@ -287,6 +319,8 @@ static int run_once(parrep_batch_t b, const double* T_end, const uint64_t* seed,
         if (rc != PARREP_OK) return bfail(b, rc, std::string("instance ") + std::to_string(i) + ": " + h->err);
         p.progress = b->d_progress;
         p.timeout_ns = (long long)(b->opt.wait_timeout_s * 1e9);
+        p.batch = BatchDev{b->d_remaining, b->d_idle, b->d_mail};
+        p.inst = i;
         b->h_params[i] = p;
     }
     if (graph) {
@@ -412,7 +446,8 @@ static int autotune(parrep_batch_t b, const double* T_end, const uint64_t* seed)
 
 static void batch_free(parrep_batch_t b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
-    void* dev[] = {b->d_params, b->d_off, b->d_items, b->d_ctl_out, b->d_progress};
+    void* dev[] = {b->d_params, b->d_off, b->d_items, b->d_ctl_out, b->d_progress, b->d_remaining, b->d_idle,
+                   b->d_mail};
     for (void* p : dev)
         if (p) cudaFree(p);
     void* host[] = {b->h_params, b->h_off, b->h_items, b->h_ctl_out};
@@ -466,6 +501,7 @@ extern "C" int parrep_batch_create(const parrep_t* instances, int32_t n, const p
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_params, sizeof(RunParams) * n);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_ctl_out, sizeof(RunCtl) * n);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_progress, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_remaining, sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_params, sizeof(RunParams) * n);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_ctl_out, sizeof(RunCtl) * n);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);

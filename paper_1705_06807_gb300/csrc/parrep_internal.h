@@ -71,6 +71,10 @@ struct RunCtl {
     // cut positions of a special chunk
     unsigned long long posT, partT, posB, partB;
     int xe0, xe1;
+    // batches: the gang's current block count, and what a block that joins
+    // at a cycle start needs to continue in step with the others
+    int nblk, pad1;
+    unsigned long long chunk_c, est_q, est_ev;
     // statistics
     unsigned long long ev_decorr, ev_dephase, ev_par_exec, ev_useful, ev_replay;
     unsigned long long escapes, chunks, special, cycles;
@@ -80,6 +84,15 @@ struct RunCtl {
     // decorrelation, dephasing, draw (P), owner chain (C), accounting (A),
     // grid barriers, special-chunk work, first-pass vote reduction
     unsigned long long phase_cycles[12];
+};
+
+// Shared state of a batch launch: instances not yet finished, the idle
+// blocks (a bit each) and one mailbox per block through which an instance
+// hands an idle block its place in the gang.
+struct BatchDev {
+    int* remaining;
+    unsigned* idle;   // [ceil(grid / 32)]
+    int4* mail;       // [grid]: (instance, block index in the gang, barrier generation, valid)
 };
 
 struct RunParams {
@@ -105,6 +118,8 @@ struct RunParams {
     int2* xs;      // [R] replica state between phases
     int2* xk;      // [R] replica state at the start of the current chunk
     int2* xe;      // [R] state a replica escaped to in the current chunk
+    BatchDev batch;  // batches only (batch.remaining == nullptr otherwise)
+    int inst;        // index of the instance in its batch
     RunCtl* ctl;
     unsigned long long* progress;  // heartbeat of the barriers: the run's own, or a whole batch's
     unsigned long long* hist_pre;
@@ -122,8 +137,8 @@ int kernel_attrs(int prec, int kind, int* max_blocks_per_sm, int smem_bytes, int
 cudaError_t launch_run(const RunParams& p, int grid, int threads, int smem_bytes, cudaStream_t st);
 int batch_kernel_attrs(int prec, int* max_blocks_per_sm, int smem_bytes, int threads);
 // zeroes the instances' control blocks and histograms, then launches the batch kernel
-cudaError_t launch_batch(int prec, const RunParams* d_params, int n, const int* d_off, const int2* d_items, int grid,
-                         int threads, int smem_bytes, cudaStream_t st);
+cudaError_t launch_batch(int prec, const RunParams* d_params, int n, const int* d_off, const int2* d_items,
+                         BatchDev bd, int grid, int threads, int smem_bytes, cudaStream_t st);
 cudaError_t launch_batch_gather(const RunParams* d_params, int n, RunCtl* out, cudaStream_t st);
 cudaError_t launch_dephase(const RunParams& p, int xt0, int xt1, int W, unsigned cycle, long long np,
                            int* out_states, int grid, int threads, cudaStream_t st);

@@ -1741,13 +1741,13 @@ __device__ void decorrelate_f32(const RunParams& P, const FastSmem& F, const His
 // blocks, each replica from its chunk-start state P.xk.
 template <bool F32, int KIND, int MODE>
 __device__ __forceinline__ void replay_vblocks(const RunParams& P, const FastSmem& F, const HistSink& hs, int lb,
-                                               int nvb, const RegionTest& rt, unsigned cycle, unsigned n0, int S,
+                                               int nblk, int nvb, const RegionTest& rt, unsigned cycle, unsigned n0, int S,
                                                uint2 key,
                                                const Cuts& cut, bool to_post, unsigned long long& ev_replay,
                                                PhaseClock& pc, unsigned long long* inc_q = nullptr,
                                                unsigned long long* inc_ev = nullptr) {
     const bool owner = (int)threadIdx.x < P.RB;
-    for (int vb = lb; vb < nvb; vb += P.nblk) {
+    for (int vb = lb; vb < nvb; vb += nblk) {
         const unsigned rbase = (unsigned)vb * (unsigned)P.RB, r = rbase + threadIdx.x;
         const bool active = owner && (long long)r < (long long)P.R;
         int y0 = 0, y1 = 0;
@@ -1770,6 +1770,62 @@ __device__ __forceinline__ void replay_vblocks(const RunParams& P, const FastSme
     }
 }
 
+// Batches: at the start of a cycle the instance's leader thread claims idle
+// blocks (up to one block per group of replicas) and posts each its place in
+// the gang; the joiners start with the dephasing, after the barrier that
+// ends this cycle's decorrelation.  Also publishes what a joiner needs to
+// stay in step (chunk count, last chunk's sums).
+__device__ void recruit(const RunParams& P, RunCtl* ctl, int nblk, int nvb, unsigned long long chunk_c,
+                        unsigned long long est_q, unsigned long long est_ev) {
+    ctl->chunk_c = chunk_c;
+    ctl->est_q = est_q;
+    ctl->est_ev = est_ev;
+    const unsigned gen = ldv(&ctl->bar_gen);
+    const int want = nvb - nblk;
+    int got = 0;
+    const int nw = ((int)gridDim.x + 31) / 32;
+    for (int w = 0; w < nw && got < want; ++w) {
+        unsigned m = ldv(&P.batch.idle[w]);
+        while (m && got < want) {
+            const unsigned bit = m & (0u - m);
+            m &= ~bit;
+            const unsigned old = atomicAnd(&P.batch.idle[w], ~bit);
+            if (old & bit) {
+                int4* mb = &P.batch.mail[w * 32 + (__ffs(bit) - 1)];
+                ((volatile int*)mb)[0] = P.inst;
+                ((volatile int*)mb)[1] = nblk + got;
+                ((volatile int*)mb)[2] = (int)gen;
+                __threadfence();
+                atomicExch(&mb->w, 1);
+                ++got;
+            }
+        }
+    }
+    ctl->nblk = nblk + got;
+    __threadfence();
+}
+
+// A joiner waits (bounded) until the barrier of generation gen has passed.
+__device__ bool wait_generation(const RunParams& P, RunCtl* ctl, unsigned gen) {
+    unsigned long long t0 = globaltimer(), p0 = ldv(P.progress);
+    unsigned ns = 32;
+    while (ldv(&ctl->bar_gen) == gen) {
+        if (ldv(&ctl->status) != 0) return false;
+        __nanosleep(ns);
+        if (ns < 1024) ns <<= 1;
+        const unsigned long long p = ldv(P.progress), t = globaltimer();
+        if (p != p0) {
+            p0 = p;
+            t0 = t;
+        } else if ((long long)(t - t0) > P.timeout_ns) {
+            atomicCAS(&ctl->status, 0, PARREP_ETIMEOUT);
+            return false;
+        }
+    }
+    __threadfence();
+    return true;
+}
+
 // One ParRep run (Algorithm 1) of the instance P by the P.nblk blocks that
 // serve it; lb is this block's index among them.  Replicas come in virtual
 // blocks of RB (vb = 0 .. ceil(R / RB) - 1); block lb takes vb = lb,
@@ -1779,10 +1835,13 @@ __device__ __forceinline__ void replay_vblocks(const RunParams& P, const FastSme
 // each replica takes the same steps whatever block takes it and in whatever
 // order, so every result is independent of nblk.
 template <bool F32, int KIND>
-__device__ __forceinline__ void run_instance(const RunParams& P, int lb, unsigned char* smem, BlockScratch& red) {
+__device__ __forceinline__ void run_instance(const RunParams& P, int lb, unsigned char* smem, BlockScratch& red,
+                                             int join_gen = -1) {
     RunCtl* ctl = P.ctl;
     const NetDev& N = P.net;
-    const int nblk = P.nblk;
+    const bool batch = P.batch.remaining != nullptr;
+    const bool join = join_gen >= 0;  // a block recruited at a cycle start
+    int nblk = P.nblk;
     const int nvb = (P.R + P.RB - 1) / P.RB;
     const bool owner = (int)threadIdx.x < P.RB;
     const bool leader = lb == 0 && threadIdx.x == 0;
@@ -1817,7 +1876,7 @@ __device__ __forceinline__ void run_instance(const RunParams& P, int lb, unsigne
     }
     unsigned long long ev_replay = 0;
 
-    if (leader) {
+    if (leader && !join) {
         int x0 = P.x00, x1 = P.x01;
         if (P.x0_hi > 0) {
             uint4 w = philox10(make_uint4(0u, 0u, 0u, kTagInit), key);
@@ -1834,6 +1893,7 @@ __device__ __forceinline__ void run_instance(const RunParams& P, int lb, unsigne
         ctl->W = region_of(N, x0, x1);
         if (out_of_range(N, x0, x1)) atomicCAS(&ctl->status, 0, PARREP_EINVAL);
         ctl->done = P.q_Tend == 0 ? 1 : 0;
+        ctl->nblk = nblk;
         for (int s = 0; s < 3; ++s) {
             ctl->minkey[s] = kNone;
             ctl->oobkey[s] = kNone;
@@ -1849,6 +1909,22 @@ __device__ __forceinline__ void run_instance(const RunParams& P, int lb, unsigne
                 N.ystride, F32 ? ((1ull << 47) >> (P.log2RB + 5)) : 0ull};
     unsigned long long chunk_c = 0;
     unsigned long long est_q = 0, est_ev = 0;  // time and jumps of the last chunk
+    if (join) {
+        __shared__ int s_ok;
+        if (threadIdx.x == 0) s_ok = wait_generation(P, ctl, (unsigned)join_gen) ? 1 : 0;
+        __syncthreads();
+        if (!s_ok) goto out;
+        nblk = ldv(&ctl->nblk);
+        bs.nblk = nblk;
+        chunk_c = ldv(&ctl->chunk_c);
+        est_q = ldv(&ctl->est_q);
+        est_ev = ldv(&ctl->est_ev);
+        if (ldv(&ctl->burn_done) && !period_post) {
+            period_post = 1;
+            hs.g = P.hist_post;
+        }
+        goto joined;
+    }
     if (!grid_sync(P, bs)) goto out;
 
     for (;;) {
@@ -1860,10 +1936,16 @@ __device__ __forceinline__ void run_instance(const RunParams& P, int lb, unsigne
         } else {
             if (leader && !ctl->done) leader_decorrelate<F32>(P);
         }
+        if (batch && leader && !ldv(&ctl->done)) recruit(P, ctl, nblk, nvb, chunk_c, est_q, est_ev);
         pc.lap(kPhDecorr);
         if (!grid_sync(P, bs)) goto out;
         pc.lap(kPhBarrier);
+        if (batch) {
+            nblk = ldv(&ctl->nblk);
+            bs.nblk = nblk;
+        }
         if (ldv(&ctl->done)) break;
+    joined:
         {
             const int W = ldv(&ctl->W);
             RegionTest rt;
@@ -2020,7 +2102,7 @@ __device__ __forceinline__ void run_instance(const RunParams& P, int lb, unsigne
                 // ------------- special chunk: escape, range error or time cut -------------
                 if (leader) ctl->special += 1;
                 pc.start();
-                replay_vblocks<F32, KIND, kRollback>(P, F, hs, lb, nvb, rt, cycle, n0, Sc, key, none, period_post,
+                replay_vblocks<F32, KIND, kRollback>(P, F, hs, lb, nblk, nvb, rt, cycle, n0, Sc, key, none, period_post,
                                                      ev_replay, pc);
                 Cuts cut{kNone, kNone, kNone, 0, kNone, 0, -1, -1};
                 cut.posE = ekey;
@@ -2031,7 +2113,7 @@ __device__ __forceinline__ void run_instance(const RunParams& P, int lb, unsigne
                         for (int j = threadIdx.x; j < Sc; j += blockDim.x) P.step_sum[j] = 0;
                     }
                     if (!grid_sync(P, bs)) goto out;
-                    replay_vblocks<F32, KIND, kStepSum>(P, F, hs, lb, nvb, rt, cycle, n0, Sc, key, cut, period_post,
+                    replay_vblocks<F32, KIND, kStepSum>(P, F, hs, lb, nblk, nvb, rt, cycle, n0, Sc, key, cut, period_post,
                                                         ev_replay, pc);
                     if (!grid_sync(P, bs)) goto out;
                     unsigned long long baseB = 0, baseT = 0;
@@ -2058,7 +2140,7 @@ __device__ __forceinline__ void run_instance(const RunParams& P, int lb, unsigne
                                 P.tau_at[P.R + r] = 0;
                             }
                         }
-                        replay_vblocks<F32, KIND, kTauAt>(P, F, hs, lb, nvb, rt, cycle, n0, Sc, key, cut, period_post,
+                        replay_vblocks<F32, KIND, kTauAt>(P, F, hs, lb, nblk, nvb, rt, cycle, n0, Sc, key, cut, period_post,
                                                           ev_replay, pc);
                         if (!grid_sync(P, bs)) goto out;
                         if (leader) {
@@ -2112,7 +2194,7 @@ __device__ __forceinline__ void run_instance(const RunParams& P, int lb, unsigne
                 {
                     unsigned long long inc_q = 0, inc_ev = 0;
                     const bool tp = period_post || cut.posB != kNone;
-                    replay_vblocks<F32, KIND, kPrecise>(P, F, hs, lb, nvb, rt, cycle, n0, Sc, key, cut, tp, ev_replay,
+                    replay_vblocks<F32, KIND, kPrecise>(P, F, hs, lb, nblk, nvb, rt, cycle, n0, Sc, key, cut, tp, ev_replay,
                                                         pc, &inc_q, &inc_ev);
                     unsigned long long a = kNone, b = kNone;
                     block_reduce4(red, a, b, inc_q, inc_ev);
@@ -2178,6 +2260,10 @@ out:
     if (threadIdx.x == 0)
         for (int i = 0; i < 12; ++i)
             if (pc.acc[i]) atomicAdd(&ctl->phase_cycles[i], pc.acc[i]);
+    if (batch && leader) {
+        __threadfence();
+        atomicSub(P.batch.remaining, 1);
+    }
 }
 
 // One instance on the whole grid.
@@ -2190,34 +2276,102 @@ __global__ void __launch_bounds__(kMaxThreads) parrep_run_kernel(RunParams P) {
 
 // Many instances in one persistent launch.  Block b works through its list
 // items[off[b] .. off[b+1]) of (instance, local block index); the blocks that
-// serve an instance (its gang, P.nblk of them) meet at its barriers.  The
-// host orders every list by the instances' start times in one schedule, so
-// any two blocks meet their shared instances in the same order and no wait
-// is circular.  Both network kinds run in the same launch.
+// serve an instance (its gang, P.nblk of them at the start) meet at its
+// barriers.  The host orders every list by the instances' start times in one
+// schedule, so any two blocks meet their shared instances in the same order
+// and no wait is circular.  A block whose list is done goes idle: it sets its
+// bit in bd.idle and waits (bounded, on the batch's progress) for a mailbox
+// entry from an instance that recruits it at a cycle start, until no
+// instance is left.  Both network kinds run in the same launch.
+template <bool F32>
+__device__ __forceinline__ void batch_item(const RunParams* Ps, RunParams& sP, int inst, int lb, int join_gen,
+                                           unsigned char* smem, BlockScratch& red) {
+    const int* src = (const int*)(Ps + inst);
+    int* dst = (int*)&sP;
+    for (int w = threadIdx.x; w < (int)(sizeof(RunParams) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
+    __syncthreads();
+    if (sP.net.kind == PARREP_SCHLOGL) run_instance<F32, PARREP_SCHLOGL>(sP, lb, smem, red, join_gen);
+    else run_instance<F32, PARREP_TOGGLE>(sP, lb, smem, red, join_gen);
+    __syncthreads();
+}
+
 template <bool F32>
 __global__ void __launch_bounds__(kMaxThreads)
     parrep_batch_kernel(const RunParams* __restrict__ Ps, const int* __restrict__ off,
-                        const int2* __restrict__ items) {
+                        const int2* __restrict__ items, BatchDev bd) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ BlockScratch red;
     __shared__ RunParams sP;
+    __shared__ int4 s_mail;
     const int k1 = off[blockIdx.x + 1];
     for (int k = off[blockIdx.x]; k < k1; ++k) {
         const int2 it = items[k];
-        const int* src = (const int*)(Ps + it.x);
-        int* dst = (int*)&sP;
-        for (int w = threadIdx.x; w < (int)(sizeof(RunParams) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
+        batch_item<F32>(Ps, sP, it.x, it.y, -1, smem, red);
+    }
+    // idle: offer this block to instances that start a cycle
+    const unsigned long long* progress = Ps[0].progress;
+    const long long timeout_ns = Ps[0].timeout_ns;
+    int4* mb = bd.mail + blockIdx.x;
+    unsigned* word = bd.idle + blockIdx.x / 32;
+    const unsigned bit = 1u << (blockIdx.x % 32);
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int4 m = make_int4(-1, 0, 0, 0);
+            ((volatile int*)mb)[3] = 0;
+            __threadfence();
+            atomicOr(word, bit);
+            unsigned long long t0 = globaltimer(), p0 = ldv(progress);
+            unsigned ns = 64;
+            bool got = false;
+            for (;;) {
+                if (ldv(&mb->w)) {
+                    got = true;
+                    break;
+                }
+                if (ldv(bd.remaining) <= 0) break;
+                __nanosleep(ns);
+                if (ns < 2048) ns <<= 1;
+                const unsigned long long p = ldv(progress), t = globaltimer();
+                if (p != p0) {
+                    p0 = p;
+                    t0 = t;
+                } else if ((long long)(t - t0) > timeout_ns) {
+                    break;
+                }
+            }
+            if (!got) {
+                // withdraw; if an instance claimed the block meanwhile, its
+                // mail follows the claim at once
+                const unsigned old = atomicAnd(word, ~bit);
+                if (!(old & bit)) {
+                    const unsigned long long t1 = globaltimer();
+                    while (!ldv(&mb->w) && (long long)(globaltimer() - t1) < timeout_ns) __nanosleep(64);
+                    got = ldv(&mb->w) != 0;
+                }
+            }
+            if (got) {
+                __threadfence();
+                m = make_int4(ldv(&mb->x), ldv(&mb->y), ldv(&mb->z), 1);
+            }
+            s_mail = m;
+        }
         __syncthreads();
-        if (sP.net.kind == PARREP_SCHLOGL) run_instance<F32, PARREP_SCHLOGL>(sP, it.y, smem, red);
-        else run_instance<F32, PARREP_TOGGLE>(sP, it.y, smem, red);
+        const int4 m = s_mail;
         __syncthreads();
+        if (m.x < 0) break;
+        batch_item<F32>(Ps, sP, m.x, m.y, m.z, smem, red);
     }
 }
 
 // Zeroes the control block and the histograms of every instance of a batch
 // (one block per instance).
-__global__ void batch_reset_kernel(const RunParams* __restrict__ Ps, int n) {
+__global__ void batch_reset_kernel(const RunParams* __restrict__ Ps, int n, BatchDev bd, int grid) {
     const RunParams& P = Ps[blockIdx.x];
+    if (blockIdx.x == 0) {
+        if (threadIdx.x == 0) *bd.remaining = n;
+        for (int w = threadIdx.x; w < (grid + 31) / 32; w += blockDim.x) bd.idle[w] = 0;
+        for (int b = threadIdx.x; b < grid; b += blockDim.x) bd.mail[b] = make_int4(0, 0, 0, 0);
+    }
     unsigned long long* c = (unsigned long long*)P.ctl;
     for (int i = threadIdx.x; i < (int)(sizeof(RunCtl) / 8); i += blockDim.x) c[i] = 0;
     for (int b = threadIdx.x; b < P.net.nbins; b += blockDim.x) {
@@ -2436,10 +2590,10 @@ int batch_kernel_attrs(int prec, int* max_blocks_per_sm, int smem_bytes, int thr
                                : batch_attrs_one<false>(max_blocks_per_sm, smem_bytes, threads);
 }
 
-cudaError_t launch_batch(int prec, const RunParams* d_params, int n, const int* d_off, const int2* d_items, int grid,
-                         int threads, int smem_bytes, cudaStream_t st) {
+cudaError_t launch_batch(int prec, const RunParams* d_params, int n, const int* d_off, const int2* d_items,
+                         BatchDev bd, int grid, int threads, int smem_bytes, cudaStream_t st) {
     if (n < 1) return cudaSuccess;
-    batch_reset_kernel<<<n, 256, 0, st>>>(d_params, n);
+    batch_reset_kernel<<<n, 256, 0, st>>>(d_params, n, bd, grid);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
@@ -2452,8 +2606,8 @@ cudaError_t launch_batch(int prec, const RunParams* d_params, int n, const int* 
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (prec == PARREP_FP32) return cudaLaunchKernelEx(&cfg, parrep_batch_kernel<true>, d_params, d_off, d_items);
-    return cudaLaunchKernelEx(&cfg, parrep_batch_kernel<false>, d_params, d_off, d_items);
+    if (prec == PARREP_FP32) return cudaLaunchKernelEx(&cfg, parrep_batch_kernel<true>, d_params, d_off, d_items, bd);
+    return cudaLaunchKernelEx(&cfg, parrep_batch_kernel<false>, d_params, d_off, d_items, bd);
 }
 
 cudaError_t launch_batch_gather(const RunParams* d_params, int n, RunCtl* out, cudaStream_t st) {
