@@ -313,6 +313,94 @@ void parrep_batch_destroy(parrep_batch_t b);
  * when b is NULL). */
 const char* parrep_batch_last_error(parrep_batch_t b);
 
+/* ---------------------------------------------------------------------------
+ * Serving: a request loop with continuous batching.  One persistent serve
+ * kernel polls a ring of requests (published through a host-mapped counter);
+ * a block that claims
+ * a newly published request leads it, and at every cycle start (Algorithm 1)
+ * the request's leader recruits idle blocks into its gang, so requests that
+ * arrive while others run start at once on free blocks and their work
+ * overlaps on the device; a gang leaves an eighth of the blocks idle for
+ * requests still to come.  Requests are admitted by device memory: their
+ * buffers (replica states, histograms, tables) come from one arena allocated
+ * at parrep_server_create, first fit, in arrival order.  The replica state
+ * stays in the arena from admission to the result.  The last block of a
+ * request's gang writes its outputs (histogram normalised by T_s, FIM and
+ * RER over [T_burn, T_s], statistics) and flags it done.  A request's
+ * results depend only on the request: the same alone and in any mix, and the
+ * same as parrep_run of a handle with the same network, options and seed.
+ * A background host thread admits requests, (re)launches the serve kernel
+ * when requests wait and it has left, and collects completions.
+ * --------------------------------------------------------------------------- */
+typedef struct parrep_server_s* parrep_server_t;
+
+typedef struct {
+    int32_t precision;          /* PARREP_FP64 or PARREP_FP32, for every request */
+    int32_t block_threads;      /* 0 = 384 (FP32) / 128 (FP64) */
+    int32_t replicas_per_block; /* FP32 form: owner threads per block (32..256), 0 = 32 */
+    int32_t ring;               /* request slots (default 4096); a slot is reused after its result is read */
+    int64_t arena_bytes;        /* device memory for admitted requests (default 4 GiB) */
+    int64_t log_cap;            /* cycle-log records kept per request (default 4096) */
+    double idle_exit_s;         /* a serve block with nothing to do this long leaves (default 0.05 s) */
+    double wait_timeout_s;      /* device wait limit without progress (default 10 s) */
+} parrep_server_options;
+
+typedef struct {
+    parrep_network net;
+    parrep_regions regions;
+    int64_t n_replicas;
+    double t_corr, t_phase;     /* as in parrep_create */
+    double T_end, T_burn;       /* as in parrep_run / parrep_options */
+    uint64_t seed;
+    int32_t thresh_mode;        /* PARREP_THRESH_TIME or PARREP_THRESH_STEPS */
+    int32_t fv_group;           /* 0 = 32 */
+    int32_t chunk_steps;        /* 0 = default */
+    int32_t n_cprime;           /* perturbed parameter vectors for the RER (0..8) */
+    const double* c_prime;      /* n_cprime x l (l = 4 Schloegl, 6 toggle), copied at submit */
+} parrep_request;
+
+enum { PARREP_REQ_QUEUED = 0, PARREP_REQ_RUNNING = 1, PARREP_REQ_DONE = 2 };
+
+typedef struct {
+    int64_t submitted, admitted, completed, released;
+    int64_t launches;           /* serve-kernel launches so far */
+    int64_t queued, running;    /* requests waiting for admission / admitted and not done */
+    int64_t arena_bytes, arena_used;
+    int32_t grid_blocks, block_threads;
+} parrep_server_stats;
+
+void parrep_server_default_options(parrep_server_options* opt);
+
+/* Allocates the arena, the ring and the serve kernel's state and starts the
+ * host thread.  Errors: EINVAL, ENOMEM, ECUDA. */
+int parrep_server_create(const parrep_server_options* opt, parrep_server_t* out);
+
+/* Checks and copies a request and queues it; returns at once with its id.
+ * EINVAL for an invalid request or one that can never fit the arena. */
+int parrep_server_submit(parrep_server_t s, const parrep_request* req, int64_t* id);
+
+/* State of a request: PARREP_REQ_QUEUED, _RUNNING or _DONE. */
+int parrep_server_poll(parrep_server_t s, int64_t id, int32_t* state);
+
+/* Waits until the request is done; ETIMEOUT after timeout_s (the request
+ * stays in the server). */
+int parrep_server_wait(parrep_server_t s, int64_t id, double timeout_s);
+
+/* After parrep_server_wait: copies the results to host buffers (any may be
+ * NULL) and releases the request's memory and slot.  hist: len = bins;
+ * fim: l*l values; rer: n_cprime values; latency_s: submit to completion as
+ * seen by the host thread.  Returns the request's own status (PARREP_OK, or
+ * ERANGE / ETIMEOUT of its run); ESTATE if it is not done. */
+int parrep_server_result(parrep_server_t s, int64_t id, parrep_stats* stats, double* hist, int64_t len,
+                         double* fim, double* rer, double* latency_s);
+
+int parrep_server_stats_get(parrep_server_t s, parrep_server_stats* out);
+
+/* Stops accepting work, lets running requests finish, and frees everything. */
+void parrep_server_destroy(parrep_server_t s);
+
+const char* parrep_server_last_error(parrep_server_t s);
+
 /* Device Philox4x32-10 of n counters (ctr: n x 4, key: n x 2, out: n x 4
  * uint32, all host pointers) -- exposes the generator the kernels use. */
 int parrep_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out);

@@ -64,6 +64,28 @@ class parrep_batch_info(C.Structure):
                 ("est_balance", C.c_double)]
 
 
+class parrep_server_options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("block_threads", C.c_int32), ("replicas_per_block", C.c_int32),
+                ("ring", C.c_int32), ("arena_bytes", C.c_int64), ("log_cap", C.c_int64),
+                ("idle_exit_s", C.c_double), ("wait_timeout_s", C.c_double)]
+
+
+class parrep_request(C.Structure):
+    _fields_ = [("net", parrep_network), ("regions", parrep_regions), ("n_replicas", C.c_int64),
+                ("t_corr", C.c_double), ("t_phase", C.c_double), ("T_end", C.c_double), ("T_burn", C.c_double),
+                ("seed", C.c_uint64), ("thresh_mode", C.c_int32), ("fv_group", C.c_int32),
+                ("chunk_steps", C.c_int32), ("n_cprime", C.c_int32), ("c_prime", C.c_void_p)]
+
+
+class parrep_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64),
+                ("released", C.c_int64), ("launches", C.c_int64), ("queued", C.c_int64), ("running", C.c_int64),
+                ("arena_bytes", C.c_int64), ("arena_used", C.c_int64), ("grid_blocks", C.c_int32),
+                ("block_threads", C.c_int32)]
+
+
+PARREP_REQ_QUEUED, PARREP_REQ_RUNNING, PARREP_REQ_DONE = 0, 1, 2
+
 PHASES = ["decorrelation", "dephasing", "draw", "chain", "account", "barrier", "special", "vote", "dec_draw",
           "dec_chain", "dec_times", "dec_commit"]
 
@@ -79,7 +101,9 @@ EXPORTS = ["parrep_default_options", "parrep_create", "parrep_set_options", "par
            "parrep_cycle_log", "parrep_dephase", "parrep_destroy", "parrep_last_error", "parrep_ssa",
            "parrep_philox", "parrep_ssa_noalloc", "parrep_batch_default_options", "parrep_batch_create",
            "parrep_batch_run", "parrep_batch_status", "parrep_batch_info_get", "parrep_batch_destroy",
-           "parrep_batch_last_error"]
+           "parrep_batch_last_error", "parrep_server_default_options", "parrep_server_create",
+           "parrep_server_submit", "parrep_server_poll", "parrep_server_wait", "parrep_server_result",
+           "parrep_server_stats_get", "parrep_server_destroy", "parrep_server_last_error"]
 
 _lib = None
 
@@ -128,9 +152,22 @@ def load():
     L.parrep_batch_destroy.restype = None
     L.parrep_batch_last_error.argtypes = [vp]
     L.parrep_batch_last_error.restype = C.c_char_p
+    L.parrep_server_default_options.argtypes = [P(parrep_server_options)]
+    L.parrep_server_default_options.restype = None
+    L.parrep_server_create.argtypes = [P(parrep_server_options), P(vp)]
+    L.parrep_server_submit.argtypes = [vp, P(parrep_request), P(C.c_int64)]
+    L.parrep_server_poll.argtypes = [vp, C.c_int64, P(C.c_int32)]
+    L.parrep_server_wait.argtypes = [vp, C.c_int64, C.c_double]
+    L.parrep_server_result.argtypes = [vp, C.c_int64, P(parrep_stats), vp, C.c_int64, vp, vp, P(C.c_double)]
+    L.parrep_server_stats_get.argtypes = [vp, P(parrep_server_stats)]
+    L.parrep_server_destroy.argtypes = [vp]
+    L.parrep_server_destroy.restype = None
+    L.parrep_server_last_error.argtypes = [vp]
+    L.parrep_server_last_error.restype = C.c_char_p
     for name in EXPORTS:
         if name not in ("parrep_default_options", "parrep_n_bins", "parrep_destroy", "parrep_last_error",
-                        "parrep_batch_default_options", "parrep_batch_destroy", "parrep_batch_last_error"):
+                        "parrep_batch_default_options", "parrep_batch_destroy", "parrep_batch_last_error",
+                        "parrep_server_default_options", "parrep_server_destroy", "parrep_server_last_error"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L

@@ -153,11 +153,7 @@ class ParRep:
     def stats(self) -> dict:
         s = L.parrep_stats()
         _check(self._lib.parrep_stats_get(self.h, C.byref(s)), self.h)
-        d = {k: getattr(s, k) for k, _ in L.parrep_stats._fields_ if k != "pad"}
-        d["x0"] = (s.x0[0], s.x0[1])
-        d["x_final"] = (s.x_final[0], s.x_final[1])
-        d["phase_cycles"] = {n: float(s.phase_cycles[i]) for i, n in enumerate(L.PHASES)}
-        return d
+        return _stats_dict(s)
 
     def cycle_log(self, cap: int = 65536):
         buf = (L.parrep_cycle * max(cap, 1))()
@@ -250,6 +246,109 @@ class ParRepBatch:
         if getattr(self, "b", None):
             self._lib.parrep_batch_destroy(self.b)
             self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _stats_dict(s) -> dict:
+    d = {k: getattr(s, k) for k, _ in L.parrep_stats._fields_ if k != "pad"}
+    d["x0"] = (s.x0[0], s.x0[1])
+    d["x_final"] = (s.x_final[0], s.x_final[1])
+    d["phase_cycles"] = {n: float(s.phase_cycles[i]) for i, n in enumerate(L.PHASES)}
+    return d
+
+
+class ParRepServer:
+    """parrep_server_*: a request loop with continuous batching.  submit()
+    returns an id at once; result() waits and returns the request's outputs."""
+
+    def __init__(self, *, precision: str = "f32", block_threads: int = 0, replicas_per_block: int = 0,
+                 ring: int = 4096, arena_bytes: int = 4 << 30, log_cap: int = 4096, idle_exit_s: float = 0.05,
+                 wait_timeout_s: float = 10.0):
+        self._lib = L.load()
+        o = L.parrep_server_options()
+        self._lib.parrep_server_default_options(C.byref(o))
+        o.precision = L.PARREP_FP32 if precision == "f32" else L.PARREP_FP64
+        o.block_threads = int(block_threads)
+        o.replicas_per_block = int(replicas_per_block)
+        o.ring = int(ring)
+        o.arena_bytes = int(arena_bytes)
+        o.log_cap = int(log_cap)
+        o.idle_exit_s = float(idle_exit_s)
+        o.wait_timeout_s = float(wait_timeout_s)
+        s = C.c_void_p()
+        rc = self._lib.parrep_server_create(C.byref(o), C.byref(s))
+        if rc != L.PARREP_OK:
+            msg = self._lib.parrep_server_last_error(None)
+            raise ParRepError(rc, msg.decode() if msg else "")
+        self.s = s
+        self._meta = {}
+
+    def _check(self, rc):
+        if rc != L.PARREP_OK:
+            msg = self._lib.parrep_server_last_error(self.s)
+            raise ParRepError(rc, msg.decode() if msg else "")
+
+    def submit(self, spec: dict, n_replicas: int, t_corr: float, t_phase: float, T_end: float, seed: int, *,
+               x0=None, x0_uniform_hi: int = 0, thresh: str = "time", fv_group: int = 32, T_burn: float = 0.0,
+               chunk_steps: int = 0, rer=None) -> int:
+        r = L.parrep_request()
+        r.net = make_network(spec, x0, x0_uniform_hi)
+        r.regions = make_regions(spec)
+        r.n_replicas = int(n_replicas)
+        r.t_corr, r.t_phase = float(t_corr), float(t_phase)
+        r.T_end, r.T_burn = float(T_end), float(T_burn)
+        r.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+        r.thresh_mode = L.PARREP_THRESH_STEPS if thresh == "steps" else L.PARREP_THRESH_TIME
+        r.fv_group = int(fv_group)
+        r.chunk_steps = int(chunk_steps)
+        cp = None
+        if rer is not None:
+            cp = np.ascontiguousarray(rer, dtype=np.float64)
+            r.n_cprime = cp.shape[0]
+            r.c_prime = cp.ctypes.data
+        rid = C.c_int64(0)
+        self._check(self._lib.parrep_server_submit(self.s, C.byref(r), C.byref(rid)))
+        nl = 4 if spec["kind"] == "schlogl" else 6
+        hm = [spec["hist_max"]] if np.isscalar(spec["hist_max"]) else spec["hist_max"]
+        self._meta[rid.value] = (int(np.prod([h + 1 for h in hm])), nl, 0 if cp is None else cp.shape[0])
+        return rid.value
+
+    def poll(self, rid: int) -> int:
+        st = C.c_int32(0)
+        self._check(self._lib.parrep_server_poll(self.s, int(rid), C.byref(st)))
+        return st.value
+
+    def wait(self, rid: int, timeout_s: float = 600.0):
+        self._check(self._lib.parrep_server_wait(self.s, int(rid), float(timeout_s)))
+
+    def result(self, rid: int, timeout_s: float = 600.0) -> dict:
+        """Waits for the request, copies its outputs and releases it."""
+        self.wait(rid, timeout_s)
+        nb, nl, ncp = self._meta.pop(int(rid))
+        st = L.parrep_stats()
+        hist = np.zeros(nb)
+        fim = np.zeros(nl * nl)
+        rer = np.zeros(max(ncp, 1))
+        lat = C.c_double(0.0)
+        rc = self._lib.parrep_server_result(self.s, int(rid), C.byref(st), _buf(hist), nb, _buf(fim), _buf(rer),
+                                            C.byref(lat))
+        return {"status": rc, "stats": _stats_dict(st), "hist": hist, "fim": fim.reshape(nl, nl),
+                "rer": rer[:ncp], "latency_s": lat.value}
+
+    def stats(self) -> dict:
+        s = L.parrep_server_stats()
+        self._check(self._lib.parrep_server_stats_get(self.s, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def close(self):
+        if getattr(self, "s", None):
+            self._lib.parrep_server_destroy(self.s)
+            self.s = None
 
     def __del__(self):
         try:

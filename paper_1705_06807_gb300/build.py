@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libparrep.so")
-SOURCES = ["parrep_kernels.cu", "parrep_api.cu", "parrep_batch.cu", "parrep_noalloc.cu"]
+SOURCES = ["parrep_kernels.cu", "parrep_api.cu", "parrep_batch.cu", "parrep_serve.cu", "parrep_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -65,7 +65,7 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".{tag}.tmp"
-    cmd = [cc, "-shared", "-o", tmp] + objs + ARCH + ["-lcudart"]
+    cmd = [cc, "-shared", "-o", tmp] + objs + ARCH + ["-lcudart", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -55,7 +55,7 @@ extern "C" void parrep_default_options(parrep_options* o) {
     o->stream = nullptr;
 }
 
-static int check_network(const parrep_network* net, const parrep_regions* reg, std::string& why) {
+int parrep::check_network(const parrep_network* net, const parrep_regions* reg, std::string& why) {
     if (!net || !reg) { why = "null network or regions"; return 0; }
     if (net->kind != PARREP_SCHLOGL && net->kind != PARREP_TOGGLE) { why = "unknown network kind"; return 0; }
     const int nsp = net->kind == PARREP_SCHLOGL ? 1 : 2;
@@ -105,7 +105,7 @@ static int check_network(const parrep_network* net, const parrep_regions* reg, s
 
 // Host-built tables (toggle production rates, their log-derivatives in the
 // Hill exponent) and the network constants as the kernels read them.
-static void build_net(const parrep_network* net, const parrep_regions* reg, NetDev& nd,
+void parrep::build_net(const parrep_network* net, const parrep_regions* reg, NetDev& nd,
                       std::vector<double>& pU, std::vector<double>& pV, std::vector<double>& gU,
                       std::vector<double>& gV) {
     memset(&nd, 0, sizeof(nd));
@@ -456,9 +456,7 @@ int parrep::run_params(parrep_t h, double T_end, uint64_t seed, const Plan& pl, 
 }
 
 // Statistics of a finished run from its control block c.
-int parrep::run_finish(parrep_t h, const RunCtl& c, double T_end, const Plan& pl, float ms) {
-    h->h_ctl = c;
-    parrep_stats& s = h->stats;
+void parrep::stats_from_ctl(const RunCtl& c, parrep_stats& s) {
     memset(&s, 0, sizeof(s));
     s.T_s = (double)c.Ts * kQInv;
     s.events_decorr = (int64_t)c.ev_decorr;
@@ -475,11 +473,17 @@ int parrep::run_finish(parrep_t h, const RunCtl& c, double T_end, const Plan& pl
     s.x_final[0] = c.xt0;
     s.x_final[1] = c.xt1;
     s.status = c.status;
+    for (int i = 0; i < 12; ++i) s.phase_cycles[i] = (double)c.phase_cycles[i];
+}
+
+int parrep::run_finish(parrep_t h, const RunCtl& c, double T_end, const Plan& pl, float ms) {
+    h->h_ctl = c;
+    parrep_stats& s = h->stats;
+    stats_from_ctl(c, s);
     s.grid_blocks = pl.grid;
     s.block_threads = pl.threads;
     s.chunk_steps = pl.S;
     s.kernel_ms = ms;
-    for (int i = 0; i < 12; ++i) s.phase_cycles[i] = (double)c.phase_cycles[i];
     h->T_end = T_end;
     h->T_burn = h->opt.T_burn;
     if (c.status != 0) {

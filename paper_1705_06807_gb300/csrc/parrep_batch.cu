@@ -300,7 +300,7 @@ static int enqueue(parrep_batch_t b) {
     BCK(b, cudaMemcpyAsync(b->d_off, b->h_off, sizeof(int) * b->off_cap, cudaMemcpyHostToDevice, b->st));
     BCK(b, cudaMemcpyAsync(b->d_items, b->h_items, sizeof(int2) * b->items_cap, cudaMemcpyHostToDevice, b->st));
     BCK(b, cudaMemsetAsync(b->d_progress, 0, sizeof(unsigned long long), b->st));
-    BatchDev bd{b->d_remaining, b->d_idle, b->d_mail};
+    BatchDev bd{b->d_remaining, b->d_idle, b->d_mail, nullptr, nullptr, 0, 0};
     BCK(b, launch_batch(b->prec, b->d_params, n, b->d_off, b->d_items, bd, b->grid, b->threads, b->smem, b->st));
     BCK(b, launch_batch_gather(b->d_params, n, b->d_ctl_out, b->st));
     BCK(b, cudaMemcpyAsync(b->h_ctl_out, b->d_ctl_out, sizeof(RunCtl) * n, cudaMemcpyDeviceToHost, b->st));
@@ -319,7 +319,7 @@ static int run_once(parrep_batch_t b, const double* T_end, const uint64_t* seed,
         if (rc != PARREP_OK) return bfail(b, rc, std::string("instance ") + std::to_string(i) + ": " + h->err);
         p.progress = b->d_progress;
         p.timeout_ns = (long long)(b->opt.wait_timeout_s * 1e9);
-        p.batch = BatchDev{b->d_remaining, b->d_idle, b->d_mail};
+        p.batch = BatchDev{b->d_remaining, b->d_idle, b->d_mail, nullptr, nullptr, 0, 0};
         p.inst = i;
         b->h_params[i] = p;
     }

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <vector>
 
 #include "parrep.h"
 #include "parrep_internal.h"
@@ -56,6 +57,11 @@ struct Plan {
 };
 
 int fail(parrep_t h, int code, const std::string& msg);
+// network and region checks of parrep_create (1 = valid, else why is set)
+int check_network(const parrep_network* net, const parrep_regions* reg, std::string& why);
+// the kernels' view of a network and the host-built toggle tables
+void build_net(const parrep_network* net, const parrep_regions* reg, NetDev& nd, std::vector<double>& pU,
+               std::vector<double>& pV, std::vector<double>& gU, std::vector<double>& gV);
 int cuda_fail(parrep_t h, cudaError_t e, const char* what);
 int align16(int x);
 // shared-memory layout of the FP32 form for RB owners in blocks of `threads`
@@ -63,5 +69,7 @@ int fast_layout(parrep_t h, int RB, int threads, int with_hist, int pipelined, P
 int run_checks(parrep_t h, double T_end);
 int run_params(parrep_t h, double T_end, uint64_t seed, const Plan& pl, RunParams& p);
 int run_finish(parrep_t h, const RunCtl& c, double T_end, const Plan& pl, float ms);
+// the statistics a control block holds (launch shape and timing left zero)
+void stats_from_ctl(const RunCtl& c, parrep_stats& s);
 
 }  // namespace parrep

@@ -73,7 +73,8 @@ struct RunCtl {
     int xe0, xe1;
     // batches: the gang's current block count, and what a block that joins
     // at a cycle start needs to continue in step with the others
-    int nblk, pad1;
+    int nblk;
+    unsigned exited;  // blocks of the gang that have left the run
     unsigned long long chunk_c, est_q, est_ev;
     // statistics
     unsigned long long ev_decorr, ev_dephase, ev_par_exec, ev_useful, ev_replay;
@@ -93,6 +94,12 @@ struct BatchDev {
     int* remaining;
     unsigned* idle;   // [ceil(grid / 32)]
     int4* mail;       // [grid]: (instance, block index in the gang, barrier generation, valid)
+    // serving: requests published (host-mapped) and claimed; a gang recruits
+    // only while no published request waits for a block (nullptr: batches)
+    const unsigned long long* tail;
+    const unsigned long long* head;
+    int reserve;      // idle blocks a gang leaves unclaimed (room for new requests)
+    int pad;
 };
 
 struct RunParams {
@@ -132,6 +139,37 @@ struct RunParams {
     int stall_barrier;
 };
 
+// Serving: one request of the ring, in device memory.  The host copies it
+// in (and waits for the copy) before it publishes it by advancing *tail
+// (host-mapped); the device block that claims it runs the instance, and the
+// last block of its gang writes the outputs and sets done[slot] (host-mapped,
+// system scope).
+struct ServeSlot {
+    RunParams P;                   // device pointers into the server's arena; P.inst = slot index
+    double c[6], s[4];             // rate constants and Schloegl factors (FIM / RER)
+    double cprime[8 * 6];          // perturbed parameter vectors of the RER
+    double T_burn;                 // as given (the FIM / RER window starts here)
+    int n_cprime, L;
+    const double* gradU_n;         // toggle: d log(production) / d Hill exponent tables (arena)
+    const double* gradV_n;
+    double* out_hist;              // [nbins] histogram normalised by T_s
+    double* out_fim;               // [36] FIM over [T_burn, T_s]
+    double* out_rer;               // [8] RER over [T_burn, T_s]
+    RunCtl* out_ctl;               // the control block at the end (statistics)
+};
+
+struct ServeDev {
+    const ServeSlot* slots;        // device ring of cap entries
+    int* done;                     // host-mapped: done[slot] = 1 when the request's outputs are written
+    int cap, pad;
+    const unsigned long long* tail;  // host-mapped: requests published
+    unsigned long long* head;      // device: requests claimed
+    const int* stop;               // host-mapped: leave when set
+    BatchDev bd;                   // idle set and mailboxes (remaining: unused counter)
+    unsigned long long* progress;
+    long long idle_exit_ns;        // a block with nothing to do this long leaves
+};
+
 // ---- launchers (parrep_kernels.cu) ----
 int kernel_attrs(int prec, int kind, int* max_blocks_per_sm, int smem_bytes, int threads);
 cudaError_t launch_run(const RunParams& p, int grid, int threads, int smem_bytes, cudaStream_t st);
@@ -140,6 +178,8 @@ int batch_kernel_attrs(int prec, int* max_blocks_per_sm, int smem_bytes, int thr
 cudaError_t launch_batch(int prec, const RunParams* d_params, int n, const int* d_off, const int2* d_items,
                          BatchDev bd, int grid, int threads, int smem_bytes, cudaStream_t st);
 cudaError_t launch_batch_gather(const RunParams* d_params, int n, RunCtl* out, cudaStream_t st);
+int serve_kernel_attrs(int prec, int* max_blocks_per_sm, int smem_bytes, int threads);
+cudaError_t launch_serve(int prec, const ServeDev& sd, int grid, int threads, int smem_bytes, cudaStream_t st);
 cudaError_t launch_dephase(const RunParams& p, int xt0, int xt1, int W, unsigned cycle, long long np,
                            int* out_states, int grid, int threads, cudaStream_t st);
 cudaError_t launch_hist_normalise(const unsigned long long* pre, const unsigned long long* post, int n, double scale,

@@ -81,6 +81,24 @@ __device__ __forceinline__ T ldv(const T* p) {
     return *(const volatile T*)p;
 }
 
+// Loads and stores that order against memory the host writes or reads
+// (host-mapped rings and flags of the serving path).
+__device__ __forceinline__ unsigned long long ld_acquire_sys(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_acquire_sys(const int* p) {
+    int v;
+    asm volatile("ld.acquire.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_sys(int* p, int v) {
+    asm volatile("st.release.sys.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // ---------------------------------------------------------------------------
 // network: propensities, selection, update, regions
 // ---------------------------------------------------------------------------
@@ -278,6 +296,9 @@ __device__ bool grid_sync(const RunParams& P, BarState& bs) {
     __shared__ int ok;
     RunCtl* ctl = P.ctl;
     const int idx = bs.index++;
+    // lanes that skipped a leader-only stretch wait for it here: a block
+    // barrier needs the whole warp at the same instruction
+    __syncwarp();
     __syncthreads();
     if (P.stall_barrier >= 0 && idx == P.stall_barrier && bs.lb == 0) {
         // fault injection: block 0 leaves without arriving
@@ -315,6 +336,7 @@ __device__ bool grid_sync(const RunParams& P, BarState& bs) {
         // one read per block, so that every thread of the block takes the same branch
         ok = ldv(&ctl->status) == 0;
     }
+    __syncwarp();
     __syncthreads();
     return ok != 0;
 }
@@ -649,6 +671,7 @@ __device__ void replay_chunk(const RunParams& P, const HistSink& hs, int x0, int
 }
 
 __device__ void flush_shared(unsigned long long* sh, unsigned long long* g, int nbins) {
+    __syncwarp();
     __syncthreads();
     for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
         const unsigned long long v = sh[b];
@@ -1781,28 +1804,37 @@ __device__ void recruit(const RunParams& P, RunCtl* ctl, int nblk, int nvb, unsi
     ctl->est_q = est_q;
     ctl->est_ev = est_ev;
     const unsigned gen = ldv(&ctl->bar_gen);
-    const int want = nvb - nblk;
+    constexpr int kMaxRecruit = 128;
+    int want = min(nvb - nblk, kMaxRecruit);
+    if (P.batch.tail && ld_acquire_sys(P.batch.tail) > ldv(P.batch.head)) want = 0;  // new requests first
     int got = 0;
     const int nw = ((int)gridDim.x + 31) / 32;
+    if (want > 0 && P.batch.reserve > 0) {
+        int idle = 0;
+        for (int w = 0; w < nw; ++w) idle += __popc(ldv(&P.batch.idle[w]));
+        want = min(want, idle - P.batch.reserve);
+    }
+    short ids[kMaxRecruit];
     for (int w = 0; w < nw && got < want; ++w) {
         unsigned m = ldv(&P.batch.idle[w]);
         while (m && got < want) {
             const unsigned bit = m & (0u - m);
             m &= ~bit;
             const unsigned old = atomicAnd(&P.batch.idle[w], ~bit);
-            if (old & bit) {
-                int4* mb = &P.batch.mail[w * 32 + (__ffs(bit) - 1)];
-                ((volatile int*)mb)[0] = P.inst;
-                ((volatile int*)mb)[1] = nblk + got;
-                ((volatile int*)mb)[2] = (int)gen;
-                __threadfence();
-                atomicExch(&mb->w, 1);
-                ++got;
-            }
+            if (old & bit) ids[got++] = (short)(w * 32 + (__ffs(bit) - 1));
         }
     }
+    // the gang size first, so that no member can ever see a smaller one
     ctl->nblk = nblk + got;
     __threadfence();
+    for (int j = 0; j < got; ++j) {
+        int4* mb = &P.batch.mail[ids[j]];
+        ((volatile int*)mb)[0] = P.inst;
+        ((volatile int*)mb)[1] = nblk + j;
+        ((volatile int*)mb)[2] = (int)gen;
+        __threadfence();
+        atomicExch(&mb->w, 1);
+    }
 }
 
 // A joiner waits (bounded) until the barrier of generation gen has passed.
@@ -1835,7 +1867,7 @@ __device__ bool wait_generation(const RunParams& P, RunCtl* ctl, unsigned gen) {
 // each replica takes the same steps whatever block takes it and in whatever
 // order, so every result is independent of nblk.
 template <bool F32, int KIND>
-__device__ __forceinline__ void run_instance(const RunParams& P, int lb, unsigned char* smem, BlockScratch& red,
+__device__ __forceinline__ bool run_instance(const RunParams& P, int lb, unsigned char* smem, BlockScratch& red,
                                              int join_gen = -1) {
     RunCtl* ctl = P.ctl;
     const NetDev& N = P.net;
@@ -1912,6 +1944,7 @@ __device__ __forceinline__ void run_instance(const RunParams& P, int lb, unsigne
     if (join) {
         __shared__ int s_ok;
         if (threadIdx.x == 0) s_ok = wait_generation(P, ctl, (unsigned)join_gen) ? 1 : 0;
+        __syncwarp();
         __syncthreads();
         if (!s_ok) goto out;
         nblk = ldv(&ctl->nblk);
@@ -1923,29 +1956,31 @@ __device__ __forceinline__ void run_instance(const RunParams& P, int lb, unsigne
             period_post = 1;
             hs.g = P.hist_post;
         }
-        goto joined;
+    } else if (!grid_sync(P, bs)) {
+        goto out;
     }
-    if (!grid_sync(P, bs)) goto out;
 
-    for (;;) {
+    for (bool first = true;; first = false) {
         // ---------------- decorrelation (serial) ----------------
-        pc.start();
-        if (F32) {
-            if (lb == 0 && !ldv(&ctl->done))
-                decorrelate_f32<KIND>(P, F, hs, period_post, pc);
-        } else {
-            if (leader && !ctl->done) leader_decorrelate<F32>(P);
+        // (a block that joined at this cycle's start begins after it)
+        if (!(join && first)) {
+            pc.start();
+            if (F32) {
+                if (lb == 0 && !ldv(&ctl->done))
+                    decorrelate_f32<KIND>(P, F, hs, period_post, pc);
+            } else {
+                if (leader && !ctl->done) leader_decorrelate<F32>(P);
+            }
+            if (batch && leader && !ldv(&ctl->done)) recruit(P, ctl, nblk, nvb, chunk_c, est_q, est_ev);
+            pc.lap(kPhDecorr);
+            if (!grid_sync(P, bs)) goto out;
+            pc.lap(kPhBarrier);
+            if (batch) {
+                nblk = ldv(&ctl->nblk);
+                bs.nblk = nblk;
+            }
+            if (ldv(&ctl->done)) break;
         }
-        if (batch && leader && !ldv(&ctl->done)) recruit(P, ctl, nblk, nvb, chunk_c, est_q, est_ev);
-        pc.lap(kPhDecorr);
-        if (!grid_sync(P, bs)) goto out;
-        pc.lap(kPhBarrier);
-        if (batch) {
-            nblk = ldv(&ctl->nblk);
-            bs.nblk = nblk;
-        }
-        if (ldv(&ctl->done)) break;
-    joined:
         {
             const int W = ldv(&ctl->W);
             RegionTest rt;
@@ -1971,6 +2006,7 @@ __device__ __forceinline__ void run_instance(const RunParams& P, int lb, unsigne
                     if (F32) derr |= dephase_f32<KIND>(P, F, rt, active, rbase, r, xt0, xt1, np, cycle, key, x0, x1);
                     else derr |= dephase_warp<F32>(N, active, r, P.G, W, xt0, xt1, np, cycle, key, x0, x1);
                     if (active) P.xs[r] = make_int2(x0, x1);
+                    __syncwarp();
                     __syncthreads();
                 }
                 if (derr && (threadIdx.x & 31) == 0) atomicCAS(&ctl->status, 0, PARREP_ERANGE);
@@ -2013,6 +2049,7 @@ __device__ __forceinline__ void run_instance(const RunParams& P, int lb, unsigne
                     ctl->inc_sum[s1] = 0;
                     ctl->inc_ev[s1] = 0;
                 }
+                __syncwarp();  // the leader's lanes meet again before the block-wide chunk
                 unsigned long long mykey = kNone, myoob = kNone, qsum = 0, ev = 0;
                 Cuts none{kNone, kNone, kNone, 0, kNone, 0, -1, -1};
                 for (int vb = lb; vb < nvb; vb += nblk) {
@@ -2101,6 +2138,7 @@ __device__ __forceinline__ void run_instance(const RunParams& P, int lb, unsigne
                 }
                 // ------------- special chunk: escape, range error or time cut -------------
                 if (leader) ctl->special += 1;
+                __syncwarp();
                 pc.start();
                 replay_vblocks<F32, KIND, kRollback>(P, F, hs, lb, nblk, nvb, rt, cycle, n0, Sc, key, none, period_post,
                                                      ev_replay, pc);
@@ -2264,6 +2302,18 @@ out:
         __threadfence();
         atomicSub(P.batch.remaining, 1);
     }
+    // the last block of the gang to leave (for an epilogue after all flushes)
+    __shared__ int s_last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned old = atomicAdd(&ctl->exited, 1u);
+        __threadfence();
+        const bool over = ldv(&ctl->done) != 0 || ldv(&ctl->status) != 0;
+        s_last = over && old + 1 == (unsigned)ldv(&ctl->nblk) ? 1 : 0;
+    }
+    __syncwarp();
+    __syncthreads();
+    return s_last != 0;
 }
 
 // One instance on the whole grid.
@@ -2355,11 +2405,142 @@ __global__ void __launch_bounds__(kMaxThreads)
             }
             s_mail = m;
         }
+        __syncwarp();
         __syncthreads();
         const int4 m = s_mail;
         __syncthreads();
         if (m.x < 0) break;
         batch_item<F32>(Ps, sP, m.x, m.y, m.z, smem, red);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// serving: requests from a host-mapped ring, continuous batching
+// ---------------------------------------------------------------------------
+
+// What a serving block does next (thread 0): join a gang that recruited it
+// (w = 2: slot, block index, barrier generation), lead a newly published
+// request (w = 1: slot), or leave (w = 0) on the stop flag or after idling
+// for idle_exit_ns.  While it waits it is in the idle set.
+__device__ int4 serve_next(const ServeDev& sd) {
+    int4* mb = sd.bd.mail + blockIdx.x;
+    unsigned* word = sd.bd.idle + blockIdx.x / 32;
+    const unsigned bit = 1u << (blockIdx.x % 32);
+    ((volatile int*)mb)[3] = 0;
+    __threadfence();
+    atomicOr(word, bit);
+    const unsigned long long t0 = globaltimer();
+    unsigned ns = 64;
+    for (;;) {
+        if (ldv(&mb->w)) {
+            __threadfence();
+            return make_int4(ldv(&mb->x), ldv(&mb->y), ldv(&mb->z), 2);
+        }
+        const unsigned long long tail = ld_acquire_sys(sd.tail);
+        const unsigned long long head = ldv(sd.head);
+        const bool stop = ld_acquire_sys(sd.stop) != 0;
+        const bool idle_out = (long long)(globaltimer() - t0) > sd.idle_exit_ns;
+        if (head < tail || stop || idle_out) {
+            const unsigned old = atomicAnd(word, ~bit);
+            if (!(old & bit)) {
+                // a gang claimed this block meanwhile: its mail follows at once
+                const unsigned long long t1 = globaltimer();
+                while (!ldv(&mb->w) && (long long)(globaltimer() - t1) < 1000000000ll) __nanosleep(64);
+                if (!ldv(&mb->w)) return make_int4(0, 0, 0, 0);
+                __threadfence();
+                return make_int4(ldv(&mb->x), ldv(&mb->y), ldv(&mb->z), 2);
+            }
+            if (stop || (head >= tail && idle_out)) return make_int4(0, 0, 0, 0);
+            if (head < tail && atomicCAS(sd.head, head, head + 1) == head)
+                return make_int4((int)(head % (unsigned long long)sd.cap), 0, -1, 1);
+            ((volatile int*)mb)[3] = 0;
+            __threadfence();
+            atomicOr(word, bit);
+            continue;
+        }
+        __nanosleep(ns);
+        if (ns < 1024) ns <<= 1;
+    }
+}
+
+__device__ void fim_rer_accumulate(const NetDev& N, const double* __restrict__ c, const double* __restrict__ s,
+                                   const unsigned long long* __restrict__ hist, const double* __restrict__ gradU_n,
+                                   const double* __restrict__ gradV_n, const double* __restrict__ cprime,
+                                   int n_cprime, double* fim_out, double* rer_out, int start, int stride);
+
+// Outputs of a finished request, by the last block of its gang: the
+// histogram normalised by T_s, the FIM and RER contracted over the post-burn
+// histogram and divided by T_s - T_burn, the control block; then done.
+__device__ void serve_epilogue(const RunParams& P, const ServeSlot* slot, int* done) {
+    __shared__ double s_c[6], s_s[4], s_cp[48];
+    __shared__ int s_n, s_L;
+    __shared__ double s_Tb;
+    RunCtl* ctl = P.ctl;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 6; ++i) s_c[i] = slot->c[i];
+        for (int i = 0; i < 4; ++i) s_s[i] = slot->s[i];
+        s_n = slot->n_cprime < 8 ? slot->n_cprime : 8;
+        s_L = slot->L;
+        s_Tb = slot->T_burn;
+        for (int i = 0; i < s_n * s_L; ++i) s_cp[i] = slot->cprime[i];
+    }
+    __syncwarp();
+    double* out_hist = slot->out_hist;
+    double* out_fim = slot->out_fim;
+    double* out_rer = slot->out_rer;
+    const double* gU = slot->gradU_n;
+    const double* gV = slot->gradV_n;
+    __syncthreads();
+    const double Ts = (double)ldv(&ctl->Ts) * kQInv;
+    const double scale = Ts > 0 ? 1.0 / Ts : 0.0;
+    for (int b = threadIdx.x; b < P.net.nbins; b += blockDim.x) {
+        const double a = (double)__ldcg(P.hist_pre + b) * kQInv, c = (double)__ldcg(P.hist_post + b) * kQInv;
+        out_hist[b] = (a + c) * scale;
+    }
+    for (int i = threadIdx.x; i < 36; i += blockDim.x) out_fim[i] = 0.0;
+    for (int i = threadIdx.x; i < 8; i += blockDim.x) out_rer[i] = 0.0;
+    __syncthreads();
+    if (ldv(&ctl->status) == 0)
+        fim_rer_accumulate(P.net, s_c, s_s, P.hist_post, gU, gV, s_cp, s_n, out_fim, out_rer, threadIdx.x,
+                           blockDim.x);
+    __syncthreads();
+    const double span = Ts - s_Tb;
+    if (span > 0.0) {
+        if ((int)threadIdx.x < s_L * s_L) out_fim[threadIdx.x] /= span;
+        if ((int)threadIdx.x < s_n) out_rer[threadIdx.x] /= span;
+    }
+    const unsigned long long* src = (const unsigned long long*)ctl;
+    unsigned long long* dst = (unsigned long long*)slot->out_ctl;
+    for (int i = threadIdx.x; i < (int)(sizeof(RunCtl) / 8); i += blockDim.x) dst[i] = ldv(src + i);
+    __threadfence_system();
+    __syncthreads();
+    if (threadIdx.x == 0) st_release_sys(done, 1);
+}
+
+template <bool F32>
+__global__ void __launch_bounds__(kMaxThreads) parrep_serve_kernel(ServeDev sd) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ BlockScratch red;
+    __shared__ RunParams sP;
+    __shared__ int4 s_cmd;
+    for (;;) {
+        if (threadIdx.x == 0) s_cmd = serve_next(sd);
+        __syncwarp();
+        __syncthreads();
+        const int4 cmd = s_cmd;
+        __syncthreads();
+        if (cmd.w == 0) break;
+        const ServeSlot* slot = sd.slots + cmd.x;
+        const int* src = (const int*)&slot->P;
+        int* dst = (int*)&sP;
+        for (int w = threadIdx.x; w < (int)(sizeof(RunParams) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
+        __syncthreads();
+        const int join_gen = cmd.w == 2 ? cmd.z : -1;
+        const bool last = sP.net.kind == PARREP_SCHLOGL
+                              ? run_instance<F32, PARREP_SCHLOGL>(sP, cmd.y, smem, red, join_gen)
+                              : run_instance<F32, PARREP_TOGGLE>(sP, cmd.y, smem, red, join_gen);
+        if (last) serve_epilogue(sP, slot, sd.done + cmd.x);
+        __syncthreads();
     }
 }
 
@@ -2420,10 +2601,10 @@ __global__ void hist_normalise_kernel(const unsigned long long* pre, const unsig
 // Per bin: w = time in the bin; FIM += w sum_j lambda_j g_j g_j^T with
 // g_j = grad_c log lambda_j; RER_k += w sum_j [lambda_j log(lambda_j/lambda'_j)
 // - lambda_j + lambda'_j].
-__global__ void fim_rer_kernel(NetDev N, const double* __restrict__ c, const double* __restrict__ s,
-                               const unsigned long long* __restrict__ hist, const double* __restrict__ gradU_n,
-                               const double* __restrict__ gradV_n, const double* __restrict__ cprime, int n_cprime,
-                               double* fim_out, double* rer_out) {
+__device__ void fim_rer_accumulate(const NetDev& N, const double* __restrict__ c, const double* __restrict__ s,
+                                   const unsigned long long* __restrict__ hist, const double* __restrict__ gradU_n,
+                                   const double* __restrict__ gradV_n, const double* __restrict__ cprime,
+                                   int n_cprime, double* fim_out, double* rer_out, int start, int stride) {
     const int L = N.kind == PARREP_SCHLOGL ? 4 : 6;
     double acc[36];
 #pragma unroll
@@ -2431,8 +2612,8 @@ __global__ void fim_rer_kernel(NetDev N, const double* __restrict__ c, const dou
     double racc[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) racc[i] = 0.0;
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < N.nbins; b += gridDim.x * blockDim.x) {
-        const unsigned long long hq = hist[b];
+    for (int b = start; b < N.nbins; b += stride) {
+        const unsigned long long hq = __ldcg(hist + b);
         if (!hq) continue;
         const double w = (double)hq * kQInv;
         const int x0 = b / N.ystride, x1 = b % N.ystride;
@@ -2495,6 +2676,14 @@ __global__ void fim_rer_kernel(NetDev N, const double* __restrict__ c, const dou
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(rer_out + k, v);
     }
+}
+
+__global__ void fim_rer_kernel(NetDev N, const double* __restrict__ c, const double* __restrict__ s,
+                               const unsigned long long* __restrict__ hist, const double* __restrict__ gradU_n,
+                               const double* __restrict__ gradV_n, const double* __restrict__ cprime, int n_cprime,
+                               double* fim_out, double* rer_out) {
+    fim_rer_accumulate(N, c, s, hist, gradU_n, gradV_n, cprime, n_cprime, fim_out, rer_out,
+                       blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -2613,6 +2802,27 @@ cudaError_t launch_batch(int prec, const RunParams* d_params, int n, const int* 
 cudaError_t launch_batch_gather(const RunParams* d_params, int n, RunCtl* out, cudaStream_t st) {
     if (n < 1) return cudaSuccess;
     batch_gather_kernel<<<n, 64, 0, st>>>(d_params, n, out);
+    return cudaGetLastError();
+}
+
+template <bool F32>
+static int serve_attrs_one(int* max_blocks_per_sm, int smem_bytes, int threads) {
+    cudaError_t e = cudaFuncSetAttribute(parrep_serve_kernel<F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem_bytes);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, parrep_serve_kernel<F32>, threads,
+                                                          smem_bytes);
+    return (int)e;
+}
+
+int serve_kernel_attrs(int prec, int* max_blocks_per_sm, int smem_bytes, int threads) {
+    return prec == PARREP_FP32 ? serve_attrs_one<true>(max_blocks_per_sm, smem_bytes, threads)
+                               : serve_attrs_one<false>(max_blocks_per_sm, smem_bytes, threads);
+}
+
+cudaError_t launch_serve(int prec, const ServeDev& sd, int grid, int threads, int smem_bytes, cudaStream_t st) {
+    if (prec == PARREP_FP32) parrep_serve_kernel<true><<<grid, threads, smem_bytes, st>>>(sd);
+    else parrep_serve_kernel<false><<<grid, threads, smem_bytes, st>>>(sd);
     return cudaGetLastError();
 }
 
