@@ -61,9 +61,12 @@ def parse():
     ap.add_argument("--t_phase", type=float, default=None, help="override t_phase (profiling)")
     ap.add_argument("--block_threads", type=int, default=0, help="CUDA block size (0 = library default)")
     ap.add_argument("--chunk_steps", type=int, default=0, help="steps between escape votes (0 = default)")
-    ap.add_argument("--workload", default="schlogl_n4096", choices=["schlogl_n4096", "batch256"],
+    ap.add_argument("--workload", default="schlogl_n4096", choices=["schlogl_n4096", "batch256", "serve"],
                     help="schlogl_n4096: one ParRep run of 4096 replicas to T_end = 1e6 per step; batch256: "
-                         "256 mixed Schloegl / toggle instances (64..65536 replicas, T_end = 1e4) in one launch")
+                         "256 mixed Schloegl / toggle instances (64..65536 replicas, T_end = 1e4) in one launch; "
+                         "serve: Poisson-arriving requests through the continuous-batching server")
+    ap.add_argument("--serve_rate", type=float, default=200.0, help="request arrivals per second (serve)")
+    ap.add_argument("--serve_seconds", type=float, default=20.0, help="length of the arrival stream (serve)")
     ap.add_argument("--batch_n", type=int, default=256, help="instances of the batch workload")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -284,6 +287,92 @@ def bench_batch(args, world, rank, local, dist):
     batch.close()
 
 
+def bench_serve(args, local):
+    """The serving workload: requests arrive at their Poisson times, are
+    submitted from host structs and their results (histogram, FIM, stats)
+    read back to host memory as they complete."""
+    import numpy as np
+    import torch
+
+    from paper_1705_06807_gb300 import ParRepServer
+    from paper_1705_06807_gb300 import configs as K
+
+    stream = K.serve_requests(rate=args.serve_rate, seconds=args.serve_seconds, seed=0)
+    srv = ParRepServer(precision=args.precision)
+    # warm-up: a few small requests (module load, first launches)
+    for i in range(max(args.warmup, 1)):
+        d = stream[i][1]
+        srv.result(srv.submit(d["network"], 64, d["t_corr"], d["t_phase"], 100.0, 1000 + i, x0=d["x0"],
+                              T_burn=50.0))
+    torch.cuda.synchronize()
+    pending, lat, useful, executed, dephase = {}, [], 0, 0, 0
+
+    tm = {"submit": 0.0, "poll": 0.0, "result": 0.0}
+
+    def collect(block=False):
+        nonlocal useful, executed, dephase
+        for rid in list(pending):
+            t1 = time.perf_counter()
+            ready = block or srv.poll(rid) == 2
+            t2 = time.perf_counter()
+            tm["poll"] += t2 - t1
+            if ready:
+                r = srv.result(rid)
+                tm["result"] += time.perf_counter() - t2
+                assert r["status"] == 0, r["status"]
+                st = r["stats"]
+                lat.append(r["latency_s"])
+                useful += st["events_decorr"] + st["events_parallel_useful"]
+                executed += (st["events_decorr"] + st["events_parallel_executed"] + st["events_replay"] +
+                             st["events_dephase"])
+                dephase += st["events_dephase"]
+                del pending[rid]
+
+    launches0 = srv.stats()["launches"]
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for t_arr, d in stream:
+            while time.perf_counter() - t0 < t_arr:
+                collect()
+                time.sleep(0.0002)
+            t1 = time.perf_counter()
+            rid = srv.submit(d["network"], d["n_replicas"], d["t_corr"], d["t_phase"], d["T_end"], d["seed"],
+                             x0=d["x0"], T_burn=0.5 * d["T_end"])
+            tm["submit"] += time.perf_counter() - t1
+            pending[rid] = t_arr
+        t_stream = time.perf_counter() - t0
+        collect(block=True)
+        wall = time.perf_counter() - t0
+    clocks = clk.summary()
+    st = srv.stats()
+    srv.close()
+    lat_a = np.array(lat)
+    peak_ops = N_SM * 4 * 32 * PEAK_SM_CLOCK_HZ
+    ops = (executed - dephase) * OPS_PER_EVENT + dephase * OPS_PER_DEPHASE_EVENT
+    line = {
+        "metric": "SSA events/s", "value": useful / wall, "unit": "events/s", "n_gpus": 1, "steps": 1,
+        "warmup": args.warmup, "ms_per_step": 1e3 * wall, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": f"serve_poisson{args.serve_rate:g}_{args.serve_seconds:g}s",
+                   "requests": len(stream), "mix": "Schloegl V in {0.5,1,2,4,8} / toggle n~U[2,3] alpha~U[30,80], "
+                   "replicas log-uniform 64..65536, T_end log-uniform 1e3..1e5, t_corr=t_phase=1",
+                   "timing": "wall clock from the first arrival to the last result on the host"},
+        "latency_s": {"p50": float(np.percentile(lat_a, 50)), "p99": float(np.percentile(lat_a, 99)),
+                      "mean": float(lat_a.mean()), "max": float(lat_a.max())},
+        "executed_events_per_s": executed / wall,
+        "roofline": {"bound": "alu", "achieved": ops / wall / 1e12, "peak": peak_ops / 1e12, "unit": "Tinst/s",
+                     "frac": ops / wall / peak_ops, "traffic": None,
+                     "note": "over the wall time of the stream, idle gaps between arrivals included"},
+        "gpu_launches": st["launches"] - launches0,
+        "server": {k: st[k] for k in ("submitted", "admitted", "completed", "launches", "grid_blocks")},
+        "host_s": {"stream": t_stream, **{k: round(v, 3) for k, v in tm.items()}},
+        "clocks": clocks,
+        "e2e": {"value": useful / wall, "unit": "events/s", "h2d_bytes_per_step": len(stream) * 600,
+                "d2h_bytes_per_step": None, "note": "the served path is end to end: host requests in, host results out"},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -304,6 +393,12 @@ def main():
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.workload == "serve":
+        if rank == 0:
+            bench_serve(args, local)
+        if dist:
+            dist.destroy_process_group()
+        return
     if args.workload == "batch256":
         bench_batch(args, world, rank, local, dist)
         if dist:

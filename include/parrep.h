@@ -320,8 +320,8 @@ const char* parrep_batch_last_error(parrep_batch_t b);
  * a newly published request leads it, and at every cycle start (Algorithm 1)
  * the request's leader recruits idle blocks into its gang, so requests that
  * arrive while others run start at once on free blocks and their work
- * overlaps on the device; a gang leaves an eighth of the blocks idle for
- * requests still to come.  Requests are admitted by device memory: their
+ * overlaps on the device; a gang leaves an eighth of the blocks, and one
+ * block for every published request not yet claimed, idle for those.  Requests are admitted by device memory: their
  * buffers (replica states, histograms, tables) come from one arena allocated
  * at parrep_server_create, first fit, in arrival order.  The replica state
  * stays in the arena from admission to the result.  The last block of a
@@ -341,7 +341,8 @@ typedef struct {
     int32_t ring;               /* request slots (default 4096); a slot is reused after its result is read */
     int64_t arena_bytes;        /* device memory for admitted requests (default 4 GiB) */
     int64_t log_cap;            /* cycle-log records kept per request (default 4096) */
-    double idle_exit_s;         /* a serve block with nothing to do this long leaves (default 0.05 s) */
+    double idle_exit_s;         /* the serve kernel ends after the server has had nothing to do this
+                                   long (default 0.05 s); the next request relaunches it */
     double wait_timeout_s;      /* device wait limit without progress (default 10 s) */
 } parrep_server_options;
 

@@ -89,3 +89,34 @@ def batch_instances(n: int = 256, seed: int = 0, T_end: float = 1e4, n_min: int 
         out.append(dict(network=net, n_replicas=R, t_corr=1.0, t_phase=1.0, T_end=T_end, x0=x0,
                         seed=int(rng.integers(0, 2**63)), precision="f32", thresh="time"))
     return out
+
+
+def serve_requests(rate: float = 200.0, seconds: float = 60.0, seed: int = 0, n_min: int = 64, n_max: int = 65536,
+                   T_min: float = 1e3, T_max: float = 1e5):
+    """Seeded request stream for the serving workload: Poisson arrivals at
+    `rate` per second for `seconds`; each request a Schloegl or toggle
+    instance (50/50, parameters drawn as in batch_instances), replica count
+    log-uniform in [n_min, n_max], T_end log-uniform in [T_min, T_max].
+    Returns a list of (arrival time in seconds, instance dict)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    t = 0.0
+    while True:
+        t += float(rng.exponential(1.0 / rate))
+        if t >= seconds:
+            break
+        R = int(np.exp(rng.uniform(np.log(n_min), np.log(n_max))))
+        T_end = float(np.exp(rng.uniform(np.log(T_min), np.log(T_max))))
+        if rng.random() < 0.5:
+            V = float(rng.choice([0.5, 1.0, 2.0, 4.0, 8.0]))
+            net = schlogl_classic(V=V)
+            x0 = [int(round(85 * V))]
+        else:
+            hill = float(rng.uniform(2.0, 3.0))
+            alpha = float(rng.uniform(30.0, 80.0))
+            hm = int(max(63, np.ceil(alpha + 10.0 * np.sqrt(alpha) + 20.0)))
+            net = toggle(alpha=alpha, n=hill, hist_max=(hm, hm))
+            x0 = [int(alpha), 0]
+        out.append((t, dict(network=net, n_replicas=R, t_corr=1.0, t_phase=1.0, T_end=T_end, x0=x0,
+                            seed=int(rng.integers(0, 2**63)), thresh="time")))
+    return out

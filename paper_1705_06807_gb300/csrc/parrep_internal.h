@@ -164,10 +164,11 @@ struct ServeDev {
     int cap, pad;
     const unsigned long long* tail;  // host-mapped: requests published
     unsigned long long* head;      // device: requests claimed
+    unsigned long long* finished;  // device: requests whose outputs are written
     const int* stop;               // host-mapped: leave when set
     BatchDev bd;                   // idle set and mailboxes (remaining: unused counter)
     unsigned long long* progress;
-    long long idle_exit_ns;        // a block with nothing to do this long leaves
+    long long idle_exit_ns;        // blocks leave after the server has been idle this long
 };
 
 // ---- launchers (parrep_kernels.cu) ----

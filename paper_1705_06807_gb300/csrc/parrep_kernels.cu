@@ -1806,13 +1806,16 @@ __device__ void recruit(const RunParams& P, RunCtl* ctl, int nblk, int nvb, unsi
     const unsigned gen = ldv(&ctl->bar_gen);
     constexpr int kMaxRecruit = 128;
     int want = min(nvb - nblk, kMaxRecruit);
-    if (P.batch.tail && ld_acquire_sys(P.batch.tail) > ldv(P.batch.head)) want = 0;  // new requests first
     int got = 0;
     const int nw = ((int)gridDim.x + 31) / 32;
-    if (want > 0 && P.batch.reserve > 0) {
+    if (want > 0 && (P.batch.reserve > 0 || P.batch.tail)) {
+        // serving: leave the reserve and one idle block for every request
+        // that is published and not yet claimed
         int idle = 0;
         for (int w = 0; w < nw; ++w) idle += __popc(ldv(&P.batch.idle[w]));
-        want = min(want, idle - P.batch.reserve);
+        long long pending = 0;
+        if (P.batch.tail) pending = (long long)(ld_acquire_sys(P.batch.tail) - ldv(P.batch.head));
+        want = (int)min((long long)want, (long long)idle - P.batch.reserve - pending);
     }
     short ids[kMaxRecruit];
     for (int w = 0; w < nw && got < want; ++w) {
@@ -2420,8 +2423,11 @@ __global__ void __launch_bounds__(kMaxThreads)
 
 // What a serving block does next (thread 0): join a gang that recruited it
 // (w = 2: slot, block index, barrier generation), lead a newly published
-// request (w = 1: slot), or leave (w = 0) on the stop flag or after idling
-// for idle_exit_ns.  While it waits it is in the idle set.
+// request (w = 1: slot), or leave (w = 0) on the stop flag, or once the
+// whole server has had nothing published and nothing in flight for
+// idle_exit_ns (a block never leaves while others still serve requests, so
+// the launch keeps all its blocks until it ends).  While it waits it is in
+// the idle set.
 __device__ int4 serve_next(const ServeDev& sd) {
     int4* mb = sd.bd.mail + blockIdx.x;
     unsigned* word = sd.bd.idle + blockIdx.x / 32;
@@ -2429,7 +2435,7 @@ __device__ int4 serve_next(const ServeDev& sd) {
     ((volatile int*)mb)[3] = 0;
     __threadfence();
     atomicOr(word, bit);
-    const unsigned long long t0 = globaltimer();
+    unsigned long long t0 = globaltimer();
     unsigned ns = 64;
     for (;;) {
         if (ldv(&mb->w)) {
@@ -2439,6 +2445,8 @@ __device__ int4 serve_next(const ServeDev& sd) {
         const unsigned long long tail = ld_acquire_sys(sd.tail);
         const unsigned long long head = ldv(sd.head);
         const bool stop = ld_acquire_sys(sd.stop) != 0;
+        const bool busy = head < tail || ldv(sd.finished) < head;
+        if (busy) t0 = globaltimer();
         const bool idle_out = (long long)(globaltimer() - t0) > sd.idle_exit_ns;
         if (head < tail || stop || idle_out) {
             const unsigned old = atomicAnd(word, ~bit);
@@ -2535,11 +2543,26 @@ __global__ void __launch_bounds__(kMaxThreads) parrep_serve_kernel(ServeDev sd) 
         int* dst = (int*)&sP;
         for (int w = threadIdx.x; w < (int)(sizeof(RunParams) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
         __syncthreads();
+        if (cmd.w == 1) {
+            // a new request: its leader clears the control block and the
+            // histograms (no other block knows the request yet)
+            unsigned long long* c = (unsigned long long*)sP.ctl;
+            for (int i = threadIdx.x; i < (int)(sizeof(RunCtl) / 8); i += blockDim.x) c[i] = 0;
+            for (int b = threadIdx.x; b < sP.net.nbins; b += blockDim.x) {
+                sP.hist_pre[b] = 0;
+                sP.hist_post[b] = 0;
+            }
+            __threadfence();
+            __syncthreads();
+        }
         const int join_gen = cmd.w == 2 ? cmd.z : -1;
         const bool last = sP.net.kind == PARREP_SCHLOGL
                               ? run_instance<F32, PARREP_SCHLOGL>(sP, cmd.y, smem, red, join_gen)
                               : run_instance<F32, PARREP_TOGGLE>(sP, cmd.y, smem, red, join_gen);
-        if (last) serve_epilogue(sP, slot, sd.done + cmd.x);
+        if (last) {
+            serve_epilogue(sP, slot, sd.done + cmd.x);
+            if (threadIdx.x == 0) atomicAdd(sd.finished, 1ull);
+        }
         __syncthreads();
     }
 }

@@ -111,6 +111,7 @@ struct parrep_server_s {
     int* stop = nullptr;
     // device state of the serve kernel
     unsigned long long* d_head = nullptr;
+    unsigned long long* d_finished = nullptr;
     unsigned* d_idle = nullptr;
     int4* d_mail = nullptr;
     int* d_unused = nullptr;
@@ -238,10 +239,8 @@ static int admit(parrep_server_t s, Request& q, int slot) {
         d_gU = gUd;
         d_gV = gVd;
     }
-    if (e == cudaSuccess) e = cudaMemsetAsync(h.d_ctl, 0, sizeof(RunCtl), s->cp);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h.d_hist_pre, 0, nb * 8, s->cp);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h.d_hist_post, 0, nb * 8, s->cp);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->cp);
+    // (the serve kernel's claiming block clears the control block and the
+    // histograms: a memset here would be a kernel that waits for free SMs)
     if (e != cudaSuccess) return sfail(s, PARREP_ECUDA, std::string("admission: ") + cudaGetErrorString(e));
     // launch shape of one gang member
     Plan pl;
@@ -349,6 +348,7 @@ static void serve_pass(parrep_server_t s) {
         sd.pad = 0;
         sd.tail = s->tail;
         sd.head = s->d_head;
+        sd.finished = s->d_finished;
         sd.stop = s->stop;
         sd.bd = BatchDev{s->d_unused, s->d_idle, s->d_mail, s->tail, s->d_head, s->grid / 8, 0};
         sd.progress = s->d_progress;
@@ -375,7 +375,7 @@ static void serve_thread(parrep_server_t s) {
 }
 
 static void server_free(parrep_server_t s) {
-    void* dev[] = {s->d_arena, s->d_head, s->d_idle, s->d_mail, s->d_unused, s->d_progress, s->d_slots};
+    void* dev[] = {s->d_arena, s->d_head, s->d_finished, s->d_idle, s->d_mail, s->d_unused, s->d_progress, s->d_slots};
     for (void* p : dev)
         if (p) cudaFree(p);
     void* host[] = {s->h_slot, s->done, s->tail, s->stop};
@@ -423,6 +423,7 @@ extern "C" int parrep_server_create(const parrep_server_options* opt, parrep_ser
     s->grid = per_sm * nsm;
     if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_arena, (size_t)o.arena_bytes);
     if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_head, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_finished, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_idle, sizeof(unsigned) * ((s->grid + 31) / 32));
     if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_mail, sizeof(int4) * s->grid);
     if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_unused, sizeof(int));
@@ -438,6 +439,7 @@ extern "C" int parrep_server_create(const parrep_server_options* opt, parrep_ser
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cp, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_end, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemset(s->d_head, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(s->d_finished, 0, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(s->d_idle, 0, sizeof(unsigned) * ((s->grid + 31) / 32));
     if (e == cudaSuccess) e = cudaMemset(s->d_mail, 0, sizeof(int4) * s->grid);
     if (e == cudaSuccess) e = cudaMemset(s->d_unused, 0x3f, sizeof(int));
