@@ -61,10 +61,11 @@ def parse():
     ap.add_argument("--t_phase", type=float, default=None, help="override t_phase (profiling)")
     ap.add_argument("--block_threads", type=int, default=0, help="CUDA block size (0 = library default)")
     ap.add_argument("--chunk_steps", type=int, default=0, help="steps between escape votes (0 = default)")
-    ap.add_argument("--workload", default="schlogl_n4096", choices=["schlogl_n4096", "batch256", "serve"],
+    ap.add_argument("--workload", default="schlogl_n4096", choices=["schlogl_n4096", "batch256", "serve", "speedup"],
                     help="schlogl_n4096: one ParRep run of 4096 replicas to T_end = 1e6 per step; batch256: "
                          "256 mixed Schloegl / toggle instances (64..65536 replicas, T_end = 1e4) in one launch; "
-                         "serve: Poisson-arriving requests through the continuous-batching server")
+                         "serve: Poisson-arriving requests through the continuous-batching server; speedup: "
+                         "ParRep vs plain SSA to the same simulated time at TV <= 1e-2 (Schloegl V=25)")
     ap.add_argument("--serve_rate", type=float, default=200.0, help="request arrivals per second (serve)")
     ap.add_argument("--serve_seconds", type=float, default=20.0, help="length of the arrival stream (serve)")
     ap.add_argument("--batch_n", type=int, default=256, help="instances of the batch workload")
@@ -373,6 +374,62 @@ def bench_serve(args, local):
     print(json.dumps(line), flush=True)
 
 
+def bench_speedup(args):
+    """ParRep speedup over plain SSA at TV <= 1e-2 against the exact law, on
+    the V = 25 Schloegl network with the paper's Sec. V.A settings (R = 100,
+    n_c = n_p = 5000): 64 seeds x 1.25e5 time units in one batch (the pooled
+    histogram's TV is measured; its well-mass standard error is about 2e-3),
+    against one plain-SSA trajectory over the same 8e6 time units -- as a
+    one-thread GPU SSA and as the oracle on one core,
+    both timed on a shorter stretch and scaled by simulated time."""
+    import numpy as np
+
+    import oracle as O
+    from oracle import exact as E
+    from paper_1705_06807_gb300 import ParRep, ParRepBatch, parrep_ssa
+    from paper_1705_06807_gb300 import configs as K
+
+    net = K.schlogl_paper(V=25)
+    n, T_each = 64, 1.25e5
+    T_total = n * T_each
+    pi = E.schlogl_stationary(net["c"], net["s"], net["hist_max"])
+    hs = [ParRep(net, 100, 5000, 5000, x0=[4], thresh="steps", precision=args.precision) for _ in range(n)]
+    b = ParRepBatch(hs)
+    b.run([T_each] * n, [77 + i for i in range(n)])  # warm-up and autotuning
+    t0 = time.perf_counter()
+    info = b.run([T_each] * n, [5000 + i for i in range(n)])
+    wall = time.perf_counter() - t0
+    pooled = sum(h.histogram() * h.stats()["T_s"] for h in hs) / T_total
+    tv = 0.5 * float(np.abs(pooled - pi).sum())
+    useful = sum(h.stats()["events_decorr"] + h.stats()["events_parallel_useful"] for h in hs)
+    b.close()
+    # plain SSA, one trajectory on one GPU thread
+    parrep_ssa(net, 1, [4], 100.0, 1, precision=args.precision)
+    T_gpu = 2e4
+    _, ev_gpu, ms_gpu = parrep_ssa(net, 1, [4], T_gpu, 2, precision=args.precision)
+    t_ssa_gpu = ms_gpu / 1e3 * T_total / T_gpu
+    # plain SSA, the oracle on one host core
+    T_cpu = 2e3
+    t1 = time.perf_counter()
+    _, ev_cpu, _ = O.ssa_run(net, 1, [4], T_cpu, 3)
+    t_ssa_cpu = (time.perf_counter() - t1) * T_total / T_cpu
+    line = {
+        "metric": "ParRep speedup vs plain SSA at TV<=1e-2", "value": t_ssa_gpu / (info["kernel_ms"] / 1e3),
+        "unit": "x", "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": info["kernel_ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": "schlogl_V25_paper_settings", "R": 100, "n_c": 5000, "n_p": 5000, "seeds": n,
+                   "T_each": T_each, "T_total": T_total},
+        "tv_vs_exact": tv,
+        "parrep": {"device_s": info["kernel_ms"] / 1e3, "wall_s": wall, "useful_events": useful},
+        "plain_ssa_gpu_thread": {"s_to_T_total": t_ssa_gpu, "events_per_s": ev_gpu / (ms_gpu / 1e3),
+                                 "timed_T": T_gpu},
+        "plain_ssa_oracle_1core": {"s_to_T_total": t_ssa_cpu, "events_per_s": ev_cpu / (t_ssa_cpu * T_cpu / T_total),
+                                   "timed_T": T_cpu},
+        "speedup_vs_oracle_1core": t_ssa_cpu / (info["kernel_ms"] / 1e3),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -393,6 +450,12 @@ def main():
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.workload == "speedup":
+        if rank == 0:
+            bench_speedup(args)
+        if dist:
+            dist.destroy_process_group()
+        return
     if args.workload == "serve":
         if rank == 0:
             bench_serve(args, local)
