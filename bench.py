@@ -42,6 +42,26 @@ OPS_PER_EVENT = 120
 OPS_PER_DEPHASE_EVENT = 107
 
 
+def rank_seed(rank: int, i: int) -> int:
+    """Seed of run i on a rank: ranks never share a seed (independent
+    instances, weak scaling)."""
+    return 1_000_003 * (rank + 1) + i
+
+
+def combine_ranks(dist, t_total, counts, device):
+    """Whole-job figures over the ranks: the maximum of the timed seconds and
+    the sums of the event counts.  Without a process group, the rank's own."""
+    if dist is None:
+        return float(t_total), [int(c) for c in counts]
+    import torch
+
+    t = torch.tensor([float(t_total)] + [float(c) for c in counts], device=device, dtype=torch.float64)
+    tmax = t.clone()
+    dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
+    dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+    return float(tmax[0]), [int(v) for v in t[1:].tolist()]
+
+
 def workload():
     from paper_1705_06807_gb300 import configs as K
 
@@ -215,13 +235,7 @@ def bench_batch(args, world, rank, local, dist):
     executed = sum(x["events_decorr"] + x["events_parallel_executed"] + x["events_replay"] + x["events_dephase"]
                    for x in flat)
     dephase = sum(x["events_dephase"] for x in flat)
-    if dist:
-        t = torch.tensor([t_total, float(useful), float(executed), float(dephase)], device="cuda",
-                         dtype=torch.float64)
-        tmax = t.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        t_total, useful, executed, dephase = float(tmax[0]), int(t[1]), int(t[2]), int(t[3])
+    t_total, (useful, executed, dephase) = combine_ranks(dist, t_total, [useful, executed, dephase], "cuda")
     clocks = clk.summary()
     e2e = None
     if not args.no_e2e:
@@ -481,7 +495,7 @@ def main():
                T_burn=c["T_burn"] * T_end / c["T_end"], stream=stream, block_threads=args.block_threads,
                chunk_steps=args.chunk_steps)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    seed0 = 1_000_003 * (rank + 1)
+    seed0 = rank_seed(rank, 0)
 
     def one(i):
         with torch.cuda.stream(stream):
@@ -523,12 +537,7 @@ def main():
     events = {k: sum(s_[k] for s_ in stats) // max(1, len(stats)) for k in
               ("events_decorr", "events_dephase", "events_parallel_useful", "events_parallel_executed",
                "events_replay", "cycles", "escapes")}
-    if dist:
-        t = torch.tensor([t_total, float(useful), float(executed)], device="cuda", dtype=torch.float64)
-        tmax = t.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        t_total, useful, executed = float(tmax[0]), int(t[1]), int(t[2])
+    t_total, (useful, executed) = combine_ranks(dist, t_total, [useful, executed], "cuda")
     clocks = clk.summary()
     value = useful / t_total
 
