@@ -380,7 +380,7 @@ static int plan_launch(parrep_t h, Plan& pl) {
                 pl.grid = (long long)per_sm * nsm >= grid ? (int)grid : per_sm * nsm;
                 if (h->opt.max_blocks > 0 && pl.grid > h->opt.max_blocks) pl.grid = h->opt.max_blocks;
                 pl.smem = smem;
-                const int S = h->opt.chunk_steps > 0 ? h->opt.chunk_steps : 512;
+                const int S = h->opt.chunk_steps > 0 ? h->opt.chunk_steps : kDefaultChunkF32;
                 pl.S = ((S + pl.B - 1) / pl.B) * pl.B;
                 return PARREP_OK;
             }

@@ -234,7 +234,7 @@ static int set_shape(parrep_batch_t b, int threads, int RB) {
             if (sz < 0) return bfail(b, PARREP_ENOMEM, "an instance's tables do not fit in shared memory");
             pl.threads = threads;
             pl.smem = sz;
-            const int S = h->opt.chunk_steps > 0 ? h->opt.chunk_steps : 512;
+            const int S = h->opt.chunk_steps > 0 ? h->opt.chunk_steps : kDefaultChunkF32;
             pl.S = ((S + pl.B - 1) / pl.B) * pl.B;
         } else {
             pl.threads = threads;

@@ -287,6 +287,13 @@ __device__ __forceinline__ void block_reduce4(BlockScratch& s, unsigned long lon
 // PARREP_ETIMEOUT and returns; every caller leaves the kernel on a nonzero
 // status.  The barrier counts calls so that a test can make block 0 skip one.
 // ---------------------------------------------------------------------------
+// Longest sleep between polls of a waiting block (one thread per block
+// polls): short, so that a barrier releases within a fraction of a microsecond.
+#ifndef PARREP_BARRIER_SLEEP_MAX_NS
+#define PARREP_BARRIER_SLEEP_MAX_NS 128
+#endif
+constexpr unsigned kBarrierSleepMaxNs = PARREP_BARRIER_SLEEP_MAX_NS;
+
 struct BarState {
     int index;
     int lb, nblk;  // this block's index among the blocks serving the instance, and their number
@@ -320,7 +327,7 @@ __device__ bool grid_sync(const RunParams& P, BarState& bs) {
             while (ldv(&ctl->bar_gen) == g) {
                 if (ldv(&ctl->status) != 0) break;
                 __nanosleep(ns);
-                if (ns < 1024) ns <<= 1;
+                if (ns < kBarrierSleepMaxNs) ns <<= 1;
                 const unsigned long long p = ldv(P.progress);
                 const unsigned long long t = globaltimer();
                 if (p != p0) {

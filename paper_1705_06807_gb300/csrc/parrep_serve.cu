@@ -254,7 +254,7 @@ static int admit(parrep_server_t s, Request& q, int slot) {
         }
         if (sz < 0) return sfail(s, PARREP_ENOMEM, "the request's tables do not fit the serve kernel's shared memory");
         pl.smem = sz;
-        const int S = r.chunk_steps > 0 ? r.chunk_steps : 512;
+        const int S = r.chunk_steps > 0 ? r.chunk_steps : kDefaultChunkF32;
         pl.S = ((S + pl.B - 1) / pl.B) * pl.B;
     } else {
         pl.RB = s->threads;
