@@ -13,6 +13,8 @@ Contents:
   * ``exact.py`` -- exact references: birth-death product formula, truncated
     CME, quasi-stationary distributions, mean first passage times, closed-form
     FIM / relative entropy rate.
+  * ``uq.py`` -- the Sec. IV.B estimators of the IAF, the stationary mean and
+    the path-space FIM over independent runs, and the information bounds.
   * ``__init__.py`` (this file) -- builds the C file with gcc and wraps it.
 """
 from __future__ import annotations

@@ -18,6 +18,11 @@ Each function is a plain definition written out in numpy/scipy:
   E_pi sum_j lambda_j grad log lambda_j grad log lambda_j^T) and the relative
   entropy rate E_pi sum_j [lambda_j log(lambda_j/lambda'_j) - lambda_j + lambda'_j].
 * ``rre_fixed_points`` -- the real roots of the Schloegl rate equation (Sec. V.A).
+* ``iaf_exact`` -- the integrated autocovariance of f (Sec. IV.B; the
+  appendix's integral of Cov_f over the real line) from the Poisson equation
+  Q g = -fbar.
+* ``stationary_sensitivity`` -- d pi(f)/d c_k by differentiating pi Q = 0
+  (the CME linear system behind Table III's approximated sensitivities).
 """
 from __future__ import annotations
 
@@ -244,3 +249,63 @@ def rre_fixed_points(c, s, V=1.0):
     r = np.roots([-A[1], A[0], -A[3], A[2]])
     r = np.sort(r[np.abs(r.imag) < 1e-9].real)
     return r[r >= 0]
+
+
+# ---------------------------------------------------------------------------
+# stationary sensitivity and the integrated autocovariance (Sec. IV.B and the
+# appendix that derives the information bounds)
+# ---------------------------------------------------------------------------
+def schlogl_generators(c, s, xmax):
+    """Truncated Schloegl generator Q on {0..xmax} (births out of xmax and
+    deaths out of 0 dropped) and its derivatives dQ/dc_k, k = 0..3.  Channels
+    0 and 2 move x up, 1 and 3 down; lambda_j is linear in c_j, so dQ/dc_k is
+    the generator of channel k alone with rates s_k h_k(x)."""
+    x = np.arange(xmax + 1)
+    lam = schlogl_props(c, s, x)
+    Q = generator(lam[0] + lam[2], lam[1] + lam[3])
+    one = schlogl_props(np.ones(4), s, x)  # s_k h_k(x) = d lambda_k / d c_k
+    zero = np.zeros(xmax + 1)
+    dQ = []
+    for k in range(4):
+        up = one[k] if k in (0, 2) else zero
+        dn = one[k] if k in (1, 3) else zero
+        dQ.append(generator(up, dn))
+    return Q, dQ
+
+
+def _bordered_solve(A, rhs, border):
+    """Solves A y + mu * 1 = rhs, border . y = 0 (A singular with null space
+    the constants); returns y."""
+    n = A.shape[0]
+    M = np.zeros((n + 1, n + 1))
+    M[:n, :n] = A
+    M[:n, n] = 1.0
+    M[n, :n] = border
+    y = np.linalg.solve(M, np.concatenate([rhs, [0.0]]))
+    return y[:n]
+
+
+def iaf_exact(Q, pi, f):
+    """Integrated autocovariance of f along the stationary chain,
+    tau(f) = integral over the real line of Cov_pi(f(X_0), f(X_s)) ds
+    = 2 sum_x pi(x) fbar(x) g(x), where fbar = f - pi(f) and
+    g = integral_0^inf exp(sQ) fbar ds solves the Poisson equation
+    Q g = -fbar with pi . g = 0."""
+    Q = np.asarray(Q, dtype=np.float64)
+    pi = np.asarray(pi, dtype=np.float64)
+    fbar = np.asarray(f, dtype=np.float64) - float(pi @ np.asarray(f, dtype=np.float64))
+    g = _bordered_solve(Q, -fbar, pi)
+    return 2.0 * float(np.sum(pi * fbar * g))
+
+
+def stationary_sensitivity(Q, dQ, pi, f):
+    """d pi(f) / d c_k for each generator derivative dQ_k: differentiating
+    pi Q = 0 and sum pi = 1 gives Q^T dpi = -dQ_k^T pi with sum dpi = 0."""
+    Q = np.asarray(Q, dtype=np.float64)
+    pi = np.asarray(pi, dtype=np.float64)
+    f = np.asarray(f, dtype=np.float64)
+    out = []
+    for dQk in dQ:
+        dpi = _bordered_solve(Q.T, -(np.asarray(dQk).T @ pi), np.ones(len(pi)))
+        out.append(float(dpi @ f))
+    return np.array(out)

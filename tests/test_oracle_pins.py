@@ -404,3 +404,128 @@ def test_parrep_rejects_bad_input():
     assert O.parrep_run(net, 4, 1, 1, 10.0, 0, [5000])["status"] == O.OR_EINVAL
     small = dict(net, hist_max=120)
     assert O.parrep_run(small, 4, 1, 1, 100.0, 0, [85])["status"] == O.OR_ERANGE
+
+
+# ---------------------------------------------------------------------------
+# stationary sensitivity, IAF and information bounds (Sec. IV.B, Sec. V.A)
+# ---------------------------------------------------------------------------
+def test_iaf_exact_closed_form_immigration_death():
+    """M/M/inf (immigration k_in, death k_out x): Cov(X_0, X_s) =
+    (k_in/k_out) exp(-k_out |s|), so tau(x) = 2 k_in / k_out^2."""
+    for k_in, k_out in [(5.0, 1.3), (20.0, 2.0)]:
+        n = 120
+        x = np.arange(n, dtype=float)
+        Q = E.generator(np.full(n, k_in), k_out * x)
+        pi = E.stationary_dense(Q)
+        assert abs(E.iaf_exact(Q, pi, x) / (2.0 * k_in / k_out**2) - 1.0) < 1e-10
+
+
+def test_iaf_exact_is_the_autocovariance_integral():
+    """A random 5-state generator: tau(f) against direct quadrature of
+    2 * int_0^inf sum_x pi(x) fbar(x) (exp(sQ) fbar)(x) ds."""
+    from scipy.integrate import quad
+    from scipy.linalg import expm
+
+    rng = np.random.default_rng(3)
+    Q = rng.uniform(0.2, 2.0, size=(5, 5))
+    np.fill_diagonal(Q, 0.0)
+    np.fill_diagonal(Q, -Q.sum(1))
+    pi = E.stationary_dense(Q)
+    f = rng.normal(size=5)
+    fbar = f - pi @ f
+    cov = lambda s: float(pi @ (fbar * (expm(s * Q) @ fbar)))
+    ref = 2.0 * quad(cov, 0.0, np.inf, limit=200)[0]
+    assert abs(E.iaf_exact(Q, pi, f) / ref - 1.0) < 1e-7
+
+
+def test_stationary_sensitivity_matches_product_formula_difference():
+    """d pi(x)/d c_k from the generator solve against central differences of
+    the detailed-balance product formula (V = 25, truncation 255)."""
+    net = K.schlogl_paper(V=25, hist_max=255)
+    x = np.arange(256.0)
+    pi = E.schlogl_stationary(net["c"], net["s"], 255)
+    Q, dQ = E.schlogl_generators(net["c"], net["s"], 255)
+    S = E.stationary_sensitivity(Q, dQ, pi, x)
+    for k in range(4):
+        h = 1e-5 * net["c"][k]
+        cp, cm = np.array(net["c"]), np.array(net["c"])
+        cp[k] += h
+        cm[k] -= h
+        fd = (E.schlogl_stationary(cp, net["s"], 255) @ x - E.schlogl_stationary(cm, net["s"], 255) @ x) / (2 * h)
+        assert abs(S[k] / fd - 1.0) < 1e-6, (k, S[k], fd)
+
+
+def _half_unit(v, digits=3):
+    """Half a unit in the last of the printed significant digits."""
+    return 0.5 * 10.0 ** (np.floor(np.log10(abs(v))) - (digits - 1))
+
+
+def test_exact_sensitivities_and_iaf_against_paper():
+    """Table III's CME approximation (truncation [0, 149]) for c1, c3, c4 to
+    the printed three digits; the printed c2 entry (+9.10E+02) is garbled,
+    the exact value is about -998.  The printed IAF 5.87e5 is a 100-sample
+    estimate whose relative standard deviation is sqrt(2/99) = 0.142; the
+    exact value lies within it."""
+    g = _golden_paper()
+    net = K.schlogl_paper(V=25, hist_max=149)
+    x = np.arange(150.0)
+    pi = E.schlogl_stationary(net["c"], net["s"], 149)
+    Q, dQ = E.schlogl_generators(net["c"], net["s"], 149)
+    S = E.stationary_sensitivity(Q, dQ, pi, x)
+    for k, key in [(0, "cme_sens_c1"), (2, "cme_sens_c3"), (3, "cme_sens_c4")]:
+        assert abs(S[k] - g[key][0]) <= _half_unit(g[key][0]), (key, S[k])
+    assert -1005.0 < S[1] < -990.0
+    tau = E.iaf_exact(Q, pi, x)
+    assert abs(tau / g["iaf_x"][0] - 1.0) < np.sqrt(2.0 / 99.0)
+    assert 5.62e5 < tau < 5.635e5
+
+
+def test_bounds_reproduce_table_iii_and_dominate_the_sensitivities():
+    """sqrt(tau) sqrt(I_kk) with the printed IAF 5.87e5 and the exact FIM
+    diagonal gives Table III's bounds to the printed three digits; with the
+    exact tau and FIM the bound dominates |v . grad pi(x)| for every
+    direction (Cauchy-Schwarz, the content of the bound)."""
+    from oracle import uq as U
+
+    g = _golden_paper()
+    net = K.schlogl_paper(V=25, hist_max=255)
+    x = np.arange(256.0)
+    pi = E.schlogl_stationary(net["c"], net["s"], 255)
+    lam = E.schlogl_props(net["c"], net["s"], x)
+    F = E.fim_exact(lam, E.schlogl_grad_log(net["c"], x), pi)
+    b = U.bounds(g["iaf_x"][0], F)
+    for k in range(4):
+        v = g["bound_c%d" % (k + 1)][0]
+        assert abs(b[k] - v) <= _half_unit(v), (k, b[k])
+    Q, dQ = E.schlogl_generators(net["c"], net["s"], 255)
+    S = E.stationary_sensitivity(Q, dQ, pi, x)
+    tau = E.iaf_exact(Q, pi, x)
+    rng = np.random.default_rng(5)
+    V = np.vstack([np.eye(4), rng.normal(size=(64, 4))])
+    assert np.all(np.abs(V @ S) <= U.bounds(tau, F, V))
+
+
+def test_uq_estimators_on_oracle_runs_of_immigration_death():
+    """The Sec. IV.B estimators over independent oracle runs (one replica, a
+    single region, so each run is one SSA path after its start) of
+    immigration-death: IAF 2 k_in / k_out^2, mean k_in / k_out and the death
+    channel's FIM entry k_in / k_out^2 within their sampling errors."""
+    from oracle import uq as U
+
+    k_in, k_out, T_b, T = 5.0, 1.0, 200.0, 420.0
+    net = K.immigration_death(k_in, k_out, hist_max=60)
+    hs, Z = [], []
+    for seed in range(240):
+        r = O.parrep_run(net, 1, 10, 10, T, 700 + seed, [5], thresh="steps", T_burn=T_b)
+        assert r["status"] == 0
+        hs.append(r["hist_post"])
+        Z.append(r["fim"] / (T - T_b))
+    f = np.arange(61.0)
+    out = U.uq(f, hs, Z, T - T_b)
+    tau = 2.0 * k_in / k_out**2
+    # a sample variance of 240 near-normal values: relative sd sqrt(2/239) = 0.091;
+    # the finite window shrinks the mean by 1/(k_out (T - T_b)) = 0.45%
+    assert abs(out["iaf"] / tau - 1.0) < 4 * 0.091
+    assert abs(out["mean_f"] - k_in / k_out) < 4 * np.sqrt(tau / (T - T_b) / 240)
+    assert abs(out["fim"][3, 3] - k_in / k_out**2) < 4 * out["fim_half_width"][3, 3] / 1.96
+    assert np.allclose(out["Y"], [h @ f for h in hs])
