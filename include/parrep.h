@@ -402,6 +402,42 @@ void parrep_server_destroy(parrep_server_t s);
 
 const char* parrep_server_last_error(parrep_server_t s);
 
+/* Stationary uncertainty quantification over independent runs (Sec. IV.B,
+ * and the appendix that derives the stationary information bound
+ * S_{f,v}(pi) <= sqrt(tau(f)) sqrt(v^T I_H v)).  The samples are n handles
+ * that each completed a run of the same network shape (kind, hist_max) and
+ * the same window [T_burn, T_end] (equal T_end - T_burn); their seeds should
+ * differ.  With Y_k the integral of f over the window of sample k (from its
+ * post-burn time sums) and w = T_end - T_burn:
+ *   iaf            = sum_k (Y_k - Ybar)^2 / (w (n - 1))   (the IAF estimator)
+ *   mean_f         = Ybar / w                             (estimate of pi(f))
+ *   fim            = the mean over samples of the per-sample FIM (parrep_fim)
+ *   fim_half_width = 1.96 sd / sqrt(n) per entry (normal 95% half widths)
+ *   bound[k]       = sqrt(iaf) sqrt(fim[k][k])            (v = e_k)
+ * Everything is computed on the device in binary64 in a fixed order (the
+ * result does not depend on scheduling). */
+typedef struct {
+    int32_t n_samples;
+    int32_t n_params;          /* l = 4 (Schloegl) or 6 (toggle) */
+    double window;             /* w = T_end - T_burn */
+    double iaf;
+    double mean_f;
+    double fim[36];            /* row-major l x l */
+    double fim_half_width[36];
+    double bound[6];
+} parrep_uq_result;
+
+/* handles: n >= 2 handles (host array).  f: one value per histogram bin
+ * (host or device, len = parrep_n_bins).  dirs / n_dirs / dir_bounds
+ * (optional, host or device): n_dirs directions v (n_dirs x l, row-major)
+ * and their bounds sqrt(iaf) sqrt(v^T fim v).  Y_out (optional, host or
+ * device, n values): the window integrals Y_k.  out: host pointer.
+ * Errors: EINVAL (n < 2, a NULL handle or the same handle twice, mismatched
+ * shapes or windows, len, empty window), ESTATE (a handle without a
+ * completed run), ECUDA.  Runs on the first handle's stream. */
+int parrep_uq(const parrep_t* handles, int32_t n, const double* f, int64_t len, const double* dirs, int32_t n_dirs,
+              double* dir_bounds, double* Y_out, parrep_uq_result* out);
+
 /* Device Philox4x32-10 of n counters (ctr: n x 4, key: n x 2, out: n x 4
  * uint32, all host pointers) -- exposes the generator the kernels use. */
 int parrep_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out);

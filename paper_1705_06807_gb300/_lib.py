@@ -96,6 +96,12 @@ class parrep_cycle(C.Structure):
                 ("T_s", C.c_double)]
 
 
+class parrep_uq_result(C.Structure):
+    _fields_ = [("n_samples", C.c_int32), ("n_params", C.c_int32), ("window", C.c_double), ("iaf", C.c_double),
+                ("mean_f", C.c_double), ("fim", C.c_double * 36), ("fim_half_width", C.c_double * 36),
+                ("bound", C.c_double * 6)]
+
+
 EXPORTS = ["parrep_default_options", "parrep_create", "parrep_set_options", "parrep_run", "parrep_n_bins",
            "parrep_histogram", "parrep_histogram_raw", "parrep_fim", "parrep_rer", "parrep_stats_get",
            "parrep_cycle_log", "parrep_dephase", "parrep_destroy", "parrep_last_error", "parrep_ssa",
@@ -103,7 +109,7 @@ EXPORTS = ["parrep_default_options", "parrep_create", "parrep_set_options", "par
            "parrep_batch_run", "parrep_batch_status", "parrep_batch_info_get", "parrep_batch_destroy",
            "parrep_batch_last_error", "parrep_server_default_options", "parrep_server_create",
            "parrep_server_submit", "parrep_server_poll", "parrep_server_wait", "parrep_server_result",
-           "parrep_server_stats_get", "parrep_server_destroy", "parrep_server_last_error"]
+           "parrep_server_stats_get", "parrep_server_destroy", "parrep_server_last_error", "parrep_uq"]
 
 _lib = None
 
@@ -164,6 +170,7 @@ def load():
     L.parrep_server_destroy.restype = None
     L.parrep_server_last_error.argtypes = [vp]
     L.parrep_server_last_error.restype = C.c_char_p
+    L.parrep_uq.argtypes = [P(vp), C.c_int32, vp, C.c_int64, vp, C.c_int32, vp, vp, P(parrep_uq_result)]
     for name in EXPORTS:
         if name not in ("parrep_default_options", "parrep_n_bins", "parrep_destroy", "parrep_last_error",
                         "parrep_batch_default_options", "parrep_batch_destroy", "parrep_batch_last_error",

@@ -394,3 +394,29 @@ def parrep_ssa_noalloc(spec: dict, n_traj: int, x0, T_end: float, seed: int, his
     _check(lib.parrep_ssa_noalloc(C.byref(net), L.PARREP_FP32 if precision == "f32" else L.PARREP_FP64,
                                   int(n_traj), float(T_end), int(seed), _buf(hist_out), int(n), C.byref(ev), st))
     return int(ev.value)
+
+
+def parrep_uq(handles, f, directions=None) -> dict:
+    """Stationary UQ over independent completed runs (Sec. IV.B): the IAF of
+    f, its stationary mean, the mean FIM with 95% half widths, and the
+    information bounds sqrt(tau) sqrt(v^T I v) for the unit vectors (and for
+    the rows of `directions`).  f: one value per histogram bin."""
+    lib = L.load()
+    hs = [h.h for h in handles]
+    n = len(hs)
+    arr = (C.c_void_p * max(n, 1))(*hs)
+    f = np.ascontiguousarray(f, dtype=np.float64).ravel()
+    l = handles[0].L if n else 4
+    dirs = None if directions is None else np.ascontiguousarray(directions, dtype=np.float64).reshape(-1, l)
+    nd = 0 if dirs is None else len(dirs)
+    db = np.zeros(max(nd, 1))
+    Y = np.zeros(max(n, 1))
+    r = L.parrep_uq_result()
+    _check(lib.parrep_uq(arr, n, _buf(f), len(f), None if dirs is None else _buf(dirs), nd,
+                         _buf(db) if nd else None, _buf(Y), C.byref(r)), hs[0] if n else None)
+    out = dict(n_samples=r.n_samples, window=r.window, iaf=r.iaf, mean_f=r.mean_f, Y=Y[:n].copy(),
+               fim=np.array(r.fim[: l * l]).reshape(l, l), fim_half_width=np.array(r.fim_half_width[: l * l]).reshape(l, l),
+               bounds=np.array(r.bound[:l]))
+    if nd:
+        out["direction_bounds"] = db[:nd].copy()
+    return out

@@ -17,7 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libparrep.so")
-SOURCES = ["parrep_kernels.cu", "parrep_api.cu", "parrep_batch.cu", "parrep_serve.cu", "parrep_noalloc.cu"]
+SOURCES = ["parrep_kernels.cu", "parrep_api.cu", "parrep_batch.cu", "parrep_serve.cu", "parrep_noalloc.cu",
+           "parrep_uq.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

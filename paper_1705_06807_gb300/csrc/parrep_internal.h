@@ -185,6 +185,24 @@ cudaError_t launch_dephase(const RunParams& p, int xt0, int xt1, int W, unsigned
                            int* out_states, int grid, int threads, cudaStream_t st);
 cudaError_t launch_hist_normalise(const unsigned long long* pre, const unsigned long long* post, int n, double scale,
                                   double* out_pre, double* out_post, double* out_norm, cudaStream_t st);
+// One sample of the stationary UQ over independent runs (Sec. IV.B): a
+// completed run's network view and its post-burn time sums.
+struct UqSample {
+    NetDev net;
+    const double* c;                  // rate constants (l)
+    const unsigned long long* hist;   // post-burn fixed-point time sums
+    const double* gradU_n;            // toggle: d log lambda / d n tables
+    const double* gradV_n;
+};
+// Device result of the UQ reduction (the fields of parrep_uq_result).
+struct UqOut {
+    double iaf, mean_f;
+    double fim[36], half[36], bound[6];
+};
+// Y[k] (window integral of f), Z[k][36] (FIM time average) per sample, then
+// the moments, the FIM mean and half widths, and the bounds.
+cudaError_t launch_uq(const UqSample* samples, int n, int L, const double* f, double window, const double* dirs,
+                      int n_dirs, double* Y, double* Z, UqOut* out, double* dir_bounds, cudaStream_t st);
 cudaError_t launch_fim_rer(const NetDev& net, const double* c, const double* s, const unsigned long long* hist,
                            const double* gradU_n, const double* gradV_n, const double* cprime, int n_cprime,
                            double* fim_out, double* rer_out, cudaStream_t st);

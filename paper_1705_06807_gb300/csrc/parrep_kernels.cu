@@ -2731,6 +2731,141 @@ __global__ void fim_rer_kernel(NetDev N, const double* __restrict__ c, const dou
 }
 
 // ---------------------------------------------------------------------------
+// stationary UQ over independent runs (Sec. IV.B)
+// ---------------------------------------------------------------------------
+constexpr int kUqThreads = 256;
+
+// Sum of v over the block in a fixed order: an xor butterfly inside each warp
+// (both partners add the same two values, so every lane holds the same
+// bits), then the warps' sums in warp order by thread 0.  red holds one slot
+// per warp; the result is valid in thread 0.
+__device__ __forceinline__ double block_sum_fixed(double v, double* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    return t;
+}
+
+// One block per sample k: Y[k] = sum_b f[b] * time(b) over the post-burn
+// sums, and Z[k] = the FIM time average (the parrep_fim contraction: per bin
+// w sum_j lambda_j g_j g_j^T with g_j = grad_c log lambda_j, over the window).
+__global__ void __launch_bounds__(kUqThreads) uq_sample_kernel(const UqSample* __restrict__ smp,
+                                                                const double* __restrict__ f, int L, double window,
+                                                                double* __restrict__ Y, double* __restrict__ Z) {
+    __shared__ double red[kUqThreads / 32];
+    const UqSample& S = smp[blockIdx.x];
+    const NetDev& N = S.net;
+    double y = 0.0;
+    double acc[36];
+#pragma unroll
+    for (int i = 0; i < 36; ++i) acc[i] = 0.0;
+    double ic[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) ic[i] = i < L ? 1.0 / S.c[i] : 0.0;
+    for (int b = threadIdx.x; b < N.nbins; b += blockDim.x) {
+        const unsigned long long hq = __ldcg(S.hist + b);
+        if (!hq) continue;
+        const double w = (double)hq * kQInv;
+        y += f[b] * w;
+        const int x0 = b / N.ystride, x1 = b % N.ystride;
+        double lam[4];
+        props_d(N, x0, x1, lam[0], lam[1], lam[2], lam[3]);
+        double g[4][6];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) g[j][k] = 0.0;
+        if (N.kind == PARREP_SCHLOGL) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) g[j][j] = ic[j];
+        } else {
+            g[0][0] = ic[0];
+            g[0][1] = S.gradU_n[x1];
+            g[1][3] = ic[3];
+            g[1][4] = S.gradV_n[x0];
+            g[2][2] = ic[2];
+            g[3][5] = ic[5];
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (lam[j] == 0.0) continue;
+            for (int a = 0; a < L; ++a)
+                for (int bb = 0; bb < L; ++bb) acc[a * L + bb] += w * lam[j] * g[j][a] * g[j][bb];
+        }
+    }
+    const double yt = block_sum_fixed(y, red);
+    if (threadIdx.x == 0) Y[blockIdx.x] = yt;
+    for (int i = 0; i < L * L; ++i) {
+        const double t = block_sum_fixed(acc[i], red);
+        if (threadIdx.x == 0) Z[(size_t)blockIdx.x * 36 + i] = t / window;
+    }
+}
+
+// One block: moments of Y (two passes), mean and 95% half width of each FIM
+// entry over the samples, and the bounds sqrt(tau) sqrt(v^T I v) -- each sum
+// in sample order.
+__global__ void uq_reduce_kernel(int n, int L, const double* __restrict__ Y, const double* __restrict__ Z,
+                                 double window, const double* __restrict__ dirs, int n_dirs, UqOut* out,
+                                 double* dir_bounds) {
+    __shared__ double sh_tau;
+    __shared__ double sh_fim[36];
+    if (threadIdx.x < 32) {
+        double s = 0.0;
+        for (int k = threadIdx.x; k < n; k += 32) s += Y[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        const double ybar = s / (double)n;
+        double v = 0.0;
+        for (int k = threadIdx.x; k < n; k += 32) {
+            const double d = Y[k] - ybar;
+            v += d * d;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) {
+            const double tau = v / (window * (double)(n - 1));
+            out->iaf = tau;
+            out->mean_f = ybar / window;
+            sh_tau = tau;
+        }
+    }
+    for (int t = threadIdx.x; t < 36; t += blockDim.x) {
+        double m = 0.0, hw = 0.0;
+        if (t < L * L) {
+            for (int k = 0; k < n; ++k) m += Z[(size_t)k * 36 + t];
+            m /= (double)n;
+            double v = 0.0;
+            for (int k = 0; k < n; ++k) {
+                const double d = Z[(size_t)k * 36 + t] - m;
+                v += d * d;
+            }
+            hw = 1.96 * sqrt(v / (double)(n - 1)) / sqrt((double)n);
+        }
+        out->fim[t] = m;
+        out->half[t] = hw;
+        sh_fim[t] = m;
+    }
+    __syncthreads();
+    const double rt = sqrt(sh_tau);
+    for (int j = threadIdx.x; j < 6; j += blockDim.x) out->bound[j] = j < L ? rt * sqrt(fmax(sh_fim[j * L + j], 0.0)) : 0.0;
+    for (int d = threadIdx.x; d < n_dirs; d += blockDim.x) {
+        const double* v = dirs + (size_t)d * L;
+        double q = 0.0;
+        for (int a = 0; a < L; ++a) {
+            double r = 0.0;
+            for (int b = 0; b < L; ++b) r += sh_fim[a * L + b] * v[b];
+            q += v[a] * r;
+        }
+        dir_bounds[d] = rt * sqrt(fmax(q, 0.0));
+    }
+}
+
+// ---------------------------------------------------------------------------
 // plain SSA: one thread per independent trajectory
 // ---------------------------------------------------------------------------
 template <bool F32>
@@ -2896,6 +3031,15 @@ cudaError_t launch_fim_rer(const NetDev& net, const double* c, const double* s, 
     if (blocks > 304) blocks = 304;
     if (blocks < 1) blocks = 1;
     fim_rer_kernel<<<blocks, 128, 0, st>>>(net, c, s, hist, gradU_n, gradV_n, cprime, n_cprime, fim_out, rer_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_uq(const UqSample* samples, int n, int L, const double* f, double window, const double* dirs,
+                      int n_dirs, double* Y, double* Z, UqOut* out, double* dir_bounds, cudaStream_t st) {
+    uq_sample_kernel<<<n, kUqThreads, 0, st>>>(samples, f, L, window, Y, Z);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    uq_reduce_kernel<<<1, 64, 0, st>>>(n, L, Y, Z, window, dirs, n_dirs, out, dir_bounds);
     return cudaGetLastError();
 }
 
