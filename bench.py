@@ -81,11 +81,12 @@ def parse():
     ap.add_argument("--t_phase", type=float, default=None, help="override t_phase (profiling)")
     ap.add_argument("--block_threads", type=int, default=0, help="CUDA block size (0 = library default)")
     ap.add_argument("--chunk_steps", type=int, default=0, help="steps between escape votes (0 = default)")
-    ap.add_argument("--workload", default="schlogl_n4096", choices=["schlogl_n4096", "batch256", "serve", "speedup"],
+    ap.add_argument("--workload", default="schlogl_n4096", choices=["schlogl_n4096", "batch256", "serve", "speedup", "uq"],
                     help="schlogl_n4096: one ParRep run of 4096 replicas to T_end = 1e6 per step; batch256: "
                          "256 mixed Schloegl / toggle instances (64..65536 replicas, T_end = 1e4) in one launch; "
                          "serve: Poisson-arriving requests through the continuous-batching server; speedup: "
-                         "ParRep vs plain SSA to the same simulated time at TV <= 1e-2 (Schloegl V=25)")
+                         "ParRep vs plain SSA to the same simulated time at TV <= 1e-2 (Schloegl V=25); uq: the "
+                         "Sec. V.A IAF / FIM / information-bound experiment (100 samples to T = 2e5)")
     ap.add_argument("--serve_rate", type=float, default=200.0, help="request arrivals per second (serve)")
     ap.add_argument("--serve_seconds", type=float, default=20.0, help="length of the arrival stream (serve)")
     ap.add_argument("--batch_n", type=int, default=256, help="instances of the batch workload")
@@ -444,6 +445,64 @@ def bench_speedup(args):
     print(json.dumps(line), flush=True)
 
 
+def bench_uq(args):
+    """The stationary UQ experiment of Sec. V.A (its Tables II and III):
+    100 independent ParRep samples of the V = 25 Schloegl network (R = 100,
+    n_c = n_p = 5000), each to T = 2e5 with [0, 1e5] as burn-in, in one batch;
+    then parrep_uq for f = x: the IAF, the stationary mean, the FIM with 95%
+    half widths and the information bounds.  value = device seconds of the
+    batch run plus the UQ call's wall time; the estimates are reported beside
+    the exact values of the truncated chain and the paper's printed ones."""
+    import numpy as np
+
+    import oracle as O
+    from oracle import exact as E
+    from paper_1705_06807_gb300 import ParRep, ParRepBatch, parrep_uq
+    from paper_1705_06807_gb300 import configs as K
+
+    net = K.schlogl_paper(V=25, hist_max=255)
+    n, T, Tb = 100, 2e5, 1e5
+    hs = [ParRep(net, 100, 5000, 5000, x0=[4], thresh="steps", precision=args.precision, T_burn=Tb)
+          for _ in range(n)]
+    b = ParRepBatch(hs)
+    b.run([T] * n, [91 + i for i in range(n)])  # warm-up and autotuning
+    x = np.arange(256.0)
+    parrep_uq(hs, x)
+    info = b.run([T] * n, [60000 + i for i in range(n)])
+    assert b.status() == [0] * n
+    t0 = time.perf_counter()
+    r = parrep_uq(hs, x)
+    t_uq = time.perf_counter() - t0
+    useful = sum(h.stats()["events_decorr"] + h.stats()["events_parallel_useful"] for h in hs)
+    b.close()
+    pi = E.schlogl_stationary(net["c"], net["s"], 255)
+    Q, dQ = E.schlogl_generators(net["c"], net["s"], 255)
+    tau = E.iaf_exact(Q, pi, x)
+    S = E.stationary_sensitivity(Q, dQ, pi, x)
+    F = E.fim_exact(E.schlogl_props(net["c"], net["s"], x), E.schlogl_grad_log(net["c"], x), pi)
+    # the oracle (one host core) on one sample over 2e4 time units, scaled to the experiment
+    T_cpu = 2e4
+    t1 = time.perf_counter()
+    O.parrep_run(net, 100, 5000, 5000, T_cpu, 1, [4], thresh="steps")
+    t_cpu = (time.perf_counter() - t1) * n * T / T_cpu
+    dev_s = info["kernel_ms"] / 1e3 + t_uq
+    line = {
+        "metric": "Sec. V.A UQ experiment time (100 samples to T=2e5)", "value": dev_s, "unit": "s",
+        "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": dev_s * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": "schlogl_V25_uq_100x2e5", "R": 100, "n_c": 5000, "n_p": 5000, "samples": n,
+                   "T": T, "T_burn": Tb, "f": "x"},
+        "batch_s": info["kernel_ms"] / 1e3, "uq_call_s": t_uq, "useful_events_per_s": useful / (info["kernel_ms"] / 1e3),
+        "estimate": {"iaf": r["iaf"], "mean_f": r["mean_f"], "fim_diag": np.diag(r["fim"]).tolist(),
+                     "fim_half_width_diag": np.diag(r["fim_half_width"]).tolist(), "bounds": r["bounds"].tolist()},
+        "exact": {"iaf": tau, "mean_f": float(pi @ x), "fim_diag": np.diag(F).tolist(), "sensitivity": S.tolist(),
+                  "bounds": (np.sqrt(tau) * np.sqrt(np.diag(F))).tolist()},
+        "paper": {"iaf": 5.87e5, "fim_diag": [87.5, 1670.0, 200.0, 24.6], "bounds": [7.16e3, 3.09e4, 1.08e4, 3.80e3]},
+        "oracle_1core_s_estimate": t_cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -464,9 +523,9 @@ def main():
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    if args.workload == "speedup":
+    if args.workload in ("speedup", "uq"):
         if rank == 0:
-            bench_speedup(args)
+            (bench_speedup if args.workload == "speedup" else bench_uq)(args)
         if dist:
             dist.destroy_process_group()
         return
