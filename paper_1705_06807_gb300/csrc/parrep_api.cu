@@ -315,7 +315,7 @@ int parrep::fast_layout(parrep_t h, int RB, int threads, int with_hist, int pipe
     pl.off_nvalid = off;
     off += ntr * RB * 4;
     pl.off_rng = off;
-    off += 48;
+    off += 32;
     pl.off_decp = off;  // decorrelation rounds of min(4 x threads, B x RB) steps
     off += (4 * threads < B * RB ? 4 * threads : B * RB) * 8;
     pl.B = B;

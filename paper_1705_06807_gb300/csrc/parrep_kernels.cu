@@ -550,10 +550,9 @@ __device__ int dephase_warp(const NetDev& N, bool active, unsigned r, int G, int
 // atomic add (it is emulated and serialises under contention), so the FP32
 // form splits q into two 32-bit limbs -- the low 16 bits and the rest -- added
 // with native 32-bit atomics and folded exactly into the 64-bit shared sums
-// once per kFoldEvery staged sub-chunks.  Those add at most kFoldEvery*B*RB
-// values to a bin, so with q < qmax = 2^47 / (kFoldEvery*B*RB) the high-limb
-// sum stays inside a signed 32-bit range (roll-backs included) and the
-// low-limb sum within 2^30.
+// after every staged sub-chunk.  A sub-chunk adds at most B*RB values to a
+// bin, so with q < qmax = 2^47 / (B*RB) the high-limb sum stays inside a
+// signed 32-bit range (roll-backs included) and the low-limb sum below 2^30.
 // Holding times too large for the limbs go straight to the global sums.
 struct HistSink {
     unsigned long long* sh;  // shared histogram or nullptr
@@ -1071,12 +1070,6 @@ __device__ __forceinline__ void consume_par(const RunParams& P, const FastSmem& 
 
 enum ChunkMode { kFirst = 4 };
 
-// The pipelined FP32 chunk folds the 32-bit limbs into the 64-bit shared sums
-// once per kFoldEvery sub-chunks (and at its end); the limb bound qmax is
-// 2^47 / (kFoldEvery * B * RB) so that no limb sum overflows in between.
-constexpr int kFoldLog2 = 2;
-constexpr int kFoldEvery = 1 << kFoldLog2;
-
 // (A) the holding times of the sub-chunk's trace, used as the mode says:
 // first pass (add), roll-back (subtract), per-step sums, one step's
 // per-replica values, or the precise pass that keeps what precedes the cut.
@@ -1196,11 +1189,10 @@ __device__ void chunk_f32(const RunParams& P, const FastSmem& F, const HistSink&
         const int nh = blockDim.x - RB, h = threadIdx.x - RB;
         const int slotsz = B << P.log2RB;
         if (owner) F.live[threadIdx.x] = running ? 1 : 0;
-        if (threadIdx.x < 12) F.rng[threadIdx.x] = (threadIdx.x & 1) ? -1 : 0x7fffffff;
+        if (threadIdx.x < 8) F.rng[threadIdx.x] = (threadIdx.x & 1) ? -1 : 0x7fffffff;
         __syncthreads();
         pc.start();
         const int nsub = S / B;
-        int* rf = F.rng + 8;  // bins touched since the last fold
         if (!owner) {
             FastSmem Fp = F;
             produce_lanes<true>(P, Fp, rbase, n0, B, cycle, kTagParallel, key, h, nh);
@@ -1237,14 +1229,8 @@ __device__ void chunk_f32(const RunParams& P, const FastSmem& F, const HistSink&
                     account<KIND, MODE>(P, Fa, hs, rbase, jp * B, cut, to_post, qs, ev, inc_ev, h, nh);
                     asm volatile("bar.sync 1, %0;" ::"r"(nh) : "memory");
                     int* rg = F.rng + (jp & 1) * 4;
-                    if (h < 4) rf[h] = (h & 1) ? max(rf[h], rg[h]) : min(rf[h], rg[h]);
-                    const bool fold_now = !consume || ((jp + 1) & (kFoldEvery - 1)) == 0;
+                    if (limbs && rg[1] >= rg[0]) fold_limbs(hs, rg[0], rg[1], P.net.ystride, rg[2], rg[3], h, nh);
                     asm volatile("bar.sync 1, %0;" ::"r"(nh) : "memory");
-                    if (fold_now) {
-                        if (limbs && rf[1] >= rf[0]) fold_limbs(hs, rf[0], rf[1], P.net.ystride, rf[2], rf[3], h, nh);
-                        asm volatile("bar.sync 1, %0;" ::"r"(nh) : "memory");
-                        if (h < 4) rf[h] = (h & 1) ? -1 : 0x7fffffff;
-                    }
                     if (h < 4) rg[h] = (h & 1) ? -1 : 0x7fffffff;
                 }
             }
@@ -1962,7 +1948,7 @@ __device__ __forceinline__ bool run_instance(const RunParams& P, int lb, unsigne
     }
     int period_post = P.q_Tburn == 0 ? 1 : 0;  // which global sums this block's histogram feeds
     HistSink hs{P.use_smem_hist ? sh_hist : nullptr, period_post ? P.hist_post : P.hist_pre, limb_lo, limb_hi,
-                N.ystride, F32 ? ((1ull << 47) >> (P.log2RB + 5 + kFoldLog2)) : 0ull};
+                N.ystride, F32 ? ((1ull << 47) >> (P.log2RB + 5)) : 0ull};
     unsigned long long chunk_c = 0;
     unsigned long long est_q = 0, est_ev = 0;  // time and jumps of the last chunk
     if (join) {
