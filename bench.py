@@ -81,12 +81,13 @@ def parse():
     ap.add_argument("--t_phase", type=float, default=None, help="override t_phase (profiling)")
     ap.add_argument("--block_threads", type=int, default=0, help="CUDA block size (0 = library default)")
     ap.add_argument("--chunk_steps", type=int, default=0, help="steps between escape votes (0 = default)")
-    ap.add_argument("--workload", default="schlogl_n4096", choices=["schlogl_n4096", "batch256", "serve", "speedup", "uq"],
+    ap.add_argument("--workload", default="schlogl_n4096", choices=["schlogl_n4096", "batch256", "serve", "speedup", "uq", "sweep"],
                     help="schlogl_n4096: one ParRep run of 4096 replicas to T_end = 1e6 per step; batch256: "
                          "256 mixed Schloegl / toggle instances (64..65536 replicas, T_end = 1e4) in one launch; "
                          "serve: Poisson-arriving requests through the continuous-batching server; speedup: "
                          "ParRep vs plain SSA to the same simulated time at TV <= 1e-2 (Schloegl V=25); uq: the "
-                         "Sec. V.A IAF / FIM / information-bound experiment (100 samples to T = 2e5)")
+                         "Sec. V.A IAF / FIM / information-bound experiment (100 samples to T = 2e5); sweep: the "
+                         "Sec. V.A accuracy and speedup studies over n_c = n_p and R")
     ap.add_argument("--serve_rate", type=float, default=200.0, help="request arrivals per second (serve)")
     ap.add_argument("--serve_seconds", type=float, default=20.0, help="length of the arrival stream (serve)")
     ap.add_argument("--batch_n", type=int, default=256, help="instances of the batch workload")
@@ -503,6 +504,55 @@ def bench_uq(args):
     print(json.dumps(line), flush=True)
 
 
+def bench_sweep(args):
+    """The STEPS-mode studies of Sec. V.A: the stationary mean of the V = 25
+    Schloegl network estimated from 100 samples to T = 1e5 (R = 100) for
+    n_c = n_p = 1000 .. 5000, and for R = 20 .. 100 at n_c = n_p = 5000.  For
+    each setting: the mean with its 95% half width against the exact value,
+    and the paper's speedup -- serial SSA jumps over the jumps on ParRep's
+    critical path (decorrelation + dephasing + parallel lockstep steps), i.e.
+    the speedup on R ideal processors -- next to the GPU time."""
+    import numpy as np
+
+    from oracle import exact as E
+    from paper_1705_06807_gb300 import ParRep, ParRepBatch
+    from paper_1705_06807_gb300 import configs as K
+
+    net = K.schlogl_paper(V=25, hist_max=255)
+    x = np.arange(256.0)
+    exact = float(E.schlogl_stationary(net["c"], net["s"], 255) @ x)
+    n, T = 100, 1e5
+    settings = [(100, nc) for nc in (1000, 2000, 3000, 4000, 5000)] + [(R, 5000) for R in (20, 40, 60, 80)]
+    rows, t_total = [], 0.0
+    for i, (R, nc) in enumerate(settings):
+        hs = [ParRep(net, R, nc, nc, x0=[4], thresh="steps", precision=args.precision) for _ in range(n)]
+        b = ParRepBatch(hs)
+        info = b.run([T] * n, [100000 * (i + 1) + k for k in range(n)])
+        assert b.status() == [0] * n
+        means = np.array([h.histogram() @ x for h in hs])
+        useful = crit = 0
+        for h in hs:
+            st = h.stats()
+            useful += st["events_decorr"] + st["events_parallel_useful"]
+            crit += sum(c["decorr_steps"] + c["dephase_steps"] + c["n_star"] for c in h.cycle_log())
+        b.close()
+        t_total += info["kernel_ms"] / 1e3
+        rows.append({"R": R, "n_c": nc, "mean": float(means.mean()),
+                     "half_width_95": float(1.96 * means.std(ddof=1) / np.sqrt(n)),
+                     "rel_error": float(means.mean() / exact - 1.0), "paper_speedup": useful / crit,
+                     "gpu_s": info["kernel_ms"] / 1e3, "useful_events_per_s": useful / (info["kernel_ms"] / 1e3)})
+    line = {
+        "metric": "Sec. V.A sweeps: ParRep speedup on R ideal processors (R=100, n_c=n_p=5000)",
+        "value": rows[4]["paper_speedup"], "unit": "x", "n_gpus": 1, "steps": 1, "warmup": 0,
+        "ms_per_step": t_total * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": "schlogl_V25_sweeps_100x1e5", "samples": n, "T": T, "exact_mean": exact},
+        "rows": rows,
+        "paper": {"rel_error_nc5000": 4e-4, "speedup_R20_to_R100": [7, 20]},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -523,9 +573,9 @@ def main():
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    if args.workload in ("speedup", "uq"):
+    if args.workload in ("speedup", "uq", "sweep"):
         if rank == 0:
-            (bench_speedup if args.workload == "speedup" else bench_uq)(args)
+            dict(speedup=bench_speedup, uq=bench_uq, sweep=bench_sweep)[args.workload](args)
         if dist:
             dist.destroy_process_group()
         return
