@@ -529,3 +529,17 @@ def test_uq_estimators_on_oracle_runs_of_immigration_death():
     assert abs(out["mean_f"] - k_in / k_out) < 4 * np.sqrt(tau / (T - T_b) / 240)
     assert abs(out["fim"][3, 3] - k_in / k_out**2) < 4 * out["fim_half_width"][3, 3] / 1.96
     assert np.allclose(out["Y"], [h @ f for h in hs])
+
+
+def test_iaf_exact_on_the_toggle_generator_at_hill_exponent_zero():
+    """With Hill exponent 0 the toggle's production rates are the constant
+    alpha/2, so U and V are independent M/M/inf chains (production alpha/2,
+    degradation delta): tau(U) = alpha/delta^2 and, by independence,
+    tau(U - V) = 2 alpha / delta^2 on the two-dimensional generator."""
+    alpha, delta, m = 6.0, 1.5, 30
+    c = [alpha, 0.0, delta, alpha, 0.0, delta]
+    Q = E.toggle_generator(c, m, m).toarray()
+    pi = E.toggle_stationary(c, m, m).ravel()
+    U, V = np.meshgrid(np.arange(m + 1.0), np.arange(m + 1.0), indexing="ij")
+    assert abs(E.iaf_exact(Q, pi, U.ravel()) / (alpha / delta**2) - 1.0) < 1e-9
+    assert abs(E.iaf_exact(Q, pi, (U - V).ravel()) / (2.0 * alpha / delta**2) - 1.0) < 1e-9
