@@ -23,6 +23,10 @@ Each function is a plain definition written out in numpy/scipy:
   Q g = -fbar.
 * ``stationary_sensitivity`` -- d pi(f)/d c_k by differentiating pi Q = 0
   (the CME linear system behind Table III's approximated sensitivities).
+* ``genetic_*`` -- the genetic switch of Sec. V.B (Table IV with the
+  switching rates F, G): propensities and their parameter derivatives, the
+  truncated three-dimensional generator, its stationary law and IAFs (sparse
+  solves), and the equilibria of the rescaled rate equations.
 """
 from __future__ import annotations
 
@@ -309,3 +313,145 @@ def stationary_sensitivity(Q, dQ, pi, f):
         dpi = _bordered_solve(Q.T, -(np.asarray(dQk).T @ pi), np.ones(len(pi)))
         out.append(float(dpi @ f))
     return np.array(out)
+
+
+# ---------------------------------------------------------------------------
+# genetic switch with positive feedback (Sec. V.B): DNA state xi in {0, 1},
+# mRNA m, protein p; six channels (Table IV and the switching rates F, G)
+# ---------------------------------------------------------------------------
+GENETIC_PARAMS = ("a", "b", "gamma", "k0min", "k0max", "k1min", "k1max", "D")
+
+
+def genetic_paper_params():
+    """Sec. V.B's values: b = 22.5, a = 2400/b, gamma = 50, k0min = k1min =
+    24/b, k0max = k1max = 2400/b, D = 1000, in the order of GENETIC_PARAMS."""
+    b = 22.5
+    return np.array([2400.0 / b, b, 50.0, 24.0 / b, 2400.0 / b, 24.0 / b, 2400.0 / b, 1000.0])
+
+
+def genetic_props(c, xi, m, p):
+    """Propensities of the six channels, shape (6, n): transcription a xi,
+    mRNA decay gamma m, translation gamma b m, protein decay p, activation
+    F(p) (1 - xi), deactivation G(p) xi, with h = p^2/(p^2 + D^2),
+    F = k0min + (k0max - k0min) h and G = k1max - (k1max - k1min) h."""
+    a, b, g, k0n, k0x, k1n, k1x, D = [float(v) for v in c]
+    xi, m, p = (np.asarray(v, dtype=np.float64) for v in (xi, m, p))
+    h = p * p / (p * p + D * D)
+    F = k0n + (k0x - k0n) * h
+    G = k1x - (k1x - k1n) * h
+    return np.stack([a * xi, g * m, g * b * m, p, F * (1.0 - xi), G * xi])
+
+
+def genetic_grad_props(c, xi, m, p):
+    """d lambda_j / d c_k, shape (6, 8, n), the parameters taken independent."""
+    a, b, g, k0n, k0x, k1n, k1x, D = [float(v) for v in c]
+    xi, m, p = (np.asarray(v, dtype=np.float64) for v in (xi, m, p))
+    h = p * p / (p * p + D * D)
+    dh_dD = -2.0 * p * p * D / (p * p + D * D) ** 2
+    out = np.zeros((6, 8) + xi.shape)
+    out[0, 0] = xi
+    out[1, 2] = m
+    out[2, 1] = g * m
+    out[2, 2] = b * m
+    out[4, 3] = (1.0 - h) * (1.0 - xi)
+    out[4, 4] = h * (1.0 - xi)
+    out[4, 7] = (k0x - k0n) * dh_dD * (1.0 - xi)
+    out[5, 5] = h * xi
+    out[5, 6] = (1.0 - h) * xi
+    out[5, 7] = -(k1x - k1n) * dh_dD * xi
+    return out
+
+
+def genetic_states(m_max, p_max):
+    """All (xi, m, p) of the truncated space, flattened in (p, m, xi) order."""
+    p, m, xi = np.meshgrid(np.arange(p_max + 1), np.arange(m_max + 1), np.arange(2), indexing="ij")
+    return xi.ravel(), m.ravel(), p.ravel()
+
+
+def genetic_generator(c, m_max, p_max):
+    """Sparse generator of the chain on {0,1} x [0, m_max] x [0, p_max]
+    (moves that would leave the box are dropped)."""
+    xi, m, p = genetic_states(m_max, p_max)
+    lam = genetic_props(c, xi, m, p)
+    nm = m_max + 1
+    idx = (p * nm + m) * 2 + xi
+    moves = [(0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1), (1, 0, 0), (-1, 0, 0)]
+    rows, cols, vals = [], [], []
+    out = np.zeros(len(idx))
+    for j, (dxi, dm, dp) in enumerate(moves):
+        xi2, m2, p2 = xi + dxi, m + dm, p + dp
+        ok = (xi2 >= 0) & (xi2 <= 1) & (m2 >= 0) & (m2 <= m_max) & (p2 >= 0) & (p2 <= p_max) & (lam[j] > 0)
+        rows.append(idx[ok])
+        cols.append(((p2 * nm + m2) * 2 + xi2)[ok])
+        vals.append(lam[j][ok])
+        out += np.where(ok, lam[j], 0.0)
+    rows.append(idx)
+    cols.append(idx)
+    vals.append(-out)
+    n = len(idx)
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+
+
+def _solve_pinned(A, rhs, r):
+    """Solves A y = rhs with equation r replaced by y(r) = rhs[r] (sparse LU)."""
+    A = A.tolil(copy=True)
+    A.rows[r] = [r]
+    A.data[r] = [1.0]
+    return spla.splu(A.tocsc()).solve(rhs)
+
+
+def genetic_stationary(c, m_max, p_max, pin=None):
+    """pi Q = 0, sum pi = 1 on the truncated box: Q^T w = 0 with the equation
+    of state `pin` (default: a state near the upper well) replaced by
+    w(pin) = 1, then pi = w / sum w."""
+    Q = genetic_generator(c, m_max, p_max)
+    n = Q.shape[0]
+    r = ((min(1840, p_max) * (m_max + 1)) + min(2, m_max)) * 2 + 1 if pin is None else pin
+    rhs = np.zeros(n)
+    rhs[r] = 1.0
+    w = _solve_pinned(Q.T, rhs, r)
+    w = np.maximum(w, 0.0)
+    return Q, w / w.sum()
+
+
+def iaf_exact_sparse(Q, pi, f, pin=None):
+    """iaf_exact for a sparse generator: Q g = -fbar with the equation of
+    state `pin` replaced by g(pin) = 0 (it follows from the others, since
+    pi . Q g = 0 = -pi . fbar); the constant left free in g does not change
+    sum pi fbar g."""
+    f = np.asarray(f, dtype=np.float64)
+    fbar = f - float(pi @ f)
+    r = int(np.argmax(pi)) if pin is None else pin
+    rhs = -fbar.copy()
+    rhs[r] = 0.0
+    g = _solve_pinned(Q, rhs, r)
+    return 2.0 * float(np.sum(pi * fbar * g))
+
+
+def genetic_rre_fixed_points(c):
+    """Equilibria of the rescaled rate equations of Sec. V.B:
+    dX1/dt = a F/(F+G) - gamma X1, dX2/dt = gamma b X1 - X2.  At rest
+    X1 = X2/(gamma b) and a F(X2)/(F(X2)+G(X2)) = X2/b; the roots in X2 are
+    bracketed on a fine grid and refined by bisection."""
+    a, b, g, k0n, k0x, k1n, k1x, D = [float(v) for v in c]
+
+    def r(X2):
+        h = X2 * X2 / (X2 * X2 + D * D)
+        F = k0n + (k0x - k0n) * h
+        G = k1x - (k1x - k1n) * h
+        return a * F / (F + G) - X2 / b
+
+    grid = np.linspace(0.0, 4.0 * a * b, 400001)
+    val = r(grid)
+    roots = []
+    for i in np.nonzero(np.sign(val[:-1]) != np.sign(val[1:]))[0]:
+        lo, hi = grid[i], grid[i + 1]
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            if np.sign(r(mid)) == np.sign(r(lo)):
+                lo = mid
+            else:
+                hi = mid
+        X2 = 0.5 * (lo + hi)
+        roots.append((X2 / (g * b), X2))
+    return roots

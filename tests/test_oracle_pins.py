@@ -543,3 +543,97 @@ def test_iaf_exact_on_the_toggle_generator_at_hill_exponent_zero():
     U, V = np.meshgrid(np.arange(m + 1.0), np.arange(m + 1.0), indexing="ij")
     assert abs(E.iaf_exact(Q, pi, U.ravel()) / (alpha / delta**2) - 1.0) < 1e-9
     assert abs(E.iaf_exact(Q, pi, (U - V).ravel()) / (2.0 * alpha / delta**2) - 1.0) < 1e-9
+
+
+# ---------------------------------------------------------------------------
+# genetic switch of Sec. V.B: exact references pinned to the paper
+# ---------------------------------------------------------------------------
+def _golden_genetic():
+    d = {}
+    with open(os.path.join(GOLDEN, "paper_genetic_switch.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            k, v, hw = line.split()[:3]
+            d[k] = (float(v), float(hw))
+    return d
+
+
+@pytest.fixture(scope="module")
+def genetic_chain():
+    c = E.genetic_paper_params()
+    Q, pi = E.genetic_stationary(c, 15, 3500)
+    return c, Q, pi, E.genetic_states(15, 3500)
+
+
+def test_genetic_rate_equation_fixed_points_match_paper():
+    """The two stable points and the saddle of the rate equations, to the
+    four printed decimals (half a unit in the last: 5e-5)."""
+    g = _golden_genetic()
+    fps = E.genetic_rre_fixed_points(E.genetic_paper_params())
+    assert len(fps) == 3
+    for (x1, x2), key in zip(fps, ["plus", "saddle", "minus"]):
+        for v, k in [(x1, "fp_%s_x1" % key), (x2, "fp_%s_x2" % key)]:
+            assert abs(v - g[k][0]) <= 5e-5, (k, v)
+
+
+def test_genetic_gradients_match_finite_differences():
+    c = E.genetic_paper_params()
+    rng = np.random.default_rng(2)
+    xi = rng.integers(0, 2, 50).astype(float)
+    m = rng.integers(0, 10, 50).astype(float)
+    p = rng.integers(0, 3000, 50).astype(float)
+    G = E.genetic_grad_props(c, xi, m, p)
+    for k in range(8):
+        h = 1e-6 * c[k]
+        cp, cm = c.copy(), c.copy()
+        cp[k] += h
+        cm[k] -= h
+        fd = (E.genetic_props(cp, xi, m, p) - E.genetic_props(cm, xi, m, p)) / (2 * h)
+        assert np.allclose(G[:, k], fd, rtol=1e-6, atol=1e-9 * np.abs(fd).max() + 1e-15), k
+
+
+def test_genetic_generator_without_feedback_is_a_two_state_switch():
+    """k0min = k0max = k_on, k1min = k1max = k_off: xi is a two-state chain
+    independent of m and p, so P(xi = 1) = k_on/(k_on + k_off), E[m] = a P(xi=1)/gamma,
+    E[p] = b E[m] gamma, and tau(xi) = 2 pi_0 pi_1 / (k_on + k_off)."""
+    kon, koff = 0.7, 1.9
+    c = np.array([6.0, 3.0, 2.0, kon, kon, koff, koff, 100.0])
+    Q, pi = E.genetic_stationary(c, 30, 160, pin=0)
+    xi, m, p = E.genetic_states(30, 160)
+    p1 = kon / (kon + koff)
+    assert abs(pi @ xi - p1) < 1e-10
+    assert abs(pi @ m - c[0] * p1 / c[2]) < 1e-8
+    assert abs(pi @ p - c[1] * c[2] * (pi @ m)) < 1e-6
+    assert abs(E.iaf_exact_sparse(Q, pi, xi, pin=0) / (2 * p1 * (1 - p1) / (kon + koff)) - 1.0) < 1e-9
+
+
+def test_genetic_fim_matches_table_v(genetic_chain):
+    """The path-space FIM diagonal E_pi[sum_j (d lambda_j/d c_k)^2 / lambda_j]
+    of the exact chain lies within Table V's half widths for all eight
+    parameters; entry (1,1) is E[xi]/a in closed form."""
+    g = _golden_genetic()
+    c, Q, pi, (xi, m, p) = genetic_chain
+    assert np.abs(pi @ Q).max() < 1e-12
+    lam = E.genetic_props(c, xi, m, p)
+    dl = E.genetic_grad_props(c, xi, m, p)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        terms = np.where(lam[:, None, :] > 0, dl**2 / lam[:, None, :], 0.0)
+    F = (terms * pi).sum(axis=(0, 2))
+    assert abs(F[0] - (pi @ xi) / c[0]) < 1e-15
+    for k in range(8):
+        v, hw = g["fim_%d%d" % (k + 1, k + 1)]
+        assert abs(F[k] - v) <= hw, (k, F[k], v, hw)
+
+
+def test_genetic_iafs_against_table_vi(genetic_chain):
+    """Table VI's IAFs are 100-sample estimates (relative standard deviation
+    sqrt(2/99) = 0.142); the exact values lie within one of it, and the IAFs
+    of xi and 1 - xi are equal."""
+    g = _golden_genetic()
+    c, Q, pi, (xi, m, p) = genetic_chain
+    t_on = E.iaf_exact_sparse(Q, pi, xi)
+    assert abs(E.iaf_exact_sparse(Q, pi, 1.0 - xi) / t_on - 1.0) < 1e-9
+    for key, f in [("iaf_active", xi), ("iaf_mrna", m), ("iaf_protein", p)]:
+        t = E.iaf_exact_sparse(Q, pi, f)
+        assert abs(t / g[key][0] - 1.0) < np.sqrt(2.0 / 99.0), (key, t)
