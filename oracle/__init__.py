@@ -33,7 +33,7 @@ _LIB = os.path.join(_HERE, "_build", "libparrep_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-SCHLOGL, TOGGLE = 1, 2
+SCHLOGL, TOGGLE, GENETIC = 1, 2, 3
 TIME, STEPS = 0, 1
 F64, F32 = 0, 1
 OR_OK, OR_EINVAL, OR_ENOMEM, OR_ERANGE = 0, -1, -2, -5
@@ -43,7 +43,7 @@ class Network(C.Structure):
     _fields_ = [
         ("kind", C.c_int32),
         ("n_species", C.c_int32),
-        ("c", C.c_double * 6),
+        ("c", C.c_double * 8),
         ("s", C.c_double * 4),
         ("hist_max", C.c_int32 * 2),
         ("n_regions", C.c_int32),
@@ -151,7 +151,7 @@ def network(spec: dict) -> Network:
     """Builds the C struct from a network spec dict (see the package's
     ``configs`` module for the field meanings)."""
     n = Network()
-    n.kind = SCHLOGL if spec["kind"] == "schlogl" else TOGGLE
+    n.kind = {"schlogl": SCHLOGL, "toggle": TOGGLE, "genetic": GENETIC}[spec["kind"]]
     n.n_species = 1 if n.kind == SCHLOGL else 2
     for i, v in enumerate(spec["c"]):
         n.c[i] = float(v)
@@ -197,7 +197,7 @@ def n_bins(spec: dict) -> int:
 
 
 def n_params(spec: dict) -> int:
-    return 4 if spec["kind"] == "schlogl" else 6
+    return {"schlogl": 4, "toggle": 6, "genetic": 8}[spec["kind"]]
 
 
 # ---------------------------------------------------------------------------

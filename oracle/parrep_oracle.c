@@ -18,6 +18,10 @@
  *     lambda_j^T (Appendix A form), and the relative entropy rate
  *     E sum_j [lambda_j log(lambda_j/lambda'_j) - lambda_j + lambda'_j].
  *   - Sec. V.A (Table I): the Schloegl network.
+ *   - Sec. V.B (Table IV with the switching rates F, G): the genetic switch,
+ *     state (xi, m, p) stored as x[0] = 2 m + xi, x[1] = p, six channels and
+ *     eight parameters (a, b, gamma, k0min, k0max, k1min, k1max, D), each
+ *     differentiated independently.
  *
  * Readings of points the paper leaves open (each is also listed in the design
  * notes of the repository):
@@ -53,15 +57,18 @@
 #define OR_ENOMEM (-2)
 #define OR_ERANGE (-5)
 
-enum { OR_SCHLOGL = 1, OR_TOGGLE = 2 };
+enum { OR_SCHLOGL = 1, OR_TOGGLE = 2, OR_GENETIC = 3 };
+#define OR_NCH 6 /* most channels of a network */
+#define OR_NPAR 8 /* most parameters of a network */
 enum { OR_TIME = 0, OR_STEPS = 1 };
 enum { OR_F64 = 0, OR_F32 = 1 };
 enum { TAG_INIT = 0, TAG_DECORR = 1, TAG_DEPHASE = 2, TAG_FV = 3, TAG_PARALLEL = 4, TAG_SSA = 5 };
 
 typedef struct {
-    int32_t kind;        /* OR_SCHLOGL or OR_TOGGLE */
+    int32_t kind;        /* OR_SCHLOGL, OR_TOGGLE or OR_GENETIC */
     int32_t n_species;   /* 1 or 2 */
-    double c[6];         /* rate constants (Schloegl c1..c4; toggle aU, nU, dU, aV, nV, dV) */
+    double c[8];         /* rate constants (Schloegl c1..c4; toggle aU, nU, dU, aV, nV, dV;
+                            genetic a, b, gamma, k0min, k0max, k1min, k1max, D) */
     double s[4];         /* Schloegl fixed factors: lambda_j = c_j * s_j * h_j(x) */
     int32_t hist_max[2]; /* states must stay in [0, hist_max] */
     int32_t n_regions;   /* region(x) = first i with a_i . x < b_i, else n_regions */
@@ -175,16 +182,42 @@ static uint32_t pick(uint32_t w, uint32_t n)
 /* ------------------------------------------------------------------------ */
 /* Networks (Sec. II.A; Table I for Schloegl)                               */
 /* ------------------------------------------------------------------------ */
-static const int ETA[3][4][2] = {
-    {{0, 0}, {0, 0}, {0, 0}, {0, 0}},
-    {{1, 0}, {-1, 0}, {1, 0}, {-1, 0}}, /* Schloegl: 2S->3S, 3S->2S, 0->S, S->0 */
-    {{1, 0}, {0, 1}, {-1, 0}, {0, -1}}, /* toggle: make U, make V, lose U, lose V */
+static const int ETA[4][OR_NCH][2] = {
+    {{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}},
+    {{1, 0}, {-1, 0}, {1, 0}, {-1, 0}, {0, 0}, {0, 0}}, /* Schloegl: 2S->3S, 3S->2S, 0->S, S->0 */
+    {{1, 0}, {0, 1}, {-1, 0}, {0, -1}, {0, 0}, {0, 0}}, /* toggle: make U, make V, lose U, lose V */
+    /* genetic: transcription (m+1), mRNA decay (m-1), translation (p+1),
+     * protein decay (p-1), activation (xi 0->1), deactivation (xi 1->0) */
+    {{2, 0}, {-2, 0}, {0, 1}, {0, -1}, {1, 0}, {-1, 0}},
 };
 
-/* propensities in binary64 */
-static void props_f64(const or_network* N, const int32_t* x, double lam[4])
+static int n_channels(const or_network* N) { return N->kind == OR_GENETIC ? 6 : 4; }
+
+/* the genetic switch's Hill factor h = p^2/(p^2 + D^2) and switching rates
+ * F = k0min + (k0max - k0min) h, G = k1max - (k1max - k1min) h */
+static void genetic_rates(const double* c, double p, double* h, double* F, double* G)
 {
-    if (N->kind == OR_SCHLOGL) {
+    *h = p * p / (p * p + c[7] * c[7]);
+    *F = c[3] + (c[4] - c[3]) * *h;
+    *G = c[6] - (c[6] - c[5]) * *h;
+}
+
+/* propensities in binary64 (channels past n_channels are zero) */
+static void props_f64(const or_network* N, const int32_t* x, double lam[OR_NCH])
+{
+    lam[4] = 0.0;
+    lam[5] = 0.0;
+    if (N->kind == OR_GENETIC) {
+        double xi = (double)(x[0] & 1), m = (double)(x[0] >> 1), p = (double)x[1];
+        double h, F, G;
+        genetic_rates(N->c, p, &h, &F, &G);
+        lam[0] = N->c[0] * xi;
+        lam[1] = N->c[2] * m;
+        lam[2] = (N->c[2] * N->c[1]) * m;
+        lam[3] = p;
+        lam[4] = F * (1.0 - xi);
+        lam[5] = G * xi;
+    } else if (N->kind == OR_SCHLOGL) {
         double xd = (double)x[0];
         double h1 = xd * (xd - 1.0);
         double h2 = h1 * (xd - 2.0);
@@ -201,10 +234,24 @@ static void props_f64(const or_network* N, const int32_t* x, double lam[4])
     }
 }
 
-/* propensities in binary32 (the constants are rounded from binary64) */
-static void props_f32(const or_network* N, const int32_t* x, float lam[4])
+/* propensities in binary32 (the constants are rounded from binary64; the
+ * toggle's production terms and the genetic switching rates are evaluated in
+ * binary64 and rounded once) */
+static void props_f32(const or_network* N, const int32_t* x, float lam[OR_NCH])
 {
-    if (N->kind == OR_SCHLOGL) {
+    lam[4] = 0.0f;
+    lam[5] = 0.0f;
+    if (N->kind == OR_GENETIC) {
+        float xi = (float)(x[0] & 1), m = (float)(x[0] >> 1);
+        double h, F, G;
+        genetic_rates(N->c, (double)x[1], &h, &F, &G);
+        lam[0] = (float)N->c[0] * xi;
+        lam[1] = (float)N->c[2] * m;
+        lam[2] = (float)(N->c[2] * N->c[1]) * m;
+        lam[3] = (float)x[1];
+        lam[4] = (float)F * (1.0f - xi);
+        lam[5] = (float)G * xi;
+    } else if (N->kind == OR_SCHLOGL) {
         float xf = (float)x[0];
         float h1 = xf * (xf - 1.0f);
         float h2 = h1 * (xf - 2.0f);
@@ -221,61 +268,74 @@ static void props_f32(const or_network* N, const int32_t* x, float lam[4])
     }
 }
 
-/* Direct method selection: first j with lambda_0 + ... + lambda_j > target.
- * If rounding leaves no such j, the last channel with positive propensity. */
-static int select_f64(const double lam[4], double target)
+/* Direct method selection over the first n channels: first j with
+ * lambda_0 + ... + lambda_j > target (sums taken left to right).  If rounding
+ * leaves no such j, the last channel with positive propensity. */
+static int select_f64(const double lam[OR_NCH], int n, double target)
 {
     double cum = lam[0];
     if (cum > target) return 0;
-    cum = cum + lam[1];
-    if (cum > target) return 1;
-    cum = cum + lam[2];
-    if (cum > target) return 2;
-    cum = cum + lam[3];
-    if (cum > target) return 3;
-    for (int j = 3; j >= 0; --j)
+    for (int j = 1; j < n; ++j) {
+        cum = cum + lam[j];
+        if (cum > target) return j;
+    }
+    for (int j = n - 1; j >= 0; --j)
         if (lam[j] > 0.0) return j;
     return -1;
 }
 
-static int select_f32(const float lam[4], float target)
+static int select_f32(const float lam[OR_NCH], int n, float target)
 {
     float cum = lam[0];
     if (cum > target) return 0;
-    cum = cum + lam[1];
-    if (cum > target) return 1;
-    cum = cum + lam[2];
-    if (cum > target) return 2;
-    cum = cum + lam[3];
-    if (cum > target) return 3;
-    for (int j = 3; j >= 0; --j)
+    for (int j = 1; j < n; ++j) {
+        cum = cum + lam[j];
+        if (cum > target) return j;
+    }
+    for (int j = n - 1; j >= 0; --j)
         if (lam[j] > 0.0f) return j;
     return -1;
+}
+
+/* total rate a0, summed left to right */
+static double a0_f64(const double lam[OR_NCH], int n)
+{
+    double a = lam[0];
+    for (int j = 1; j < n; ++j) a = a + lam[j];
+    return a;
+}
+
+static float a0_f32(const float lam[OR_NCH], int n)
+{
+    float a = lam[0];
+    for (int j = 1; j < n; ++j) a = a + lam[j];
+    return a;
 }
 
 /* One SSA step at state x from the four Philox words: the holding time tau
  * (needs_tau) and the reaction J.  Returns J, or -1 if a0 <= 0. */
 static int ssa_step(const or_network* N, int prec, const int32_t* x, const uint32_t* w, double* tau)
 {
+    const int n = n_channels(N);
     if (prec == OR_F64) {
-        double lam[4];
+        double lam[OR_NCH];
         props_f64(N, x, lam);
-        double a0 = ((lam[0] + lam[1]) + lam[2]) + lam[3];
+        double a0 = a0_f64(lam, n);
         if (!(a0 > 0.0)) return -1;
         double u1 = or_u01_f64(w[0], w[1]);
         double u2 = or_u01_f64(w[2], w[3]);
         *tau = -log(u1) / a0;
-        return select_f64(lam, u2 * a0);
+        return select_f64(lam, n, u2 * a0);
     } else {
-        float lam[4];
+        float lam[OR_NCH];
         props_f32(N, x, lam);
-        float a0 = ((lam[0] + lam[1]) + lam[2]) + lam[3];
+        float a0 = a0_f32(lam, n);
         if (!(a0 > 0.0f)) return -1;
         float u1 = or_u01_f32(w[0]);
         float u2 = or_u01_f32(w[1]);
         float t = -logf(u1) / a0;
         *tau = (double)t;
-        return select_f32(lam, u2 * a0);
+        return select_f32(lam, n, u2 * a0);
     }
 }
 
@@ -302,13 +362,33 @@ static int64_t bin_of(const or_network* N, const int32_t* x)
     return (int64_t)x[0] * (N->hist_max[1] + 1) + x[1];
 }
 
-static int n_params(const or_network* N) { return N->kind == OR_SCHLOGL ? 4 : 6; }
+static int n_params(const or_network* N) { return N->kind == OR_SCHLOGL ? 4 : (N->kind == OR_TOGGLE ? 6 : 8); }
 
-/* d log lambda_j / d c_k for the network's rate constants (row j). */
-static void grad_log(const or_network* N, const int32_t* x, double g[4][6])
+/* d log lambda_j / d c_k for the network's rate constants (row j; only rows
+ * of channels with positive propensity are used). */
+static void grad_log(const or_network* N, const int32_t* x, double g[OR_NCH][OR_NPAR])
 {
-    memset(g, 0, sizeof(double) * 24);
-    if (N->kind == OR_SCHLOGL) {
+    memset(g, 0, sizeof(double) * OR_NCH * OR_NPAR);
+    if (N->kind == OR_GENETIC) {
+        const double* c = N->c;
+        double p = (double)x[1], h, F, G;
+        genetic_rates(c, p, &h, &F, &G);
+        double dh = -2.0 * p * p * c[7] / ((p * p + c[7] * c[7]) * (p * p + c[7] * c[7]));
+        g[0][0] = 1.0 / c[0];
+        g[1][2] = 1.0 / c[2];
+        g[2][1] = 1.0 / c[1];
+        g[2][2] = 1.0 / c[2];
+        if (F > 0.0) {
+            g[4][3] = (1.0 - h) / F;
+            g[4][4] = h / F;
+            g[4][7] = (c[4] - c[3]) * dh / F;
+        }
+        if (G > 0.0) {
+            g[5][5] = h / G;
+            g[5][6] = (1.0 - h) / G;
+            g[5][7] = -(c[6] - c[5]) * dh / G;
+        }
+    } else if (N->kind == OR_SCHLOGL) {
         for (int j = 0; j < 4; ++j) g[j][j] = 1.0 / N->c[j];
     } else {
         double U = (double)x[0], V = (double)x[1];
@@ -346,12 +426,12 @@ typedef struct {
 static void add_fim_rer(acc_t* A, const int32_t* x, double w)
 {
     const or_network* N = A->N;
-    int l = n_params(N);
-    double lam[4], g[4][6];
+    int l = n_params(N), nch = n_channels(N);
+    double lam[OR_NCH], g[OR_NCH][OR_NPAR];
     props_f64(N, x, lam);
     if (A->fim) {
         grad_log(N, x, g);
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < nch; ++j) {
             if (lam[j] == 0.0) continue;
             for (int a = 0; a < l; ++a)
                 for (int b = 0; b < l; ++b)
@@ -361,10 +441,10 @@ static void add_fim_rer(acc_t* A, const int32_t* x, double w)
     for (int k = 0; k < A->n_rer; ++k) {
         or_network Np = *N;
         for (int i = 0; i < l; ++i) Np.c[i] = A->rer_cp[k * l + i];
-        double lp[4];
+        double lp[OR_NCH];
         props_f64(&Np, x, lp);
         double h = 0.0;
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < nch; ++j) {
             double t = lp[j] - lam[j];
             if (lam[j] > 0.0) t += lam[j] * log(lam[j] / lp[j]);
             h += t;
@@ -409,9 +489,9 @@ static int contribute(acc_t* A, const int32_t* x, double tau)
 int64_t or_dephase_steps(const or_network* N, const or_config* C, const int32_t* x_tilde)
 {
     if (C->thresh_mode == OR_STEPS) return (int64_t)C->t_phase;
-    double lam[4];
+    double lam[OR_NCH];
     props_f64(N, x_tilde, lam);
-    double a0 = ((lam[0] + lam[1]) + lam[2]) + lam[3];
+    double a0 = a0_f64(lam, n_channels(N));
     double n = ceil(C->t_phase * a0);
     if (!(n < 4294967295.0)) return OR_ERANGE;
     return (int64_t)n;
@@ -446,10 +526,10 @@ int64_t or_dephase(const or_network* N, const or_config* C, const int32_t* x_til
             if (C->precision == OR_F32) {
                 /* the choice uniform only: word i%4 of counter (r, i/4, cycle, DEPHASE) */
                 draw(C->seed, (uint32_t)r, (uint32_t)(i >> 2), cycle, TAG_DEPHASE, w);
-                float lam[4];
+                float lam[OR_NCH];
                 props_f32(N, xs + 2 * r, lam);
-                float a0 = ((lam[0] + lam[1]) + lam[2]) + lam[3];
-                J = a0 > 0.0f ? select_f32(lam, or_u01_f32(w[i & 3]) * a0) : -1;
+                float a0 = a0_f32(lam, n_channels(N));
+                J = a0 > 0.0f ? select_f32(lam, n_channels(N), or_u01_f32(w[i & 3]) * a0) : -1;
             } else {
                 draw(C->seed, (uint32_t)r, (uint32_t)i, cycle, TAG_DEPHASE, w);
                 double tau = 0.0;
@@ -566,7 +646,7 @@ int or_parallel_from(const or_network* N, const or_config* C, int32_t* xs, int32
 /* ------------------------------------------------------------------------ */
 static int check_inputs(const or_network* N, const or_config* C)
 {
-    if (N->kind != OR_SCHLOGL && N->kind != OR_TOGGLE) return OR_EINVAL;
+    if (N->kind != OR_SCHLOGL && N->kind != OR_TOGGLE && N->kind != OR_GENETIC) return OR_EINVAL;
     if (N->n_species != (N->kind == OR_SCHLOGL ? 1 : 2)) return OR_EINVAL;
     if (N->n_regions < 1 || N->n_regions > 4) return OR_EINVAL;
     if (C->n_replicas < 1 || C->fv_group < 1) return OR_EINVAL;

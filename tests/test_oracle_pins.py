@@ -637,3 +637,91 @@ def test_genetic_iafs_against_table_vi(genetic_chain):
     for key, f in [("iaf_active", xi), ("iaf_mrna", m), ("iaf_protein", p)]:
         t = E.iaf_exact_sparse(Q, pi, f)
         assert abs(t / g[key][0] - 1.0) < np.sqrt(2.0 / 99.0), (key, t)
+
+
+# the genetic switch in the Algorithm 1 oracle (state x[0] = 2 m + xi, x[1] = p)
+GEN_SMALL = np.array([12.0, 5.0, 10.0, 0.2, 20.0, 0.2, 20.0, 25.0])  # bistable: p ~ 0.6 / 46, saddle 12.8
+
+
+def _genetic_spec(c, m_max, p_max, split):
+    return dict(kind="genetic", c=list(c), s=[1.0, 1.0, 1.0, 1.0], hist_max=[2 * m_max + 1, p_max],
+                regions=[([0, 1], split)])
+
+
+def _genetic_exact_bins(c, m_max, p_max):
+    """Exact law laid out like the oracle's histogram: bin (2 m + xi) * (p_max + 1) + p."""
+    Q, pi = E.genetic_stationary(c, m_max, p_max, pin=((min(40, p_max) * (m_max + 1)) + 1) * 2 + 1)
+    xi, m, p = E.genetic_states(m_max, p_max)
+    out = np.zeros((2 * m_max + 2) * (p_max + 1))
+    out[(2 * m + xi) * (p_max + 1) + p] = pi
+    return out
+
+
+def _marginals(h, m_max, p_max):
+    h = h.reshape(2 * m_max + 2, p_max + 1)
+    return h.sum(0), h[1::2].sum()  # protein marginal, P(xi = 1)
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_genetic_ssa_matches_exact_law(precision):
+    """The oracle's SSA on a small bistable switch (wells at p ~ 0.6 and 46,
+    saddle 12.8): the protein marginal within TV 0.03 of the exact law and
+    P(xi = 1) within 4.5 standard errors."""
+    mm, pm = 16, 250
+    spec = _genetic_spec(GEN_SMALL, mm, pm, 13)
+    ex = _genetic_exact_bins(GEN_SMALL, mm, pm)
+    tot, on = np.zeros(len(ex)), []
+    for seed in range(8):
+        h, ev, _ = O.ssa_run(spec, 1, [0, 0], 5000.0, 300 + seed, precision=precision)
+        tot += h
+        on.append(_marginals(h / h.sum(), mm, pm)[1])
+    pm_hat, _ = _marginals(tot / tot.sum(), mm, pm)
+    pm_ex, on_ex = _marginals(ex, mm, pm)
+    assert 0.5 * np.abs(pm_hat - pm_ex).sum() < 0.03
+    assert _z(on, on_ex) < 4.5
+
+
+def test_genetic_parrep_matches_exact_law():
+    """Algorithm 1 on the small switch (R = 16, n_c = n_p = 1000 jumps, regions
+    p <= 12 | p >= 13): the pooled protein marginal within TV 0.02 of the
+    exact law over about a hundred escapes (with 200-jump thresholds the
+    well mass is 1.6% off: ParRep converges as n_c, n_p grow, Sec. III.B)."""
+    mm, pm = 16, 250
+    spec = _genetic_spec(GEN_SMALL, mm, pm, 13)
+    ex = _genetic_exact_bins(GEN_SMALL, mm, pm)
+    tot, esc = np.zeros(len(ex)), 0
+    for seed in range(6):
+        r = O.parrep_run(spec, 16, 1000, 1000, 5000.0, 40 + seed, [0, 0], thresh="steps")
+        assert r["status"] == 0
+        tot += r["hist_pre"] + r["hist_post"]
+        esc += r["escapes"]
+    assert esc > 50
+    pm_hat, _ = _marginals(tot / tot.sum(), mm, pm)
+    pm_ex, _ = _marginals(ex, mm, pm)
+    assert 0.5 * np.abs(pm_hat - pm_ex).sum() < 0.02
+
+
+def test_genetic_parrep_fim_rer_are_histogram_contractions():
+    """The per-jump FIM and RER sums of the six-channel network equal the
+    post-burn occupation times contracted with the closed-form per-state
+    rates sum_j (d lambda_j / d c)^2 / lambda_j and the RER integrand."""
+    mm, pm = 16, 250
+    spec = _genetic_spec(GEN_SMALL, mm, pm, 13)
+    cp = np.array([GEN_SMALL, GEN_SMALL])
+    cp[0, 4] *= 1.3
+    cp[1, 7] *= 0.8
+    r = O.parrep_run(spec, 8, 100, 100, 400.0, 5, [0, 0], thresh="steps", T_burn=50.0, rer_cprime=cp)
+    assert r["status"] == 0
+    b = np.arange((2 * mm + 2) * (pm + 1))
+    x0, p = b // (pm + 1), b % (pm + 1)
+    xi, m = x0 & 1, x0 >> 1
+    lam = E.genetic_props(GEN_SMALL, xi, m, p)
+    dl = E.genetic_grad_props(GEN_SMALL, xi, m, p)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        rate = np.where(lam[:, None, None, :] > 0, dl[:, :, None, :] * dl[:, None, :, :] / lam[:, None, None, :], 0.0)
+    w = r["hist_post"]
+    F = np.einsum("jabn,n->ab", rate, w)
+    assert np.allclose(r["fim"], F, rtol=1e-12, atol=1e-12 * np.abs(F).max())
+    for k in range(2):
+        Rk = E.rer_exact(lam, E.genetic_props(cp[k], xi, m, p), w)
+        assert abs(r["rer"][k] - Rk) <= 1e-11 * abs(Rk)
