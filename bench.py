@@ -62,10 +62,15 @@ def combine_ranks(dist, t_total, counts, device):
     return float(tmax[0]), [int(v) for v in t[1:].tolist()]
 
 
-def workload():
+def workload(name="schlogl_n4096"):
+    """The single-run workloads: the Schloegl run with 4096 replicas (the
+    default) or the toggle-switch run with 16384 replicas."""
     from paper_1705_06807_gb300 import configs as K
 
-    return K.C2
+    c = dict(K.C3 if name == "toggle_n16384" else K.C2)
+    c.setdefault("x0_uniform_hi", 0)
+    c.setdefault("T_burn", c["T_end"] / 2)
+    return c
 
 
 def parse():
@@ -81,8 +86,10 @@ def parse():
     ap.add_argument("--t_phase", type=float, default=None, help="override t_phase (profiling)")
     ap.add_argument("--block_threads", type=int, default=0, help="CUDA block size (0 = library default)")
     ap.add_argument("--chunk_steps", type=int, default=0, help="steps between escape votes (0 = default)")
-    ap.add_argument("--workload", default="schlogl_n4096", choices=["schlogl_n4096", "batch256", "serve", "speedup", "uq", "sweep"],
-                    help="schlogl_n4096: one ParRep run of 4096 replicas to T_end = 1e6 per step; batch256: "
+    ap.add_argument("--workload", default="schlogl_n4096", choices=["schlogl_n4096", "toggle_n16384", "batch256", "serve", "speedup", "uq", "sweep"],
+                    help="schlogl_n4096: one ParRep run of 4096 replicas to T_end = 1e6 per step; toggle_n16384: "
+                         "one run of the toggle switch (alpha = 50, n = 2.5) with 16384 replicas to T_end = 1e5; "
+                         "batch256: "
                          "256 mixed Schloegl / toggle instances (64..65536 replicas, T_end = 1e4) in one launch; "
                          "serve: Poisson-arriving requests through the continuous-batching server; speedup: "
                          "ParRep vs plain SSA to the same simulated time at TV <= 1e-2 (Schloegl V=25); uq: the "
@@ -590,7 +597,7 @@ def main():
         if dist:
             dist.destroy_process_group()
         return
-    c = dict(workload())
+    c = workload(args.workload)
     T_end = args.T_end or c["T_end"]
     if args.x0 is not None:
         c["x0"], c["x0_uniform_hi"] = [args.x0], 0
@@ -681,7 +688,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {"workload": c["name"], "replicas": c["n_replicas"], "T_end": T_end,
-                   "thresholds": "time t_corr=t_phase=1", "x0": "uniform {0..1000}",
+                   "thresholds": "time t_corr=t_phase=1",
+                   "x0": f"uniform {{0..{c['x0_uniform_hi']}}}" if c["x0_uniform_hi"] else str(c["x0"]),
                    "fim_window": [c["T_burn"] * T_end / c["T_end"], T_end],
                    "accumulators": "64-bit fixed point 2^-40", "l2": "flushed (256 MiB write) between steps",
                    "parallelism": f"independent instances x{world}"},
