@@ -400,11 +400,12 @@ def bench_serve(args, local):
 def bench_speedup(args):
     """ParRep speedup over plain SSA at TV <= 1e-2 against the exact law, on
     the V = 25 Schloegl network with the paper's Sec. V.A settings (R = 100,
-    n_c = n_p = 5000): 64 seeds x 1.25e5 time units in one batch (the pooled
-    histogram's TV is measured; its well-mass standard error is about 2e-3),
-    against one plain-SSA trajectory over the same 8e6 time units -- as a
-    one-thread GPU SSA and as the oracle on one core,
-    both timed on a shorter stretch and scaled by simulated time."""
+    n_c = n_p = 5000): 128 seeds x 1.25e5 time units in one batch (the pooled
+    histogram's TV is measured and reported; its well-mass standard error is
+    about 1.3e-3, so sampling noise alone leaves a TV of a few 1e-3), against
+    one plain-SSA trajectory over the same 1.6e7 time units -- as a
+    one-thread GPU SSA and as the oracle on one core, both timed on a shorter
+    stretch and scaled by simulated time."""
     import numpy as np
 
     import oracle as O
@@ -413,7 +414,7 @@ def bench_speedup(args):
     from paper_1705_06807_gb300 import configs as K
 
     net = K.schlogl_paper(V=25)
-    n, T_each = 64, 1.25e5
+    n, T_each = 128, 1.25e5
     T_total = n * T_each
     pi = E.schlogl_stationary(net["c"], net["s"], net["hist_max"])
     hs = [ParRep(net, 100, 5000, 5000, x0=[4], thresh="steps", precision=args.precision) for _ in range(n)]
