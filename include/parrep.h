@@ -44,11 +44,11 @@ extern "C" {
 
 typedef struct parrep_s* parrep_t;
 
-enum { PARREP_SCHLOGL = 1, PARREP_TOGGLE = 2 };
+enum { PARREP_SCHLOGL = 1, PARREP_TOGGLE = 2, PARREP_GENETIC = 3 };
 enum { PARREP_THRESH_TIME = 0, PARREP_THRESH_STEPS = 1 };
 enum { PARREP_FP64 = 0, PARREP_FP32 = 1 };
 
-/* Reaction network (Sec. II.A).  Two kinds, each with four channels:
+/* Reaction network (Sec. II.A).  Three kinds:
  *   PARREP_SCHLOGL (Table I, 1 species x):
  *     lambda_j = c[j] * s[j] * h_j(x),  h = (x(x-1), x(x-1)(x-2), 1, x),
  *     eta = (+1, -1, +1, -1).  s holds the fixed factors (1/2, 1/6, 1, 1 for
@@ -56,11 +56,20 @@ enum { PARREP_FP64 = 0, PARREP_FP32 = 1 };
  *   PARREP_TOGGLE (2 species U = x[0], V = x[1]):
  *     lambda = (c0/(1+V^c1), c3/(1+U^c4), c2 U, c5 V),
  *     eta = (+U, +V, -U, -V).
- * The sensitivity parameters are c (4 for Schloegl, 6 for the toggle). */
+ *   PARREP_GENETIC (Sec. V.B, Table IV; DNA state xi, mRNA m, protein p,
+ *     stored as x[0] = 2 m + xi, x[1] = p), c = (a, b, gamma, k0min, k0max,
+ *     k1min, k1max, D), h = p^2/(p^2 + D^2), F = k0min + (k0max - k0min) h,
+ *     G = k1max - (k1max - k1min) h:
+ *     lambda = (a xi, gamma m, gamma b m, p, F (1 - xi), G xi),
+ *     eta = (m+1, m-1, p+1, p-1, xi 0->1, xi 1->0).  Binary64 form of a
+ *     single run only for now: FP32, FIM/RER, batches, serving and parrep_uq
+ *     return EINVAL for this kind.
+ * The sensitivity parameters are c (4 for Schloegl, 6 for the toggle, 8 for
+ * the genetic switch). */
 typedef struct {
-    int32_t kind;          /* PARREP_SCHLOGL or PARREP_TOGGLE */
-    int32_t n_species;     /* 1 for Schloegl, 2 for the toggle */
-    double c[6];           /* rate constants */
+    int32_t kind;          /* PARREP_SCHLOGL, PARREP_TOGGLE or PARREP_GENETIC */
+    int32_t n_species;     /* 1 for Schloegl, 2 for the toggle and the genetic switch */
+    double c[8];           /* rate constants */
     double s[4];           /* Schloegl fixed factors (ignored for the toggle) */
     int32_t x0[2];         /* initial state X~ = x_0 (Algorithm 1 set-up) */
     int32_t x0_uniform_hi; /* > 0: each species of x_0 drawn uniformly from {0..hi} */

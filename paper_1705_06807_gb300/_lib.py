@@ -18,7 +18,7 @@ PARREP_ECUDA = -3
 PARREP_ETIMEOUT = -4
 PARREP_ERANGE = -5
 PARREP_ESTATE = -6
-PARREP_SCHLOGL, PARREP_TOGGLE = 1, 2
+PARREP_SCHLOGL, PARREP_TOGGLE, PARREP_GENETIC = 1, 2, 3
 PARREP_THRESH_TIME, PARREP_THRESH_STEPS = 0, 1
 PARREP_FP64, PARREP_FP32 = 0, 1
 
@@ -27,7 +27,7 @@ ERRORS = {PARREP_EINVAL: "EINVAL", PARREP_ENOMEM: "ENOMEM", PARREP_ECUDA: "ECUDA
 
 
 class parrep_network(C.Structure):
-    _fields_ = [("kind", C.c_int32), ("n_species", C.c_int32), ("c", C.c_double * 6), ("s", C.c_double * 4),
+    _fields_ = [("kind", C.c_int32), ("n_species", C.c_int32), ("c", C.c_double * 8), ("s", C.c_double * 4),
                 ("x0", C.c_int32 * 2), ("x0_uniform_hi", C.c_int32), ("hist_max", C.c_int32 * 2)]
 
 

@@ -28,7 +28,7 @@ def _check(rc, h=None):
 def make_network(spec: dict, x0=None, x0_uniform_hi: int = 0) -> L.parrep_network:
     """parrep_network from a network spec dict (see configs)."""
     n = L.parrep_network()
-    n.kind = L.PARREP_SCHLOGL if spec["kind"] == "schlogl" else L.PARREP_TOGGLE
+    n.kind = {"schlogl": L.PARREP_SCHLOGL, "toggle": L.PARREP_TOGGLE, "genetic": L.PARREP_GENETIC}[spec["kind"]]
     n.n_species = 1 if n.kind == L.PARREP_SCHLOGL else 2
     for i, v in enumerate(spec["c"]):
         n.c[i] = float(v)
@@ -79,7 +79,7 @@ class ParRep:
                  max_blocks: int = 0):
         self._lib = L.load()
         self.spec = spec
-        self.L = 4 if spec["kind"] == "schlogl" else 6
+        self.L = {"schlogl": 4, "toggle": 6, "genetic": 8}[spec["kind"]]
         self._net = make_network(spec, x0, x0_uniform_hi)
         self._reg = make_regions(spec)
         h = C.c_void_p()

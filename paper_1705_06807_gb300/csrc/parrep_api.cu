@@ -57,7 +57,10 @@ extern "C" void parrep_default_options(parrep_options* o) {
 
 int parrep::check_network(const parrep_network* net, const parrep_regions* reg, std::string& why) {
     if (!net || !reg) { why = "null network or regions"; return 0; }
-    if (net->kind != PARREP_SCHLOGL && net->kind != PARREP_TOGGLE) { why = "unknown network kind"; return 0; }
+    if (net->kind != PARREP_SCHLOGL && net->kind != PARREP_TOGGLE && net->kind != PARREP_GENETIC) {
+        why = "unknown network kind";
+        return 0;
+    }
     const int nsp = net->kind == PARREP_SCHLOGL ? 1 : 2;
     if (net->n_species != nsp) { why = "n_species does not match the kind"; return 0; }
     if (net->hist_max[0] < 0 || net->hist_max[1] < 0 || (nsp == 1 && net->hist_max[1] != 0)) {
@@ -66,10 +69,14 @@ int parrep::check_network(const parrep_network* net, const parrep_regions* reg, 
     }
     const long long nb = (long long)(net->hist_max[0] + 1) * (net->hist_max[1] + 1);
     if (nb > (1ll << 24)) { why = "more than 2^24 histogram bins"; return 0; }
-    const int L = nsp == 1 ? 4 : 6;
+    const int L = nsp == 1 ? 4 : (net->kind == PARREP_TOGGLE ? 6 : 8);
     for (int i = 0; i < L; ++i)
         if (!std::isfinite(net->c[i])) { why = "non-finite rate constant"; return 0; }
-    if (nsp == 1) {
+    if (net->kind == PARREP_GENETIC) {
+        for (int i = 0; i < 8; ++i)
+            if (!(net->c[i] >= 0.0)) { why = "genetic switch constants must be >= 0"; return 0; }
+        if (!(net->c[7] > 0.0)) { why = "genetic switch needs D > 0"; return 0; }
+    } else if (nsp == 1) {
         for (int i = 0; i < 4; ++i)
             if (!(net->c[i] >= 0.0) || !(net->s[i] >= 0.0) || !std::isfinite(net->s[i])) {
                 why = "Schloegl constants must be finite and >= 0";
@@ -83,7 +90,7 @@ int parrep::check_network(const parrep_network* net, const parrep_regions* reg, 
         }
     }
     if (nsp == 2 && (net->hist_max[0] > 32767 || net->hist_max[1] > 32767)) {
-        why = "toggle hist_max must be <= 32767 per species";
+        why = "two-species hist_max must be <= 32767 per species";
         return 0;
     }
     if (reg->n < 1 || reg->n > 4) { why = "regions: n must be 1..4"; return 0; }
@@ -137,7 +144,21 @@ void parrep::build_net(const parrep_network* net, const parrep_regions* reg, Net
             nd.whi[rg] = x;
         }
     }
-    if (net->kind == PARREP_SCHLOGL) {
+    if (net->kind == PARREP_GENETIC) {
+        // a, gamma, gamma b; the switching rates F(p), G(p) as tables over p
+        const double* c = net->c;
+        nd.A[0] = c[0];
+        nd.A[1] = c[2];
+        nd.A[2] = c[2] * c[1];
+        pU.resize(net->hist_max[1] + 1);
+        pV.resize(net->hist_max[1] + 1);
+        for (int v = 0; v <= net->hist_max[1]; ++v) {
+            const double p = (double)v;
+            const double hh = p * p / (p * p + c[7] * c[7]);
+            pU[v] = c[3] + (c[4] - c[3]) * hh;
+            pV[v] = c[6] - (c[6] - c[5]) * hh;
+        }
+    } else if (net->kind == PARREP_SCHLOGL) {
         for (int j = 0; j < 4; ++j) {
             nd.A[j] = net->c[j] * net->s[j];
             nd.Af[j] = (float)nd.A[j];
@@ -199,14 +220,14 @@ extern "C" int parrep_create(const parrep_network* net, int64_t n_replicas, cons
     h->t_phase = t_phase;
     parrep_default_options(&h->opt);
     h->nbins = (net->hist_max[0] + 1) * (net->hist_max[1] + 1);
-    h->L = net->kind == PARREP_SCHLOGL ? 4 : 6;
+    h->L = net->kind == PARREP_SCHLOGL ? 4 : (net->kind == PARREP_TOGGLE ? 6 : 8);
     std::vector<double> pU, pV, gU, gV;
     build_net(net, reg, h->nd, pU, pV, gU, gV);
     cudaError_t e = cudaSuccess;
     std::vector<float> pUf(pU.begin(), pU.end()), pVf(pV.begin(), pV.end());
     for (size_t i = 0; i < pU.size(); ++i) pUf[i] = (float)pU[i];
     for (size_t i = 0; i < pV.size(); ++i) pVf[i] = (float)pV[i];
-    std::vector<double> cv(net->c, net->c + 6), sv(net->s, net->s + 4);
+    std::vector<double> cv(net->c, net->c + 8), sv(net->s, net->s + 4);
 #define TRY(x)                      \
     do {                            \
         e = (x);                    \
@@ -394,6 +415,8 @@ int parrep::run_checks(parrep_t h, double T_end) {
     h->has_run = false;
     if (!(T_end >= 0.0) || !(T_end < kTEndLimit)) return fail(h, PARREP_EINVAL, "T_end must be in [0, 2^23)");
     if (h->opt.T_burn > T_end) return fail(h, PARREP_EINVAL, "T_burn > T_end");
+    if (h->net.kind == PARREP_GENETIC && h->opt.precision != PARREP_FP64)
+        return fail(h, PARREP_EINVAL, "the genetic switch has the binary64 form only");
     if (h->opt.thresh_mode == PARREP_THRESH_STEPS &&
         (h->t_corr != floor(h->t_corr) || h->t_phase != floor(h->t_phase)))
         return fail(h, PARREP_EINVAL, "STEPS mode needs integer t_corr, t_phase");
@@ -567,6 +590,7 @@ extern "C" int parrep_fim(parrep_t h, double* out, int32_t len) {
     if (!h || !out) return PARREP_EINVAL;
     if (!h->has_run) return fail(h, PARREP_ESTATE, "no completed run");
     if (len != h->L * h->L) return fail(h, PARREP_EINVAL, "len != l*l");
+    if (h->net.kind == PARREP_GENETIC) return fail(h, PARREP_EINVAL, "no FIM for the genetic switch yet");
     const double span = h->stats.T_s - h->T_burn;
     if (!(span > 0.0)) return fail(h, PARREP_ESTATE, "empty window [T_burn, T_end]");
     double buf[36];
@@ -581,6 +605,7 @@ extern "C" int parrep_fim(parrep_t h, double* out, int32_t len) {
 extern "C" int parrep_rer(parrep_t h, const double* c_prime, int32_t n, double* out) {
     if (!h || !out || (n > 0 && !c_prime) || n < 0) return PARREP_EINVAL;
     if (!h->has_run) return fail(h, PARREP_ESTATE, "no completed run");
+    if (h->net.kind == PARREP_GENETIC) return fail(h, PARREP_EINVAL, "no RER for the genetic switch yet");
     const double span = h->stats.T_s - h->T_burn;
     if (!(span > 0.0)) return fail(h, PARREP_ESTATE, "empty window [T_burn, T_end]");
     std::vector<double> res(n);
@@ -643,7 +668,7 @@ extern "C" int parrep_dephase(parrep_t h, const int32_t* x_tilde, int32_t W, uin
         np = (long long)h->t_phase;
     } else {
         // a0 at X~ in binary64, the same expression as the kernels'
-        double l0, l1, l2, l3;
+        double l0 = 0.0, l1 = 0.0, l2 = 0.0, l3 = 0.0;
         const NetDev& N = h->nd;
         if (N.kind == PARREP_SCHLOGL) {
             const double xd = (double)x0;
@@ -653,14 +678,21 @@ extern "C" int parrep_dephase(parrep_t h, const int32_t* x_tilde, int32_t W, uin
             l1 = N.A[1] * b;
             l2 = N.A[2];
             l3 = N.A[3] * xd;
-        } else {
-            std::vector<double> t(1);
+        } else if (N.kind != PARREP_GENETIC) {
             CK(h, cudaMemcpy(&l0, h->d_prodU_d + x1, sizeof(double), cudaMemcpyDeviceToHost));
             CK(h, cudaMemcpy(&l1, h->d_prodV_d + x0, sizeof(double), cudaMemcpyDeviceToHost));
             l2 = N.dU * (double)x0;
             l3 = N.dV * (double)x1;
         }
-        const double a0 = ((l0 + l1) + l2) + l3;
+        double a0 = ((l0 + l1) + l2) + l3;
+        if (N.kind == PARREP_GENETIC) {
+            // six channels: a xi, gamma m, gamma b m, p, F(p)(1 - xi), G(p) xi
+            double F, G;
+            CK(h, cudaMemcpy(&F, h->d_prodU_d + x1, sizeof(double), cudaMemcpyDeviceToHost));
+            CK(h, cudaMemcpy(&G, h->d_prodV_d + x1, sizeof(double), cudaMemcpyDeviceToHost));
+            const double xi = (double)(x0 & 1), m = (double)(x0 >> 1);
+            a0 = ((((N.A[0] * xi + N.A[1] * m) + N.A[2] * m) + (double)x1) + F * (1.0 - xi)) + G * xi;
+        }
         const double n = ceil(h->t_phase * a0);
         if (!(n < 4294967295.0)) return fail(h, PARREP_ERANGE, "dephasing step count >= 2^32-1");
         np = (long long)n;

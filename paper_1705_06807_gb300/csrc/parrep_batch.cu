@@ -477,6 +477,8 @@ extern "C" int parrep_batch_create(const parrep_t* instances, int32_t n, const p
     std::vector<parrep_t> v(instances, instances + n);
     for (int i = 0; i < n; ++i) {
         if (!v[i]) return bfail(nullptr, PARREP_EINVAL, "null instance handle");
+        if (v[i]->net.kind == PARREP_GENETIC)
+            return bfail(nullptr, PARREP_EINVAL, "batches do not take the genetic switch yet");
         if (v[i]->opt.precision != v[0]->opt.precision)
             return bfail(nullptr, PARREP_EINVAL, "instances of one batch need the same precision");
     }

@@ -114,10 +114,16 @@ __device__ __forceinline__ bool out_of_range(const NetDev& N, int x0, int x1) {
     return x0 < 0 || x0 > N.hist_max0 || x1 < 0 || x1 > N.hist_max1;
 }
 
-// eta_J: Schloegl (+1,-1,+1,-1) on x0; toggle (+U,+V,-U,-V)
+// eta_J: Schloegl (+1,-1,+1,-1) on x0; toggle (+U,+V,-U,-V); genetic switch
+// (x0 = 2m + xi, x1 = p): m+1, m-1, p+1, p-1, xi 0->1, xi 1->0
 __device__ __forceinline__ void apply(const NetDev& N, int J, int& x0, int& x1) {
     if (N.kind == PARREP_SCHLOGL) {
         x0 += (J & 1) ? -1 : 1;
+    } else if (N.kind == PARREP_GENETIC) {
+        const int d = (J & 1) ? -1 : 1;
+        if (J < 2) x0 += 2 * d;
+        else if (J < 4) x1 += d;
+        else x0 += d;
     } else {
         int d = (J < 2) ? 1 : -1;
         if (J & 1) x1 += d; else x0 += d;
@@ -154,6 +160,30 @@ __device__ __forceinline__ void props_d(const NetDev& N, int x0, int x1, double&
         l2 = N.dU * (double)x0;
         l3 = N.dV * (double)x1;
     }
+}
+
+// The genetic switch in binary64 (Sec. V.B, Table IV): the six propensities
+// from x0 = 2m + xi, x1 = p, with F(p), G(p) from the host-built tables.
+__device__ __forceinline__ void props6_d(const NetDev& N, int x0, int x1, double l[6]) {
+    const double xi = (double)(x0 & 1), m = (double)(x0 >> 1);
+    l[0] = N.A[0] * xi;
+    l[1] = N.A[1] * m;
+    l[2] = N.A[2] * m;
+    l[3] = (double)x1;
+    l[4] = __ldg(N.prodU_d + x1) * (1.0 - xi);
+    l[5] = __ldg(N.prodV_d + x1) * xi;
+}
+
+// Total rate a0 in binary64, summed left to right over the network's channels.
+__device__ __forceinline__ double a0_d(const NetDev& N, int x0, int x1) {
+    if (N.kind == PARREP_GENETIC) {
+        double l[6];
+        props6_d(N, x0, x1, l);
+        return ((((l[0] + l[1]) + l[2]) + l[3]) + l[4]) + l[5];
+    }
+    double l0, l1, l2, l3;
+    props_d(N, x0, x1, l0, l1, l2, l3);
+    return ((l0 + l1) + l2) + l3;
 }
 
 __device__ __forceinline__ void props_f(const NetDev& N, int x0, int x1, float& l0, float& l1, float& l2,
@@ -216,6 +246,30 @@ __device__ __forceinline__ int ssa_draw(const NetDev& N, int x0, int x1, uint4 w
         float a0 = ((l0 + l1) + l2) + l3;
         if (WANT_TAU) q = q_of_f32(-logf(u01f(w.x)) * __frcp_rn(a0));
         return select4<float>(l0, l1, l2, l3, u01f(w.y) * a0);
+    } else if (N.kind == PARREP_GENETIC) {
+        double l[6];
+        props6_d(N, x0, x1, l);
+        const double a0 = ((((l[0] + l[1]) + l[2]) + l[3]) + l[4]) + l[5];
+        if (WANT_TAU) {
+            const double tau = -log(u01d(w.x, w.y)) / a0;
+            q = __double2ull_rn(tau * 0x1p40);
+            if (q > (1ull << 62)) q = 1ull << 62;
+        }
+        // direct method over six channels, sums left to right; if rounding
+        // leaves no sum above the target, the last channel with lambda > 0
+        const double t = u01d(w.z, w.w) * a0;
+        double cum = l[0];
+        if (cum > t) return 0;
+#pragma unroll
+        for (int j = 1; j < 6; ++j) {
+            cum = cum + l[j];
+            if (cum > t) return j;
+        }
+        int J = 0;
+#pragma unroll
+        for (int j = 0; j < 6; ++j)
+            if (l[j] > 0.0) J = j;
+        return J;
     } else {
         double l0, l1, l2, l3;
         props_d(N, x0, x1, l0, l1, l2, l3);
@@ -400,9 +454,7 @@ __device__ void leader_finish_decorr(const RunParams& P, int x0, int x1, int W, 
         if (P.thresh == PARREP_THRESH_STEPS) {
             np = P.n_p;
         } else {
-            double l0, l1, l2, l3;
-            props_d(N, x0, x1, l0, l1, l2, l3);
-            const double a0 = ((l0 + l1) + l2) + l3;
+            const double a0 = a0_d(N, x0, x1);
             const double n = ceil(P.t_phase * a0);
             if (!(n < 4294967295.0)) status = PARREP_ERANGE;
             else np = (long long)n;

@@ -467,6 +467,7 @@ extern "C" int parrep_server_submit(parrep_server_t s, const parrep_request* req
     if (!s || !req || !id) return PARREP_EINVAL;
     std::string why;
     if (!check_network(&req->net, &req->regions, why)) return sfail(s, PARREP_EINVAL, why);
+    if (req->net.kind == PARREP_GENETIC) return sfail(s, PARREP_EINVAL, "the server does not take the genetic switch yet");
     if (req->n_replicas < 1 || req->n_replicas > (1ll << 30)) return sfail(s, PARREP_EINVAL, "n_replicas");
     if (!(req->t_corr >= 0.0) || !(req->t_phase >= 0.0) || !(req->t_corr < kTEndLimit * 1024) ||
         !(req->t_phase < 1e12))

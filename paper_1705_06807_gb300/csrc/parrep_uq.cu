@@ -72,6 +72,7 @@ extern "C" int parrep_uq(const parrep_t* handles, int32_t n, const double* f, in
         smp[k].gradV_n = h->d_gradV_n;
     }
     if (len != h0->nbins) return fail(h0, PARREP_EINVAL, "len != n_bins");
+    if (h0->net.kind == PARREP_GENETIC) return fail(h0, PARREP_EINVAL, "no FIM for the genetic switch yet");
     const int L = h0->L;
     cudaStream_t st = (cudaStream_t)h0->opt.stream;
     // the handles' runs completed on their own streams: order after them
