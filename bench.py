@@ -183,15 +183,18 @@ def reference_arm(args):
     if rank != 0:
         return
     c = workload()
-    vals, tot_t, tot_ev = [], 0.0, 0
-    sample_T = 300.0
+    vals, secs = [], []
+    sample_T = 1000.0  # about 2 s of one host core per step
     for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
         b = cpu_baseline(c, sample_T=sample_T, seed=1000 + i)
         if i >= args.warmup:
             vals.append(b)
+            secs.append(time.perf_counter() - t0)
     v = statistics.mean(x["value"] for x in vals)
     line = {"impl": "reference", "metric": "SSA events/s", "value": v, "unit": "events/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs),
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": c["name"], "replicas": c["n_replicas"], "T_end_sample": sample_T},
             "cpu_baseline": {"value": v, "unit": "events/s", "cores": 1, "kind": "oracle",
