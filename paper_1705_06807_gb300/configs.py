@@ -5,11 +5,13 @@ draws of instance parameters.  Nothing here computes any part of the method,
 so both the CUDA path and the CPU oracle can be fed from it.
 
 A network spec is a dict:
-  kind      "schlogl" (1 species, 4 channels) or "toggle" (2 species, 4 channels)
+  kind      "schlogl" (1 species, 4 channels), "toggle" (2 species, 4 channels)
+            or "genetic" (state x0 = 2m + xi, x1 = p; 6 channels)
   c         rate constants.  Schloegl: (c1, c2, c3, c4) with
             lambda_j = c_j * s_j * h_j(x), h = (x(x-1), x(x-1)(x-2), 1, x).
             Toggle: (aU, nU, dU, aV, nV, dV) with production aU/(1+V^nU) of U,
             aV/(1+U^nV) of V, degradation dU*U and dV*V.
+            Genetic switch: (a, b, gamma, k0min, k0max, k1min, k1max, D).
   s         Schloegl fixed factors s_j (combinatorial factors or volume scaling)
   hist_max  largest state kept per species (states must stay in [0, hist_max])
   regions   list of (a, b): region(x) = first i with a . x < b, else len(regions)
@@ -44,6 +46,19 @@ def immigration_death(k_in: float, k_out: float, hist_max: int = 200, split: int
     Its stationary law is Poisson(k_in / k_out)."""
     return dict(kind="schlogl", c=[0.0, 0.0, k_in, k_out], s=[1.0, 1.0, 1.0, 1.0],
                 hist_max=hist_max, regions=[([1], split)])
+
+
+def genetic_switch(c=None, m_max: int = 15, p_max: int = 3500, split: int = 512) -> dict:
+    """Genetic switch of Sec. V.B (Table IV): DNA state xi, mRNA m, protein
+    p, stored as x0 = 2m + xi and x1 = p.  Default constants are the paper's
+    (b = 22.5, a = 2400/b, gamma = 50, k0min = k1min = 24/b, k0max = k1max =
+    2400/b, D = 1000); regions p < split and p >= split (the paper's line
+    through the saddle at p = 511.2865)."""
+    if c is None:
+        b = 22.5
+        c = [2400.0 / b, b, 50.0, 24.0 / b, 2400.0 / b, 24.0 / b, 2400.0 / b, 1000.0]
+    return dict(kind="genetic", c=[float(v) for v in c], s=[1.0, 1.0, 1.0, 1.0], hist_max=[2 * m_max + 1, p_max],
+                regions=[([0, 1], split)])
 
 
 def toggle(alpha: float = 50.0, n: float = 2.5, delta: float = 1.0, hist_max=(127, 127)) -> dict:
