@@ -660,6 +660,8 @@ extern "C" int parrep_cycle_log(parrep_t h, parrep_cycle* out, int64_t cap, int6
 extern "C" int parrep_dephase(parrep_t h, const int32_t* x_tilde, int32_t W, uint32_t cycle, uint64_t seed,
                               int32_t* out_states) {
     if (!h || !x_tilde || !out_states) return PARREP_EINVAL;
+    if (h->net.kind == PARREP_GENETIC && h->opt.precision != PARREP_FP64)
+        return fail(h, PARREP_EINVAL, "the genetic switch has the binary64 form only");
     const int x0 = x_tilde[0], x1 = h->net.n_species > 1 ? x_tilde[1] : 0;
     if (x0 < 0 || x0 > h->net.hist_max[0] || x1 < 0 || x1 > h->net.hist_max[1])
         return fail(h, PARREP_EINVAL, "x_tilde outside [0, hist_max]");
@@ -742,6 +744,8 @@ extern "C" int parrep_ssa(const parrep_network* net, int32_t precision, int64_t 
     std::string why;
     if (!check_network(net, &reg, why)) return fail(nullptr, PARREP_EINVAL, why);
     if (precision != PARREP_FP64 && precision != PARREP_FP32) return fail(nullptr, PARREP_EINVAL, "precision");
+    if (net->kind == PARREP_GENETIC && precision != PARREP_FP64)
+        return fail(nullptr, PARREP_EINVAL, "the genetic switch has the binary64 form only");
     if (n_traj < 1 || n_traj > (1ll << 31)) return fail(nullptr, PARREP_EINVAL, "n_traj");
     if (!(T_end >= 0.0) || !(T_end < kTEndLimit)) return fail(nullptr, PARREP_EINVAL, "T_end");
     NetDev nd;

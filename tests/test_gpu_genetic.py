@@ -90,6 +90,8 @@ def test_genetic_parts_not_built_refuse_it():
     g = ParRep(spec, 16, 50, 50, x0=[0, 0], thresh="steps", precision="f32")
     with pytest.raises(ParRepError):
         g.run(10.0, 1)
+    with pytest.raises(ParRepError):
+        parrep_ssa(spec, 1, [0, 0], 1.0, 1, precision="f32")
     g = ParRep(spec, 16, 50, 50, x0=[0, 0], thresh="steps", T_burn=2.0)
     g.run(10.0, 1)
     with pytest.raises(ParRepError):
