@@ -61,9 +61,10 @@ enum { PARREP_FP64 = 0, PARREP_FP32 = 1 };
  *     k1min, k1max, D), h = p^2/(p^2 + D^2), F = k0min + (k0max - k0min) h,
  *     G = k1max - (k1max - k1min) h:
  *     lambda = (a xi, gamma m, gamma b m, p, F (1 - xi), G xi),
- *     eta = (m+1, m-1, p+1, p-1, xi 0->1, xi 1->0).  Binary64 form of a
- *     single run only for now: FP32, FIM/RER, batches, serving and parrep_uq
- *     return EINVAL for this kind.
+ *     eta = (m+1, m-1, p+1, p-1, xi 0->1, xi 1->0).  Binary64 single runs,
+ *     parrep_dephase and parrep_ssa only for now: the FP32 form, FIM/RER,
+ *     batches, serving, parrep_uq and parrep_ssa_noalloc return EINVAL for
+ *     this kind.
  * The sensitivity parameters are c (4 for Schloegl, 6 for the toggle, 8 for
  * the genetic switch). */
 typedef struct {
