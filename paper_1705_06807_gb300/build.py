@@ -1,8 +1,11 @@
 """Builds the CUDA library libparrep.so in-tree for sm_103a with nvcc.
 
-The two translation units are compiled in parallel; arithmetic contraction
-is off (-fmad=false) so that the binary64/binary32 propensity and selection
-expressions round exactly as written.
+The translation units are compiled in parallel; parrep_kernels.cu is compiled
+once per part (-DPARREP_PART=0..6: the small kernels, then the run, batch and
+serve kernels in binary64 and binary32), since each persistent kernel inlines
+the whole of Algorithm 1.  Arithmetic contraction is off (-fmad=false) so that
+the binary64/binary32 propensity and selection expressions round exactly as
+written.
 """
 from __future__ import annotations
 
@@ -17,8 +20,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libparrep.so")
-SOURCES = ["parrep_kernels.cu", "parrep_api.cu", "parrep_batch.cu", "parrep_serve.cu", "parrep_noalloc.cu",
-           "parrep_uq.cu"]
+KERNEL_PARTS = 7
+SOURCES = [("parrep_kernels.cu", i) for i in range(KERNEL_PARTS)] + [
+    (f, None) for f in ["parrep_api.cu", "parrep_batch.cu", "parrep_serve.cu", "parrep_noalloc.cu", "parrep_uq.cu"]]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -53,9 +57,13 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     fl = flags(verbose_ptxas)
     tag = f"{os.getpid()}"
 
-    def compile_one(src):
-        obj = os.path.join(OUT_DIR, src.replace(".cu", f".{tag}.o"))
+    def compile_one(item):
+        src, part = item
+        stem = src.replace(".cu", "" if part is None else f".part{part}")
+        obj = os.path.join(OUT_DIR, f"{stem}.{tag}.o")
         cmd = [cc, "-c", os.path.join(CSRC, src), "-o", obj] + fl
+        if part is not None:
+            cmd += [f"-DPARREP_PART={part}"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -63,8 +71,10 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
             sys.stderr.write(r.stderr)
         return obj
 
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
+    # the binary32 run / batch / serve parts take longest: start them first
+    order = sorted(SOURCES, key=lambda it: (0 if it[1] in (2, 4, 6) else 1 if it[1] else 2))
+    with ThreadPoolExecutor(max_workers=min(len(SOURCES), max(2, os.cpu_count() or 2))) as ex:
+        objs = list(ex.map(compile_one, order))
     tmp = LIB + f".{tag}.tmp"
     cmd = [cc, "-shared", "-o", tmp] + objs + ARCH + ["-lcudart", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -17,10 +17,19 @@
 //     cut in the paper's (step, replica) order.
 // Every wait on another block is bounded by a no-progress timeout and turns
 // into PARREP_ETIMEOUT instead of a hang.
+//
+// The file is compiled once per part (-DPARREP_PART=0..6) so that the
+// persistent kernels, each of which inlines the whole of Algorithm 1, build
+// in parallel: part 0 holds the small kernels and the dispatchers, parts 1-6
+// instantiate the run, batch and serve kernels in binary64 and binary32.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "parrep_internal.h"
+
+#ifndef PARREP_PART
+#define PARREP_PART 0
+#endif
 
 namespace parrep {
 
@@ -353,7 +362,7 @@ struct BarState {
     int lb, nblk;  // this block's index among the blocks serving the instance, and their number
 };
 
-__device__ bool grid_sync(const RunParams& P, BarState& bs) {
+static __device__ bool grid_sync(const RunParams& P, BarState& bs) {
     __shared__ int ok;
     RunCtl* ctl = P.ctl;
     const int idx = bs.index++;
@@ -405,7 +414,7 @@ __device__ bool grid_sync(const RunParams& P, BarState& bs) {
 // ---------------------------------------------------------------------------
 // leader (block 0, thread 0): initial state and decorrelation
 // ---------------------------------------------------------------------------
-__device__ void leader_contribute(const RunParams& P, RunCtl* ctl, int x0, int x1, unsigned long long q,
+static __device__ void leader_contribute(const RunParams& P, RunCtl* ctl, int x0, int x1, unsigned long long q,
                                   unsigned long long& Ts, int& burn_done, bool& ended,
                                   unsigned long long* sh = nullptr, int sh_post = 0) {
     const NetDev& N = P.net;
@@ -436,7 +445,7 @@ __device__ void leader_contribute(const RunParams& P, RunCtl* ctl, int x0, int x
     Ts += t;
 }
 
-__device__ void leader_log(const RunParams& P, RunCtl* ctl, const CycleRecDev& rec) {
+static __device__ void leader_log(const RunParams& P, RunCtl* ctl, const CycleRecDev& rec) {
     long long i = ctl->log_n;
     if (i < P.log_cap) P.log[i] = rec;
     ctl->log_n = i + 1;
@@ -444,7 +453,7 @@ __device__ void leader_log(const RunParams& P, RunCtl* ctl, const CycleRecDev& r
 
 // End of a decorrelation (leader): n_p of the coming dephasing, the cycle
 // record's first half, the shared state for the other blocks.
-__device__ void leader_finish_decorr(const RunParams& P, int x0, int x1, int W, unsigned long long Ts, int burn_done,
+static __device__ void leader_finish_decorr(const RunParams& P, int x0, int x1, int W, unsigned long long Ts, int burn_done,
                                      unsigned long long step, bool ended, int status, unsigned cycle) {
     RunCtl* ctl = P.ctl;
     const NetDev& N = P.net;
@@ -492,7 +501,7 @@ __device__ void leader_finish_decorr(const RunParams& P, int x0, int x1, int W, 
 
 
 template <bool F32>
-__device__ void leader_decorrelate(const RunParams& P) {
+static __device__ void leader_decorrelate(const RunParams& P) {
     RunCtl* ctl = P.ctl;
     const NetDev& N = P.net;
     const uint2 key = seed_key(P.seed);
@@ -545,7 +554,7 @@ __device__ __forceinline__ int kth_set_bit(unsigned m, unsigned k) {
 }
 
 template <bool F32>
-__device__ int dephase_warp(const NetDev& N, bool active, unsigned r, int G, int W, int xt0, int xt1, long long np,
+static __device__ int dephase_warp(const NetDev& N, bool active, unsigned r, int G, int W, int xt0, int xt1, long long np,
                             unsigned cycle, uint2 key, int& x0, int& x1) {
     const int lane = threadIdx.x & 31;
     const unsigned act = __ballot_sync(0xffffffffu, active);
@@ -676,7 +685,7 @@ struct Cuts {
 
 // Re-simulates the chunk of replica r from (x0,x1) exactly as the first pass.
 template <bool F32, int MODE>
-__device__ void replay_chunk(const RunParams& P, const HistSink& hs, int x0, int x1, unsigned r, int W,
+static __device__ void replay_chunk(const RunParams& P, const HistSink& hs, int x0, int x1, unsigned r, int W,
                              unsigned cycle, unsigned n0, int S, const Cuts& cut, bool to_post,
                              unsigned long long& inc_q, unsigned long long& inc_ev, unsigned long long& ev) {
     const NetDev& N = P.net;
@@ -729,7 +738,7 @@ __device__ void replay_chunk(const RunParams& P, const HistSink& hs, int x0, int
     }
 }
 
-__device__ void flush_shared(unsigned long long* sh, unsigned long long* g, int nbins) {
+static __device__ void flush_shared(unsigned long long* sh, unsigned long long* g, int nbins) {
     __syncwarp();
     __syncthreads();
     for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
@@ -798,7 +807,7 @@ __device__ __forceinline__ void unpack_state(int nsp, int p, int& x0, int& x1) {
     x1 = nsp > 1 ? (p >> 16) : 0;
 }
 
-__device__ void build_fast_tables(const NetDev& N, float4* tab, float* inv, float* pU, float* pV) {
+static __device__ void build_fast_tables(const NetDev& N, float4* tab, float* inv, float* pU, float* pV) {
     if (N.kind == PARREP_SCHLOGL) {
         if (!tab) return;
         // entries -2..hist_max+2: the two on each side are copies of the
@@ -952,7 +961,7 @@ __device__ __forceinline__ int count_le(float4 c, float t) {
 
 // J == 4: rounding left no cumulative sum above the target; the direct
 // method then takes the last channel with positive propensity.
-__device__ __noinline__ int last_positive(const NetDev& N, int x0, int x1) {
+static __device__ __noinline__ int last_positive(const NetDev& N, int x0, int x1) {
     float l0, l1, l2, l3;
     props_f(N, x0, x1, l0, l1, l2, l3);
     return l3 > 0.f ? 3 : (l2 > 0.f ? 2 : (l1 > 0.f ? 1 : 0));
@@ -1222,7 +1231,7 @@ __device__ __forceinline__ void account(const RunParams& P, const FastSmem& F, c
 // One chunk (S steps) of the parallel step for the whole block, in a mode.
 // Every thread of the block calls it; owners carry the replica states.
 template <int KIND, int MODE>
-__device__ void chunk_f32(const RunParams& P, const FastSmem& F, const HistSink& hs, bool active, unsigned rbase,
+static __device__ void chunk_f32(const RunParams& P, const FastSmem& F, const HistSink& hs, bool active, unsigned rbase,
                           unsigned r, const RegionTest& rt, unsigned cycle, unsigned n0, int S, uint2 key, int& x0,
                           int& x1, const Cuts& cut, bool to_post, unsigned long long& mykey, unsigned long long& myoob,
                           int& xe0, int& xe1, unsigned long long& qs, unsigned long long& ev,
@@ -1332,7 +1341,7 @@ __device__ void chunk_f32(const RunParams& P, const FastSmem& F, const HistSink&
 // from shared memory; the owner warps run the jumps and the Fleming-Viot
 // ballots exactly as dephase_warp does.
 template <int KIND>
-__device__ int dephase_f32(const RunParams& P, const FastSmem& F, const RegionTest& rt, bool active, unsigned rbase,
+static __device__ int dephase_f32(const RunParams& P, const FastSmem& F, const RegionTest& rt, bool active, unsigned rbase,
                            unsigned r, int xt0, int xt1, long long np, unsigned cycle, uint2 key, int& x0, int& x1) {
     const NetDev& N = P.net;
     const bool owner = threadIdx.x < P.RB;  // whole warps, RB is a multiple of 32
@@ -1467,7 +1476,7 @@ __device__ int dephase_f32(const RunParams& P, const FastSmem& F, const RegionTe
 // histogram, and stops where Algorithm 1 stops.  Draws beyond the stop are
 // discarded; the next round starts at the step where this one stopped.
 template <int KIND>
-__device__ int decorr_chain(const NetDev& N, const FastSmem& F, int x0, int x1, int M, int& last0, int& last1) {
+static __device__ int decorr_chain(const NetDev& N, const FastSmem& F, int x0, int x1, int M, int& last0, int& last1) {
     // (2): states before each of the M jumps; returns the number of jumps
     // made (a jump that leaves [0, hist_max] ends the round, its state is
     // returned in last0/last1)
@@ -1565,7 +1574,7 @@ __device__ __forceinline__ void block_scan_sum_max(unsigned long long v, int m, 
 // parallel.  Draws beyond the stop are discarded; the next round starts at
 // the step where this one stopped.
 template <int KIND>
-__device__ void decorrelate_f32(const RunParams& P, const FastSmem& F, const HistSink& hs, int sh_post,
+static __device__ void decorrelate_f32(const RunParams& P, const FastSmem& F, const HistSink& hs, int sh_post,
                                 PhaseClock& pc) {
     __shared__ int s_more, s_n, s_l0, s_l1, s_x0, s_x1, s_W, s_burn, s_status, s_ended;
     __shared__ int s_stop, s_end, s_bcross, s_c;
@@ -1857,7 +1866,7 @@ __device__ __forceinline__ void replay_vblocks(const RunParams& P, const FastSme
 // the gang; the joiners start with the dephasing, after the barrier that
 // ends this cycle's decorrelation.  Also publishes what a joiner needs to
 // stay in step (chunk count, last chunk's sums).
-__device__ void recruit(const RunParams& P, RunCtl* ctl, int nblk, int nvb, unsigned long long chunk_c,
+static __device__ void recruit(const RunParams& P, RunCtl* ctl, int nblk, int nvb, unsigned long long chunk_c,
                         unsigned long long est_q, unsigned long long est_ev) {
     ctl->chunk_c = chunk_c;
     ctl->est_q = est_q;
@@ -1900,7 +1909,7 @@ __device__ void recruit(const RunParams& P, RunCtl* ctl, int nblk, int nvb, unsi
 }
 
 // A joiner waits (bounded) until the barrier of generation gen has passed.
-__device__ bool wait_generation(const RunParams& P, RunCtl* ctl, unsigned gen) {
+static __device__ bool wait_generation(const RunParams& P, RunCtl* ctl, unsigned gen) {
     unsigned long long t0 = globaltimer(), p0 = ldv(P.progress);
     unsigned ns = 32;
     while (ldv(&ctl->bar_gen) == gen) {
@@ -2487,7 +2496,7 @@ __global__ void __launch_bounds__(kMaxThreads)
 // idle_exit_ns (a block never leaves while others still serve requests, so
 // the launch keeps all its blocks until it ends).  While it waits it is in
 // the idle set.
-__device__ int4 serve_next(const ServeDev& sd) {
+static __device__ int4 serve_next(const ServeDev& sd) {
     int4* mb = sd.bd.mail + blockIdx.x;
     unsigned* word = sd.bd.idle + blockIdx.x / 32;
     const unsigned bit = 1u << (blockIdx.x % 32);
@@ -2530,7 +2539,7 @@ __device__ int4 serve_next(const ServeDev& sd) {
     }
 }
 
-__device__ void fim_rer_accumulate(const NetDev& N, const double* __restrict__ c, const double* __restrict__ s,
+static __device__ void fim_rer_accumulate(const NetDev& N, const double* __restrict__ c, const double* __restrict__ s,
                                    const unsigned long long* __restrict__ hist, const double* __restrict__ gradU_n,
                                    const double* __restrict__ gradV_n, const double* __restrict__ cprime,
                                    int n_cprime, double* fim_out, double* rer_out, int start, int stride);
@@ -2538,7 +2547,7 @@ __device__ void fim_rer_accumulate(const NetDev& N, const double* __restrict__ c
 // Outputs of a finished request, by the last block of its gang: the
 // histogram normalised by T_s, the FIM and RER contracted over the post-burn
 // histogram and divided by T_s - T_burn, the control block; then done.
-__device__ void serve_epilogue(const RunParams& P, const ServeSlot* slot, int* done) {
+static __device__ void serve_epilogue(const RunParams& P, const ServeSlot* slot, int* done) {
     __shared__ double s_c[6], s_s[4], s_cp[48];
     __shared__ int s_n, s_L;
     __shared__ double s_Tb;
@@ -2626,6 +2635,7 @@ __global__ void __launch_bounds__(kMaxThreads) parrep_serve_kernel(ServeDev sd) 
     }
 }
 
+#if PARREP_PART == 0
 // Zeroes the control block and the histograms of every instance of a batch
 // (one block per instance).
 __global__ void batch_reset_kernel(const RunParams* __restrict__ Ps, int n, BatchDev bd, int grid) {
@@ -2642,13 +2652,16 @@ __global__ void batch_reset_kernel(const RunParams* __restrict__ Ps, int n, Batc
         P.hist_post[b] = 0;
     }
 }
+#endif
 
+#if PARREP_PART == 0
 // Copies every instance's control block into one array for the host.
 __global__ void batch_gather_kernel(const RunParams* __restrict__ Ps, int n, RunCtl* out) {
     const unsigned long long* c = (const unsigned long long*)Ps[blockIdx.x].ctl;
     unsigned long long* o = (unsigned long long*)(out + blockIdx.x);
     for (int i = threadIdx.x; i < (int)(sizeof(RunCtl) / 8); i += blockDim.x) o[i] = c[i];
 }
+#endif
 
 // ---------------------------------------------------------------------------
 // stand-alone dephasing (for tests and diagnostics)
@@ -2667,6 +2680,7 @@ __global__ void dephase_kernel(RunParams P, int xt0, int xt1, int W, unsigned cy
     }
 }
 
+#if PARREP_PART == 0
 // ---------------------------------------------------------------------------
 // histogram normalisation, FIM and RER contractions (Sec. IV, Appendix A)
 // ---------------------------------------------------------------------------
@@ -2679,11 +2693,12 @@ __global__ void hist_normalise_kernel(const unsigned long long* pre, const unsig
         if (out_norm) out_norm[b] = (a + c) * scale;
     }
 }
+#endif
 
 // Per bin: w = time in the bin; FIM += w sum_j lambda_j g_j g_j^T with
 // g_j = grad_c log lambda_j; RER_k += w sum_j [lambda_j log(lambda_j/lambda'_j)
 // - lambda_j + lambda'_j].
-__device__ void fim_rer_accumulate(const NetDev& N, const double* __restrict__ c, const double* __restrict__ s,
+static __device__ void fim_rer_accumulate(const NetDev& N, const double* __restrict__ c, const double* __restrict__ s,
                                    const unsigned long long* __restrict__ hist, const double* __restrict__ gradU_n,
                                    const double* __restrict__ gradV_n, const double* __restrict__ cprime,
                                    int n_cprime, double* fim_out, double* rer_out, int start, int stride) {
@@ -2760,6 +2775,7 @@ __device__ void fim_rer_accumulate(const NetDev& N, const double* __restrict__ c
     }
 }
 
+#if PARREP_PART == 0
 __global__ void fim_rer_kernel(NetDev N, const double* __restrict__ c, const double* __restrict__ s,
                                const unsigned long long* __restrict__ hist, const double* __restrict__ gradU_n,
                                const double* __restrict__ gradV_n, const double* __restrict__ cprime, int n_cprime,
@@ -2767,6 +2783,7 @@ __global__ void fim_rer_kernel(NetDev N, const double* __restrict__ c, const dou
     fim_rer_accumulate(N, c, s, hist, gradU_n, gradV_n, cprime, n_cprime, fim_out, rer_out,
                        blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
+#endif
 
 // ---------------------------------------------------------------------------
 // stationary UQ over independent runs (Sec. IV.B)
@@ -2789,6 +2806,7 @@ __device__ __forceinline__ double block_sum_fixed(double v, double* red) {
     return t;
 }
 
+#if PARREP_PART == 0
 // One block per sample k: Y[k] = sum_b f[b] * time(b) over the post-burn
 // sums, and Z[k] = the FIM time average (the parrep_fim contraction: per bin
 // w sum_j lambda_j g_j g_j^T with g_j = grad_c log lambda_j, over the window).
@@ -2843,7 +2861,9 @@ __global__ void __launch_bounds__(kUqThreads) uq_sample_kernel(const UqSample* _
         if (threadIdx.x == 0) Z[(size_t)blockIdx.x * 36 + i] = t / window;
     }
 }
+#endif
 
+#if PARREP_PART == 0
 // One block: moments of Y (two passes), mean and 95% half width of each FIM
 // entry over the samples, and the bounds sqrt(tau) sqrt(v^T I v) -- each sum
 // in sample order.
@@ -2902,6 +2922,7 @@ __global__ void uq_reduce_kernel(int n, int L, const double* __restrict__ Y, con
         dir_bounds[d] = rt * sqrt(fmax(q, 0.0));
     }
 }
+#endif
 
 // ---------------------------------------------------------------------------
 // plain SSA: one thread per independent trajectory
@@ -2943,57 +2964,112 @@ __global__ void ssa_kernel(NetDev N, long long n_traj, int x00, int x01, unsigne
     if ((threadIdx.x & 31) == 0 && ev) atomicAdd(events, ev);
 }
 
+#if PARREP_PART == 0
 __global__ void philox_kernel(const uint4* ctr, const uint2* key, long long n, uint4* out) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = philox10(ctr[i], key[i]);
 }
+#endif
 
 // ---------------------------------------------------------------------------
-// launchers
+// launchers (one precision and one kernel family per part)
 // ---------------------------------------------------------------------------
-template <bool F32, int KIND>
-static int attrs_one(int* max_blocks_per_sm, int smem_bytes, int threads) {
-    cudaError_t e = cudaFuncSetAttribute(parrep_run_kernel<F32, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         smem_bytes);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, parrep_run_kernel<F32, KIND>, threads,
-                                                          smem_bytes);
+int kernel_attrs_f64(int kind, int* max_blocks_per_sm, int smem_bytes, int threads);
+int kernel_attrs_f32(int kind, int* max_blocks_per_sm, int smem_bytes, int threads);
+cudaError_t launch_run_f64(const RunParams& p, int grid, int threads, int smem_bytes, cudaStream_t st);
+cudaError_t launch_run_f32(const RunParams& p, int grid, int threads, int smem_bytes, cudaStream_t st);
+int batch_attrs_f64(int* max_blocks_per_sm, int smem_bytes, int threads);
+int batch_attrs_f32(int* max_blocks_per_sm, int smem_bytes, int threads);
+cudaError_t launch_batch_f64(const cudaLaunchConfig_t& cfg, const RunParams* d_params, const int* d_off,
+                             const int2* d_items, BatchDev bd);
+cudaError_t launch_batch_f32(const cudaLaunchConfig_t& cfg, const RunParams* d_params, const int* d_off,
+                             const int2* d_items, BatchDev bd);
+int serve_attrs_f64(int* max_blocks_per_sm, int smem_bytes, int threads);
+int serve_attrs_f32(int* max_blocks_per_sm, int smem_bytes, int threads);
+cudaError_t launch_serve_f64(const ServeDev& sd, int grid, int threads, int smem_bytes, cudaStream_t st);
+cudaError_t launch_serve_f32(const ServeDev& sd, int grid, int threads, int smem_bytes, cudaStream_t st);
+
+template <typename K>
+static int attrs_of(K kernel, int* max_blocks_per_sm, int smem_bytes, int threads) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, kernel, threads, smem_bytes);
     return (int)e;
 }
 
+#if PARREP_PART == 1 || PARREP_PART == 2
+#if PARREP_PART == 1
+#define PARREP_F32 false
+#define PARREP_SFX(name) name##_f64
+#else
+#define PARREP_F32 true
+#define PARREP_SFX(name) name##_f32
+#endif
+// The genetic switch runs in the two-species instantiation (its channels are
+// chosen by N.kind inside).
+int PARREP_SFX(kernel_attrs)(int kind, int* max_blocks_per_sm, int smem_bytes, int threads) {
+    return kind == PARREP_SCHLOGL
+               ? attrs_of(parrep_run_kernel<PARREP_F32, PARREP_SCHLOGL>, max_blocks_per_sm, smem_bytes, threads)
+               : attrs_of(parrep_run_kernel<PARREP_F32, PARREP_TOGGLE>, max_blocks_per_sm, smem_bytes, threads);
+}
+
+cudaError_t PARREP_SFX(launch_run)(const RunParams& p, int grid, int threads, int smem_bytes, cudaStream_t st) {
+    void* args[] = {(void*)&p};
+    void* fn = p.net.kind == PARREP_SCHLOGL ? (void*)parrep_run_kernel<PARREP_F32, PARREP_SCHLOGL>
+                                            : (void*)parrep_run_kernel<PARREP_F32, PARREP_TOGGLE>;
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(threads), args, (size_t)smem_bytes, st);
+}
+#endif
+
+#if PARREP_PART == 3 || PARREP_PART == 4
+#if PARREP_PART == 3
+#define PARREP_F32 false
+#define PARREP_SFX(name) name##_f64
+#else
+#define PARREP_F32 true
+#define PARREP_SFX(name) name##_f32
+#endif
+int PARREP_SFX(batch_attrs)(int* max_blocks_per_sm, int smem_bytes, int threads) {
+    return attrs_of(parrep_batch_kernel<PARREP_F32>, max_blocks_per_sm, smem_bytes, threads);
+}
+
+cudaError_t PARREP_SFX(launch_batch)(const cudaLaunchConfig_t& cfg, const RunParams* d_params, const int* d_off,
+                                     const int2* d_items, BatchDev bd) {
+    return cudaLaunchKernelEx(&cfg, parrep_batch_kernel<PARREP_F32>, d_params, d_off, d_items, bd);
+}
+#endif
+
+#if PARREP_PART == 5 || PARREP_PART == 6
+#if PARREP_PART == 5
+#define PARREP_F32 false
+#define PARREP_SFX(name) name##_f64
+#else
+#define PARREP_F32 true
+#define PARREP_SFX(name) name##_f32
+#endif
+int PARREP_SFX(serve_attrs)(int* max_blocks_per_sm, int smem_bytes, int threads) {
+    return attrs_of(parrep_serve_kernel<PARREP_F32>, max_blocks_per_sm, smem_bytes, threads);
+}
+
+cudaError_t PARREP_SFX(launch_serve)(const ServeDev& sd, int grid, int threads, int smem_bytes, cudaStream_t st) {
+    parrep_serve_kernel<PARREP_F32><<<grid, threads, smem_bytes, st>>>(sd);
+    return cudaGetLastError();
+}
+#endif
+
+#if PARREP_PART == 0
 int kernel_attrs(int prec, int kind, int* max_blocks_per_sm, int smem_bytes, int threads) {
-    if (prec == PARREP_FP32)
-        return kind == PARREP_SCHLOGL ? attrs_one<true, PARREP_SCHLOGL>(max_blocks_per_sm, smem_bytes, threads)
-                                      : attrs_one<true, PARREP_TOGGLE>(max_blocks_per_sm, smem_bytes, threads);
-    return kind == PARREP_SCHLOGL ? attrs_one<false, PARREP_SCHLOGL>(max_blocks_per_sm, smem_bytes, threads)
-                                  : attrs_one<false, PARREP_TOGGLE>(max_blocks_per_sm, smem_bytes, threads);
+    return prec == PARREP_FP32 ? kernel_attrs_f32(kind, max_blocks_per_sm, smem_bytes, threads)
+                               : kernel_attrs_f64(kind, max_blocks_per_sm, smem_bytes, threads);
 }
 
 cudaError_t launch_run(const RunParams& p, int grid, int threads, int smem_bytes, cudaStream_t st) {
-    void* args[] = {(void*)&p};
-    void* fn;
-    if (p.prec == PARREP_FP32)
-        fn = p.net.kind == PARREP_SCHLOGL ? (void*)parrep_run_kernel<true, PARREP_SCHLOGL>
-                                          : (void*)parrep_run_kernel<true, PARREP_TOGGLE>;
-    else
-        fn = p.net.kind == PARREP_SCHLOGL ? (void*)parrep_run_kernel<false, PARREP_SCHLOGL>
-                                          : (void*)parrep_run_kernel<false, PARREP_TOGGLE>;
-    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(threads), args, (size_t)smem_bytes, st);
-}
-
-template <bool F32>
-static int batch_attrs_one(int* max_blocks_per_sm, int smem_bytes, int threads) {
-    cudaError_t e = cudaFuncSetAttribute(parrep_batch_kernel<F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         smem_bytes);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, parrep_batch_kernel<F32>, threads,
-                                                          smem_bytes);
-    return (int)e;
+    return p.prec == PARREP_FP32 ? launch_run_f32(p, grid, threads, smem_bytes, st)
+                                 : launch_run_f64(p, grid, threads, smem_bytes, st);
 }
 
 int batch_kernel_attrs(int prec, int* max_blocks_per_sm, int smem_bytes, int threads) {
-    return prec == PARREP_FP32 ? batch_attrs_one<true>(max_blocks_per_sm, smem_bytes, threads)
-                               : batch_attrs_one<false>(max_blocks_per_sm, smem_bytes, threads);
+    return prec == PARREP_FP32 ? batch_attrs_f32(max_blocks_per_sm, smem_bytes, threads)
+                               : batch_attrs_f64(max_blocks_per_sm, smem_bytes, threads);
 }
 
 cudaError_t launch_batch(int prec, const RunParams* d_params, int n, const int* d_off, const int2* d_items,
@@ -3012,8 +3088,8 @@ cudaError_t launch_batch(int prec, const RunParams* d_params, int n, const int* 
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (prec == PARREP_FP32) return cudaLaunchKernelEx(&cfg, parrep_batch_kernel<true>, d_params, d_off, d_items, bd);
-    return cudaLaunchKernelEx(&cfg, parrep_batch_kernel<false>, d_params, d_off, d_items, bd);
+    return prec == PARREP_FP32 ? launch_batch_f32(cfg, d_params, d_off, d_items, bd)
+                               : launch_batch_f64(cfg, d_params, d_off, d_items, bd);
 }
 
 cudaError_t launch_batch_gather(const RunParams* d_params, int n, RunCtl* out, cudaStream_t st) {
@@ -3022,27 +3098,15 @@ cudaError_t launch_batch_gather(const RunParams* d_params, int n, RunCtl* out, c
     return cudaGetLastError();
 }
 
-template <bool F32>
-static int serve_attrs_one(int* max_blocks_per_sm, int smem_bytes, int threads) {
-    cudaError_t e = cudaFuncSetAttribute(parrep_serve_kernel<F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         smem_bytes);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, parrep_serve_kernel<F32>, threads,
-                                                          smem_bytes);
-    return (int)e;
-}
-
 int serve_kernel_attrs(int prec, int* max_blocks_per_sm, int smem_bytes, int threads) {
-    return prec == PARREP_FP32 ? serve_attrs_one<true>(max_blocks_per_sm, smem_bytes, threads)
-                               : serve_attrs_one<false>(max_blocks_per_sm, smem_bytes, threads);
+    return prec == PARREP_FP32 ? serve_attrs_f32(max_blocks_per_sm, smem_bytes, threads)
+                               : serve_attrs_f64(max_blocks_per_sm, smem_bytes, threads);
 }
 
 cudaError_t launch_serve(int prec, const ServeDev& sd, int grid, int threads, int smem_bytes, cudaStream_t st) {
-    if (prec == PARREP_FP32) parrep_serve_kernel<true><<<grid, threads, smem_bytes, st>>>(sd);
-    else parrep_serve_kernel<false><<<grid, threads, smem_bytes, st>>>(sd);
-    return cudaGetLastError();
+    return prec == PARREP_FP32 ? launch_serve_f32(sd, grid, threads, smem_bytes, st)
+                               : launch_serve_f64(sd, grid, threads, smem_bytes, st);
 }
-
 cudaError_t launch_dephase(const RunParams& p, int xt0, int xt1, int W, unsigned cycle, long long np,
                            int* out_states, int grid, int threads, cudaStream_t st) {
     int* status = &p.ctl->status;
@@ -3101,5 +3165,7 @@ cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, long long n,
     philox_kernel<<<(unsigned)blocks, threads, 0, st>>>((const uint4*)ctr, (const uint2*)key, n, (uint4*)out);
     return cudaGetLastError();
 }
+
+#endif  // PARREP_PART == 0
 
 }  // namespace parrep
