@@ -223,9 +223,11 @@ int parrep_ssa(const parrep_network* net, int32_t precision, int64_t n_traj, dou
  * inside a framework that owns the whole device memory pool and forbids side
  * allocations, or a latency-sensitive loop in which cudaMalloc/cudaFree would
  * synchronise the device.  The paper has no counterpart: this is an interface
- * variant of the plain SSA above, with the same arguments, results and
- * counters, except that hist_out (host or device, len = bins, time units) is
- * required and no kernel time is reported.
+ * variant of the plain SSA above, with the same arguments, checks, results
+ * and counters, except that hist_out (host or device, len = bins, time units)
+ * is required, x0_uniform_hi must be 0 and no kernel time is reported.
+ *   - The call waits for its stream (cudaStreamSynchronize) before it
+ *     returns, like parrep_ssa; errors set parrep_last_error(NULL).
  *   - It calls no cudaMalloc/cudaFree and no allocating library routine.  Its
  *     scratch (fixed-point histogram, jump counter, status, toggle tables) is
  *     one file-scope device array of about 0.6 MB, which every GPU that loads

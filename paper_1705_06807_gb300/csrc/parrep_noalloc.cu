@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <string>
 
 #include "parrep.h"
 #include "parrep_internal.h"
@@ -68,34 +69,41 @@ cudaError_t scratch_of_current_device(unsigned char** out) {
 
 }  // namespace
 
+// Errors go through fail() like parrep_ssa's, so parrep_last_error(NULL)
+// names the reason.
+static int noalloc_fail(int code, const std::string& why) {
+    return fail(nullptr, code, "parrep_ssa_noalloc: " + why);
+}
+
 extern "C" int parrep_ssa_noalloc(const parrep_network* net, int32_t precision, int64_t n_traj, double T_end,
                                   uint64_t seed, double* hist_out, int64_t len, int64_t* events_out,
                                   void* stream) {
-    if (!net || !hist_out) return PARREP_EINVAL;
-    if (net->kind != PARREP_SCHLOGL && net->kind != PARREP_TOGGLE) return PARREP_EINVAL;
-    const int nsp = net->kind == PARREP_SCHLOGL ? 1 : 2;
-    if (net->n_species != nsp || net->hist_max[0] < 0 || net->hist_max[1] < 0 ||
-        (nsp == 1 && net->hist_max[1] != 0))
-        return PARREP_EINVAL;
+    if (!net || !hist_out) return noalloc_fail(PARREP_EINVAL, "null network or output");
+    // the same network checks as parrep_ssa (one region: the plain SSA has no
+    // metastable sets); check_network allocates nothing
+    parrep_regions reg;
+    memset(&reg, 0, sizeof(reg));
+    reg.n = 1;
+    std::string why;
+    if (!check_network(net, &reg, why)) return noalloc_fail(PARREP_EINVAL, why);
+    if (net->kind != PARREP_SCHLOGL && net->kind != PARREP_TOGGLE)
+        return noalloc_fail(PARREP_EINVAL, "only the Schloegl and toggle networks");
+    if (net->x0_uniform_hi != 0) return noalloc_fail(PARREP_EINVAL, "x0_uniform_hi is not used by the plain SSA");
+    const int nsp = net->n_species;
     // sizes beyond the fixed scratch are refused, never truncated
     const long long nb = (long long)(net->hist_max[0] + 1) * (net->hist_max[1] + 1);
-    if (nb > (long long)kMaxBins) return PARREP_EINVAL;
-    if ((size_t)net->hist_max[0] + 1 > kMaxTab || (size_t)net->hist_max[1] + 1 > kMaxTab) return PARREP_EINVAL;
-    if (len != nb) return PARREP_EINVAL;
-    if (precision != PARREP_FP64 && precision != PARREP_FP32) return PARREP_EINVAL;
-    if (n_traj < 1 || n_traj > (1ll << 31)) return PARREP_EINVAL;
-    if (!(T_end >= 0.0) || !(T_end < kTEndLimit)) return PARREP_EINVAL;
+    if (nb > (long long)kMaxBins) return noalloc_fail(PARREP_EINVAL, "more histogram bins than the fixed scratch holds");
+    if ((size_t)net->hist_max[0] + 1 > kMaxTab || (size_t)net->hist_max[1] + 1 > kMaxTab)
+        return noalloc_fail(PARREP_EINVAL, "more states per species than the fixed scratch holds");
+    if (len != nb) return noalloc_fail(PARREP_EINVAL, "len != n_bins");
+    if (precision != PARREP_FP64 && precision != PARREP_FP32) return noalloc_fail(PARREP_EINVAL, "precision");
+    if (n_traj < 1 || n_traj > (1ll << 31)) return noalloc_fail(PARREP_EINVAL, "n_traj");
+    if (!(T_end >= 0.0) || !(T_end < kTEndLimit)) return noalloc_fail(PARREP_EINVAL, "T_end");
     const int x0 = net->x0[0], x1 = nsp > 1 ? net->x0[1] : 0;
-    if (x0 < 0 || x0 > net->hist_max[0] || x1 < 0 || x1 > net->hist_max[1]) return PARREP_EINVAL;
-    if (nsp == 1) {
-        if (!(net->c[2] * net->s[2] > 0.0)) return PARREP_EINVAL;
-    } else if (!(net->c[0] > 0.0) || !(net->c[3] > 0.0)) {
-        return PARREP_EINVAL;
-    }
 
     unsigned char* base = nullptr;
     cudaError_t e = scratch_of_current_device(&base);
-    if (e != cudaSuccess) return PARREP_ECUDA;
+    if (e != cudaSuccess) return noalloc_fail(PARREP_ECUDA, std::string("scratch address: ") + cudaGetErrorString(e));
     cudaStream_t st = (cudaStream_t)stream;
 
     NetDev nd;
@@ -138,7 +146,7 @@ extern "C" int parrep_ssa_noalloc(const parrep_network* net, int32_t precision, 
         if (e == cudaSuccess) e = cudaMemcpyAsync(base + kOffTabVf, g_hVf, nV * 4, cudaMemcpyHostToDevice, st);
         // the host tables are reused by the next call: wait until they are copied
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return PARREP_ECUDA;
+        if (e != cudaSuccess) return noalloc_fail(PARREP_ECUDA, cudaGetErrorString(e));
     }
     unsigned long long* hist = (unsigned long long*)(base + kOffHist);
     unsigned long long* events = (unsigned long long*)(base + kOffEvents);
@@ -157,7 +165,8 @@ extern "C" int parrep_ssa_noalloc(const parrep_network* net, int32_t precision, 
     if (e == cudaSuccess) e = cudaMemcpyAsync(&ev, events, 8, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&stat, status, 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return PARREP_ECUDA;
+    if (e != cudaSuccess) return noalloc_fail(PARREP_ECUDA, cudaGetErrorString(e));
     if (events_out) *events_out = (int64_t)ev;
-    return stat;
+    if (stat) return noalloc_fail(stat, "a state left [0, hist_max]");
+    return PARREP_OK;
 }

@@ -211,11 +211,15 @@ def _tiny_chain():
     return net, nu, lmb, b + d
 
 
+@pytest.mark.parametrize("precision", ["f64", "f32"])
 @pytest.mark.parametrize("R", [1, 7, 32])
-def test_first_escape_lemma_tiny_chain(R):
+def test_first_escape_lemma_tiny_chain(R, precision):
     """With R iid replicas started from the jump-chain QSD, R(N*-1)+K (K
     1-based) is geometric with parameter 1 - lambda, whatever R; the summed
-    holding time of the contributions has mean E_nu[1/a0] / (1 - lambda)."""
+    holding time of the contributions has mean E_nu[1/a0] / (1 - lambda).
+    In binary32 one Philox call serves two lockstep steps of a replica: a
+    layout that reused a word for both steps would correlate them and bend
+    the geometric law of M."""
     net, nu, lmb, a0 = _tiny_chain()
     rng = np.random.default_rng(R)
     M, T = [], []
@@ -223,7 +227,7 @@ def test_first_escape_lemma_tiny_chain(R):
     for t in range(trials):
         st = rng.choice(3, size=R, p=nu)
         states = np.stack([st, np.zeros(R, dtype=int)], axis=1)
-        rc, nstar, k, xe, ts = O.parallel_from(net, states, 0, t, 1234 + R)
+        rc, nstar, k, xe, ts = O.parallel_from(net, states, 0, t, 1234 + R, precision=precision)
         assert rc == 0 and xe[0] == 3
         M.append(R * (nstar - 1) + k + 1)
         T.append(ts)
@@ -242,14 +246,17 @@ def test_first_escape_lemma_tiny_chain(R):
 # ---------------------------------------------------------------------------
 # dephasing: Fleming-Viot samples the jump-chain QSD
 # ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", ["f64", "f32"])
 @pytest.mark.parametrize("G", [32, 4096])
 @pytest.mark.parametrize("n_p", [200, 201])
-def test_dephasing_samples_jump_chain_qsd(G, n_p):
+def test_dephasing_samples_jump_chain_qsd(G, n_p, precision):
     """Fleming-Viot dephasing (Algorithm 1) samples the QSD of the jump chain.
     A birth-death jump chain moves by +-1, so it is bipartite: after n_p
     lockstep jumps from X~ every replica has the parity of X~ + n_p, and the
     two-step chain's QSD on that parity class is the QSD nu restricted to it
-    (nu P^2 = lambda^2 nu and P^2 keeps the parity)."""
+    (nu P^2 = lambda^2 nu and P^2 keeps the parity).  In binary32 one Philox
+    call serves four dephasing jumps (word i mod 4): reusing a word would
+    correlate the jumps and move the sampled law off nu."""
     net = K.immigration_death(5.0, 1.0, hist_max=60, split=8)  # W = {0..7}
     x = np.arange(61)
     lam = E.schlogl_props(net["c"], net["s"], x)
@@ -259,7 +266,7 @@ def test_dephasing_samples_jump_chain_qsd(G, n_p):
     target /= target.sum()
     cnt = np.zeros(8)
     for cyc in range(4):
-        xs, steps, ev = O.dephase(net, 4096, [0], 0, cyc, n_p, 99, thresh="steps", fv_group=G)
+        xs, steps, ev = O.dephase(net, 4096, [0], 0, cyc, n_p, 99, thresh="steps", fv_group=G, precision=precision)
         assert steps == n_p and ev == n_p * 4096
         assert xs[:, 0].max() < 8
         cnt += np.bincount(xs[:, 0], minlength=8)[:8]
@@ -355,18 +362,20 @@ def test_parrep_without_escapes_is_stationary_poisson():
     assert _z(f44, 20.0 / 4.0) < 4.5
 
 
+@pytest.mark.parametrize("precision", ["f64", "f32"])
 @pytest.mark.parametrize("thresh,tc", [("steps", 3000), ("time", 4.0)])
-def test_parrep_bistable_schlogl_matches_exact(thresh, tc):
+def test_parrep_bistable_schlogl_matches_exact(thresh, tc, precision):
     """ParRep on the Schloegl network (Table I form, V = 10) with long
     decorrelation/dephasing: the ergodic mean of x and the mass of the lower
     well against the exact birth-death law (cf. the Sec. V.A comparison with
-    the CME)."""
+    the CME), in both precision forms."""
     net = K.schlogl_paper(V=10, hist_max=200, split=11)
     pi = E.schlogl_stationary(net["c"], net["s"], 200)
     x = np.arange(201)
     means, lows, esc = [], [], 0
     for seed in range(12):
-        r = O.parrep_run(net, 16, tc, tc, 8000.0, 300 + seed, [2], thresh=thresh, fv_group=16)
+        r = O.parrep_run(net, 16, tc, tc, 8000.0, 300 + seed, [2], thresh=thresh, fv_group=16,
+                         precision=precision)
         assert r["status"] == 0
         h = r["hist_pre"] + r["hist_post"]
         means.append((h * x).sum() / h.sum())
@@ -375,6 +384,25 @@ def test_parrep_bistable_schlogl_matches_exact(thresh, tc):
     assert esc > 100
     assert _z(means, (pi * x).sum()) < 4.5
     assert _z(lows, pi[:11].sum()) < 4.5
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_decorrelation_alone_is_the_exact_chain(precision):
+    """With t_corr beyond T_end the run never leaves the decorrelation step
+    (Algorithm 1), which simulates X~ with the exact SSA under its own counter
+    layout (binary32: one Philox call per two jumps).  Immigration-death then
+    has the Poisson(k_in/k_out) law, and every jump's time enters T_s."""
+    from scipy.stats import poisson
+
+    net = K.immigration_death(20.0, 2.0, hist_max=80, split=9)
+    p_tot = np.zeros(81)
+    for seed in range(8):
+        r = O.parrep_run(net, 8, 1e6, 5.0, 4000.0, 70 + seed, [10], thresh="time", precision=precision)
+        assert r["status"] == 0 and r["n_cycles"] == 1 and r["escapes"] == 0
+        assert r["events_parallel_useful"] == 0 and r["events_decorr"] > 0
+        p_tot += r["hist_pre"] + r["hist_post"]
+    p = p_tot / p_tot.sum()
+    assert 0.5 * np.abs(p - poisson.pmf(np.arange(81), 10.0)).sum() < 0.01
 
 
 def test_parrep_cycle_log_is_consistent():
