@@ -17,6 +17,7 @@
 
 #include "parrep.h"
 #include "parrep_internal.h"
+#include "parrep_handle.h"
 
 using namespace parrep;
 
