@@ -14,6 +14,9 @@ Each function is a plain definition written out in numpy/scipy:
   (Sec. III.A): principal left eigenvectors of the jump-chain matrix or of Q
   restricted to W.
 * ``bd_mfpt`` -- mean first passage time of a birth-death chain (textbook sum).
+* ``bd_decorrelated_exit_rate`` -- the stationary rate of the exits that
+  follow a completed TIME-mode decorrelation (Algorithm 1): the rate at which
+  an exact ParRep run should see parallel-step escapes.
 * ``fim_exact`` / ``rer_exact`` -- the path-space FIM (Appendix A form
   E_pi sum_j lambda_j grad log lambda_j grad log lambda_j^T) and the relative
   entropy rate E_pi sum_j [lambda_j log(lambda_j/lambda'_j) - lambda_j + lambda'_j].
@@ -140,6 +143,57 @@ def bd_mfpt_down(birth, death, x_from, x_to, xmax):
     d = np.asarray(death, dtype=np.float64)[::-1][: xmax + 1]
     # reflect: state y -> xmax - y, births become deaths
     return bd_mfpt(d, b, xmax - x_from, xmax - x_to)
+
+
+def bd_decorrelated_exit_rate(birth, death, split, t_corr):
+    """Escapes per unit time that follow a completed decorrelation step.
+
+    Birth-death chain on {0..n-1}, regions W- = {x < split} and W+ = {x >=
+    split}.  In the TIME form of Algorithm 1's decorrelation the in-W time is
+    the sum of the holding times of the jumps that stayed in W since the chain
+    entered W, and the step ends at the first such jump with in-W time >=
+    t_corr; the dephasing and parallel steps then produce the one exit that
+    ends this sojourn.  So an exact ParRep run has one parallel-step escape per
+    sojourn whose first jump at or after t_corr stays in W.
+
+    A sojourn in W+ starts at `split` (entered from split-1) and one in W- at
+    split-1.  By detailed balance both entries happen at the stationary flux
+    J = pi(split-1) b(split-1) = pi(split) d(split), and sojourns are i.i.d.
+    given their entry state, so the rate is J (S-(t) + S+(t)) with
+        S_W(t) = sum_x P_entry(X_t = x, no exit by t) (1 - p_exit(x)),
+    P = exp(t Q_W) (Q restricted to W, exits killed) and p_exit(x) the
+    probability that the next jump from x leaves W.
+
+    Q_W is reversible with respect to pi on W, so D^(1/2) Q_W D^(-1/2) (D =
+    diag pi) is the symmetric tridiagonal matrix with diagonal -a0(x) and
+    off-diagonal sqrt(b(x) d(x+1)); exp(t Q_W) comes from its eigenpairs,
+    which stays exact for the stiff generators (rates up to 1e5) where a
+    Krylov or Pade exponential is slow."""
+    from scipy.linalg import eigh_tridiagonal
+
+    b = np.asarray(birth, dtype=np.float64).copy()
+    d = np.asarray(death, dtype=np.float64).copy()
+    n = len(b)
+    b[-1] = 0.0  # truncation: no births out of the last state
+    d[0] = 0.0
+    pi = bd_stationary(b, d)
+    J = pi[split - 1] * b[split - 1]
+    total = 0.0
+    for lo, hi, entry in ((0, split - 1, split - 1), (split, n - 1, split)):
+        xs = np.arange(lo, hi + 1)
+        a0 = b[xs] + d[xs]  # every jump leaves the state (exits are killed)
+        out = np.zeros(len(xs))  # rate of the jump that leaves W
+        if entry == split - 1:
+            out[-1] = b[split - 1]
+        else:
+            out[0] = d[split]
+        p_stay = np.where(a0 > 0, 1.0 - out / np.where(a0 > 0, a0, 1.0), 0.0)
+        w = pi[xs] / pi[xs].sum()
+        lam, V = eigh_tridiagonal(-a0, np.sqrt(b[xs][:-1] * d[xs][1:]))
+        e = entry - lo
+        coef = V.T @ (np.sqrt(w) * p_stay)
+        total += float(np.sum(V[e] * np.exp(lam * float(t_corr)) * coef) / np.sqrt(w[e]))
+    return J * total
 
 
 # ---------------------------------------------------------------------------

@@ -405,6 +405,76 @@ def test_decorrelation_alone_is_the_exact_chain(precision):
     assert 0.5 * np.abs(p - poisson.pmf(np.arange(81), 10.0)).sum() < 0.01
 
 
+def _decorrelated_sojourns(xs, tau, x0, split, t_corr):
+    """Brute-force count on an exact SSA trace (pre-jump states, holding times):
+    sojourns between two region changes whose time up to their last in-region
+    jump (the sojourn minus the exit's holding time) is >= t_corr, i.e. those
+    in which a TIME-mode decorrelation would have completed; and the time
+    between the first and the last region change."""
+    pre = np.concatenate([[x0], xs[:-1, 0]])
+    t = np.cumsum(tau)
+    ex = np.nonzero((pre >= split) != (xs[:, 0] >= split))[0]
+    L = t[ex[1:]] - t[ex[:-1]]
+    return int(np.sum(L - tau[ex[1:]] >= t_corr)), t[ex[-1]] - t[ex[0]]
+
+
+def _schlogl_v10_rates():
+    net = K.schlogl_paper(V=10, hist_max=200, split=11)
+    lam = E.schlogl_props(net["c"], net["s"], np.arange(201))
+    return net, lam[0] + lam[2], lam[1] + lam[3]
+
+
+@pytest.mark.parametrize("t_corr", [0.1, 1.0])
+def test_decorrelated_exit_rate_against_exact_chain_trace(t_corr):
+    """bd_decorrelated_exit_rate (the escapes per unit time an exact ParRep
+    run has in TIME mode) against the same event counted on exact SSA traces
+    of the V = 10 Schloegl chain; at t_corr = 0.1 the exit-on-the-next-jump
+    correction is 6% and the pin resolves it."""
+    net, b, d = _schlogl_v10_rates()
+    exact = E.bd_decorrelated_exit_rate(b, d, 11, t_corr)
+    rates = []
+    for tr in range(32):
+        J, xs, tau = O.ssa_trace(net, [2], 5, tr, 400000)
+        c, T = _decorrelated_sojourns(xs, tau, 2, 11, t_corr)
+        rates.append(c / T)
+    assert _z(rates, exact) < 4.5
+
+
+def test_decorrelated_exit_rate_limits():
+    """t_corr = 0: every sojourn whose first jump stays in its region counts,
+    J (2 - p(split-1 -> split) - p(split -> split-1)) with J the stationary
+    flux; the rate falls as t_corr grows (fewer sojourns last long enough)."""
+    net, b, d = _schlogl_v10_rates()
+    pi = E.bd_stationary(b, d)
+    J = pi[10] * b[10]
+    r0 = J * (2.0 - b[10] / (b[10] + d[10]) - d[11] / (b[11] + d[11]))
+    assert abs(E.bd_decorrelated_exit_rate(b, d, 11, 0.0) - r0) < 1e-12 * r0
+    rates = [E.bd_decorrelated_exit_rate(b, d, 11, t) for t in (0.5, 1.0, 2.0, 4.0)]
+    assert all(a > c for a, c in zip(rates, rates[1:]))
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_parrep_escape_rate_is_exact_only_for_long_thresholds(precision):
+    """Sec. III.B: ParRep is exact as the decorrelation and dephasing grow.
+    With t_corr = t_phase = 4 (TIME mode, R = 16) the parallel-step escapes of
+    the V = 10 Schloegl chain come at the exact decorrelated-exit rate; with
+    0.25 / 0.25 the dephased replicas are not yet quasi-stationary, the first
+    of the R replicas escapes early, and the rate is far too high."""
+    net, b, d = _schlogl_v10_rates()
+    for tc, ok in ((4.0, True), (0.25, False)):
+        exact = E.bd_decorrelated_exit_rate(b, d, 11, tc)
+        rates = []
+        for seed in range(12):
+            r = O.parrep_run(net, 16, tc, tc, 8000.0, 300 + seed, [2], thresh="time", fv_group=16,
+                             precision=precision)
+            assert r["status"] == 0
+            rates.append(r["escapes"] / 8000.0)
+        if ok:
+            assert _z(rates, exact) < 4.5
+        else:
+            assert np.mean(rates) > 1.2 * exact and _z(rates, exact) > 6
+
+
 def test_parrep_cycle_log_is_consistent():
     net = K.schlogl_paper(V=10, hist_max=200, split=11)
     r = O.parrep_run(net, 16, 400, 400, 3000.0, 11, [2], thresh="steps")
