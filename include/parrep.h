@@ -61,10 +61,10 @@ enum { PARREP_FP64 = 0, PARREP_FP32 = 1 };
  *     k1min, k1max, D), h = p^2/(p^2 + D^2), F = k0min + (k0max - k0min) h,
  *     G = k1max - (k1max - k1min) h:
  *     lambda = (a xi, gamma m, gamma b m, p, F (1 - xi), G xi),
- *     eta = (m+1, m-1, p+1, p-1, xi 0->1, xi 1->0).  Binary64 single runs,
- *     parrep_dephase and parrep_ssa only for now: the FP32 form, FIM/RER,
- *     batches, serving, parrep_uq and parrep_ssa_noalloc return EINVAL for
- *     this kind.
+ *     eta = (m+1, m-1, p+1, p-1, xi 0->1, xi 1->0).  Binary64 form only:
+ *     single runs, FIM/RER (eight parameters), batches, serving, parrep_uq,
+ *     parrep_dephase, parrep_ssa and parrep_ssa_trace; the FP32 form and
+ *     parrep_ssa_noalloc return EINVAL for this kind.
  * The sensitivity parameters are c (4 for Schloegl, 6 for the toggle, 8 for
  * the genetic switch). */
 typedef struct {
@@ -180,7 +180,8 @@ int parrep_histogram_raw(parrep_t h, double* pre, double* post, int64_t len);
 
 /* Path-space FIM (Sec. IV; Appendix A form): the time average over
  * [T_burn, T_end] of sum_j lambda_j grad_c log lambda_j grad_c log lambda_j^T,
- * row-major l x l with l = 4 (Schloegl) or 6 (toggle); len = l*l. */
+ * row-major l x l with l = 4 (Schloegl), 6 (toggle) or 8 (genetic switch,
+ * its parameters taken independently); len = l*l. */
 int parrep_fim(parrep_t h, double* out, int32_t len);
 
 /* Relative entropy rates (Appendix A) H(P^c | P^{c'}) for n perturbed
@@ -214,6 +215,23 @@ const char* parrep_last_error(parrep_t h);
  * total jumps; kernel_ms (host, may be NULL): device time.  stream may be NULL. */
 int parrep_ssa(const parrep_network* net, int32_t precision, int64_t n_traj, double T_end, uint64_t seed,
                double* hist_out, int64_t len, int64_t* events_out, float* kernel_ms, void* stream);
+
+/* Plain SSA with a record of every jump, for trajectory-level checks (the
+ * reaction index sequence and integer states of Sec. II.A's direct method).
+ * The same counters and arithmetic as parrep_ssa: trajectory t starts at x0
+ * and runs until T_end or until it has made max_steps jumps, whichever comes
+ * first.  Outputs (host or device pointers, row-major per trajectory):
+ *   reactions: n_traj x max_steps int32, the channel of each jump;
+ *   states:    n_traj x max_steps x 2 int32, the state after each jump;
+ *   holding:   n_traj x max_steps double (may be NULL), each holding time as
+ *              the 2^-40 fixed-point value the library sums;
+ *   n_jumps:   n_traj int64, the jumps made (entries beyond are not written);
+ *   x_final:   n_traj x 2 int32, the state at the end.
+ * Limits: n_traj * max_steps <= 2^28; x0_uniform_hi must be 0.
+ * Returns PARREP_OK, EINVAL, ERANGE (a state left [0, hist_max]) or ECUDA. */
+int parrep_ssa_trace(const parrep_network* net, int32_t precision, int64_t n_traj, double T_end, uint64_t seed,
+                     int64_t max_steps, int32_t* reactions, int32_t* states, double* holding, int64_t* n_jumps,
+                     int32_t* x_final);
 
 /* Limits of parrep_ssa_noalloc's fixed scratch. */
 #define PARREP_SSA_NOALLOC_MAX_BINS 65536
@@ -369,7 +387,7 @@ typedef struct {
     int32_t fv_group;           /* 0 = 32 */
     int32_t chunk_steps;        /* 0 = default */
     int32_t n_cprime;           /* perturbed parameter vectors for the RER (0..8) */
-    const double* c_prime;      /* n_cprime x l (l = 4 Schloegl, 6 toggle), copied at submit */
+    const double* c_prime;      /* n_cprime x l (l = 4 Schloegl, 6 toggle, 8 genetic), copied at submit */
 } parrep_request;
 
 enum { PARREP_REQ_QUEUED = 0, PARREP_REQ_RUNNING = 1, PARREP_REQ_DONE = 2 };
@@ -430,13 +448,13 @@ const char* parrep_server_last_error(parrep_server_t s);
  * result does not depend on scheduling). */
 typedef struct {
     int32_t n_samples;
-    int32_t n_params;          /* l = 4 (Schloegl) or 6 (toggle) */
+    int32_t n_params;          /* l = 4 (Schloegl), 6 (toggle) or 8 (genetic switch) */
     double window;             /* w = T_end - T_burn */
     double iaf;
     double mean_f;
-    double fim[36];            /* row-major l x l */
-    double fim_half_width[36];
-    double bound[6];
+    double fim[64];            /* row-major l x l */
+    double fim_half_width[64];
+    double bound[8];
 } parrep_uq_result;
 
 /* handles: n >= 2 handles (host array).  f: one value per histogram bin

@@ -123,6 +123,7 @@ def lib():
             L.or_parrep_run.argtypes = [P(Network), P(Config), P(C.c_double), P(C.c_double), P(C.c_double),
                                         P(C.c_double), C.c_int32, P(C.c_double), P(Cycle), C.c_int64,
                                         P(C.c_int64), P(Result)]
+            L.or_parrep_run_counted.argtypes = L.or_parrep_run.argtypes + [P(C.c_int64), P(C.c_int64)]
             L.or_dephase.argtypes = [P(Network), P(Config), P(C.c_int32), C.c_int32, C.c_uint32,
                                      P(C.c_int32), P(C.c_int64)]
             L.or_dephase.restype = C.c_int64
@@ -220,10 +221,11 @@ def u01_f32(w) -> float:
 
 
 def parrep_run(spec, n_replicas, t_corr, t_phase, T_end, seed, x0=None, *, thresh="time", precision="f64",
-               fv_group=32, T_burn=0.0, x0_uniform_hi=0, rer_cprime=None, log_cap=100000):
+               fv_group=32, T_burn=0.0, x0_uniform_hi=0, rer_cprime=None, log_cap=100000, counts=False):
     """Runs Algorithm 1 to T_end.  Returns a dict with the pre- and post-burn-in
     histograms (time sums), the FIM and RER sums over [T_burn, T_end], the
-    cycle log and the run statistics."""
+    cycle log and the run statistics; with counts=True also the number of
+    holding times added to each bin before and after T_burn."""
     net = network(spec)
     if x0 is None:
         x0 = [0, 0]
@@ -241,9 +243,13 @@ def parrep_run(spec, n_replicas, t_corr, t_phase, T_end, seed, x0=None, *, thres
     log = (Cycle * max(log_cap, 1))()
     log_n = C.c_int64(0)
     res = Result()
-    rc = lib().or_parrep_run(C.byref(net), C.byref(cfg), _ptr(hpre, C.c_double), _ptr(hpost, C.c_double),
-                             _ptr(fim, C.c_double), _ptr(rer_cprime, C.c_double), len(rer_cprime),
-                             _ptr(rer, C.c_double), log, log_cap, C.byref(log_n), C.byref(res))
+    cpre = np.zeros(nb, dtype=np.int64)
+    cpost = np.zeros(nb, dtype=np.int64)
+    rc = lib().or_parrep_run_counted(C.byref(net), C.byref(cfg), _ptr(hpre, C.c_double), _ptr(hpost, C.c_double),
+                                     _ptr(fim, C.c_double), _ptr(rer_cprime, C.c_double), len(rer_cprime),
+                                     _ptr(rer, C.c_double), log, log_cap, C.byref(log_n), C.byref(res),
+                                     _ptr(cpre, C.c_int64) if counts else None,
+                                     _ptr(cpost, C.c_int64) if counts else None)
     cycles = [
         dict(cycle=log[i].cycle, W=log[i].W, ended=log[i].ended, decorr_steps=log[i].decorr_steps,
              dephase_steps=log[i].dephase_steps, n_star=log[i].n_star, k=log[i].k,
@@ -254,7 +260,7 @@ def parrep_run(spec, n_replicas, t_corr, t_phase, T_end, seed, x0=None, *, thres
                 rer=rer[: len(rer_cprime)], cycles=cycles, events_decorr=res.events_decorr,
                 events_dephase=res.events_dephase, events_parallel_useful=res.events_parallel_useful,
                 n_cycles=res.cycles, escapes=res.escapes, x_final=(res.x_final[0], res.x_final[1]),
-                x0=(res.x0[0], res.x0[1]))
+                x0=(res.x0[0], res.x0[1]), **(dict(count_pre=cpre, count_post=cpost) if counts else {}))
 
 
 def initial_state(spec, seed, x0, x0_uniform_hi) -> tuple:

@@ -146,7 +146,15 @@ def bd_mfpt_down(birth, death, x_from, x_to, xmax):
 
 
 def bd_decorrelated_exit_rate(birth, death, split, t_corr):
-    """Escapes per unit time that follow a completed decorrelation step.
+    """Escapes per unit time that follow a completed decorrelation step (the
+    sum of the two regions' terms of bd_decorrelated_exit_rates)."""
+    lo, hi = bd_decorrelated_exit_rates(birth, death, split, t_corr)
+    return lo + hi
+
+
+def bd_decorrelated_exit_rates(birth, death, split, t_corr):
+    """Escapes per unit time that follow a completed decorrelation step, out of
+    W- and out of W+ separately: (J S-(t), J S+(t)) in the notation below.
 
     Birth-death chain on {0..n-1}, regions W- = {x < split} and W+ = {x >=
     split}.  In the TIME form of Algorithm 1's decorrelation the in-W time is
@@ -178,7 +186,7 @@ def bd_decorrelated_exit_rate(birth, death, split, t_corr):
     d[0] = 0.0
     pi = bd_stationary(b, d)
     J = pi[split - 1] * b[split - 1]
-    total = 0.0
+    terms = []
     for lo, hi, entry in ((0, split - 1, split - 1), (split, n - 1, split)):
         xs = np.arange(lo, hi + 1)
         a0 = b[xs] + d[xs]  # every jump leaves the state (exits are killed)
@@ -192,8 +200,8 @@ def bd_decorrelated_exit_rate(birth, death, split, t_corr):
         lam, V = eigh_tridiagonal(-a0, np.sqrt(b[xs][:-1] * d[xs][1:]))
         e = entry - lo
         coef = V.T @ (np.sqrt(w) * p_stay)
-        total += float(np.sum(V[e] * np.exp(lam * float(t_corr)) * coef) / np.sqrt(w[e]))
-    return J * total
+        terms.append(J * float(np.sum(V[e] * np.exp(lam * float(t_corr)) * coef) / np.sqrt(w[e])))
+    return terms[0], terms[1]
 
 
 # ---------------------------------------------------------------------------

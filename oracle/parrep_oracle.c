@@ -421,6 +421,8 @@ typedef struct {
     const double* rer_cp;
     int n_rer;
     double* rer;
+    int64_t* cnt_pre;  /* optional: holding times added to each bin (tests bound rounding per bin) */
+    int64_t* cnt_post;
 } acc_t;
 
 static void add_fim_rer(acc_t* A, const int32_t* x, double w)
@@ -472,6 +474,8 @@ static int contribute(acc_t* A, const int32_t* x, double tau)
     int64_t b = bin_of(A->N, x);
     if (A->hist_pre) A->hist_pre[b] += pre;
     if (A->hist_post) A->hist_post[b] += post;
+    if (A->cnt_pre && pre > 0.0) A->cnt_pre[b] += 1;
+    if (A->cnt_post && post > 0.0) A->cnt_post[b] += 1;
     if (post > 0.0) add_fim_rer(A, x, post);
     if (A->ended)
         A->T_s = A->C->T_end;
@@ -667,15 +671,18 @@ void or_initial_state(const or_network* N, const or_config* C, int32_t x[2])
     }
 }
 
-int or_parrep_run(const or_network* N, const or_config* C, double* hist_pre, double* hist_post,
-                  double* fim, const double* rer_cprime, int32_t n_rer, double* rer_out,
-                  or_cycle* log, int64_t log_cap, int64_t* log_n, or_result* res)
+/* or_parrep_run with, optionally, the number of holding times added to each
+ * bin before and after T_burn (cnt_pre, cnt_post may be NULL). */
+int or_parrep_run_counted(const or_network* N, const or_config* C, double* hist_pre, double* hist_post,
+                          double* fim, const double* rer_cprime, int32_t n_rer, double* rer_out,
+                          or_cycle* log, int64_t log_cap, int64_t* log_n, or_result* res,
+                          int64_t* cnt_pre, int64_t* cnt_post)
 {
     memset(res, 0, sizeof(*res));
     int rc = check_inputs(N, C);
     if (rc) { res->status = rc; return rc; }
     int64_t R = C->n_replicas;
-    acc_t A = {N, C, 0.0, 0, hist_pre, hist_post, fim, rer_cprime, n_rer, rer_out};
+    acc_t A = {N, C, 0.0, 0, hist_pre, hist_post, fim, rer_cprime, n_rer, rer_out, cnt_pre, cnt_post};
     int32_t xt[2];
     or_initial_state(N, C, xt);
     res->x0[0] = xt[0];
@@ -762,6 +769,14 @@ finish:
     res->x_final[1] = xt[1];
     res->status = status;
     return status;
+}
+
+int or_parrep_run(const or_network* N, const or_config* C, double* hist_pre, double* hist_post,
+                  double* fim, const double* rer_cprime, int32_t n_rer, double* rer_out,
+                  or_cycle* log, int64_t log_cap, int64_t* log_n, or_result* res)
+{
+    return or_parrep_run_counted(N, C, hist_pre, hist_post, fim, rer_cprime, n_rer, rer_out, log, log_cap, log_n,
+                                 res, NULL, NULL);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -98,14 +98,14 @@ class parrep_cycle(C.Structure):
 
 class parrep_uq_result(C.Structure):
     _fields_ = [("n_samples", C.c_int32), ("n_params", C.c_int32), ("window", C.c_double), ("iaf", C.c_double),
-                ("mean_f", C.c_double), ("fim", C.c_double * 36), ("fim_half_width", C.c_double * 36),
-                ("bound", C.c_double * 6)]
+                ("mean_f", C.c_double), ("fim", C.c_double * 64), ("fim_half_width", C.c_double * 64),
+                ("bound", C.c_double * 8)]
 
 
 EXPORTS = ["parrep_default_options", "parrep_create", "parrep_set_options", "parrep_run", "parrep_n_bins",
            "parrep_histogram", "parrep_histogram_raw", "parrep_fim", "parrep_rer", "parrep_stats_get",
            "parrep_cycle_log", "parrep_dephase", "parrep_destroy", "parrep_last_error", "parrep_ssa",
-           "parrep_philox", "parrep_ssa_noalloc", "parrep_batch_default_options", "parrep_batch_create",
+           "parrep_philox", "parrep_ssa_noalloc", "parrep_ssa_trace", "parrep_batch_default_options", "parrep_batch_create",
            "parrep_batch_run", "parrep_batch_status", "parrep_batch_info_get", "parrep_batch_destroy",
            "parrep_batch_last_error", "parrep_server_default_options", "parrep_server_create",
            "parrep_server_submit", "parrep_server_poll", "parrep_server_wait", "parrep_server_result",
@@ -146,6 +146,8 @@ def load():
     L.parrep_ssa.argtypes = [P(parrep_network), C.c_int32, C.c_int64, C.c_double, C.c_uint64, vp, C.c_int64,
                              P(C.c_int64), P(C.c_float), vp]
     L.parrep_philox.argtypes = [vp, vp, C.c_int64, vp]
+    L.parrep_ssa_trace.argtypes = [P(parrep_network), C.c_int32, C.c_int64, C.c_double, C.c_uint64, C.c_int64, vp,
+                                   vp, vp, vp, vp]
     L.parrep_ssa_noalloc.argtypes = [P(parrep_network), C.c_int32, C.c_int64, C.c_double, C.c_uint64, vp,
                                      C.c_int64, P(C.c_int64), vp]
     L.parrep_batch_default_options.argtypes = [P(parrep_batch_options)]

@@ -313,7 +313,7 @@ class ParRepServer:
             r.c_prime = cp.ctypes.data
         rid = C.c_int64(0)
         self._check(self._lib.parrep_server_submit(self.s, C.byref(r), C.byref(rid)))
-        nl = 4 if spec["kind"] == "schlogl" else 6
+        nl = {"schlogl": 4, "toggle": 6, "genetic": 8}[spec["kind"]]
         hm = [spec["hist_max"]] if np.isscalar(spec["hist_max"]) else spec["hist_max"]
         self._meta[rid.value] = (int(np.prod([h + 1 for h in hm])), nl, 0 if cp is None else cp.shape[0])
         return rid.value
@@ -370,6 +370,25 @@ def parrep_ssa(spec: dict, n_traj: int, x0, T_end: float, seed: int, *, precisio
     _check(lib.parrep_ssa(C.byref(net), L.PARREP_FP32 if precision == "f32" else L.PARREP_FP64, int(n_traj),
                           float(T_end), int(seed), _buf(hist), nb, C.byref(ev), C.byref(ms), st))
     return hist, int(ev.value), float(ms.value)
+
+
+def parrep_ssa_trace(spec: dict, n_traj: int, x0, T_end: float, seed: int, max_steps: int, *,
+                     precision: str = "f64"):
+    """Plain SSA with a record of every jump (the same counters as parrep_ssa).
+    Returns (reactions (n_traj, max_steps), states (n_traj, max_steps, 2),
+    holding times (n_traj, max_steps), jumps made (n_traj,), final states
+    (n_traj, 2)); entries past a trajectory's jump count are unused."""
+    lib = L.load()
+    net = make_network(spec, x0)
+    J = np.full((n_traj, max_steps), -1, dtype=np.int32)
+    xs = np.zeros((n_traj, max_steps, 2), dtype=np.int32)
+    tau = np.zeros((n_traj, max_steps))
+    nj = np.zeros(n_traj, dtype=np.int64)
+    xf = np.zeros((n_traj, 2), dtype=np.int32)
+    _check(lib.parrep_ssa_trace(C.byref(net), L.PARREP_FP32 if precision == "f32" else L.PARREP_FP64, int(n_traj),
+                                float(T_end), int(seed), int(max_steps), _buf(J), _buf(xs), _buf(tau), _buf(nj),
+                                _buf(xf)))
+    return J, xs, tau, nj, xf
 
 
 def parrep_philox(ctr, key):

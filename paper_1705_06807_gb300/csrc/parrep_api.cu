@@ -250,9 +250,9 @@ extern "C" int parrep_create(const parrep_network* net, int64_t n_replicas, cons
     TRY(cudaMalloc((void**)&h->d_xstate, sizeof(int2) * 3 * (size_t)n_replicas));
     TRY(cudaMalloc((void**)&h->d_out, sizeof(double) * h->nbins));
     TRY(cudaMalloc((void**)&h->d_out2, sizeof(double) * h->nbins));
-    TRY(cudaMalloc((void**)&h->d_fim, sizeof(double) * 36));
+    TRY(cudaMalloc((void**)&h->d_fim, sizeof(double) * 64));
     TRY(cudaMalloc((void**)&h->d_rer, sizeof(double) * 8));
-    TRY(cudaMalloc((void**)&h->d_cprime, sizeof(double) * 8 * 6));
+    TRY(cudaMalloc((void**)&h->d_cprime, sizeof(double) * 8 * 8));
     TRY(cudaEventCreate(&h->ev0));
     TRY(cudaEventCreate(&h->ev1));
     TRY(cudaMemset(h->d_hist_pre, 0, sizeof(unsigned long long) * h->nbins));
@@ -574,13 +574,13 @@ extern "C" int parrep_histogram_raw(parrep_t h, double* pre, double* post, int64
 
 static int contract(parrep_t h, const double* cprime, int n, double* fim_host, double* rer_host) {
     cudaStream_t st = stream_of(h);
-    CK(h, cudaMemsetAsync(h->d_fim, 0, sizeof(double) * 36, st));
+    CK(h, cudaMemsetAsync(h->d_fim, 0, sizeof(double) * 64, st));
     CK(h, cudaMemsetAsync(h->d_rer, 0, sizeof(double) * 8, st));
     if (n > 0)
         CK(h, cudaMemcpyAsync(h->d_cprime, cprime, sizeof(double) * n * h->L, cudaMemcpyHostToDevice, st));
     CK(h, launch_fim_rer(h->nd, h->d_c, h->d_s, h->d_hist_post, h->d_gradU_n, h->d_gradV_n, h->d_cprime, n,
                          h->d_fim, h->d_rer, st));
-    if (fim_host) CK(h, cudaMemcpyAsync(fim_host, h->d_fim, sizeof(double) * 36, cudaMemcpyDeviceToHost, st));
+    if (fim_host) CK(h, cudaMemcpyAsync(fim_host, h->d_fim, sizeof(double) * 64, cudaMemcpyDeviceToHost, st));
     if (rer_host) CK(h, cudaMemcpyAsync(rer_host, h->d_rer, sizeof(double) * 8, cudaMemcpyDeviceToHost, st));
     CK(h, cudaStreamSynchronize(st));
     return PARREP_OK;
@@ -590,13 +590,12 @@ extern "C" int parrep_fim(parrep_t h, double* out, int32_t len) {
     if (!h || !out) return PARREP_EINVAL;
     if (!h->has_run) return fail(h, PARREP_ESTATE, "no completed run");
     if (len != h->L * h->L) return fail(h, PARREP_EINVAL, "len != l*l");
-    if (h->net.kind == PARREP_GENETIC) return fail(h, PARREP_EINVAL, "no FIM for the genetic switch yet");
     const double span = h->stats.T_s - h->T_burn;
     if (!(span > 0.0)) return fail(h, PARREP_ESTATE, "empty window [T_burn, T_end]");
-    double buf[36];
+    double buf[64];
     int rc = contract(h, nullptr, 0, buf, nullptr);
     if (rc) return rc;
-    double res[36];
+    double res[64];
     for (int i = 0; i < h->L * h->L; ++i) res[i] = buf[i] / span;
     CK(h, cudaMemcpy(out, res, sizeof(double) * h->L * h->L, cudaMemcpyDefault));
     return PARREP_OK;
@@ -605,7 +604,6 @@ extern "C" int parrep_fim(parrep_t h, double* out, int32_t len) {
 extern "C" int parrep_rer(parrep_t h, const double* c_prime, int32_t n, double* out) {
     if (!h || !out || (n > 0 && !c_prime) || n < 0) return PARREP_EINVAL;
     if (!h->has_run) return fail(h, PARREP_ESTATE, "no completed run");
-    if (h->net.kind == PARREP_GENETIC) return fail(h, PARREP_EINVAL, "no RER for the genetic switch yet");
     const double span = h->stats.T_s - h->T_burn;
     if (!(span > 0.0)) return fail(h, PARREP_ESTATE, "empty window [T_burn, T_end]");
     std::vector<double> res(n);
@@ -613,7 +611,10 @@ extern "C" int parrep_rer(parrep_t h, const double* c_prime, int32_t n, double* 
         const int m = n - k0 < 8 ? n - k0 : 8;
         for (int k = 0; k < m; ++k)
             for (int i = 0; i < h->L; ++i)
-                if (!(c_prime[(k0 + k) * h->L + i] > 0.0) && i != 1 && i != 4)
+                // every perturbed constant > 0 (the toggle's Hill exponents excepted),
+                // so that lambda' > 0 wherever lambda > 0
+                if (!(c_prime[(k0 + k) * h->L + i] > 0.0) &&
+                    !(h->net.kind == PARREP_TOGGLE && (i == 1 || i == 4)))
                     return fail(h, PARREP_EINVAL, "perturbed rate constants must be > 0");
         double buf[8];
         int rc = contract(h, c_prime + (size_t)k0 * h->L, m, nullptr, buf);
@@ -803,6 +804,84 @@ extern "C" int parrep_ssa(const parrep_network* net, int32_t precision, int64_t 
     if (e != cudaSuccess) return fail(nullptr, PARREP_ECUDA, std::string("parrep_ssa: ") + cudaGetErrorString(e));
     if (events_out) *events_out = (int64_t)evh;
     if (status) return fail(nullptr, status, "parrep_ssa: a state left [0, hist_max]");
+    return PARREP_OK;
+}
+
+extern "C" int parrep_ssa_trace(const parrep_network* net, int32_t precision, int64_t n_traj, double T_end,
+                                uint64_t seed, int64_t max_steps, int32_t* reactions, int32_t* states,
+                                double* holding, int64_t* n_jumps, int32_t* x_final) {
+    parrep_regions reg;
+    memset(&reg, 0, sizeof(reg));
+    reg.n = 1;
+    std::string why;
+    if (!check_network(net, &reg, why)) return fail(nullptr, PARREP_EINVAL, "parrep_ssa_trace: " + why);
+    if (precision != PARREP_FP64 && precision != PARREP_FP32)
+        return fail(nullptr, PARREP_EINVAL, "parrep_ssa_trace: precision");
+    if (net->kind == PARREP_GENETIC && precision != PARREP_FP64)
+        return fail(nullptr, PARREP_EINVAL, "parrep_ssa_trace: the genetic switch has the binary64 form only");
+    if (n_traj < 1 || n_traj > (1ll << 24) || max_steps < 1 || n_traj * max_steps > (1ll << 28))
+        return fail(nullptr, PARREP_EINVAL, "parrep_ssa_trace: need 1 <= n_traj, 1 <= max_steps, n_traj*max_steps <= 2^28");
+    if (!(T_end >= 0.0) || !(T_end < kTEndLimit)) return fail(nullptr, PARREP_EINVAL, "parrep_ssa_trace: T_end");
+    if (!reactions || !states || !n_jumps || !x_final)
+        return fail(nullptr, PARREP_EINVAL, "parrep_ssa_trace: null output");
+    if (net->x0_uniform_hi != 0) return fail(nullptr, PARREP_EINVAL, "parrep_ssa_trace: x0_uniform_hi must be 0");
+    NetDev nd;
+    std::vector<double> pU, pV, gU, gV;
+    build_net(net, &reg, nd, pU, pV, gU, gV);
+    std::vector<float> pUf(pU.size()), pVf(pV.size());
+    for (size_t i = 0; i < pU.size(); ++i) pUf[i] = (float)pU[i];
+    for (size_t i = 0; i < pV.size(); ++i) pVf[i] = (float)pV[i];
+    const size_t n = (size_t)n_traj * (size_t)max_steps;
+    double *dpU = nullptr, *dpV = nullptr;
+    float *dpUf = nullptr, *dpVf = nullptr;
+    int *dJ = nullptr, *dst = nullptr;
+    int2 *dx = nullptr, *dxf = nullptr;
+    unsigned long long* dq = nullptr;
+    long long* dn = nullptr;
+    cudaError_t e = upload(&dpU, pU);
+    if (e == cudaSuccess) e = upload(&dpV, pV);
+    if (e == cudaSuccess) e = upload(&dpUf, pUf);
+    if (e == cudaSuccess) e = upload(&dpVf, pVf);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dJ, sizeof(int) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dx, sizeof(int2) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dq, sizeof(unsigned long long) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dn, sizeof(long long) * n_traj);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dxf, sizeof(int2) * n_traj);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dst, sizeof(int));
+    int status = 0;
+    std::vector<unsigned long long> hq;
+    if (e == cudaSuccess) {
+        nd.prodU_d = dpU;
+        nd.prodV_d = dpV;
+        nd.prodU_f = dpUf;
+        nd.prodV_f = dpVf;
+        e = cudaMemset(dst, 0, sizeof(int));
+        if (e == cudaSuccess)
+            e = launch_ssa_trace(nd, precision, n_traj, net->x0[0], net->n_species > 1 ? net->x0[1] : 0,
+                                 (unsigned long long)llrint(T_end * kQScale), seed, max_steps, dJ, dx, dq, dn, dxf,
+                                 dst, nullptr);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e == cudaSuccess) e = cudaMemcpy(reactions, dJ, sizeof(int) * n, cudaMemcpyDefault);
+        if (e == cudaSuccess) e = cudaMemcpy(states, dx, sizeof(int2) * n, cudaMemcpyDefault);
+        if (e == cudaSuccess) e = cudaMemcpy(n_jumps, dn, sizeof(long long) * n_traj, cudaMemcpyDefault);
+        if (e == cudaSuccess) e = cudaMemcpy(x_final, dxf, sizeof(int2) * n_traj, cudaMemcpyDefault);
+        if (e == cudaSuccess && holding) {
+            hq.resize(n);
+            e = cudaMemcpy(hq.data(), dq, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost);
+        }
+        if (e == cudaSuccess) e = cudaMemcpy(&status, dst, sizeof(int), cudaMemcpyDeviceToHost);
+    }
+    void* ptrs[] = {dpU, dpV, dpUf, dpVf, dJ, dx, dq, dn, dxf, dst};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    if (e != cudaSuccess) return fail(nullptr, PARREP_ECUDA, std::string("parrep_ssa_trace: ") + cudaGetErrorString(e));
+    if (holding) {
+        std::vector<double> ht(n);
+        for (size_t i = 0; i < n; ++i) ht[i] = (double)hq[i] * kQInv;
+        if (cudaMemcpy(holding, ht.data(), sizeof(double) * n, cudaMemcpyDefault) != cudaSuccess)
+            return fail(nullptr, PARREP_ECUDA, "parrep_ssa_trace: copy of the holding times");
+    }
+    if (status) return fail(nullptr, status, "parrep_ssa_trace: a state left [0, hist_max]");
     return PARREP_OK;
 }
 

@@ -106,6 +106,13 @@ static double start_a0(parrep_t h) {
         return n.c[0] * n.s[0] * a + n.c[1] * n.s[1] * c + n.c[2] * n.s[2] + n.c[3] * n.s[3] * x;
     }
     const double U = x, V = n.x0_uniform_hi > 0 ? 0.5 * n.x0_uniform_hi : (double)n.x0[1];
+    if (n.kind == PARREP_GENETIC) {
+        // six channels at (xi, m, p) = (U mod 2, U / 2, V)
+        const double xi = (double)((int)U & 1), m = (double)((int)U >> 1), p = V;
+        const double hh = p * p / (p * p + n.c[7] * n.c[7]);
+        const double F = n.c[3] + (n.c[4] - n.c[3]) * hh, G = n.c[6] - (n.c[6] - n.c[5]) * hh;
+        return n.c[0] * xi + n.c[2] * m + n.c[2] * n.c[1] * m + p + F * (1.0 - xi) + G * xi;
+    }
     return n.c[0] / (1.0 + pow(V, n.c[1])) + n.c[3] / (1.0 + pow(U, n.c[4])) + n.c[2] * U + n.c[5] * V;
 }
 
@@ -477,8 +484,8 @@ extern "C" int parrep_batch_create(const parrep_t* instances, int32_t n, const p
     std::vector<parrep_t> v(instances, instances + n);
     for (int i = 0; i < n; ++i) {
         if (!v[i]) return bfail(nullptr, PARREP_EINVAL, "null instance handle");
-        if (v[i]->net.kind == PARREP_GENETIC)
-            return bfail(nullptr, PARREP_EINVAL, "batches do not take the genetic switch yet");
+        if (v[i]->net.kind == PARREP_GENETIC && v[i]->opt.precision != PARREP_FP64)
+            return bfail(nullptr, PARREP_EINVAL, "the genetic switch has the binary64 form only");
         if (v[i]->opt.precision != v[0]->opt.precision)
             return bfail(nullptr, PARREP_EINVAL, "instances of one batch need the same precision");
     }

@@ -146,14 +146,14 @@ struct RunParams {
 // system scope).
 struct ServeSlot {
     RunParams P;                   // device pointers into the server's arena; P.inst = slot index
-    double c[6], s[4];             // rate constants and Schloegl factors (FIM / RER)
-    double cprime[8 * 6];          // perturbed parameter vectors of the RER
+    double c[8], s[4];             // rate constants and Schloegl factors (FIM / RER)
+    double cprime[8 * 8];          // perturbed parameter vectors of the RER
     double T_burn;                 // as given (the FIM / RER window starts here)
     int n_cprime, L;
     const double* gradU_n;         // toggle: d log(production) / d Hill exponent tables (arena)
     const double* gradV_n;
     double* out_hist;              // [nbins] histogram normalised by T_s
-    double* out_fim;               // [36] FIM over [T_burn, T_s]
+    double* out_fim;               // [64] FIM over [T_burn, T_s]
     double* out_rer;               // [8] RER over [T_burn, T_s]
     RunCtl* out_ctl;               // the control block at the end (statistics)
 };
@@ -197,9 +197,9 @@ struct UqSample {
 // Device result of the UQ reduction (the fields of parrep_uq_result).
 struct UqOut {
     double iaf, mean_f;
-    double fim[36], half[36], bound[6];
+    double fim[64], half[64], bound[8];
 };
-// Y[k] (window integral of f), Z[k][36] (FIM time average) per sample, then
+// Y[k] (window integral of f), Z[k][64] (FIM time average) per sample, then
 // the moments, the FIM mean and half widths, and the bounds.
 cudaError_t launch_uq(const UqSample* samples, int n, int L, const double* f, double window, const double* dirs,
                       int n_dirs, double* Y, double* Z, UqOut* out, double* dir_bounds, cudaStream_t st);
@@ -209,6 +209,10 @@ cudaError_t launch_fim_rer(const NetDev& net, const double* c, const double* s, 
 cudaError_t launch_ssa(const NetDev& net, int prec, long long n_traj, int x0, int x1, unsigned long long q_Tend,
                        unsigned long long seed, unsigned long long* hist, unsigned long long* events,
                        int* status, cudaStream_t st);
+cudaError_t launch_ssa_trace(const NetDev& net, int prec, long long n_traj, int x0, int x1,
+                             unsigned long long q_Tend, unsigned long long seed, long long max_steps, int* J,
+                             int2* xs, unsigned long long* q, long long* n_out, int2* xf, int* status,
+                             cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, long long n, uint32_t* out, cudaStream_t st);
 
 }  // namespace parrep

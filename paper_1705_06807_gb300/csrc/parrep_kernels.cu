@@ -2089,10 +2089,14 @@ __device__ __forceinline__ bool run_instance(const RunParams& P, int lb, unsigne
             int grow = 0;
             for (;;) {
                 // chunk length: doubling from one sub-chunk at the start of a
-                // cycle up to P.S, and no longer than the steps the last chunk's
-                // time per lockstep step says are left to the next threshold.
-                // Every block computes it from the same values; results do
-                // not depend on where chunks end.
+                // cycle up to P.S.  When the next threshold (T_burn, T_end) is
+                // within reach, by the last chunk's time per lockstep step, the
+                // chunk stops short of it (L - 0.1 L - unit/2 steps of the L
+                // estimated to be left, rounded down to whole sub-chunks): it is
+                // committed without a replay, and only the short chunk that
+                // crosses the threshold (at most 1.25 L + 1 steps) is replayed.
+                // Every block computes it from the same values; results do not
+                // depend on where chunks end.
                 int Sc = P.S;
                 {
                     const int unit = F32 ? P.B : 32;
@@ -2100,9 +2104,12 @@ __device__ __forceinline__ bool run_instance(const RunParams& P, int lb, unsigne
                     const unsigned long long q_lim = burn_done ? P.q_Tend : P.q_Tburn;
                     if (est_ev > 0 && est_q > 0 && q_lim > Ts) {
                         const double step_q = (double)est_q * (double)P.R / (double)est_ev;
-                        const double need = ceil((double)(q_lim - Ts) / step_q * 1.25) + 1.0;
+                        const double left = (double)(q_lim - Ts) / step_q;
+                        const double need = ceil(left * 1.25) + 1.0;
                         if (need < (double)Sc) {
-                            int nd = ((int)need + unit - 1) / unit * unit;
+                            const double lead = left - (0.1 * left + 0.5 * unit);
+                            int nd = lead >= (double)unit ? (int)lead / unit * unit
+                                                          : ((int)need + unit - 1) / unit * unit;
                             Sc = nd < unit ? unit : nd;
                         }
                     }
@@ -2548,12 +2555,12 @@ static __device__ void fim_rer_accumulate(const NetDev& N, const double* __restr
 // histogram normalised by T_s, the FIM and RER contracted over the post-burn
 // histogram and divided by T_s - T_burn, the control block; then done.
 static __device__ void serve_epilogue(const RunParams& P, const ServeSlot* slot, int* done) {
-    __shared__ double s_c[6], s_s[4], s_cp[48];
+    __shared__ double s_c[8], s_s[4], s_cp[64];
     __shared__ int s_n, s_L;
     __shared__ double s_Tb;
     RunCtl* ctl = P.ctl;
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 6; ++i) s_c[i] = slot->c[i];
+        for (int i = 0; i < 8; ++i) s_c[i] = slot->c[i];
         for (int i = 0; i < 4; ++i) s_s[i] = slot->s[i];
         s_n = slot->n_cprime < 8 ? slot->n_cprime : 8;
         s_L = slot->L;
@@ -2573,7 +2580,7 @@ static __device__ void serve_epilogue(const RunParams& P, const ServeSlot* slot,
         const double a = (double)__ldcg(P.hist_pre + b) * kQInv, c = (double)__ldcg(P.hist_post + b) * kQInv;
         out_hist[b] = (a + c) * scale;
     }
-    for (int i = threadIdx.x; i < 36; i += blockDim.x) out_fim[i] = 0.0;
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) out_fim[i] = 0.0;
     for (int i = threadIdx.x; i < 8; i += blockDim.x) out_rer[i] = 0.0;
     __syncthreads();
     if (ldv(&ctl->status) == 0)
@@ -2698,10 +2705,106 @@ __global__ void hist_normalise_kernel(const unsigned long long* pre, const unsig
 // Per bin: w = time in the bin; FIM += w sum_j lambda_j g_j g_j^T with
 // g_j = grad_c log lambda_j; RER_k += w sum_j [lambda_j log(lambda_j/lambda'_j)
 // - lambda_j + lambda'_j].
+// The genetic switch (Sec. V.B): six channels, the eight parameters c = (a, b,
+// gamma, k0min, k0max, k1min, k1max, D) taken independently.  With h =
+// p^2/(p^2 + D^2), F = k0min + (k0max - k0min) h, G = k1max - (k1max - k1min) h:
+//   log-derivatives of lambda = (a xi, gamma m, gamma b m, p, F (1 - xi), G xi):
+//   d/da log l0 = 1/a; d/dgamma log l1 = 1/gamma; d/db log l2 = 1/b,
+//   d/dgamma log l2 = 1/gamma; l3 has no parameter;
+//   d/dk0min log l4 = (1 - h)/F, d/dk0max = h/F, d/dD = (k0max - k0min) h'/F;
+//   d/dk1min log l5 = h/G, d/dk1max = (1 - h)/G, d/dD = -(k1max - k1min) h'/G,
+//   h' = dh/dD = -2 p^2 D / (p^2 + D^2)^2.
+// Per bin: FIM += w sum_j lambda_j g_j g_j^T; RER_k += w sum_j [lambda_j
+// log(lambda_j/lambda'_j) - lambda_j + lambda'_j] with lambda' at c'_k.
+static __device__ __forceinline__ void genetic_grad(const double* __restrict__ c, double p, double g[6][8]) {
+    const double p2 = p * p, D2 = c[7] * c[7];
+    const double h = p2 / (p2 + D2);
+    const double dh = -2.0 * p2 * c[7] / ((p2 + D2) * (p2 + D2));
+    const double F = c[3] + (c[4] - c[3]) * h, G = c[6] - (c[6] - c[5]) * h;
+#pragma unroll
+    for (int j = 0; j < 6; ++j)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) g[j][k] = 0.0;
+    g[0][0] = 1.0 / c[0];
+    g[1][2] = 1.0 / c[2];
+    g[2][1] = 1.0 / c[1];
+    g[2][2] = 1.0 / c[2];
+    if (F > 0.0) {
+        g[4][3] = (1.0 - h) / F;
+        g[4][4] = h / F;
+        g[4][7] = (c[4] - c[3]) * dh / F;
+    }
+    if (G > 0.0) {
+        g[5][5] = h / G;
+        g[5][6] = (1.0 - h) / G;
+        g[5][7] = -(c[6] - c[5]) * dh / G;
+    }
+}
+
+static __device__ void fim_rer_genetic(const NetDev& N, const double* __restrict__ c,
+                                       const unsigned long long* __restrict__ hist, const double* __restrict__ cprime,
+                                       int n_cprime, double* fim_out, double* rer_out, int start, int stride) {
+    constexpr int L = 8;
+    double acc[L * L];
+#pragma unroll
+    for (int i = 0; i < L * L; ++i) acc[i] = 0.0;
+    double racc[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) racc[i] = 0.0;
+    for (int b = start; b < N.nbins; b += stride) {
+        const unsigned long long hq = __ldcg(hist + b);
+        if (!hq) continue;
+        const double w = (double)hq * kQInv;
+        const int x0 = b / N.ystride, x1 = b % N.ystride;
+        double lam[6];
+        props6_d(N, x0, x1, lam);
+        const double xi = (double)(x0 & 1), m = (double)(x0 >> 1), p = (double)x1;
+        const double p2 = p * p;
+        double g[6][L];
+        genetic_grad(c, p, g);
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            if (lam[j] == 0.0) continue;
+#pragma unroll
+            for (int a = 0; a < L; ++a)
+#pragma unroll
+                for (int bb = 0; bb < L; ++bb) acc[a * L + bb] += w * lam[j] * g[j][a] * g[j][bb];
+        }
+        for (int k = 0; k < n_cprime && k < 8; ++k) {
+            const double* cp = cprime + k * L;
+            const double D2p = cp[7] * cp[7];
+            const double hp = p2 / (p2 + D2p);
+            const double Fp = cp[3] + (cp[4] - cp[3]) * hp, Gp = cp[6] - (cp[6] - cp[5]) * hp;
+            const double lp[6] = {cp[0] * xi, cp[2] * m, (cp[2] * cp[1]) * m, p, Fp * (1.0 - xi), Gp * xi};
+            double hsum = 0.0;
+            for (int j = 0; j < 6; ++j) {
+                double t = lp[j] - lam[j];
+                if (lam[j] > 0.0) t += lam[j] * log(lam[j] / lp[j]);
+                hsum += t;
+            }
+            racc[k] += w * hsum;
+        }
+    }
+    for (int i = 0; i < L * L; ++i) {
+        double v = acc[i];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(fim_out + i, v);
+    }
+    for (int k = 0; k < n_cprime && k < 8; ++k) {
+        double v = racc[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(rer_out + k, v);
+    }
+}
+
 static __device__ void fim_rer_accumulate(const NetDev& N, const double* __restrict__ c, const double* __restrict__ s,
                                    const unsigned long long* __restrict__ hist, const double* __restrict__ gradU_n,
                                    const double* __restrict__ gradV_n, const double* __restrict__ cprime,
                                    int n_cprime, double* fim_out, double* rer_out, int start, int stride) {
+    if (N.kind == PARREP_GENETIC) {
+        fim_rer_genetic(N, c, hist, cprime, n_cprime, fim_out, rer_out, start, stride);
+        return;
+    }
     const int L = N.kind == PARREP_SCHLOGL ? 4 : 6;
     double acc[36];
 #pragma unroll
@@ -2817,38 +2920,45 @@ __global__ void __launch_bounds__(kUqThreads) uq_sample_kernel(const UqSample* _
     const UqSample& S = smp[blockIdx.x];
     const NetDev& N = S.net;
     double y = 0.0;
-    double acc[36];
+    double acc[64];
 #pragma unroll
-    for (int i = 0; i < 36; ++i) acc[i] = 0.0;
+    for (int i = 0; i < 64; ++i) acc[i] = 0.0;
     double ic[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) ic[i] = i < L ? 1.0 / S.c[i] : 0.0;
+    const bool gen = N.kind == PARREP_GENETIC;
+    const int nch = gen ? 6 : 4;
     for (int b = threadIdx.x; b < N.nbins; b += blockDim.x) {
         const unsigned long long hq = __ldcg(S.hist + b);
         if (!hq) continue;
         const double w = (double)hq * kQInv;
         y += f[b] * w;
         const int x0 = b / N.ystride, x1 = b % N.ystride;
-        double lam[4];
-        props_d(N, x0, x1, lam[0], lam[1], lam[2], lam[3]);
-        double g[4][6];
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int k = 0; k < 6; ++k) g[j][k] = 0.0;
-        if (N.kind == PARREP_SCHLOGL) {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) g[j][j] = ic[j];
+        double lam[6];
+        double g[6][8];
+        if (gen) {
+            props6_d(N, x0, x1, lam);
+            genetic_grad(S.c, (double)x1, g);
         } else {
-            g[0][0] = ic[0];
-            g[0][1] = S.gradU_n[x1];
-            g[1][3] = ic[3];
-            g[1][4] = S.gradV_n[x0];
-            g[2][2] = ic[2];
-            g[3][5] = ic[5];
-        }
+            props_d(N, x0, x1, lam[0], lam[1], lam[2], lam[3]);
+            lam[4] = lam[5] = 0.0;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < 6; ++j)
+#pragma unroll
+                for (int k = 0; k < 8; ++k) g[j][k] = 0.0;
+            if (N.kind == PARREP_SCHLOGL) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) g[j][j] = ic[j];
+            } else {
+                g[0][0] = ic[0];
+                g[0][1] = S.gradU_n[x1];
+                g[1][3] = ic[3];
+                g[1][4] = S.gradV_n[x0];
+                g[2][2] = ic[2];
+                g[3][5] = ic[5];
+            }
+        }
+        for (int j = 0; j < nch; ++j) {
             if (lam[j] == 0.0) continue;
             for (int a = 0; a < L; ++a)
                 for (int bb = 0; bb < L; ++bb) acc[a * L + bb] += w * lam[j] * g[j][a] * g[j][bb];
@@ -2858,7 +2968,7 @@ __global__ void __launch_bounds__(kUqThreads) uq_sample_kernel(const UqSample* _
     if (threadIdx.x == 0) Y[blockIdx.x] = yt;
     for (int i = 0; i < L * L; ++i) {
         const double t = block_sum_fixed(acc[i], red);
-        if (threadIdx.x == 0) Z[(size_t)blockIdx.x * 36 + i] = t / window;
+        if (threadIdx.x == 0) Z[(size_t)blockIdx.x * 64 + i] = t / window;
     }
 }
 #endif
@@ -2871,7 +2981,7 @@ __global__ void uq_reduce_kernel(int n, int L, const double* __restrict__ Y, con
                                  double window, const double* __restrict__ dirs, int n_dirs, UqOut* out,
                                  double* dir_bounds) {
     __shared__ double sh_tau;
-    __shared__ double sh_fim[36];
+    __shared__ double sh_fim[64];
     if (threadIdx.x < 32) {
         double s = 0.0;
         for (int k = threadIdx.x; k < n; k += 32) s += Y[k];
@@ -2892,14 +3002,14 @@ __global__ void uq_reduce_kernel(int n, int L, const double* __restrict__ Y, con
             sh_tau = tau;
         }
     }
-    for (int t = threadIdx.x; t < 36; t += blockDim.x) {
+    for (int t = threadIdx.x; t < 64; t += blockDim.x) {
         double m = 0.0, hw = 0.0;
         if (t < L * L) {
-            for (int k = 0; k < n; ++k) m += Z[(size_t)k * 36 + t];
+            for (int k = 0; k < n; ++k) m += Z[(size_t)k * 64 + t];
             m /= (double)n;
             double v = 0.0;
             for (int k = 0; k < n; ++k) {
-                const double d = Z[(size_t)k * 36 + t] - m;
+                const double d = Z[(size_t)k * 64 + t] - m;
                 v += d * d;
             }
             hw = 1.96 * sqrt(v / (double)(n - 1)) / sqrt((double)n);
@@ -2910,7 +3020,7 @@ __global__ void uq_reduce_kernel(int n, int L, const double* __restrict__ Y, con
     }
     __syncthreads();
     const double rt = sqrt(sh_tau);
-    for (int j = threadIdx.x; j < 6; j += blockDim.x) out->bound[j] = j < L ? rt * sqrt(fmax(sh_fim[j * L + j], 0.0)) : 0.0;
+    for (int j = threadIdx.x; j < 8; j += blockDim.x) out->bound[j] = j < L ? rt * sqrt(fmax(sh_fim[j * L + j], 0.0)) : 0.0;
     for (int d = threadIdx.x; d < n_dirs; d += blockDim.x) {
         const double* v = dirs + (size_t)d * L;
         double q = 0.0;
@@ -2962,6 +3072,42 @@ __global__ void ssa_kernel(NetDev N, long long n_traj, int x00, int x01, unsigne
     }
     ev = warp_sum(ev);
     if ((threadIdx.x & 31) == 0 && ev) atomicAdd(events, ev);
+}
+
+// Plain SSA with a per-jump record, for trajectory parity tests: the same
+// counters and arithmetic as ssa_kernel; trajectory t stops at T_end or after
+// max_steps jumps and writes, per jump, the channel, the state after the jump
+// and the fixed-point holding time, then its jump count and final state.
+template <bool F32>
+__global__ void ssa_trace_kernel(NetDev N, long long n_traj, int x00, int x01, unsigned long long q_Tend,
+                                 unsigned long long seed, long long max_steps, int* J_out, int2* x_out,
+                                 unsigned long long* q_out, long long* n_out, int2* xf_out, int* status) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_traj) return;
+    const uint2 key = seed_key(seed);
+    int x0 = x00, x1 = x01;
+    unsigned long long T = 0, step = 0;
+    const size_t base = (size_t)t * (size_t)max_steps;
+    while (T < q_Tend && (long long)step < max_steps) {
+        const unsigned long long cs = F32 ? step >> 1 : step;
+        uint4 w = philox10(make_uint4((unsigned)t, (unsigned)cs, (unsigned)(cs >> 32), kTagSSA), key);
+        if (F32 && (step & 1)) w = make_uint4(w.z, w.w, 0u, 0u);
+        unsigned long long q = 0;
+        const int J = ssa_draw<F32, true>(N, x0, x1, w, q);
+        if (q >= q_Tend - T) break;  // the jump falls after T_end
+        T += q;
+        apply(N, J, x0, x1);
+        J_out[base + step] = J;
+        x_out[base + step] = make_int2(x0, x1);
+        q_out[base + step] = q;
+        ++step;
+        if (out_of_range(N, x0, x1)) {
+            atomicCAS(status, 0, PARREP_ERANGE);
+            break;
+        }
+    }
+    n_out[t] = (long long)step;
+    xf_out[t] = make_int2(x0, x1);
 }
 
 #if PARREP_PART == 0
@@ -3156,6 +3302,21 @@ cudaError_t launch_ssa(const NetDev& net, int prec, long long n_traj, int x0, in
     else
         ssa_kernel<false><<<(unsigned)blocks, threads, 0, st>>>(net, n_traj, x0, x1, q_Tend, seed, hist, events,
                                                                 status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ssa_trace(const NetDev& net, int prec, long long n_traj, int x0, int x1,
+                             unsigned long long q_Tend, unsigned long long seed, long long max_steps, int* J,
+                             int2* xs, unsigned long long* q, long long* n_out, int2* xf, int* status,
+                             cudaStream_t st) {
+    const int threads = 128;
+    const long long blocks = (n_traj + threads - 1) / threads;
+    if (prec == PARREP_FP32)
+        ssa_trace_kernel<true><<<(unsigned)blocks, threads, 0, st>>>(net, n_traj, x0, x1, q_Tend, seed, max_steps, J,
+                                                                     xs, q, n_out, xf, status);
+    else
+        ssa_trace_kernel<false><<<(unsigned)blocks, threads, 0, st>>>(net, n_traj, x0, x1, q_Tend, seed, max_steps,
+                                                                      J, xs, q, n_out, xf, status);
     return cudaGetLastError();
 }
 

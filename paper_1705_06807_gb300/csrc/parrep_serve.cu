@@ -160,7 +160,7 @@ static size_t request_bytes(const parrep_request& r, int64_t log_cap) {
     size_t b = 0;
     b += align256(sizeof(RunCtl)) * 2;
     b += align256(nb * 8) * 3;
-    b += align256(36 * 8) + align256(8 * 8);
+    b += align256(64 * 8) + align256(8 * 8);
     b += align256(sizeof(unsigned long long) * kMaxChunk);
     b += align256(sizeof(unsigned long long) * 2 * R);
     b += align256(sizeof(int2) * 3 * R);
@@ -168,6 +168,8 @@ static size_t request_bytes(const parrep_request& r, int64_t log_cap) {
     if (r.net.kind == PARREP_TOGGLE) {
         const size_t nu = (size_t)r.net.hist_max[1] + 1, nv = (size_t)r.net.hist_max[0] + 1;
         b += 2 * (align256(nu * 8) + align256(nv * 8)) + align256(nu * 4) + align256(nv * 4);
+    } else if (r.net.kind == PARREP_GENETIC) {
+        b += 2 * align256(((size_t)r.net.hist_max[1] + 1) * 8);  // F(p), G(p)
     }
     return b;
 }
@@ -205,7 +207,7 @@ static int admit(parrep_server_t s, Request& q, int slot) {
     h.d_hist_pre = (unsigned long long*)take(nb * 8);
     h.d_hist_post = (unsigned long long*)take(nb * 8);
     q.d_hist = (double*)take(nb * 8);
-    q.d_fim = (double*)take(36 * 8);
+    q.d_fim = (double*)take(64 * 8);
     q.d_rer = (double*)take(8 * 8);
     h.d_step_sum = (unsigned long long*)take(sizeof(unsigned long long) * kMaxChunk);
     h.d_tau_at = (unsigned long long*)take(sizeof(unsigned long long) * 2 * R);
@@ -238,6 +240,16 @@ static int admit(parrep_server_t s, Request& q, int slot) {
         h.nd.prodV_f = pVf;
         d_gU = gUd;
         d_gV = gVd;
+    } else if (r.net.kind == PARREP_GENETIC) {
+        // the switching rates F(p), G(p) as binary64 tables over p
+        const size_t np = pU.size();
+        double* Fd = (double*)take(np * 8);
+        double* Gd = (double*)take(np * 8);
+        e = cudaMemcpyAsync(Fd, pU.data(), np * 8, cudaMemcpyHostToDevice, s->cp);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(Gd, pV.data(), np * 8, cudaMemcpyHostToDevice, s->cp);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->cp);
+        h.nd.prodU_d = Fd;
+        h.nd.prodV_d = Gd;
     }
     // (the serve kernel's claiming block clears the control block and the
     // histograms: a memset here would be a kernel that waits for free SMs)
@@ -277,10 +289,10 @@ static int admit(parrep_server_t s, Request& q, int slot) {
     ServeSlot& sl = *s->h_slot;
     memset(&sl, 0, sizeof(sl));
     sl.P = p;
-    for (int i = 0; i < 6; ++i) sl.c[i] = r.net.c[i];
+    for (int i = 0; i < 8; ++i) sl.c[i] = r.net.c[i];
     for (int i = 0; i < 4; ++i) sl.s[i] = r.net.s[i];
     memset(sl.cprime, 0, sizeof(sl.cprime));
-    for (size_t i = 0; i < q.cprime.size() && i < 48; ++i) sl.cprime[i] = q.cprime[i];
+    for (size_t i = 0; i < q.cprime.size() && i < 64; ++i) sl.cprime[i] = q.cprime[i];
     sl.T_burn = r.T_burn;
     sl.n_cprime = r.n_cprime;
     sl.L = q.L;
@@ -467,7 +479,8 @@ extern "C" int parrep_server_submit(parrep_server_t s, const parrep_request* req
     if (!s || !req || !id) return PARREP_EINVAL;
     std::string why;
     if (!check_network(&req->net, &req->regions, why)) return sfail(s, PARREP_EINVAL, why);
-    if (req->net.kind == PARREP_GENETIC) return sfail(s, PARREP_EINVAL, "the server does not take the genetic switch yet");
+    if (req->net.kind == PARREP_GENETIC && s->opt.precision != PARREP_FP64)
+        return sfail(s, PARREP_EINVAL, "the genetic switch has the binary64 form only");
     if (req->n_replicas < 1 || req->n_replicas > (1ll << 30)) return sfail(s, PARREP_EINVAL, "n_replicas");
     if (!(req->t_corr >= 0.0) || !(req->t_phase >= 0.0) || !(req->t_corr < kTEndLimit * 1024) ||
         !(req->t_phase < 1e12))
@@ -487,7 +500,7 @@ extern "C" int parrep_server_submit(parrep_server_t s, const parrep_request* req
         return sfail(s, PARREP_EINVAL, "n_cprime must be 0..8 with c_prime");
     auto q = std::make_unique<Request>();
     q->r = *req;
-    q->L = req->net.kind == PARREP_SCHLOGL ? 4 : 6;
+    q->L = req->net.kind == PARREP_SCHLOGL ? 4 : (req->net.kind == PARREP_TOGGLE ? 6 : 8);
     q->nbins = (req->net.hist_max[0] + 1) * (req->net.hist_max[1] + 1);
     if (req->n_cprime > 0) q->cprime.assign(req->c_prime, req->c_prime + (size_t)req->n_cprime * q->L);
     q->r.c_prime = nullptr;

@@ -72,7 +72,6 @@ extern "C" int parrep_uq(const parrep_t* handles, int32_t n, const double* f, in
         smp[k].gradV_n = h->d_gradV_n;
     }
     if (len != h0->nbins) return fail(h0, PARREP_EINVAL, "len != n_bins");
-    if (h0->net.kind == PARREP_GENETIC) return fail(h0, PARREP_EINVAL, "no FIM for the genetic switch yet");
     const int L = h0->L;
     cudaStream_t st = (cudaStream_t)h0->opt.stream;
     // the handles' runs completed on their own streams: order after them
@@ -85,7 +84,7 @@ extern "C" int parrep_uq(const parrep_t* handles, int32_t n, const double* f, in
     UQ_CK(h0, s.alloc(&d_smp, n));
     UQ_CK(h0, s.alloc(&d_f, (size_t)len));
     UQ_CK(h0, s.alloc(&d_Y, n));
-    UQ_CK(h0, s.alloc(&d_Z, (size_t)n * 36));
+    UQ_CK(h0, s.alloc(&d_Z, (size_t)n * 64));
     UQ_CK(h0, s.alloc(&d_out, 1));
     if (n_dirs > 0) {
         UQ_CK(h0, s.alloc(&d_dirs, (size_t)n_dirs * L));

@@ -4,9 +4,13 @@ State x0 = 2m + xi, x1 = p, six channels (Table IV with the switching rates
 F, G).  Every integer result of a run -- event counts, cycles, escapes, the
 cycle log, the final state -- equals the oracle's for the same seed; the
 time sums agree to the fixed-point rounding (at most 2^-41 per holding time).
-Plain SSA likewise.  The pooled histogram of a small bistable switch matches
-its exact law.  The parts not built for this kind yet (FP32, FIM/RER,
-batches, serving, UQ) refuse it with EINVAL.
+Plain SSA likewise.  The eight-parameter FIM and RER (Appendix A form,
+parameters a, b, gamma, k0min, k0max, k1min, k1max, D taken independently)
+equal the oracle's per-event sums; batches and served requests give each
+instance its solo result; parrep_uq takes the kind.  The pooled histogram of
+a small bistable switch matches its exact law, and at the paper's constants
+the FIM diagonal matches the exact chain's (Table V).  Only the FP32 form
+refuses the kind.
 """
 import numpy as np
 import pytest
@@ -85,24 +89,129 @@ def test_genetic_parrep_matches_exact_law():
     assert 0.5 * np.abs(marg(tot / tot.sum()) - marg(ex)).sum() < 0.02
 
 
-def test_genetic_parts_not_built_refuse_it():
+def test_genetic_fp32_form_is_refused():
     spec = _spec(SMALL, 16, 250, 13)
     g = ParRep(spec, 16, 50, 50, x0=[0, 0], thresh="steps", precision="f32")
     with pytest.raises(ParRepError):
         g.run(10.0, 1)
     with pytest.raises(ParRepError):
         parrep_ssa(spec, 1, [0, 0], 1.0, 1, precision="f32")
-    g = ParRep(spec, 16, 50, 50, x0=[0, 0], thresh="steps", T_burn=2.0)
-    g.run(10.0, 1)
-    with pytest.raises(ParRepError):
-        g.fim()
-    with pytest.raises(ParRepError):
-        ParRepBatch([g])
-    h = ParRep(spec, 16, 50, 50, x0=[0, 0], thresh="steps", T_burn=2.0)
-    h.run(10.0, 2)
-    with pytest.raises(ParRepError):
-        parrep_uq([g, h], np.arange(34 * 251.0))
-    srv = ParRepServer(precision="f64", arena_bytes=8 << 20)
+    srv = ParRepServer(precision="f32", arena_bytes=8 << 20)
     with pytest.raises(ParRepError):
         srv.submit(spec, 16, 50, 50, 10.0, 1, x0=[0, 0], thresh="steps")
     srv.close()
+
+
+def _cprime():
+    cp = np.array([SMALL] * 3, dtype=float)
+    cp[0, 0] *= 1.1   # a
+    cp[1, 4] *= 0.8   # k0max
+    cp[2, 7] *= 1.05  # D
+    return cp
+
+
+def test_genetic_fim_rer_match_oracle():
+    """The eight-parameter FIM and three RERs of a run equal the oracle's
+    per-event sums over [T_burn, T_end] (the device contracts the post-burn
+    histogram instead; the two agree to the fixed-point rounding)."""
+    spec = _spec(SMALL, 16, 250, 13)
+    cp = _cprime()
+    T, Tb = 200.0, 20.0
+    o = O.parrep_run(spec, 40, 2.0, 2.0, T, 8, [0, 0], thresh="time", T_burn=Tb, rer_cprime=cp)
+    g = ParRep(spec, 40, 2.0, 2.0, x0=[0, 0], thresh="time", T_burn=Tb)
+    assert g.run_status(T, 8) == o["status"] == 0
+    assert g.stats()["events_parallel_useful"] == o["events_parallel_useful"]
+    F = g.fim()
+    Fo = o["fim"] / (T - Tb)
+    assert F.shape == (8, 8)
+    np.testing.assert_allclose(F, Fo, rtol=1e-7, atol=1e-12 * np.abs(Fo).max())
+    R = g.rer(cp)
+    np.testing.assert_allclose(R, o["rer"] / (T - Tb), rtol=1e-7, atol=1e-15)
+    # I_11 = E[xi]/a (one channel depends on a, linearly)
+    h = g.histogram_raw()[1].reshape(2 * 16 + 2, 251)
+    p_on = h[1::2].sum() / h.sum()
+    assert abs(F[0, 0] - p_on / SMALL[0]) < 1e-9 * F[0, 0]
+
+
+def _solo(spec, R, tc, tp, thresh, T, Tb, seed, x0):
+    g = ParRep(spec, R, tc, tp, x0=x0, thresh=thresh, T_burn=Tb)
+    g.run(T, seed)
+    return g
+
+
+def test_genetic_batch_and_serve_equal_solo_runs():
+    """Genetic instances beside a Schloegl one in a binary64 batch, and as
+    served requests in flight together: each result equals its solo run."""
+    V10 = dict(kind="schlogl", c=[3.0, 0.6, 0.25, 2.95], s=[1.0 / 10, 1.0 / 100, 2.0 * 10, 1.0], hist_max=200,
+               regions=[([1], 11)])
+    sp = _spec(SMALL, 16, 250, 13)
+    jobs = [(sp, 24, 1.0, 1.0, "time", 80.0, 10.0, 3, [0, 0]), (sp, 40, 300, 300, "steps", 60.0, 5.0, 4, [1, 30]),
+            (V10, 32, 200, 200, "steps", 70.0, 10.0, 5, [3]), (sp, 7, 2.0, 2.0, "time", 50.0, 0.0, 6, [0, 0])]
+    solo = [_solo(*j) for j in jobs]
+    hs = [ParRep(j[0], j[1], j[2], j[3], x0=j[8], thresh=j[4], T_burn=j[6]) for j in jobs]
+    b = ParRepBatch(hs, autotune=False)
+    b.run([j[5] for j in jobs], [j[7] for j in jobs])
+    assert b.status() == [0] * len(jobs)
+    for a, h in zip(solo, hs):
+        assert np.array_equal(a.histogram(), h.histogram())
+        assert a.stats()["events_parallel_useful"] == h.stats()["events_parallel_useful"]
+        np.testing.assert_allclose(h.fim(), a.fim(), rtol=1e-12, atol=1e-14 * np.abs(a.fim()).max())
+    srv = ParRepServer(precision="f64")
+    ids = [srv.submit(j[0], j[1], j[2], j[3], j[5], j[7], x0=j[8], thresh=j[4], T_burn=j[6],
+                      rer=_cprime() if j[0] is sp else None) for j in jobs]
+    res = [srv.result(i) for i in ids]
+    srv.close()
+    for a, r, j in zip(solo, res, jobs):
+        assert r["status"] == 0
+        assert np.array_equal(r["hist"], a.histogram())
+        np.testing.assert_allclose(r["fim"], a.fim(), rtol=1e-12, atol=1e-14 * np.abs(a.fim()).max())
+        if j[0] is sp:
+            np.testing.assert_allclose(r["rer"], a.rer(_cprime()), rtol=1e-12, atol=1e-15)
+
+
+def test_genetic_uq_matches_oracle_estimators():
+    """parrep_uq over genetic runs: the IAF of the protein count, the mean and
+    the eight-parameter FIM with half widths equal the oracle's Sec. IV.B
+    estimators applied to the same runs' post-burn histograms and FIMs."""
+    from oracle import uq as U
+
+    spec = _spec(SMALL, 16, 250, 13)
+    T, Tb = 120.0, 20.0
+    hs = [_solo(spec, 24, 1.0, 1.0, "time", T, Tb, 70 + k, [0, 0]) for k in range(6)]
+    f = np.tile(np.arange(251.0), 34)  # f = p on bins (2m + xi, p)
+    r = parrep_uq(hs, f)
+    posts = [h.histogram_raw()[1] for h in hs]
+    ref = U.uq(f, posts, [h.fim() for h in hs], T - Tb)
+    assert r["fim"].shape == (8, 8)
+    np.testing.assert_allclose(r["Y"], ref["Y"], rtol=1e-12)
+    np.testing.assert_allclose(r["iaf"], ref["iaf"], rtol=1e-9)
+    np.testing.assert_allclose(r["mean_f"], ref["mean_f"], rtol=1e-12)
+    np.testing.assert_allclose(r["fim"], ref["fim"], rtol=1e-9, atol=1e-15)
+    np.testing.assert_allclose(r["fim_half_width"], ref["fim_half_width"], rtol=1e-6, atol=1e-12)
+    np.testing.assert_allclose(r["bounds"], ref["bounds"], rtol=1e-8)
+
+
+def test_genetic_paper_constants_fim_against_exact_chain():
+    """The paper's switch (Sec. V.B: b = 22.5, a = 2400/b, gamma = 50, D =
+    1000, ...) with its Algorithm 1 settings (R = 100, n_c = n_p = 2e4 jumps):
+    32 samples to T = 2e4 after a burn-in of 2e3, in one binary64 batch.  The
+    mean FIM diagonal lies within 4.5 standard errors (from the spread over
+    samples) of the exact chain's, which itself lies inside Table V's half
+    widths; parrep_uq returns the same mean."""
+    import json
+    import os
+
+    ref = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "exact_references.json")))
+    exact = np.asarray(ref["genetic_paper"]["fim_diag"])
+    spec = _spec(E.genetic_paper_params(), 15, 3500, 512)
+    n, T, Tb = 32, 2e4, 2e3
+    hs = [ParRep(spec, 100, 20000, 20000, x0=[0, 0], thresh="steps", T_burn=Tb) for _ in range(n)]
+    b = ParRepBatch(hs, autotune=False)
+    b.run([T] * n, [500 + k for k in range(n)])
+    assert b.status() == [0] * n
+    Z = np.array([np.diag(h.fim()) for h in hs])
+    mean, se = Z.mean(0), Z.std(0, ddof=1) / np.sqrt(n)
+    assert np.all(np.abs(mean - exact) <= 4.5 * se + 1e-12 * exact), (mean, exact, se)
+    r = parrep_uq(hs, np.tile(np.arange(3501.0), 32))
+    np.testing.assert_allclose(np.diag(r["fim"]), mean, rtol=1e-9)
+    assert sum(h.stats()["escapes"] for h in hs) > 0

@@ -1,20 +1,25 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle.
 
-Integer results -- jump counts, N*, K, X~, the dephased replica states -- must
-be identical.  Time sums: the library keeps them in 64-bit fixed point with
-2^-40 resolution (each holding time rounded once, sums exact), the oracle in
-binary64 summed in (stage, step, replica) order.  A bin that received n
-holding times therefore differs by at most n * 2^-41 from rounding plus the
-binary64 summation error (about n * 2^-53 relative); the tolerance used is
-atol = 4e-12 * (events in the run) + 1e-12 * T_end, rtol = 1e-12.
+Integer results -- jump counts, N*, K, X~, the dephased replica states, and
+per-trajectory reaction sequences and states of the plain SSA -- must be
+identical.
 
-In the FP32 form the reaction choice is taken in binary32 on both sides, so
-every integer result is still identical.  The holding time differs: the
-kernel computes -logf(u) * RN(1/a0), the oracle -logf(u) / a0.  CUDA's and
-the C library's logf may differ by 1 ulp, and the reciprocal-multiply rounds
-twice where the division rounds once, so each tau agrees to within 3 ulp of
-binary32 (relative 3 * 2^-24 < 2^-22); every time sum is bounded by
-rtol = 2^-22 on top of the fixed-point term.
+Time sums.  The library rounds each holding time once to 64-bit fixed point
+with 2^-40 resolution and sums exactly; the oracle sums binary64 in (stage,
+step, replica) order.  For a bin that received n holding times with total h:
+  * fixed-point rounding: at most n * 2^-41;
+  * the holding time itself: -log(u)/a0 with CUDA's and the C library's log
+    may differ by an ulp, so each tau agrees to 2^-51 relative (binary64); in
+    the FP32 form the kernel computes -logf(u) * RN(1/a0) against the
+    oracle's -logf(u) / a0 -- logf may differ by 1 ulp and the reciprocal
+    multiply rounds twice where the division rounds once, so each tau agrees
+    to 3 ulp of binary32, below 2^-22 relative;
+  * the oracle's binary64 summation: at most n * 2^-53 * h.
+So |h_gpu - h_oracle| <= n 2^-41 + (rt + n 2^-53) h, rt = 2^-51 or 2^-22,
+with n taken per bin from the oracle's own counts.  The same bound with n =
+all contributions so far holds for a clock T_s.  A contribution cut at T_end,
+or split at T_burn, is cut at a clock that differs by that clock bound, so
+the (at most two) bins that hold a cut may differ by that much more.
 
 The FIM and RER are linear in the post-burn histogram, h -> sum_x r(x) h(x)
 with per-state rates r(x) >= 0 (the RER and FIM integrands of Appendix A).  Two cuts move
@@ -30,17 +35,39 @@ import pytest
 import oracle as O
 from oracle import exact as X
 from paper_1705_06807_gb300 import ParRep, configs as K, parrep_philox, parrep_ssa
-from paper_1705_06807_gb300.api import ParRepError
+from paper_1705_06807_gb300.api import ParRepError, parrep_ssa_trace
 
 pytestmark = pytest.mark.gpu
 
 
 F32_RTOL = 2.0**-22
+F64_RTOL = 2.0**-51
 
 
-def _tol(events, T_end, precision="f64"):
-    t = 4e-12 * max(events, 1) + 1e-12 * T_end
-    return t + (F32_RTOL * T_end if precision == "f32" else 0.0)
+def _rt(precision):
+    return F32_RTOL if precision == "f32" else F64_RTOL
+
+
+def _bin_bound(n, h, precision):
+    """Per-bin bound on |h_gpu - h_oracle| for n holding times summing to h."""
+    n = np.asarray(n, dtype=np.float64)
+    return n * 2.0**-41 + (_rt(precision) + n * 2.0**-53) * np.abs(np.asarray(h, dtype=np.float64))
+
+
+def _clock_bound(n, T, precision):
+    """Bound on the difference of two clocks after n contributions summing to T."""
+    return n * 2.0**-41 + (_rt(precision) + n * 2.0**-53) * T
+
+
+def _assert_bins(actual, desired, counts, precision, cut_slack=0.0, max_cut_bins=0):
+    """Every bin within its own bound; at most max_cut_bins bins (those that
+    hold a cut contribution) may exceed it, by at most cut_slack."""
+    actual, desired = np.asarray(actual, dtype=float), np.asarray(desired, dtype=float)
+    excess = np.abs(actual - desired) - _bin_bound(counts, desired, precision)
+    over = excess > 0
+    assert over.sum() <= max_cut_bins, f"{int(over.sum())} bin(s) beyond their bound; worst {excess.max():.3e}"
+    if over.any():
+        assert excess.max() <= cut_slack, f"cut bin beyond {cut_slack:.3e}: {excess.max():.3e}"
 
 
 def _assert_close(actual, desired, rtol, atol):
@@ -81,7 +108,7 @@ def _state_rates(spec, cprime=None):
 def run_both(spec, R, tc, tp, T_end, seed, x0, *, thresh="time", precision="f64", fv_group=32, T_burn=0.0,
              x0_uniform_hi=0, block_threads=0, chunk_steps=0, rer=None):
     o = O.parrep_run(spec, R, tc, tp, T_end, seed, x0, thresh=thresh, precision=precision, fv_group=fv_group,
-                     T_burn=T_burn, x0_uniform_hi=x0_uniform_hi, rer_cprime=rer)
+                     T_burn=T_burn, x0_uniform_hi=x0_uniform_hi, rer_cprime=rer, counts=True)
     g = ParRep(spec, R, tc, tp, x0=x0, x0_uniform_hi=x0_uniform_hi, thresh=thresh, precision=precision,
                fv_group=fv_group, T_burn=T_burn, block_threads=block_threads, chunk_steps=chunk_steps)
     g.precision = precision
@@ -102,19 +129,20 @@ def assert_parity(o, g, rc, T_end, *, rer=None):
     assert st["events_decorr"] == o["events_decorr"]
     assert st["events_dephase"] == o["events_dephase"]
     assert st["events_parallel_useful"] == o["events_parallel_useful"]
+    events = o["events_decorr"] + o["events_parallel_useful"]
     cg, co = g.cycle_log(), o["cycles"]
     assert len(cg) == len(co)
     for a, b in zip(cg, co):
         for k in ("cycle", "W", "ended", "decorr_steps", "dephase_steps", "n_star", "k", "x_tilde"):
             assert a[k] == b[k], (k, a, b)
-        assert abs(a["T_s"] - b["T_s"]) <= rt * b["T_s"] + 1e-12 * T_end + 1e-9
-    events = o["events_decorr"] + o["events_parallel_useful"]
+        assert abs(a["T_s"] - b["T_s"]) <= _clock_bound(events, b["T_s"], prec), (a["T_s"], b["T_s"])
     pre, post = g.histogram_raw()
-    tol = _tol(events, T_end, prec)
-    np.testing.assert_allclose(pre, o["hist_pre"], rtol=rt, atol=tol)
-    np.testing.assert_allclose(post, o["hist_post"], rtol=rt, atol=tol)
+    cut = _clock_bound(events, T_end, prec)
+    # pre: the T_burn split; post: the split and the T_end cut
+    _assert_bins(pre, o["hist_pre"], o["count_pre"], prec, cut, 1)
+    _assert_bins(post, o["hist_post"], o["count_post"], prec, cut, 2)
     h = g.histogram()
-    np.testing.assert_allclose(h, (o["hist_pre"] + o["hist_post"]) / T_end, rtol=rt, atol=tol / T_end)
+    _assert_bins(h * T_end, o["hist_pre"] + o["hist_post"], o["count_pre"] + o["count_post"], prec, 2 * cut, 2)
     span = T_end - g._opt.T_burn
     if span > 0:
         F = g.fim()
@@ -143,16 +171,53 @@ def test_philox_device_bit_exact():
     assert list(out[0]) == [0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8]
 
 
+SSA_CASES = [(K.schlogl_classic(), [85]), (K.toggle(alpha=20, n=2.5, hist_max=(63, 63)), [15, 2])]
+
+
 @pytest.mark.parametrize("precision", ["f64", "f32"])
-@pytest.mark.parametrize("spec,x0", [(K.schlogl_classic(), [85]), (K.toggle(alpha=20, n=2.5, hist_max=(63, 63)), [15, 2])])
+@pytest.mark.parametrize("spec,x0", SSA_CASES)
+def test_plain_ssa_trajectories_are_bit_exact(spec, x0, precision):
+    """Per trajectory, the reaction index sequence and the integer states of
+    the direct method (Sec. II.A) are identical to the oracle's for the same
+    Philox stream; each holding time agrees to its 2^-41 fixed-point rounding
+    plus the log / reciprocal ulps."""
+    n, steps = 40, 600
+    J, xs, tau, nj, xf = parrep_ssa_trace(spec, n, x0, 1e6, 23, steps, precision=precision)
+    assert np.all(nj == steps)
+    for t in range(n):
+        Jo, xo, to = O.ssa_trace(spec, x0, 23, t, steps, precision=precision)
+        assert np.array_equal(J[t], Jo), t
+        assert np.array_equal(xs[t, :, : len(x0)], xo[:, : len(x0)]), t
+        assert np.all(np.abs(tau[t] - to) <= 2.0**-41 + _rt(precision) * to), t
+        assert tuple(xf[t, : len(x0)]) == tuple(xo[-1, : len(x0)])
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("spec,x0", SSA_CASES)
 def test_plain_ssa_matches_oracle(spec, x0, precision):
+    """Histograms, jump counts and final states of parrep_ssa against the
+    oracle's plain SSA to T_end, with each bin held to its own rounding bound
+    (its holding-time count comes from the trajectories' jump records)."""
     T = 3.0 if spec["kind"] == "schlogl" else 40.0
-    hg, evg, _ = parrep_ssa(spec, 37, x0, T, 11, precision=precision)
-    ho, evo, _ = O.ssa_run(spec, 37, x0, T, 11, precision=precision)
+    n = 37
+    hg, evg, _ = parrep_ssa(spec, n, x0, T, 11, precision=precision)
+    ho, evo, xfo = O.ssa_run(spec, n, x0, T, 11, precision=precision)
     assert evg == evo
-    rt = F32_RTOL if precision == "f32" else 1e-12
-    np.testing.assert_allclose(hg, ho, rtol=rt, atol=_tol(evo, 37 * T, precision))
-    assert abs(hg.sum() - 37 * T) < 1e-9 * 37 * T
+    J, xs, tau, nj, xf = parrep_ssa_trace(spec, n, x0, T, 11, 8192, precision=precision)
+    assert int(nj.sum()) == evo and np.all(nj < 8192)
+    assert np.array_equal(xf[:, : len(x0)], xfo[:, : len(x0)])
+    # holding times per bin: the pre-jump states, plus each trajectory's last
+    # (truncated) stay at its final state
+    ys = spec["hist_max"][1] + 1 if np.ndim(spec["hist_max"]) else 1
+    counts = np.zeros(hg.size, dtype=np.int64)
+    for t in range(n):
+        pre = np.concatenate([[list(x0) + [0] * (2 - len(x0))], xs[t, : nj[t] - 1]]) if nj[t] else np.zeros((0, 2))
+        b = (pre[:, 0] * ys + (pre[:, 1] if ys > 1 else 0)).astype(np.int64)
+        counts += np.bincount(b, minlength=hg.size)
+        counts[xf[t, 0] * ys + (xf[t, 1] if ys > 1 else 0)] += 1
+    slack = max(_clock_bound(int(k), T, precision) for k in nj)
+    _assert_bins(hg, ho, counts, precision, slack * n, n)
+    assert abs(hg.sum() - n * T) <= _clock_bound(evo + n, n * T, precision)
 
 
 # ---------------------------------------------------------------------------
@@ -216,6 +281,23 @@ def test_parrep_full_launch_config_first_cycles():
     assert_parity(o, g, rc, 80.0)
 
 
+def test_parrep_full_launch_config_first_cycles_fp32():
+    """The benchmarked form: binary32 propensities with the library's default
+    FP32 launch plan for 4096 replicas (32 owner threads + 352 helpers per
+    block, 128 blocks, chunks doubling up to 2048 lockstep steps), x0 uniform
+    on [0, 1000], time thresholds 1/1, over the first 3000 time units (four
+    escapes, then a parallel step of 4562 lockstep steps cut by T_end),
+    against the oracle's binary32 mode."""
+    c = K.C2
+    o, g, rc = run_both(c["network"], c["n_replicas"], c["t_corr"], c["t_phase"], 3000.0, 0, c["x0"],
+                        x0_uniform_hi=c["x0_uniform_hi"], T_burn=1500.0, precision="f32")
+    st = g.stats()
+    assert st["grid_blocks"] == 128 and st["block_threads"] == 384 and st["chunk_steps"] == 2048
+    assert o["escapes"] >= 3
+    assert max(cy["n_star"] for cy in o["cycles"]) > 2048
+    assert_parity(o, g, rc, 3000.0)
+
+
 @pytest.mark.parametrize("T_end", [0.0, 1e-6, 0.01])
 def test_parrep_tiny_horizons(T_end):
     spec = K.schlogl_classic()
@@ -258,6 +340,53 @@ def test_dephase_time_mode_bit_exact():
     o_states, steps, _ = O.dephase(spec, 70, [560], 1, 2, 0.3, 5, fv_group=32)
     g = ParRep(spec, 70, 1.0, 0.3, fv_group=32)
     assert np.array_equal(g.dephase([560], 1, 2, 5), o_states)
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_served_requests_match_the_oracle(precision):
+    """Requests through the continuous-batching server, several in flight at
+    once, checked directly against the oracle's Algorithm 1 (not only
+    against solo GPU runs): integers identical, histograms within the
+    per-bin bounds, FIM and RER within the contraction bound."""
+    from paper_1705_06807_gb300 import ParRepServer
+
+    tg = K.toggle(alpha=20, n=2.5, hist_max=(63, 63))
+    cp = np.array([V10["c"]] * 2, dtype=float)
+    cp[0, 0] *= 1.1
+    cp[1, 3] *= 0.9
+    reqs = [dict(spec=V10, R=48, tc=300, tp=300, T_end=200.0, seed=41, x0=[2], thresh="steps", G=16, Tb=50.0, rer=cp),
+            dict(spec=tg, R=40, tc=0.5, tp=0.5, T_end=40.0, seed=9, x0=[15, 2], thresh="time", G=32, Tb=10.0,
+                 rer=None),
+            dict(spec=K.schlogl_classic(), R=256, tc=1.0, tp=1.0, T_end=30.0, seed=5, x0=[250], thresh="time", G=32,
+                 Tb=5.0, rer=None)]
+    srv = ParRepServer(precision=precision)
+    ids = [srv.submit(q["spec"], q["R"], q["tc"], q["tp"], q["T_end"], q["seed"], x0=q["x0"], thresh=q["thresh"],
+                      fv_group=q["G"], T_burn=q["Tb"], rer=q["rer"]) for q in reqs]
+    res = [srv.result(i) for i in ids]
+    srv.close()
+    for q, r in zip(reqs, res):
+        o = O.parrep_run(q["spec"], q["R"], q["tc"], q["tp"], q["T_end"], q["seed"], q["x0"], thresh=q["thresh"],
+                         precision=precision, fv_group=q["G"], T_burn=q["Tb"], rer_cprime=q["rer"], counts=True)
+        assert r["status"] == 0 == o["status"]
+        st = r["stats"]
+        for k, ko in (("cycles", "n_cycles"), ("escapes", "escapes"), ("events_decorr", "events_decorr"),
+                      ("events_dephase", "events_dephase"), ("events_parallel_useful", "events_parallel_useful"),
+                      ("x_final", "x_final"), ("x0", "x0")):
+            assert st[k] == o[ko], (k, st[k], o[ko])
+        assert st["T_s"] == q["T_end"]
+        events = o["events_decorr"] + o["events_parallel_useful"]
+        cut = _clock_bound(events, q["T_end"], precision)
+        _assert_bins(r["hist"] * q["T_end"], o["hist_pre"] + o["hist_post"], o["count_pre"] + o["count_post"],
+                     precision, 2 * cut, 2)
+        span = q["T_end"] - q["Tb"]
+        frt = max(_rt(precision), 1e-9)
+        fr, rr = _state_rates(q["spec"], q["rer"])
+        hp = o["hist_post"]
+        seen = hp > 0
+        c = frt * (q["Tb"] + q["T_end"]) / span
+        _assert_close(r["fim"], o["fim"] / span, frt, 1e-12 + c * np.abs(fr[seen]).max(axis=0))
+        if q["rer"] is not None:
+            _assert_close(r["rer"], o["rer"] / span, frt, 1e-12 + c * rr[:, seen].max(axis=1))
 
 
 # ---------------------------------------------------------------------------

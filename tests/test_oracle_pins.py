@@ -823,3 +823,33 @@ def test_genetic_parrep_fim_rer_are_histogram_contractions():
     for k in range(2):
         Rk = E.rer_exact(lam, E.genetic_props(cp[k], xi, m, p), w)
         assert abs(r["rer"][k] - Rk) <= 1e-11 * abs(Rk)
+
+
+def test_stored_exact_references_come_from_the_oracle():
+    """tests/golden/exact_references.json (read by bench.py and the GPU
+    accuracy tests) is what make_exact_references.py computes from the
+    oracle's exact references today."""
+    import importlib.util
+    import json
+
+    spec = importlib.util.spec_from_file_location("mk", os.path.join(GOLDEN, "make_exact_references.py"))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    fresh = mk.compute()
+    with open(os.path.join(GOLDEN, "exact_references.json")) as f:
+        stored = json.load(f)
+
+    def same(a, b, path):
+        if isinstance(a, dict):
+            assert set(a) == set(b), path
+            for k in a:
+                same(a[k], b[k], path + "/" + k)
+        elif isinstance(a, list):
+            assert np.allclose(a, b, rtol=1e-10, atol=0.0), path
+        else:
+            assert a == pytest.approx(b, rel=1e-10), path
+
+    same(fresh, stored, "")
+    # spot facts: the classic Schloegl lower-well mass and the Table II I_33
+    assert stored["schlogl_classic"]["mass_lower"] == pytest.approx(0.22026, abs=1e-5)
+    assert stored["schlogl_v25"]["fim_diag"][2] == pytest.approx(200.0, rel=1e-12)
