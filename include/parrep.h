@@ -47,6 +47,12 @@ typedef struct parrep_s* parrep_t;
 enum { PARREP_SCHLOGL = 1, PARREP_TOGGLE = 2, PARREP_GENETIC = 3 };
 enum { PARREP_THRESH_TIME = 0, PARREP_THRESH_STEPS = 1 };
 enum { PARREP_FP64 = 0, PARREP_FP32 = 1 };
+/* Layout of the FP32 form's kernel: staged (each block's replica owner threads
+ * walk the jump chains while helper warps draw the random numbers and account
+ * the holding times), direct (one thread per replica), or auto (staged, except
+ * for the genetic switch, which runs direct only).  Both give the same results
+ * bit for bit. */
+enum { PARREP_F32_AUTO = 0, PARREP_F32_STAGED = 1, PARREP_F32_DIRECT = 2 };
 
 /* Reaction network (Sec. II.A).  Three kinds:
  *   PARREP_SCHLOGL (Table I, 1 species x):
@@ -99,6 +105,8 @@ typedef struct {
                               replicas at once when the grid fits, else a full co-resident
                               grid); fewer blocks than groups run several groups per
                               block with the same results */
+    int32_t f32_layout;    /* FP32 form: PARREP_F32_AUTO (default: staged, direct for the
+                              genetic switch), _STAGED or _DIRECT */
     double T_burn;         /* FIM / RER integrate over [T_burn, T_end] (default 0) */
     double wait_timeout_s; /* device wait limit without progress (default 10 s) */
     void* stream;          /* cudaStream_t to run on (NULL = legacy default stream) */
@@ -289,14 +297,17 @@ typedef struct parrep_batch_s* parrep_batch_t;
 
 typedef struct {
     int32_t block_threads;      /* threads per block; 0 = chosen by the autotuner */
-    int32_t replicas_per_block; /* FP32 form: owner threads per block (32, 64, 128 or 256);
-                                   0 = chosen by the autotuner.  FP64 form: = block_threads */
+    int32_t replicas_per_block; /* FP32 staged layout: owner threads per block (32, 64, 128 or
+                                   256); 0 = chosen by the autotuner.  FP64 form and FP32 direct
+                                   layout: = block_threads */
     int32_t autotune;           /* 1 (default): the first run times candidate block shapes on a
                                    shortened copy of the batch (T_end scaled by tune_fraction)
                                    and keeps the fastest; 0: defaults (384 x 32 / 128) */
     int32_t use_graph;          /* 1 (default): capture the launch sequence (parameter upload,
                                    reset, batch kernel, read-back) in a CUDA graph and replay it
                                    while the shape stays the same */
+    int32_t f32_layout;         /* FP32 form: PARREP_F32_AUTO (default: staged shapes; direct if an
+                                   instance is a genetic switch), _STAGED or _DIRECT */
     double tune_fraction;       /* default 0.05 */
     double wait_timeout_s;      /* device wait limit without progress anywhere (default 10 s) */
     void* stream;               /* cudaStream_t (NULL = legacy default stream) */
@@ -369,6 +380,8 @@ typedef struct {
     int32_t block_threads;      /* 0 = 384 (FP32) / 128 (FP64) */
     int32_t replicas_per_block; /* FP32 form: owner threads per block (32..256), 0 = 32 */
     int32_t ring;               /* request slots (default 4096); a slot is reused after its result is read */
+    int32_t f32_layout;         /* FP32 form, one for all requests: PARREP_F32_STAGED (default; AUTO
+                                   means the same) or PARREP_F32_DIRECT (needed for genetic switches) */
     int64_t arena_bytes;        /* device memory for admitted requests (default 4 GiB) */
     int64_t log_cap;            /* cycle-log records kept per request (default 4096) */
     double idle_exit_s;         /* the serve kernel ends after the server has had nothing to do this

@@ -16,6 +16,8 @@ PARREP_EINVAL = -1
 PARREP_ENOMEM = -2
 PARREP_ECUDA = -3
 PARREP_ETIMEOUT = -4
+PARREP_F32_AUTO, PARREP_F32_STAGED, PARREP_F32_DIRECT = 0, 1, 2
+LAYOUTS = {"auto": 0, "staged": 1, "direct": 2}
 PARREP_ERANGE = -5
 PARREP_ESTATE = -6
 PARREP_SCHLOGL, PARREP_TOGGLE, PARREP_GENETIC = 1, 2, 3
@@ -38,7 +40,7 @@ class parrep_regions(C.Structure):
 class parrep_options(C.Structure):
     _fields_ = [("thresh_mode", C.c_int32), ("precision", C.c_int32), ("fv_group", C.c_int32),
                 ("block_threads", C.c_int32), ("chunk_steps", C.c_int32), ("debug_stall_barrier", C.c_int32),
-                ("serial_stages", C.c_int32), ("max_blocks", C.c_int32),
+                ("serial_stages", C.c_int32), ("max_blocks", C.c_int32), ("f32_layout", C.c_int32),
                 ("T_burn", C.c_double), ("wait_timeout_s", C.c_double), ("stream", C.c_void_p)]
 
 
@@ -53,8 +55,8 @@ class parrep_stats(C.Structure):
 
 class parrep_batch_options(C.Structure):
     _fields_ = [("block_threads", C.c_int32), ("replicas_per_block", C.c_int32), ("autotune", C.c_int32),
-                ("use_graph", C.c_int32), ("tune_fraction", C.c_double), ("wait_timeout_s", C.c_double),
-                ("stream", C.c_void_p)]
+                ("use_graph", C.c_int32), ("f32_layout", C.c_int32), ("tune_fraction", C.c_double),
+                ("wait_timeout_s", C.c_double), ("stream", C.c_void_p)]
 
 
 class parrep_batch_info(C.Structure):
@@ -66,7 +68,7 @@ class parrep_batch_info(C.Structure):
 
 class parrep_server_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("block_threads", C.c_int32), ("replicas_per_block", C.c_int32),
-                ("ring", C.c_int32), ("arena_bytes", C.c_int64), ("log_cap", C.c_int64),
+                ("ring", C.c_int32), ("f32_layout", C.c_int32), ("arena_bytes", C.c_int64), ("log_cap", C.c_int64),
                 ("idle_exit_s", C.c_double), ("wait_timeout_s", C.c_double)]
 
 

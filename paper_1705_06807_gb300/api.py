@@ -76,7 +76,7 @@ class ParRep:
                  x0_uniform_hi: int = 0, thresh: str = "time", precision: str = "f64", fv_group: int = 32,
                  T_burn: float = 0.0, block_threads: int = 0, chunk_steps: int = 0, stream=None,
                  wait_timeout_s: float = 10.0, debug_stall_barrier: int = -1, serial_stages: int = 0,
-                 max_blocks: int = 0):
+                 max_blocks: int = 0, f32_layout: str = "auto"):
         self._lib = L.load()
         self.spec = spec
         self.L = {"schlogl": 4, "toggle": 6, "genetic": 8}[spec["kind"]]
@@ -90,11 +90,11 @@ class ParRep:
         self.set_options(thresh=thresh, precision=precision, fv_group=fv_group, T_burn=T_burn,
                          block_threads=block_threads, chunk_steps=chunk_steps, stream=stream,
                          wait_timeout_s=wait_timeout_s, debug_stall_barrier=debug_stall_barrier,
-                         serial_stages=serial_stages, max_blocks=max_blocks)
+                         serial_stages=serial_stages, max_blocks=max_blocks, f32_layout=f32_layout)
 
     def set_options(self, *, thresh="time", precision="f64", fv_group=32, T_burn=0.0, block_threads=0,
                     chunk_steps=0, stream=None, wait_timeout_s=10.0, debug_stall_barrier=-1, serial_stages=0,
-                    max_blocks=0):
+                    max_blocks=0, f32_layout="auto"):
         o = L.parrep_options()
         self._lib.parrep_default_options(C.byref(o))
         o.thresh_mode = L.PARREP_THRESH_STEPS if thresh == "steps" else L.PARREP_THRESH_TIME
@@ -107,6 +107,7 @@ class ParRep:
         o.debug_stall_barrier = int(debug_stall_barrier)
         o.serial_stages = int(serial_stages)
         o.max_blocks = int(max_blocks)
+        o.f32_layout = L.LAYOUTS[f32_layout]
         if stream is not None:
             o.stream = C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
         _check(self._lib.parrep_set_options(self.h, C.byref(o)), self.h)
@@ -193,7 +194,8 @@ class ParRepBatch:
     every handle holds its own results (read them with its methods)."""
 
     def __init__(self, instances, *, block_threads: int = 0, replicas_per_block: int = 0, autotune: bool = True,
-                 use_graph: bool = True, tune_fraction: float = 0.05, wait_timeout_s: float = 10.0, stream=None):
+                 use_graph: bool = True, tune_fraction: float = 0.05, wait_timeout_s: float = 10.0, stream=None,
+                 f32_layout: str = "auto"):
         self._lib = L.load()
         self.instances = list(instances)
         o = L.parrep_batch_options()
@@ -202,6 +204,7 @@ class ParRepBatch:
         o.replicas_per_block = int(replicas_per_block)
         o.autotune = 1 if autotune else 0
         o.use_graph = 1 if use_graph else 0
+        o.f32_layout = L.LAYOUTS[f32_layout]
         o.tune_fraction = float(tune_fraction)
         o.wait_timeout_s = float(wait_timeout_s)
         if stream is not None:
@@ -268,7 +271,7 @@ class ParRepServer:
 
     def __init__(self, *, precision: str = "f32", block_threads: int = 0, replicas_per_block: int = 0,
                  ring: int = 4096, arena_bytes: int = 4 << 30, log_cap: int = 4096, idle_exit_s: float = 0.05,
-                 wait_timeout_s: float = 10.0):
+                 wait_timeout_s: float = 10.0, f32_layout: str = "staged"):
         self._lib = L.load()
         o = L.parrep_server_options()
         self._lib.parrep_server_default_options(C.byref(o))
@@ -276,6 +279,7 @@ class ParRepServer:
         o.block_threads = int(block_threads)
         o.replicas_per_block = int(replicas_per_block)
         o.ring = int(ring)
+        o.f32_layout = L.LAYOUTS[f32_layout]
         o.arena_bytes = int(arena_bytes)
         o.log_cap = int(log_cap)
         o.idle_exit_s = float(idle_exit_s)

@@ -150,6 +150,7 @@ void parrep::build_net(const parrep_network* net, const parrep_regions* reg, Net
         nd.A[0] = c[0];
         nd.A[1] = c[2];
         nd.A[2] = c[2] * c[1];
+        for (int j = 0; j < 3; ++j) nd.Af[j] = (float)nd.A[j];  // the binary32 form's constants
         pU.resize(net->hist_max[1] + 1);
         pV.resize(net->hist_max[1] + 1);
         for (int v = 0; v <= net->hist_max[1]; ++v) {
@@ -287,6 +288,10 @@ extern "C" int parrep_set_options(parrep_t h, const parrep_options* o) {
         return fail(h, PARREP_EINVAL, "block_threads must be a multiple of 32 up to 384 (0 = auto)");
     if (o->chunk_steps < 0 || o->chunk_steps > kMaxChunk) return fail(h, PARREP_EINVAL, "chunk_steps");
     if (o->max_blocks < 0) return fail(h, PARREP_EINVAL, "max_blocks must be >= 0");
+    if (o->f32_layout != PARREP_F32_AUTO && o->f32_layout != PARREP_F32_STAGED && o->f32_layout != PARREP_F32_DIRECT)
+        return fail(h, PARREP_EINVAL, "f32_layout must be PARREP_F32_AUTO, _STAGED or _DIRECT");
+    if (h->net.kind == PARREP_GENETIC && o->precision == PARREP_FP32 && o->f32_layout == PARREP_F32_STAGED)
+        return fail(h, PARREP_EINVAL, "the genetic switch's FP32 form runs in the direct layout only");
     if (!(o->T_burn >= 0.0) || !(o->T_burn < kTEndLimit)) return fail(h, PARREP_EINVAL, "T_burn");
     if (!(o->wait_timeout_s > 0.0) || !(o->wait_timeout_s <= 3600.0)) return fail(h, PARREP_EINVAL, "wait_timeout_s");
     if (o->thresh_mode == PARREP_THRESH_STEPS) {
@@ -347,6 +352,19 @@ int parrep::fast_layout(parrep_t h, int RB, int threads, int with_hist, int pipe
     return off;
 }
 
+// The kernel form of a handle's runs: binary64; or, in the FP32 form, the
+// staged layout (each owner thread's chain fed by helper warps) or the direct
+// one (one thread per replica): as the option asks, else staged -- measured
+// faster on every workload here, 4096 to 65536 replicas and the batches --
+// except for the genetic switch, whose six channels the staged chain does not
+// take.
+int parrep::f32_form(parrep_t h) {
+    if (h->opt.precision != PARREP_FP32) return kFormF64;
+    if (h->opt.f32_layout == PARREP_F32_STAGED) return kFormF32Staged;
+    if (h->opt.f32_layout == PARREP_F32_DIRECT || h->net.kind == PARREP_GENETIC) return kFormF32Direct;
+    return kFormF32Staged;
+}
+
 static int plan_launch(parrep_t h, Plan& pl) {
     int dev = 0, nsm = 0;
     CK(h, cudaGetDevice(&dev));
@@ -354,9 +372,14 @@ static int plan_launch(parrep_t h, Plan& pl) {
     const int prec = h->opt.precision, kind = h->net.kind;
     memset(&pl, 0, sizeof(pl));
     int per_sm = 0;
-    if (prec == PARREP_FP64) {
-        int threads = h->opt.block_threads > 0 ? h->opt.block_threads : 128;
+    const int form = f32_form(h);
+    if (form != kFormF32Staged) {
+        // one thread per replica (binary64, or binary32 direct)
+        const int cap = form == kFormF32Direct ? kDirectThreads : kMaxThreads;
+        int threads = h->opt.block_threads > 0 ? h->opt.block_threads : (form == kFormF32Direct ? kDirectThreads : 128);
+        if (threads > cap) threads = cap;
         if ((long long)threads > ((h->R + 31) / 32) * 32) threads = (int)(((h->R + 31) / 32) * 32);
+        pl.form = form;
         pl.threads = threads;
         pl.RB = threads;
         pl.grid = (int)((h->R + threads - 1) / threads);
@@ -368,7 +391,7 @@ static int plan_launch(parrep_t h, Plan& pl) {
             if (with_hist && h->nbins * 8 > kSmemHistLimit) continue;
             pl.use_smem_hist = with_hist;
             pl.smem = with_hist ? h->nbins * 8 : 0;
-            int ea = kernel_attrs(prec, kind, &per_sm, pl.smem, threads);
+            int ea = kernel_attrs_form(form, kind, &per_sm, pl.smem, threads);
             if (ea != 0) return cuda_fail(h, (cudaError_t)ea, "kernel attributes");
             if (per_sm < 1) continue;
             // more replica groups than co-resident blocks: blocks take several
@@ -393,7 +416,8 @@ static int plan_launch(parrep_t h, Plan& pl) {
             if ((cfg & 2) && !pipe) continue;
             const int smem = fast_layout(h, RB, threads, with_hist, pipe, pl);
             if (smem > 200 * 1024) continue;
-            int ea = kernel_attrs(prec, kind, &per_sm, smem, threads);
+            pl.form = kFormF32Staged;
+            int ea = kernel_attrs_form(kFormF32Staged, kind, &per_sm, smem, threads);
             if (ea != 0) return cuda_fail(h, (cudaError_t)ea, "kernel attributes");
             if (per_sm < 1) continue;
             if ((long long)per_sm * nsm >= grid || pass == 1) {
@@ -415,8 +439,6 @@ int parrep::run_checks(parrep_t h, double T_end) {
     h->has_run = false;
     if (!(T_end >= 0.0) || !(T_end < kTEndLimit)) return fail(h, PARREP_EINVAL, "T_end must be in [0, 2^23)");
     if (h->opt.T_burn > T_end) return fail(h, PARREP_EINVAL, "T_burn > T_end");
-    if (h->net.kind == PARREP_GENETIC && h->opt.precision != PARREP_FP64)
-        return fail(h, PARREP_EINVAL, "the genetic switch has the binary64 form only");
     if (h->opt.thresh_mode == PARREP_THRESH_STEPS &&
         (h->t_corr != floor(h->t_corr) || h->t_phase != floor(h->t_phase)))
         return fail(h, PARREP_EINVAL, "STEPS mode needs integer t_corr, t_phase");
@@ -430,6 +452,7 @@ int parrep::run_params(parrep_t h, double T_end, uint64_t seed, const Plan& pl, 
     memset(&p, 0, sizeof(p));
     p.net = h->nd;
     p.prec = h->opt.precision;
+    p.form = pl.form;
     p.thresh = h->opt.thresh_mode;
     p.R = (int)h->R;
     p.G = h->opt.fv_group;
@@ -661,8 +684,6 @@ extern "C" int parrep_cycle_log(parrep_t h, parrep_cycle* out, int64_t cap, int6
 extern "C" int parrep_dephase(parrep_t h, const int32_t* x_tilde, int32_t W, uint32_t cycle, uint64_t seed,
                               int32_t* out_states) {
     if (!h || !x_tilde || !out_states) return PARREP_EINVAL;
-    if (h->net.kind == PARREP_GENETIC && h->opt.precision != PARREP_FP64)
-        return fail(h, PARREP_EINVAL, "the genetic switch has the binary64 form only");
     const int x0 = x_tilde[0], x1 = h->net.n_species > 1 ? x_tilde[1] : 0;
     if (x0 < 0 || x0 > h->net.hist_max[0] || x1 < 0 || x1 > h->net.hist_max[1])
         return fail(h, PARREP_EINVAL, "x_tilde outside [0, hist_max]");
@@ -745,8 +766,6 @@ extern "C" int parrep_ssa(const parrep_network* net, int32_t precision, int64_t 
     std::string why;
     if (!check_network(net, &reg, why)) return fail(nullptr, PARREP_EINVAL, why);
     if (precision != PARREP_FP64 && precision != PARREP_FP32) return fail(nullptr, PARREP_EINVAL, "precision");
-    if (net->kind == PARREP_GENETIC && precision != PARREP_FP64)
-        return fail(nullptr, PARREP_EINVAL, "the genetic switch has the binary64 form only");
     if (n_traj < 1 || n_traj > (1ll << 31)) return fail(nullptr, PARREP_EINVAL, "n_traj");
     if (!(T_end >= 0.0) || !(T_end < kTEndLimit)) return fail(nullptr, PARREP_EINVAL, "T_end");
     NetDev nd;
@@ -817,8 +836,6 @@ extern "C" int parrep_ssa_trace(const parrep_network* net, int32_t precision, in
     if (!check_network(net, &reg, why)) return fail(nullptr, PARREP_EINVAL, "parrep_ssa_trace: " + why);
     if (precision != PARREP_FP64 && precision != PARREP_FP32)
         return fail(nullptr, PARREP_EINVAL, "parrep_ssa_trace: precision");
-    if (net->kind == PARREP_GENETIC && precision != PARREP_FP64)
-        return fail(nullptr, PARREP_EINVAL, "parrep_ssa_trace: the genetic switch has the binary64 form only");
     if (n_traj < 1 || n_traj > (1ll << 24) || max_steps < 1 || n_traj * max_steps > (1ll << 28))
         return fail(nullptr, PARREP_EINVAL, "parrep_ssa_trace: need 1 <= n_traj, 1 <= max_steps, n_traj*max_steps <= 2^28");
     if (!(T_end >= 0.0) || !(T_end < kTEndLimit)) return fail(nullptr, PARREP_EINVAL, "parrep_ssa_trace: T_end");

@@ -34,6 +34,7 @@ struct parrep_batch_s {
     bool own_stream = false;
     // current block shape and its co-resident grid
     int threads = 0, RB = 0, grid = 0, smem = 0;
+    int form = 0;  // kernel Form of the current shape
     bool tuned = false;
     std::vector<Plan> plans;
     std::vector<int> gang;
@@ -59,7 +60,7 @@ struct parrep_batch_s {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // captured launch sequence and the shape it was captured for
     cudaGraphExec_t exec = nullptr;
-    int g_threads = 0, g_grid = 0, g_smem = 0, g_items_cap = 0, g_off_cap = 0;
+    int g_threads = 0, g_grid = 0, g_smem = 0, g_items_cap = 0, g_off_cap = 0, g_form = -1;
     std::vector<int32_t> status;
     parrep_batch_info info{};
     std::string err;
@@ -220,7 +221,7 @@ static void make_schedule(parrep_batch_t b, const double* T_end) {
 
 // Per-instance layouts for blocks of `threads` with RB owners, the largest
 // dynamic shared memory they need, and the co-resident grid.
-static int set_shape(parrep_batch_t b, int threads, int RB) {
+static int set_shape(parrep_batch_t b, int threads, int RB, int form) {
     int dev = 0, nsm = 0;
     BCK(b, cudaGetDevice(&dev));
     BCK(b, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -231,7 +232,8 @@ static int set_shape(parrep_batch_t b, int threads, int RB) {
         parrep_t h = b->inst[i];
         Plan& pl = b->plans[i];
         memset(&pl, 0, sizeof(pl));
-        if (b->prec == PARREP_FP32) {
+        pl.form = form;
+        if (form == kFormF32Staged) {
             const int pipe = threads - RB >= 64 && !h->opt.serial_stages;
             int sz = -1;
             for (int with_hist = 1; with_hist >= 0 && sz < 0; --with_hist) {
@@ -257,11 +259,12 @@ static int set_shape(parrep_batch_t b, int threads, int RB) {
         smem = std::max(smem, pl.smem);
     }
     int per_sm = 0;
-    const int ea = batch_kernel_attrs(b->prec, &per_sm, smem, threads);
+    const int ea = batch_attrs_form(form, &per_sm, smem, threads);
     if (ea != 0) return bcuda(b, (cudaError_t)ea, "batch kernel attributes");
     if (per_sm < 1) return bfail(b, PARREP_ENOMEM, "the batch kernel does not fit on one SM");
     b->threads = threads;
     b->RB = RB;
+    b->form = form;
     b->smem = smem;
     b->grid = per_sm * nsm;
     b->info.block_threads = threads;
@@ -308,7 +311,7 @@ static int enqueue(parrep_batch_t b) {
     BCK(b, cudaMemcpyAsync(b->d_items, b->h_items, sizeof(int2) * b->items_cap, cudaMemcpyHostToDevice, b->st));
     BCK(b, cudaMemsetAsync(b->d_progress, 0, sizeof(unsigned long long), b->st));
     BatchDev bd{b->d_remaining, b->d_idle, b->d_mail, nullptr, nullptr, 0, 0};
-    BCK(b, launch_batch(b->prec, b->d_params, n, b->d_off, b->d_items, bd, b->grid, b->threads, b->smem, b->st));
+    BCK(b, launch_batch(b->form, b->d_params, n, b->d_off, b->d_items, bd, b->grid, b->threads, b->smem, b->st));
     BCK(b, launch_batch_gather(b->d_params, n, b->d_ctl_out, b->st));
     BCK(b, cudaMemcpyAsync(b->h_ctl_out, b->d_ctl_out, sizeof(RunCtl) * n, cudaMemcpyDeviceToHost, b->st));
     return PARREP_OK;
@@ -332,7 +335,7 @@ static int run_once(parrep_batch_t b, const double* T_end, const uint64_t* seed,
     }
     if (graph) {
         const bool same = b->exec && b->g_threads == b->threads && b->g_grid == b->grid && b->g_smem == b->smem &&
-                          b->g_items_cap == b->items_cap && b->g_off_cap == b->off_cap;
+                          b->g_items_cap == b->items_cap && b->g_off_cap == b->off_cap && b->g_form == b->form;
         if (!same) {
             if (b->exec) cudaGraphExecDestroy(b->exec);
             b->exec = nullptr;
@@ -356,6 +359,7 @@ static int run_once(parrep_batch_t b, const double* T_end, const uint64_t* seed,
             b->g_smem = b->smem;
             b->g_items_cap = b->items_cap;
             b->g_off_cap = b->off_cap;
+            b->g_form = b->form;
         }
         BCK(b, cudaEventRecord(b->ev0, b->st));
         BCK(b, cudaGraphLaunch(b->exec, b->st));
@@ -374,20 +378,40 @@ static int run_once(parrep_batch_t b, const double* T_end, const uint64_t* seed,
     return PARREP_OK;
 }
 
-// Candidate shapes: (threads, RB), FP32 owners + helpers; FP64 one replica a thread.
-static std::vector<std::pair<int, int>> candidates(parrep_batch_t b) {
-    std::vector<std::pair<int, int>> c;
+// Candidate shapes: {threads, RB, form}.  FP32 staged: RB owners + helpers;
+// FP32 direct and FP64: one replica a thread (RB = threads).  The FP32 form
+// tries the staged shapes unless an instance is a genetic switch or the
+// layout option asks for the direct one (measured slower on these batches).
+struct Shape {
+    int threads, RB, form;
+};
+
+static std::vector<Shape> candidates(parrep_batch_t b) {
+    std::vector<Shape> c;
     const int T = b->opt.block_threads, RB = b->opt.replicas_per_block;
     if (b->prec == PARREP_FP32) {
-        const std::pair<int, int> all[] = {{384, 32}, {256, 32}, {384, 64}, {256, 64}, {384, 128}};
-        for (auto& s : all)
-            if ((T == 0 || s.first == T) && (RB == 0 || s.second == RB)) c.push_back(s);
-        if (c.empty()) c.push_back({T ? T : 384, RB ? RB : 32});
+        bool genetic = false;
+        for (parrep_t h : b->inst) genetic |= h->net.kind == PARREP_GENETIC;
+        const bool staged = !genetic && b->opt.f32_layout != PARREP_F32_DIRECT;
+        const bool direct = genetic || b->opt.f32_layout == PARREP_F32_DIRECT;
+        if (staged) {
+            const Shape all[] = {{384, 32, kFormF32Staged}, {256, 32, kFormF32Staged}, {384, 64, kFormF32Staged},
+                                 {256, 64, kFormF32Staged}, {384, 128, kFormF32Staged}};
+            for (auto& s : all)
+                if ((T == 0 || s.threads == T) && (RB == 0 || s.RB == RB)) c.push_back(s);
+            if (c.empty() && (T == 0 || RB == 0 || RB < T)) c.push_back({T ? T : 384, RB ? RB : 32, kFormF32Staged});
+        }
+        if (direct) {
+            const int all[] = {kDirectThreads, 128};
+            for (int t : all)
+                if ((T == 0 || t == T) && (RB == 0 || RB == t)) c.push_back({t, t, kFormF32Direct});
+            if (c.empty()) c.push_back({kDirectThreads, kDirectThreads, kFormF32Direct});
+        }
     } else {
         const int all[] = {128, 256, 64};
         for (int t : all)
-            if (T == 0 || t == T) c.push_back({t, t});
-        if (c.empty()) c.push_back({T, T});
+            if (T == 0 || t == T) c.push_back({t, t, kFormF64});
+        if (c.empty()) c.push_back({T, T, kFormF64});
     }
     if (!b->opt.autotune) c.resize(1);
     return c;
@@ -409,14 +433,14 @@ static int autotune(parrep_batch_t b, const double* T_end, const uint64_t* seed)
         if (!b->have_cost) {
             // one unscored run to measure the instances' costs, so that every
             // candidate is timed with a measured schedule
-            rc = set_shape(b, cand[0].first, cand[0].second);
+            rc = set_shape(b, cand[0].threads, cand[0].RB, cand[0].form);
             float ms = 0.f;
             if (rc == PARREP_OK) rc = run_once(b, Tt.data(), seed, false, &ms);
             if (rc == PARREP_OK) record_costs(b, Tt.data());
             if (rc == PARREP_ENOMEM) rc = PARREP_OK;
         }
         for (size_t k = 0; k < cand.size() && rc == PARREP_OK; ++k) {
-            rc = set_shape(b, cand[k].first, cand[k].second);
+            rc = set_shape(b, cand[k].threads, cand[k].RB, cand[k].form);
             if (rc == PARREP_ENOMEM) {  // this shape does not fit some instance: skip it
                 rc = PARREP_OK;
                 continue;
@@ -435,10 +459,10 @@ static int autotune(parrep_batch_t b, const double* T_end, const uint64_t* seed)
         for (int i = 0; i < n; ++i) b->inst[i]->opt.T_burn = burn[i];
         if (rc != PARREP_OK) return rc;
         if (best_k < 0) return bfail(b, PARREP_ENOMEM, "no candidate block shape fits every instance");
-        int rc2 = set_shape(b, cand[best_k].first, cand[best_k].second);
+        int rc2 = set_shape(b, cand[best_k].threads, cand[best_k].RB, cand[best_k].form);
         if (rc2 != PARREP_OK) return rc2;
     } else {
-        int rc = set_shape(b, cand[0].first, cand[0].second);
+        int rc = set_shape(b, cand[0].threads, cand[0].RB, cand[0].form);
         if (rc != PARREP_OK) return rc;
     }
     b->tuned = true;
@@ -475,6 +499,8 @@ extern "C" int parrep_batch_create(const parrep_t* instances, int32_t n, const p
     if (opt) o = *opt;
     if (o.block_threads < 0 || o.block_threads > kMaxThreads || o.block_threads % 32 != 0)
         return bfail(nullptr, PARREP_EINVAL, "block_threads must be a multiple of 32 up to 384 (0 = autotune)");
+    if (o.f32_layout != PARREP_F32_AUTO && o.f32_layout != PARREP_F32_STAGED && o.f32_layout != PARREP_F32_DIRECT)
+        return bfail(nullptr, PARREP_EINVAL, "f32_layout");
     const int rb = o.replicas_per_block;
     if (!(rb == 0 || rb == 32 || rb == 64 || rb == 128 || rb == 256))
         return bfail(nullptr, PARREP_EINVAL, "replicas_per_block must be 0, 32, 64, 128 or 256");
@@ -484,8 +510,7 @@ extern "C" int parrep_batch_create(const parrep_t* instances, int32_t n, const p
     std::vector<parrep_t> v(instances, instances + n);
     for (int i = 0; i < n; ++i) {
         if (!v[i]) return bfail(nullptr, PARREP_EINVAL, "null instance handle");
-        if (v[i]->net.kind == PARREP_GENETIC && v[i]->opt.precision != PARREP_FP64)
-            return bfail(nullptr, PARREP_EINVAL, "the genetic switch has the binary64 form only");
+
         if (v[i]->opt.precision != v[0]->opt.precision)
             return bfail(nullptr, PARREP_EINVAL, "instances of one batch need the same precision");
     }

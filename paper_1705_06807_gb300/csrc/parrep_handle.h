@@ -55,6 +55,7 @@ namespace parrep {
 // blocks of T threads of which the first RB own replicas (RB a power of two,
 // >= 32), the smallest RB whose grid is co-resident; B = 32 staged steps.
 struct Plan {
+    int form;  // Form (parrep_internal.h)
     int threads, grid, smem, RB, log2RB, B, S, use_smem_hist;
     int off_tab, off_buf, off_trace, off_live, off_nvalid;
     int off_limbs, off_inv, off_rng, off_decp;
@@ -72,6 +73,8 @@ int align16(int x);
 // shared-memory layout of the FP32 form for RB owners in blocks of `threads`
 int fast_layout(parrep_t h, int RB, int threads, int with_hist, int pipelined, Plan& pl);
 int run_checks(parrep_t h, double T_end);
+// kernel Form of the handle's runs (binary64, binary32 staged or direct)
+int f32_form(parrep_t h);
 int run_params(parrep_t h, double T_end, uint64_t seed, const Plan& pl, RunParams& p);
 int run_finish(parrep_t h, const RunCtl& c, double T_end, const Plan& pl, float ms);
 // the statistics a control block holds (launch shape and timing left zero)

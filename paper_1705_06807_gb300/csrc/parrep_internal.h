@@ -25,6 +25,9 @@ constexpr unsigned long long kNone = ~0ull;
 
 // Largest block of the run kernels (their register budget is set for it).
 constexpr int kMaxThreads = 384;
+// binary32 direct form: threads per block and blocks per SM it is built for
+constexpr int kDirectThreads = 256;
+constexpr int kDirectMinBlocks = 3;
 
 // Network as the kernels see it (Sec. II.A).  Schloegl: lambda_j = A[j] h_j(x)
 // with A[j] = c_j s_j.  Toggle: production rates come from host-built tables
@@ -102,9 +105,15 @@ struct BatchDev {
     int pad;
 };
 
+// Kernel forms: binary64 (one thread per replica), binary32 staged (owner
+// threads + helper warps per block, for few replicas per SM), binary32 direct
+// (one thread per replica at high occupancy, for many replicas).
+enum Form { kFormF64 = 0, kFormF32Staged = 1, kFormF32Direct = 2 };
+
 struct RunParams {
     NetDev net;
     int prec, thresh;
+    int form;      // Form of the kernel that runs this instance
     int R, G, S;
     int use_smem_hist;
     // block layout: the first RB threads of a block own replicas (RB = blockDim.x
@@ -172,15 +181,16 @@ struct ServeDev {
 };
 
 // ---- launchers (parrep_kernels.cu) ----
-int kernel_attrs(int prec, int kind, int* max_blocks_per_sm, int smem_bytes, int threads);
+// (form: Form; the run kernel's is taken from p.form)
+int kernel_attrs_form(int form, int kind, int* max_blocks_per_sm, int smem_bytes, int threads);
 cudaError_t launch_run(const RunParams& p, int grid, int threads, int smem_bytes, cudaStream_t st);
-int batch_kernel_attrs(int prec, int* max_blocks_per_sm, int smem_bytes, int threads);
+int batch_attrs_form(int form, int* max_blocks_per_sm, int smem_bytes, int threads);
 // zeroes the instances' control blocks and histograms, then launches the batch kernel
-cudaError_t launch_batch(int prec, const RunParams* d_params, int n, const int* d_off, const int2* d_items,
+cudaError_t launch_batch(int form, const RunParams* d_params, int n, const int* d_off, const int2* d_items,
                          BatchDev bd, int grid, int threads, int smem_bytes, cudaStream_t st);
 cudaError_t launch_batch_gather(const RunParams* d_params, int n, RunCtl* out, cudaStream_t st);
-int serve_kernel_attrs(int prec, int* max_blocks_per_sm, int smem_bytes, int threads);
-cudaError_t launch_serve(int prec, const ServeDev& sd, int grid, int threads, int smem_bytes, cudaStream_t st);
+int serve_attrs_form(int form, int* max_blocks_per_sm, int smem_bytes, int threads);
+cudaError_t launch_serve(int form, const ServeDev& sd, int grid, int threads, int smem_bytes, cudaStream_t st);
 cudaError_t launch_dephase(const RunParams& p, int xt0, int xt1, int W, unsigned cycle, long long np,
                            int* out_states, int grid, int threads, cudaStream_t st);
 cudaError_t launch_hist_normalise(const unsigned long long* pre, const unsigned long long* post, int n, double scale,

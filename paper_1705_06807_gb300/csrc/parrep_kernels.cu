@@ -18,10 +18,11 @@
 // Every wait on another block is bounded by a no-progress timeout and turns
 // into PARREP_ETIMEOUT instead of a hang.
 //
-// The file is compiled once per part (-DPARREP_PART=0..6) so that the
+// The file is compiled once per part (-DPARREP_PART=0..9) so that the
 // persistent kernels, each of which inlines the whole of Algorithm 1, build
-// in parallel: part 0 holds the small kernels and the dispatchers, parts 1-6
-// instantiate the run, batch and serve kernels in binary64 and binary32.
+// in parallel: part 0 holds the small kernels and the dispatchers, parts 1-9
+// instantiate the run, batch and serve kernels in each form (binary64,
+// binary32 staged, binary32 direct).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -249,7 +250,32 @@ __device__ __forceinline__ uint4 decorr_words(unsigned long long step, unsigned 
 // steps: words 0,1 for the even and 2,3 for the odd step).
 template <bool F32, bool WANT_TAU>
 __device__ __forceinline__ int ssa_draw(const NetDev& N, int x0, int x1, uint4 w, unsigned long long& q) {
-    if (F32) {
+    if (F32 && N.kind == PARREP_GENETIC) {
+        // six channels in binary32: F(p), G(p) from the binary32 tables
+        const float xi = (float)(x0 & 1), m = (float)(x0 >> 1);
+        float l[6];
+        l[0] = N.Af[0] * xi;
+        l[1] = N.Af[1] * m;
+        l[2] = N.Af[2] * m;
+        l[3] = (float)x1;
+        l[4] = __ldg(N.prodU_f + x1) * (1.0f - xi);
+        l[5] = __ldg(N.prodV_f + x1) * xi;
+        const float a0 = ((((l[0] + l[1]) + l[2]) + l[3]) + l[4]) + l[5];
+        if (WANT_TAU) q = q_of_f32(-logf(u01f(w.x)) * __frcp_rn(a0));
+        const float t = u01f(w.y) * a0;
+        float cum = l[0];
+        if (cum > t) return 0;
+#pragma unroll
+        for (int j = 1; j < 6; ++j) {
+            cum = cum + l[j];
+            if (cum > t) return j;
+        }
+        int J = 0;
+#pragma unroll
+        for (int j = 0; j < 6; ++j)
+            if (l[j] > 0.0f) J = j;
+        return J;
+    } else if (F32) {
         float l0, l1, l2, l3;
         props_f(N, x0, x1, l0, l1, l2, l3);
         float a0 = ((l0 + l1) + l2) + l3;
@@ -562,14 +588,18 @@ static __device__ int dephase_warp(const NetDev& N, bool active, unsigned r, int
     x1 = xt1;
     if (act == 0) return 0;
     const unsigned gm = (G >= 32) ? 0xffffffffu : (((1u << G) - 1u) << ((lane / G) * G));
+    uint4 w4 = make_uint4(0u, 0u, 0u, 0u);
     for (long long i = 0; i < np; ++i) {
         int n0 = x0, n1 = x1;
         bool ex = false, bad = false;
         if (active) {
-            uint4 w = philox10(make_uint4(r, F32 ? (unsigned)(i >> 2) : (unsigned)i, cycle, kTagDephase), key);
-            if (F32) {
-                const unsigned wi = (i & 3) == 0 ? w.x : (i & 3) == 1 ? w.y : (i & 3) == 2 ? w.z : w.w;
+            uint4 w;
+            if (F32) {  // one Philox call per four jumps, word i mod 4
+                if ((i & 3) == 0) w4 = philox10(make_uint4(r, (unsigned)(i >> 2), cycle, kTagDephase), key);
+                const unsigned wi = (i & 3) == 0 ? w4.x : (i & 3) == 1 ? w4.y : (i & 3) == 2 ? w4.z : w4.w;
                 w = make_uint4(0u, wi, 0u, 0u);
+            } else {
+                w = philox10(make_uint4(r, (unsigned)i, cycle, kTagDephase), key);
             }
             unsigned long long q;
             const int J = ssa_draw<F32, false>(N, x0, x1, w, q);
@@ -690,10 +720,18 @@ static __device__ void replay_chunk(const RunParams& P, const HistSink& hs, int 
                              unsigned long long& inc_q, unsigned long long& inc_ev, unsigned long long& ev) {
     const NetDev& N = P.net;
     const uint2 key = seed_key(P.seed);
+    uint4 wp = make_uint4(0u, 0u, 0u, 0u);
     for (int s = 0; s < S; ++s) {
         const unsigned long long pos = pos_of(s, r);
         if (MODE != kRollback && pos > cut.posC) break;
-        const uint4 w = par_words<F32>(r, n0 + (unsigned)s, cycle, key);
+        const unsigned n = n0 + (unsigned)s;
+        uint4 w;
+        if (F32) {  // one Philox call per step pair (n0 is even)
+            if ((n & 1u) == 0u) wp = philox10(make_uint4(r, n >> 1, cycle, kTagParallel), key);
+            w = (n & 1u) ? make_uint4(wp.z, wp.w, 0u, 0u) : wp;
+        } else {
+            w = par_words<F32>(r, n, cycle, key);
+        }
         unsigned long long q = 0;
         const int J = ssa_draw<F32, true>(N, x0, x1, w, q);
         ++ev;
@@ -1830,7 +1868,7 @@ static __device__ void decorrelate_f32(const RunParams& P, const FastSmem& F, co
 // ---------------------------------------------------------------------------
 // A replay pass (MODE) of the current chunk over this block's virtual
 // blocks, each replica from its chunk-start state P.xk.
-template <bool F32, int KIND, int MODE>
+template <int FORM, int KIND, int MODE>
 __device__ __forceinline__ void replay_vblocks(const RunParams& P, const FastSmem& F, const HistSink& hs, int lb,
                                                int nblk, int nvb, const RegionTest& rt, unsigned cycle, unsigned n0, int S,
                                                uint2 key,
@@ -1850,13 +1888,13 @@ __device__ __forceinline__ void replay_vblocks(const RunParams& P, const FastSme
         unsigned long long d0 = 0, d1 = 0;
         unsigned long long& q = MODE == kPrecise ? *inc_q : d0;
         unsigned long long& e = MODE == kPrecise ? *inc_ev : d1;
-        if (F32) {
+        if (FORM == kFormF32Staged) {
             unsigned long long k0 = kNone, k1 = kNone;
             int e0 = 0, e1 = 0;
             chunk_f32<KIND, MODE>(P, F, hs, active, rbase, r, rt, cycle, n0, S, key, y0, y1, cut, to_post, k0, k1, e0,
                                   e1, q, ev_replay, e, pc);
         } else if (active) {
-            replay_chunk<F32, MODE>(P, hs, y0, y1, r, rt.W, cycle, n0, S, cut, to_post, q, e, ev_replay);
+            replay_chunk<FORM != kFormF64, MODE>(P, hs, y0, y1, r, rt.W, cycle, n0, S, cut, to_post, q, e, ev_replay);
         }
     }
 }
@@ -1937,9 +1975,11 @@ static __device__ bool wait_generation(const RunParams& P, RunCtl* ctl, unsigned
 // have more replicas than its blocks have owner threads.  Lockstep is logical:
 // each replica takes the same steps whatever block takes it and in whatever
 // order, so every result is independent of nblk.
-template <bool F32, int KIND>
+template <int FORM, int KIND>
 __device__ __forceinline__ bool run_instance(const RunParams& P, int lb, unsigned char* smem, BlockScratch& red,
                                              int join_gen = -1) {
+    constexpr bool F32 = FORM != kFormF64;           // binary32 propensities and selection
+    constexpr bool STAGED = FORM == kFormF32Staged;  // owner threads + helper warps
     RunCtl* ctl = P.ctl;
     const NetDev& N = P.net;
     const bool batch = P.batch.remaining != nullptr;
@@ -1955,7 +1995,7 @@ __device__ __forceinline__ bool run_instance(const RunParams& P, int lb, unsigne
     FastSmem F{};
     unsigned* limb_lo = nullptr;
     unsigned* limb_hi = nullptr;
-    if (F32) {
+    if (STAGED) {
         if (P.use_smem_hist) {
             limb_lo = (unsigned*)(smem + P.off_limbs);
             limb_hi = limb_lo + N.nbins;
@@ -2009,7 +2049,7 @@ __device__ __forceinline__ bool run_instance(const RunParams& P, int lb, unsigne
     }
     int period_post = P.q_Tburn == 0 ? 1 : 0;  // which global sums this block's histogram feeds
     HistSink hs{P.use_smem_hist ? sh_hist : nullptr, period_post ? P.hist_post : P.hist_pre, limb_lo, limb_hi,
-                N.ystride, F32 ? ((1ull << 47) >> (P.log2RB + 5)) : 0ull};
+                N.ystride, STAGED ? ((1ull << 47) >> (P.log2RB + 5)) : 0ull};
     unsigned long long chunk_c = 0;
     unsigned long long est_q = 0, est_ev = 0;  // time and jumps of the last chunk
     if (join) {
@@ -2036,7 +2076,7 @@ __device__ __forceinline__ bool run_instance(const RunParams& P, int lb, unsigne
         // (a block that joined at this cycle's start begins after it)
         if (!(join && first)) {
             pc.start();
-            if (F32) {
+            if (STAGED) {
                 if (lb == 0 && !ldv(&ctl->done))
                     decorrelate_f32<KIND>(P, F, hs, period_post, pc);
             } else {
@@ -2074,7 +2114,7 @@ __device__ __forceinline__ bool run_instance(const RunParams& P, int lb, unsigne
                     const unsigned rbase = (unsigned)vb * (unsigned)P.RB, r = rbase + threadIdx.x;
                     const bool active = owner && (long long)r < (long long)P.R;
                     int x0, x1;
-                    if (F32) derr |= dephase_f32<KIND>(P, F, rt, active, rbase, r, xt0, xt1, np, cycle, key, x0, x1);
+                    if (STAGED) derr |= dephase_f32<KIND>(P, F, rt, active, rbase, r, xt0, xt1, np, cycle, key, x0, x1);
                     else derr |= dephase_warp<F32>(N, active, r, P.G, W, xt0, xt1, np, cycle, key, x0, x1);
                     if (active) P.xs[r] = make_int2(x0, x1);
                     __syncwarp();
@@ -2099,7 +2139,7 @@ __device__ __forceinline__ bool run_instance(const RunParams& P, int lb, unsigne
                 // depend on where chunks end.
                 int Sc = P.S;
                 {
-                    const int unit = F32 ? P.B : 32;
+                    const int unit = STAGED ? P.B : 32;
                     if (grow < 30 && ((long long)unit << grow) < (long long)Sc) Sc = unit << grow;
                     const unsigned long long q_lim = burn_done ? P.q_Tend : P.q_Tburn;
                     if (est_ev > 0 && est_q > 0 && q_lim > Ts) {
@@ -2141,13 +2181,22 @@ __device__ __forceinline__ bool run_instance(const RunParams& P, int lb, unsigne
                         P.xk[r] = xv;
                     }
                     unsigned long long k0 = kNone, k1 = kNone;
-                    if (F32) {
+                    if (STAGED) {
                         unsigned long long dummy = 0;
                         chunk_f32<KIND, kFirst>(P, F, hs, active, rbase, r, rt, cycle, n0, Sc, key, x0, x1, none,
                                                 period_post, k0, k1, xe0, xe1, qsum, ev, dummy, pc);
                     } else if (active) {
+                        uint4 wp = make_uint4(0u, 0u, 0u, 0u);
                         for (int s = 0; s < Sc; ++s) {
-                            const uint4 w = par_words<F32>(r, n0 + (unsigned)s, cycle, key);
+                            // binary32: one Philox call per step pair (n0 is even)
+                            const unsigned n = n0 + (unsigned)s;
+                            uint4 w;
+                            if (F32) {
+                                if ((n & 1u) == 0u) wp = philox10(make_uint4(r, n >> 1, cycle, kTagParallel), key);
+                                w = (n & 1u) ? make_uint4(wp.z, wp.w, 0u, 0u) : wp;
+                            } else {
+                                w = par_words<F32>(r, n, cycle, key);
+                            }
                             unsigned long long q = 0;
                             const int J = ssa_draw<F32, true>(N, x0, x1, w, q);
                             qsum += q;
@@ -2218,7 +2267,7 @@ __device__ __forceinline__ bool run_instance(const RunParams& P, int lb, unsigne
                 if (leader) ctl->special += 1;
                 __syncwarp();
                 pc.start();
-                replay_vblocks<F32, KIND, kRollback>(P, F, hs, lb, nblk, nvb, rt, cycle, n0, Sc, key, none, period_post,
+                replay_vblocks<FORM, KIND, kRollback>(P, F, hs, lb, nblk, nvb, rt, cycle, n0, Sc, key, none, period_post,
                                                      ev_replay, pc);
                 Cuts cut{kNone, kNone, kNone, 0, kNone, 0, -1, -1};
                 cut.posE = ekey;
@@ -2229,7 +2278,7 @@ __device__ __forceinline__ bool run_instance(const RunParams& P, int lb, unsigne
                         for (int j = threadIdx.x; j < Sc; j += blockDim.x) P.step_sum[j] = 0;
                     }
                     if (!grid_sync(P, bs)) goto out;
-                    replay_vblocks<F32, KIND, kStepSum>(P, F, hs, lb, nblk, nvb, rt, cycle, n0, Sc, key, cut, period_post,
+                    replay_vblocks<FORM, KIND, kStepSum>(P, F, hs, lb, nblk, nvb, rt, cycle, n0, Sc, key, cut, period_post,
                                                         ev_replay, pc);
                     if (!grid_sync(P, bs)) goto out;
                     unsigned long long baseB = 0, baseT = 0;
@@ -2256,7 +2305,7 @@ __device__ __forceinline__ bool run_instance(const RunParams& P, int lb, unsigne
                                 P.tau_at[P.R + r] = 0;
                             }
                         }
-                        replay_vblocks<F32, KIND, kTauAt>(P, F, hs, lb, nblk, nvb, rt, cycle, n0, Sc, key, cut, period_post,
+                        replay_vblocks<FORM, KIND, kTauAt>(P, F, hs, lb, nblk, nvb, rt, cycle, n0, Sc, key, cut, period_post,
                                                           ev_replay, pc);
                         if (!grid_sync(P, bs)) goto out;
                         if (leader) {
@@ -2310,7 +2359,7 @@ __device__ __forceinline__ bool run_instance(const RunParams& P, int lb, unsigne
                 {
                     unsigned long long inc_q = 0, inc_ev = 0;
                     const bool tp = period_post || cut.posB != kNone;
-                    replay_vblocks<F32, KIND, kPrecise>(P, F, hs, lb, nblk, nvb, rt, cycle, n0, Sc, key, cut, tp, ev_replay,
+                    replay_vblocks<FORM, KIND, kPrecise>(P, F, hs, lb, nblk, nvb, rt, cycle, n0, Sc, key, cut, tp, ev_replay,
                                                         pc, &inc_q, &inc_ev);
                     unsigned long long a = kNone, b = kNone;
                     block_reduce4(red, a, b, inc_q, inc_ev);
@@ -2395,11 +2444,18 @@ out:
 }
 
 // One instance on the whole grid.
-template <bool F32, int KIND>
-__global__ void __launch_bounds__(kMaxThreads) parrep_run_kernel(RunParams P) {
+// Launch bounds per form: the binary32 direct form runs kDirectThreads
+// threads per block with kDirectMinBlocks blocks per SM (one thread per
+// replica at high occupancy); the others up to kMaxThreads with one block.
+#define PARREP_BOUNDS(FORM) \
+    __launch_bounds__((FORM) == kFormF32Direct ? kDirectThreads : kMaxThreads, \
+                      (FORM) == kFormF32Direct ? kDirectMinBlocks : 1)
+
+template <int FORM, int KIND>
+__global__ void PARREP_BOUNDS(FORM) parrep_run_kernel(RunParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ BlockScratch red;
-    run_instance<F32, KIND>(P, (int)blockIdx.x, smem, red);
+    run_instance<FORM, KIND>(P, (int)blockIdx.x, smem, red);
 }
 
 // Many instances in one persistent launch.  Block b works through its list
@@ -2411,20 +2467,20 @@ __global__ void __launch_bounds__(kMaxThreads) parrep_run_kernel(RunParams P) {
 // bit in bd.idle and waits (bounded, on the batch's progress) for a mailbox
 // entry from an instance that recruits it at a cycle start, until no
 // instance is left.  Both network kinds run in the same launch.
-template <bool F32>
+template <int FORM>
 __device__ __forceinline__ void batch_item(const RunParams* Ps, RunParams& sP, int inst, int lb, int join_gen,
                                            unsigned char* smem, BlockScratch& red) {
     const int* src = (const int*)(Ps + inst);
     int* dst = (int*)&sP;
     for (int w = threadIdx.x; w < (int)(sizeof(RunParams) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
     __syncthreads();
-    if (sP.net.kind == PARREP_SCHLOGL) run_instance<F32, PARREP_SCHLOGL>(sP, lb, smem, red, join_gen);
-    else run_instance<F32, PARREP_TOGGLE>(sP, lb, smem, red, join_gen);
+    if (sP.net.kind == PARREP_SCHLOGL) run_instance<FORM, PARREP_SCHLOGL>(sP, lb, smem, red, join_gen);
+    else run_instance<FORM, PARREP_TOGGLE>(sP, lb, smem, red, join_gen);
     __syncthreads();
 }
 
-template <bool F32>
-__global__ void __launch_bounds__(kMaxThreads)
+template <int FORM>
+__global__ void PARREP_BOUNDS(FORM)
     parrep_batch_kernel(const RunParams* __restrict__ Ps, const int* __restrict__ off,
                         const int2* __restrict__ items, BatchDev bd) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -2434,7 +2490,7 @@ __global__ void __launch_bounds__(kMaxThreads)
     const int k1 = off[blockIdx.x + 1];
     for (int k = off[blockIdx.x]; k < k1; ++k) {
         const int2 it = items[k];
-        batch_item<F32>(Ps, sP, it.x, it.y, -1, smem, red);
+        batch_item<FORM>(Ps, sP, it.x, it.y, -1, smem, red);
     }
     // idle: offer this block to instances that start a cycle
     const unsigned long long* progress = Ps[0].progress;
@@ -2488,7 +2544,7 @@ __global__ void __launch_bounds__(kMaxThreads)
         const int4 m = s_mail;
         __syncthreads();
         if (m.x < 0) break;
-        batch_item<F32>(Ps, sP, m.x, m.y, m.z, smem, red);
+        batch_item<FORM>(Ps, sP, m.x, m.y, m.z, smem, red);
     }
 }
 
@@ -2600,8 +2656,8 @@ static __device__ void serve_epilogue(const RunParams& P, const ServeSlot* slot,
     if (threadIdx.x == 0) st_release_sys(done, 1);
 }
 
-template <bool F32>
-__global__ void __launch_bounds__(kMaxThreads) parrep_serve_kernel(ServeDev sd) {
+template <int FORM>
+__global__ void PARREP_BOUNDS(FORM) parrep_serve_kernel(ServeDev sd) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ BlockScratch red;
     __shared__ RunParams sP;
@@ -2632,8 +2688,8 @@ __global__ void __launch_bounds__(kMaxThreads) parrep_serve_kernel(ServeDev sd) 
         }
         const int join_gen = cmd.w == 2 ? cmd.z : -1;
         const bool last = sP.net.kind == PARREP_SCHLOGL
-                              ? run_instance<F32, PARREP_SCHLOGL>(sP, cmd.y, smem, red, join_gen)
-                              : run_instance<F32, PARREP_TOGGLE>(sP, cmd.y, smem, red, join_gen);
+                              ? run_instance<FORM, PARREP_SCHLOGL>(sP, cmd.y, smem, red, join_gen)
+                              : run_instance<FORM, PARREP_TOGGLE>(sP, cmd.y, smem, red, join_gen);
         if (last) {
             serve_epilogue(sP, slot, sd.done + cmd.x);
             if (threadIdx.x == 0) atomicAdd(sd.finished, 1ull);
@@ -3120,20 +3176,14 @@ __global__ void philox_kernel(const uint4* ctr, const uint2* key, long long n, u
 // ---------------------------------------------------------------------------
 // launchers (one precision and one kernel family per part)
 // ---------------------------------------------------------------------------
-int kernel_attrs_f64(int kind, int* max_blocks_per_sm, int smem_bytes, int threads);
-int kernel_attrs_f32(int kind, int* max_blocks_per_sm, int smem_bytes, int threads);
-cudaError_t launch_run_f64(const RunParams& p, int grid, int threads, int smem_bytes, cudaStream_t st);
-cudaError_t launch_run_f32(const RunParams& p, int grid, int threads, int smem_bytes, cudaStream_t st);
-int batch_attrs_f64(int* max_blocks_per_sm, int smem_bytes, int threads);
-int batch_attrs_f32(int* max_blocks_per_sm, int smem_bytes, int threads);
-cudaError_t launch_batch_f64(const cudaLaunchConfig_t& cfg, const RunParams* d_params, const int* d_off,
-                             const int2* d_items, BatchDev bd);
-cudaError_t launch_batch_f32(const cudaLaunchConfig_t& cfg, const RunParams* d_params, const int* d_off,
-                             const int2* d_items, BatchDev bd);
-int serve_attrs_f64(int* max_blocks_per_sm, int smem_bytes, int threads);
-int serve_attrs_f32(int* max_blocks_per_sm, int smem_bytes, int threads);
-cudaError_t launch_serve_f64(const ServeDev& sd, int grid, int threads, int smem_bytes, cudaStream_t st);
-cudaError_t launch_serve_f32(const ServeDev& sd, int grid, int threads, int smem_bytes, cudaStream_t st);
+// per form (0 = binary64, 1 = binary32 staged, 2 = binary32 direct)
+int kernel_attrs_form(int form, int kind, int* max_blocks_per_sm, int smem_bytes, int threads);
+cudaError_t launch_run_form(const RunParams& p, int grid, int threads, int smem_bytes, cudaStream_t st);
+int batch_attrs_form(int form, int* max_blocks_per_sm, int smem_bytes, int threads);
+cudaError_t launch_batch_form(int form, const cudaLaunchConfig_t& cfg, const RunParams* d_params, const int* d_off,
+                              const int2* d_items, BatchDev bd);
+int serve_attrs_form(int form, int* max_blocks_per_sm, int smem_bytes, int threads);
+cudaError_t launch_serve_form(int form, const ServeDev& sd, int grid, int threads, int smem_bytes, cudaStream_t st);
 
 template <typename K>
 static int attrs_of(K kernel, int* max_blocks_per_sm, int smem_bytes, int threads) {
@@ -3142,83 +3192,123 @@ static int attrs_of(K kernel, int* max_blocks_per_sm, int smem_bytes, int thread
     return (int)e;
 }
 
-#if PARREP_PART == 1 || PARREP_PART == 2
-#if PARREP_PART == 1
-#define PARREP_F32 false
-#define PARREP_SFX(name) name##_f64
-#else
-#define PARREP_F32 true
-#define PARREP_SFX(name) name##_f32
+// parts 1-3: the run kernels, parts 4-6: the batch kernels, parts 7-9: the
+// serve kernels, each in binary64, binary32 staged and binary32 direct form
+#if PARREP_PART >= 1 && PARREP_PART <= 9
+constexpr int kPartForm = (PARREP_PART - 1) % 3;
 #endif
+
+#if PARREP_PART >= 1 && PARREP_PART <= 3
 // The genetic switch runs in the two-species instantiation (its channels are
 // chosen by N.kind inside).
-int PARREP_SFX(kernel_attrs)(int kind, int* max_blocks_per_sm, int smem_bytes, int threads) {
+static int run_attrs_here(int kind, int* max_blocks_per_sm, int smem_bytes, int threads) {
     return kind == PARREP_SCHLOGL
-               ? attrs_of(parrep_run_kernel<PARREP_F32, PARREP_SCHLOGL>, max_blocks_per_sm, smem_bytes, threads)
-               : attrs_of(parrep_run_kernel<PARREP_F32, PARREP_TOGGLE>, max_blocks_per_sm, smem_bytes, threads);
+               ? attrs_of(parrep_run_kernel<kPartForm, PARREP_SCHLOGL>, max_blocks_per_sm, smem_bytes, threads)
+               : attrs_of(parrep_run_kernel<kPartForm, PARREP_TOGGLE>, max_blocks_per_sm, smem_bytes, threads);
 }
-
-cudaError_t PARREP_SFX(launch_run)(const RunParams& p, int grid, int threads, int smem_bytes, cudaStream_t st) {
+static cudaError_t run_launch_here(const RunParams& p, int grid, int threads, int smem_bytes, cudaStream_t st) {
     void* args[] = {(void*)&p};
-    void* fn = p.net.kind == PARREP_SCHLOGL ? (void*)parrep_run_kernel<PARREP_F32, PARREP_SCHLOGL>
-                                            : (void*)parrep_run_kernel<PARREP_F32, PARREP_TOGGLE>;
+    void* fn = p.net.kind == PARREP_SCHLOGL ? (void*)parrep_run_kernel<kPartForm, PARREP_SCHLOGL>
+                                            : (void*)parrep_run_kernel<kPartForm, PARREP_TOGGLE>;
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(threads), args, (size_t)smem_bytes, st);
 }
-#endif
-
-#if PARREP_PART == 3 || PARREP_PART == 4
-#if PARREP_PART == 3
-#define PARREP_F32 false
-#define PARREP_SFX(name) name##_f64
+#if PARREP_PART == 1
+int run_attrs_f64(int kind, int* m, int s, int t) { return run_attrs_here(kind, m, s, t); }
+cudaError_t run_launch_f64(const RunParams& p, int g, int t, int s, cudaStream_t st) { return run_launch_here(p, g, t, s, st); }
+#elif PARREP_PART == 2
+int run_attrs_f32s(int kind, int* m, int s, int t) { return run_attrs_here(kind, m, s, t); }
+cudaError_t run_launch_f32s(const RunParams& p, int g, int t, int s, cudaStream_t st) { return run_launch_here(p, g, t, s, st); }
 #else
-#define PARREP_F32 true
-#define PARREP_SFX(name) name##_f32
+int run_attrs_f32d(int kind, int* m, int s, int t) { return run_attrs_here(kind, m, s, t); }
+cudaError_t run_launch_f32d(const RunParams& p, int g, int t, int s, cudaStream_t st) { return run_launch_here(p, g, t, s, st); }
 #endif
-int PARREP_SFX(batch_attrs)(int* max_blocks_per_sm, int smem_bytes, int threads) {
-    return attrs_of(parrep_batch_kernel<PARREP_F32>, max_blocks_per_sm, smem_bytes, threads);
-}
+#endif
 
-cudaError_t PARREP_SFX(launch_batch)(const cudaLaunchConfig_t& cfg, const RunParams* d_params, const int* d_off,
+#if PARREP_PART >= 4 && PARREP_PART <= 6
+static int batch_attrs_here(int* max_blocks_per_sm, int smem_bytes, int threads) {
+    return attrs_of(parrep_batch_kernel<kPartForm>, max_blocks_per_sm, smem_bytes, threads);
+}
+static cudaError_t batch_launch_here(const cudaLaunchConfig_t& cfg, const RunParams* d_params, const int* d_off,
                                      const int2* d_items, BatchDev bd) {
-    return cudaLaunchKernelEx(&cfg, parrep_batch_kernel<PARREP_F32>, d_params, d_off, d_items, bd);
+    return cudaLaunchKernelEx(&cfg, parrep_batch_kernel<kPartForm>, d_params, d_off, d_items, bd);
 }
-#endif
-
-#if PARREP_PART == 5 || PARREP_PART == 6
-#if PARREP_PART == 5
-#define PARREP_F32 false
-#define PARREP_SFX(name) name##_f64
+#if PARREP_PART == 4
+int batch_attrs_f64(int* m, int s, int t) { return batch_attrs_here(m, s, t); }
+cudaError_t batch_launch_f64(const cudaLaunchConfig_t& c, const RunParams* p, const int* o, const int2* i, BatchDev b) {
+    return batch_launch_here(c, p, o, i, b);
+}
+#elif PARREP_PART == 5
+int batch_attrs_f32s(int* m, int s, int t) { return batch_attrs_here(m, s, t); }
+cudaError_t batch_launch_f32s(const cudaLaunchConfig_t& c, const RunParams* p, const int* o, const int2* i, BatchDev b) {
+    return batch_launch_here(c, p, o, i, b);
+}
 #else
-#define PARREP_F32 true
-#define PARREP_SFX(name) name##_f32
-#endif
-int PARREP_SFX(serve_attrs)(int* max_blocks_per_sm, int smem_bytes, int threads) {
-    return attrs_of(parrep_serve_kernel<PARREP_F32>, max_blocks_per_sm, smem_bytes, threads);
+int batch_attrs_f32d(int* m, int s, int t) { return batch_attrs_here(m, s, t); }
+cudaError_t batch_launch_f32d(const cudaLaunchConfig_t& c, const RunParams* p, const int* o, const int2* i, BatchDev b) {
+    return batch_launch_here(c, p, o, i, b);
 }
+#endif
+#endif
 
-cudaError_t PARREP_SFX(launch_serve)(const ServeDev& sd, int grid, int threads, int smem_bytes, cudaStream_t st) {
-    parrep_serve_kernel<PARREP_F32><<<grid, threads, smem_bytes, st>>>(sd);
+#if PARREP_PART >= 7 && PARREP_PART <= 9
+static int serve_attrs_here(int* max_blocks_per_sm, int smem_bytes, int threads) {
+    return attrs_of(parrep_serve_kernel<kPartForm>, max_blocks_per_sm, smem_bytes, threads);
+}
+static cudaError_t serve_launch_here(const ServeDev& sd, int grid, int threads, int smem_bytes, cudaStream_t st) {
+    parrep_serve_kernel<kPartForm><<<grid, threads, smem_bytes, st>>>(sd);
     return cudaGetLastError();
 }
+#if PARREP_PART == 7
+int serve_attrs_f64(int* m, int s, int t) { return serve_attrs_here(m, s, t); }
+cudaError_t serve_launch_f64(const ServeDev& d, int g, int t, int s, cudaStream_t st) { return serve_launch_here(d, g, t, s, st); }
+#elif PARREP_PART == 8
+int serve_attrs_f32s(int* m, int s, int t) { return serve_attrs_here(m, s, t); }
+cudaError_t serve_launch_f32s(const ServeDev& d, int g, int t, int s, cudaStream_t st) { return serve_launch_here(d, g, t, s, st); }
+#else
+int serve_attrs_f32d(int* m, int s, int t) { return serve_attrs_here(m, s, t); }
+cudaError_t serve_launch_f32d(const ServeDev& d, int g, int t, int s, cudaStream_t st) { return serve_launch_here(d, g, t, s, st); }
+#endif
 #endif
 
 #if PARREP_PART == 0
-int kernel_attrs(int prec, int kind, int* max_blocks_per_sm, int smem_bytes, int threads) {
-    return prec == PARREP_FP32 ? kernel_attrs_f32(kind, max_blocks_per_sm, smem_bytes, threads)
-                               : kernel_attrs_f64(kind, max_blocks_per_sm, smem_bytes, threads);
+int run_attrs_f64(int, int*, int, int);
+int run_attrs_f32s(int, int*, int, int);
+int run_attrs_f32d(int, int*, int, int);
+cudaError_t run_launch_f64(const RunParams&, int, int, int, cudaStream_t);
+cudaError_t run_launch_f32s(const RunParams&, int, int, int, cudaStream_t);
+cudaError_t run_launch_f32d(const RunParams&, int, int, int, cudaStream_t);
+int batch_attrs_f64(int*, int, int);
+int batch_attrs_f32s(int*, int, int);
+int batch_attrs_f32d(int*, int, int);
+cudaError_t batch_launch_f64(const cudaLaunchConfig_t&, const RunParams*, const int*, const int2*, BatchDev);
+cudaError_t batch_launch_f32s(const cudaLaunchConfig_t&, const RunParams*, const int*, const int2*, BatchDev);
+cudaError_t batch_launch_f32d(const cudaLaunchConfig_t&, const RunParams*, const int*, const int2*, BatchDev);
+int serve_attrs_f64(int*, int, int);
+int serve_attrs_f32s(int*, int, int);
+int serve_attrs_f32d(int*, int, int);
+cudaError_t serve_launch_f64(const ServeDev&, int, int, int, cudaStream_t);
+cudaError_t serve_launch_f32s(const ServeDev&, int, int, int, cudaStream_t);
+cudaError_t serve_launch_f32d(const ServeDev&, int, int, int, cudaStream_t);
+
+int kernel_attrs_form(int form, int kind, int* m, int s, int t) {
+    return form == kFormF32Direct ? run_attrs_f32d(kind, m, s, t)
+           : form == kFormF32Staged ? run_attrs_f32s(kind, m, s, t)
+                                    : run_attrs_f64(kind, m, s, t);
 }
 
 cudaError_t launch_run(const RunParams& p, int grid, int threads, int smem_bytes, cudaStream_t st) {
-    return p.prec == PARREP_FP32 ? launch_run_f32(p, grid, threads, smem_bytes, st)
-                                 : launch_run_f64(p, grid, threads, smem_bytes, st);
+    return p.form == kFormF32Direct ? run_launch_f32d(p, grid, threads, smem_bytes, st)
+           : p.form == kFormF32Staged ? run_launch_f32s(p, grid, threads, smem_bytes, st)
+                                      : run_launch_f64(p, grid, threads, smem_bytes, st);
 }
 
-int batch_kernel_attrs(int prec, int* max_blocks_per_sm, int smem_bytes, int threads) {
-    return prec == PARREP_FP32 ? batch_attrs_f32(max_blocks_per_sm, smem_bytes, threads)
-                               : batch_attrs_f64(max_blocks_per_sm, smem_bytes, threads);
+int batch_attrs_form(int form, int* m, int s, int t) {
+    return form == kFormF32Direct ? batch_attrs_f32d(m, s, t)
+           : form == kFormF32Staged ? batch_attrs_f32s(m, s, t)
+                                    : batch_attrs_f64(m, s, t);
 }
 
-cudaError_t launch_batch(int prec, const RunParams* d_params, int n, const int* d_off, const int2* d_items,
+cudaError_t launch_batch(int form, const RunParams* d_params, int n, const int* d_off, const int2* d_items,
                          BatchDev bd, int grid, int threads, int smem_bytes, cudaStream_t st) {
     if (n < 1) return cudaSuccess;
     batch_reset_kernel<<<n, 256, 0, st>>>(d_params, n, bd, grid);
@@ -3234,8 +3324,9 @@ cudaError_t launch_batch(int prec, const RunParams* d_params, int n, const int* 
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return prec == PARREP_FP32 ? launch_batch_f32(cfg, d_params, d_off, d_items, bd)
-                               : launch_batch_f64(cfg, d_params, d_off, d_items, bd);
+    return form == kFormF32Direct ? batch_launch_f32d(cfg, d_params, d_off, d_items, bd)
+           : form == kFormF32Staged ? batch_launch_f32s(cfg, d_params, d_off, d_items, bd)
+                                    : batch_launch_f64(cfg, d_params, d_off, d_items, bd);
 }
 
 cudaError_t launch_batch_gather(const RunParams* d_params, int n, RunCtl* out, cudaStream_t st) {
@@ -3244,15 +3335,18 @@ cudaError_t launch_batch_gather(const RunParams* d_params, int n, RunCtl* out, c
     return cudaGetLastError();
 }
 
-int serve_kernel_attrs(int prec, int* max_blocks_per_sm, int smem_bytes, int threads) {
-    return prec == PARREP_FP32 ? serve_attrs_f32(max_blocks_per_sm, smem_bytes, threads)
-                               : serve_attrs_f64(max_blocks_per_sm, smem_bytes, threads);
+int serve_attrs_form(int form, int* m, int s, int t) {
+    return form == kFormF32Direct ? serve_attrs_f32d(m, s, t)
+           : form == kFormF32Staged ? serve_attrs_f32s(m, s, t)
+                                    : serve_attrs_f64(m, s, t);
 }
 
-cudaError_t launch_serve(int prec, const ServeDev& sd, int grid, int threads, int smem_bytes, cudaStream_t st) {
-    return prec == PARREP_FP32 ? launch_serve_f32(sd, grid, threads, smem_bytes, st)
-                               : launch_serve_f64(sd, grid, threads, smem_bytes, st);
+cudaError_t launch_serve(int form, const ServeDev& sd, int grid, int threads, int smem_bytes, cudaStream_t st) {
+    return form == kFormF32Direct ? serve_launch_f32d(sd, grid, threads, smem_bytes, st)
+           : form == kFormF32Staged ? serve_launch_f32s(sd, grid, threads, smem_bytes, st)
+                                    : serve_launch_f64(sd, grid, threads, smem_bytes, st);
 }
+
 cudaError_t launch_dephase(const RunParams& p, int xt0, int xt1, int W, unsigned cycle, long long np,
                            int* out_states, int grid, int threads, cudaStream_t st) {
     int* status = &p.ctl->status;

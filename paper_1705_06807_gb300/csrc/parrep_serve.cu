@@ -100,6 +100,7 @@ struct Request {
 struct parrep_server_s {
     parrep_server_options opt{};
     int threads = 0, RB = 0, smem = 0, grid = 0;
+    int form = 0;  // kernel Form of the serve kernel
     char* d_arena = nullptr;
     Arena arena;
     // ring of requests in device memory, a host staging copy of one slot, and
@@ -146,6 +147,7 @@ extern "C" void parrep_server_default_options(parrep_server_options* o) {
     o->block_threads = 0;
     o->replicas_per_block = 0;
     o->ring = 4096;
+    o->f32_layout = PARREP_F32_STAGED;
     o->arena_bytes = 4ll << 30;
     o->log_cap = 4096;
     o->idle_exit_s = 0.05;
@@ -169,7 +171,8 @@ static size_t request_bytes(const parrep_request& r, int64_t log_cap) {
         const size_t nu = (size_t)r.net.hist_max[1] + 1, nv = (size_t)r.net.hist_max[0] + 1;
         b += 2 * (align256(nu * 8) + align256(nv * 8)) + align256(nu * 4) + align256(nv * 4);
     } else if (r.net.kind == PARREP_GENETIC) {
-        b += 2 * align256(((size_t)r.net.hist_max[1] + 1) * 8);  // F(p), G(p)
+        const size_t np = (size_t)r.net.hist_max[1] + 1;
+        b += 2 * align256(np * 8) + 2 * align256(np * 4);  // F(p), G(p) in binary64 and binary32
     }
     return b;
 }
@@ -241,15 +244,27 @@ static int admit(parrep_server_t s, Request& q, int slot) {
         d_gU = gUd;
         d_gV = gVd;
     } else if (r.net.kind == PARREP_GENETIC) {
-        // the switching rates F(p), G(p) as binary64 tables over p
+        // the switching rates F(p), G(p) as tables over p, in binary64 (the
+        // binary64 form and the FIM / RER) and binary32 (the binary32 form)
         const size_t np = pU.size();
         double* Fd = (double*)take(np * 8);
         double* Gd = (double*)take(np * 8);
+        float* Ff = (float*)take(np * 4);
+        float* Gf = (float*)take(np * 4);
+        std::vector<float> fF(np), fG(np);
+        for (size_t i = 0; i < np; ++i) {
+            fF[i] = (float)pU[i];
+            fG[i] = (float)pV[i];
+        }
         e = cudaMemcpyAsync(Fd, pU.data(), np * 8, cudaMemcpyHostToDevice, s->cp);
         if (e == cudaSuccess) e = cudaMemcpyAsync(Gd, pV.data(), np * 8, cudaMemcpyHostToDevice, s->cp);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(Ff, fF.data(), np * 4, cudaMemcpyHostToDevice, s->cp);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(Gf, fG.data(), np * 4, cudaMemcpyHostToDevice, s->cp);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s->cp);
         h.nd.prodU_d = Fd;
         h.nd.prodV_d = Gd;
+        h.nd.prodU_f = Ff;
+        h.nd.prodV_f = Gf;
     }
     // (the serve kernel's claiming block clears the control block and the
     // histograms: a memset here would be a kernel that waits for free SMs)
@@ -257,7 +272,8 @@ static int admit(parrep_server_t s, Request& q, int slot) {
     // launch shape of one gang member
     Plan pl;
     memset(&pl, 0, sizeof(pl));
-    if (s->opt.precision == PARREP_FP32) {
+    pl.form = s->form;
+    if (s->form == kFormF32Staged) {
         const int pipe = s->threads - s->RB >= 64;
         int sz = -1;
         for (int with_hist = 1; with_hist >= 0 && sz < 0; --with_hist) {
@@ -365,7 +381,7 @@ static void serve_pass(parrep_server_t s) {
         sd.bd = BatchDev{s->d_unused, s->d_idle, s->d_mail, s->tail, s->d_head, s->grid / 8, 0};
         sd.progress = s->d_progress;
         sd.idle_exit_ns = (long long)(s->opt.idle_exit_s * 1e9);
-        cudaError_t e = launch_serve(s->opt.precision, sd, s->grid, s->threads, s->smem, s->st);
+        cudaError_t e = launch_serve(s->form, sd, s->grid, s->threads, s->smem, s->st);
         if (e == cudaSuccess) e = cudaEventRecord(s->ev_end, s->st);
         if (e == cudaSuccess) {
             s->kernel_live = true;
@@ -416,18 +432,30 @@ extern "C" int parrep_server_create(const parrep_server_options* opt, parrep_ser
     if (!(o.idle_exit_s > 0.0 && o.idle_exit_s <= 60.0)) return sfail(nullptr, PARREP_EINVAL, "idle_exit_s");
     if (!(o.wait_timeout_s > 0.0 && o.wait_timeout_s <= 3600.0))
         return sfail(nullptr, PARREP_EINVAL, "wait_timeout_s");
-    const int threads = o.block_threads ? o.block_threads : (o.precision == PARREP_FP32 ? 384 : 128);
-    const int RB = o.precision == PARREP_FP32 ? (rb ? rb : 32) : threads;
+    if (o.f32_layout != PARREP_F32_AUTO && o.f32_layout != PARREP_F32_STAGED && o.f32_layout != PARREP_F32_DIRECT)
+        return sfail(nullptr, PARREP_EINVAL, "f32_layout");
+    // one form for every request: binary64, or binary32 staged (the default;
+    // auto means staged here) or direct
+    const int form = o.precision == PARREP_FP64 ? kFormF64
+                     : o.f32_layout == PARREP_F32_DIRECT ? kFormF32Direct
+                                                           : kFormF32Staged;
+    if (form == kFormF32Direct && o.block_threads > kDirectThreads)
+        return sfail(nullptr, PARREP_EINVAL, "the direct layout takes at most 256 threads per block");
+    const int threads = o.block_threads ? o.block_threads
+                                        : (form == kFormF32Staged ? 384 : form == kFormF32Direct ? kDirectThreads : 128);
+    const int RB = form == kFormF32Staged ? (rb ? rb : 32) : threads;
     if (threads < RB) return sfail(nullptr, PARREP_EINVAL, "block_threads < replicas_per_block");
     auto* s = new parrep_server_s();
     s->opt = o;
+    s->form = form;
     s->threads = threads;
     s->RB = RB;
-    s->smem = 200 * 1024;
+    // the direct layout keeps several blocks per SM: a smaller histogram slice
+    s->smem = form == kFormF32Direct ? 64 * 1024 : 200 * 1024;
     int nsm = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&s->dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s->dev);
-    if (e == cudaSuccess) e = (cudaError_t)serve_kernel_attrs(o.precision, &per_sm, s->smem, s->threads);
+    if (e == cudaSuccess) e = (cudaError_t)serve_attrs_form(form, &per_sm, s->smem, s->threads);
     if (e == cudaSuccess && per_sm < 1) {
         delete s;
         return sfail(nullptr, PARREP_ENOMEM, "the serve kernel does not fit on one SM");
@@ -479,8 +507,8 @@ extern "C" int parrep_server_submit(parrep_server_t s, const parrep_request* req
     if (!s || !req || !id) return PARREP_EINVAL;
     std::string why;
     if (!check_network(&req->net, &req->regions, why)) return sfail(s, PARREP_EINVAL, why);
-    if (req->net.kind == PARREP_GENETIC && s->opt.precision != PARREP_FP64)
-        return sfail(s, PARREP_EINVAL, "the genetic switch has the binary64 form only");
+    if (req->net.kind == PARREP_GENETIC && s->form == kFormF32Staged)
+        return sfail(s, PARREP_EINVAL, "the genetic switch's FP32 form needs the direct layout (f32_layout)");
     if (req->n_replicas < 1 || req->n_replicas > (1ll << 30)) return sfail(s, PARREP_EINVAL, "n_replicas");
     if (!(req->t_corr >= 0.0) || !(req->t_phase >= 0.0) || !(req->t_corr < kTEndLimit * 1024) ||
         !(req->t_phase < 1e12))

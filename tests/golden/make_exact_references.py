@@ -30,7 +30,7 @@ from oracle import exact as E  # noqa: E402
 from paper_1705_06807_gb300 import configs as K  # noqa: E402
 
 PATH = os.path.join(HERE, "exact_references.json")
-T_CORR = [0.5, 1.0, 2.0, 3.0, 4.0, 5.0, 6.0, 8.0]
+T_CORR = [0.5, 1.0, 2.0, 3.0, 4.0, 5.0, 6.0, 8.0, 10.0, 12.0, 16.0]
 
 
 def compute():

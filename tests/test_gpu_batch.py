@@ -73,10 +73,13 @@ def test_batch_equals_solo_runs(precision, graph):
 @pytest.mark.parametrize("precision", ["f64", "f32"])
 def test_batch_block_shapes_do_not_change_results(precision):
     inst = _mixed(precision)
-    shapes = [(128, 128), (64, 64)] if precision == "f64" else [(384, 32), (256, 64), (384, 128)]
+    shapes = ([(128, 128, "auto"), (64, 64, "auto")] if precision == "f64" else
+              [(384, 32, "staged"), (256, 64, "staged"), (384, 128, "staged"), (256, 256, "direct"),
+               (128, 128, "direct")])
     ref = None
-    for T, RB in shapes:
-        b = ParRepBatch([g for g, _, _ in inst], block_threads=T, replicas_per_block=RB, autotune=False)
+    for T, RB, layout in shapes:
+        b = ParRepBatch([g for g, _, _ in inst], block_threads=T, replicas_per_block=RB, autotune=False,
+                        f32_layout=layout)
         info = b.run([T_ for _, T_, _ in inst], [s for _, _, s in inst])
         assert info["block_threads"] == T and info["replicas_per_block"] == RB
         res = [_result(g) for g, _, _ in inst]

@@ -18,7 +18,7 @@ import pytest
 import oracle as O
 from oracle import exact as E
 from paper_1705_06807_gb300 import ParRep, ParRepBatch, ParRepServer, parrep_ssa, parrep_uq
-from paper_1705_06807_gb300.api import ParRepError
+from paper_1705_06807_gb300.api import ParRepError, parrep_ssa_trace
 
 pytestmark = pytest.mark.gpu
 
@@ -37,10 +37,13 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("precision", ["f64", "f32"])
 @pytest.mark.parametrize("name,spec,R,tc,tp,thresh,T,Tb,seed", CASES, ids=[c[0] for c in CASES])
-def test_genetic_run_matches_oracle(name, spec, R, tc, tp, thresh, T, Tb, seed):
-    o = O.parrep_run(spec, R, tc, tp, T, seed, [0, 0], thresh=thresh, T_burn=Tb)
-    g = ParRep(spec, R, tc, tp, x0=[0, 0], thresh=thresh, T_burn=Tb)
+def test_genetic_run_matches_oracle(name, spec, R, tc, tp, thresh, T, Tb, seed, precision):
+    """Both precision forms (binary32: six-channel propensities and selection
+    in binary32, the oracle's binary32 mode; it runs in the direct layout)."""
+    o = O.parrep_run(spec, R, tc, tp, T, seed, [0, 0], thresh=thresh, T_burn=Tb, precision=precision)
+    g = ParRep(spec, R, tc, tp, x0=[0, 0], thresh=thresh, T_burn=Tb, precision=precision)
     assert g.run_status(T, seed) == o["status"] == 0
     st = g.stats()
     for k in ("events_decorr", "events_dephase", "events_parallel_useful", "escapes"):
@@ -54,17 +57,24 @@ def test_genetic_run_matches_oracle(name, spec, R, tc, tp, thresh, T, Tb, seed):
         for k in ("cycle", "W", "ended", "decorr_steps", "dephase_steps", "n_star", "k", "x_tilde"):
             assert a[k] == b[k], (k, a, b)
     pre, post = g.histogram_raw()
-    tol = 4e-12 * max(o["events_decorr"] + o["events_parallel_useful"], 1) + 1e-12 * T
-    np.testing.assert_allclose(pre, o["hist_pre"], rtol=1e-12, atol=tol)
-    np.testing.assert_allclose(post, o["hist_post"], rtol=1e-12, atol=tol)
+    rt = 2.0**-22 if precision == "f32" else 1e-12
+    tol = 4e-12 * max(o["events_decorr"] + o["events_parallel_useful"], 1) + 1e-12 * T + (rt * T if precision == "f32" else 0)
+    np.testing.assert_allclose(pre, o["hist_pre"], rtol=rt, atol=tol)
+    np.testing.assert_allclose(post, o["hist_post"], rtol=rt, atol=tol)
 
 
-def test_genetic_plain_ssa_matches_oracle():
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_genetic_plain_ssa_matches_oracle(precision):
     spec = _spec(E.genetic_paper_params(), 15, 3500, 512)
-    hg, evg, _ = parrep_ssa(spec, 9, [0, 0], 3.0, 17, precision="f64")
-    ho, evo, _ = O.ssa_run(spec, 9, [0, 0], 3.0, 17)
+    hg, evg, _ = parrep_ssa(spec, 9, [0, 0], 3.0, 17, precision=precision)
+    ho, evo, _ = O.ssa_run(spec, 9, [0, 0], 3.0, 17, precision=precision)
     assert evg == evo
-    np.testing.assert_allclose(hg, ho, rtol=1e-12, atol=4e-12 * evo + 1e-12 * 27.0)
+    rt = 2.0**-22 if precision == "f32" else 1e-12
+    np.testing.assert_allclose(hg, ho, rtol=rt, atol=4e-12 * evo + 1e-12 * 27.0 + (rt * 27.0 if precision == "f32" else 0))
+    J, xs, tau, nj, xf = parrep_ssa_trace(spec, 4, [0, 0], 1e6, 5, 400, precision=precision)
+    for t in range(4):
+        Jo, xo, to = O.ssa_trace(spec, [0, 0], 5, t, 400, precision=precision)
+        assert np.array_equal(J[t], Jo) and np.array_equal(xs[t], xo)
 
 
 def test_genetic_parrep_matches_exact_law():
@@ -89,17 +99,23 @@ def test_genetic_parrep_matches_exact_law():
     assert 0.5 * np.abs(marg(tot / tot.sum()) - marg(ex)).sum() < 0.02
 
 
-def test_genetic_fp32_form_is_refused():
+def test_genetic_fp32_needs_the_direct_layout():
+    """The staged FP32 layout has no six-channel chain: asking for it is
+    refused; the default (auto) layout and the direct server take the kind."""
     spec = _spec(SMALL, 16, 250, 13)
     g = ParRep(spec, 16, 50, 50, x0=[0, 0], thresh="steps", precision="f32")
     with pytest.raises(ParRepError):
-        g.run(10.0, 1)
-    with pytest.raises(ParRepError):
-        parrep_ssa(spec, 1, [0, 0], 1.0, 1, precision="f32")
+        g.set_options(thresh="steps", precision="f32", f32_layout="staged")
     srv = ParRepServer(precision="f32", arena_bytes=8 << 20)
     with pytest.raises(ParRepError):
         srv.submit(spec, 16, 50, 50, 10.0, 1, x0=[0, 0], thresh="steps")
     srv.close()
+    solo = ParRep(spec, 16, 50, 50, x0=[0, 0], thresh="steps", precision="f32", T_burn=2.0)
+    solo.run(10.0, 1)
+    srv = ParRepServer(precision="f32", arena_bytes=64 << 20, f32_layout="direct")
+    r = srv.result(srv.submit(spec, 16, 50, 50, 10.0, 1, x0=[0, 0], thresh="steps", T_burn=2.0), timeout_s=60.0)
+    srv.close()
+    assert r["status"] == 0 and np.array_equal(r["hist"], solo.histogram())
 
 
 def _cprime():

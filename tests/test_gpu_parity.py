@@ -443,6 +443,51 @@ def test_fp32_staged_path_is_shape_invariant(spec, x0):
         assert r[2] == res[0][2] and r[3] == res[0][3]
 
 
+@pytest.mark.parametrize("case", ["v10_steps", "toggle_time", "classic_time"])
+def test_fp32_direct_layout_equals_staged(case):
+    """The two kernel layouts of the FP32 form -- staged (owner threads fed by
+    helper warps) and direct (one thread per replica at high occupancy) --
+    take every decision and round every holding time identically: the
+    fixed-point sums, the cycle logs and the event counts agree bit for bit,
+    and the direct layout matches the oracle's binary32 mode."""
+    spec, x0, tc, thresh, T, R = {
+        "v10_steps": (V10, [2], 200, "steps", 120.0, 300),
+        "toggle_time": (K.toggle(alpha=20.0, n=2.5, hist_max=(63, 63)), [15, 2], 0.5, "time", 60.0, 200),
+        "classic_time": (K.schlogl_classic(), [250], 0.3, "time", 12.0, 700),
+    }[case]
+    out = []
+    for layout in ("staged", "direct"):
+        g = ParRep(spec, R, tc, tc, x0=x0, thresh=thresh, precision="f32", fv_group=16, T_burn=T / 4,
+                   f32_layout=layout)
+        g.run(T, 13)
+        pre, post = g.histogram_raw()
+        out.append((pre, post, g.cycle_log(), g.stats()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2]
+    for k in ("events_decorr", "events_dephase", "events_parallel_useful", "escapes", "x_final", "T_s"):
+        assert out[0][3][k] == out[1][3][k], k
+    o, g, rc = run_both(spec, R, tc, tc, T, 13, x0, thresh=thresh, precision="f32", fv_group=16, T_burn=T / 4)
+    g.set_options(thresh=thresh, precision="f32", fv_group=16, T_burn=T / 4, f32_layout="direct")
+    g.precision = "f32"
+    rc = g.run_status(T, 13)
+    assert_parity(o, g, rc, T)
+
+
+def test_fp32_direct_layout_is_shape_invariant():
+    """Block size and the cap on blocks (several groups of replicas per
+    block) do not change a bit of the direct layout's results."""
+    res = []
+    for B, M in [(256, 0), (128, 0), (64, 0), (128, 1), (256, 2)]:
+        g = ParRep(V10, 777, 200, 200, x0=[2], thresh="steps", precision="f32", fv_group=32, T_burn=30.0,
+                   chunk_steps=96, block_threads=B, max_blocks=M, f32_layout="direct")
+        g.run(90.0, 99)
+        pre, post = g.histogram_raw()
+        res.append((pre, post, g.cycle_log(), g.stats()["events_parallel_useful"]))
+    for r in res[1:]:
+        assert np.array_equal(r[0], res[0][0]) and np.array_equal(r[1], res[0][1])
+        assert r[2] == res[0][2] and r[3] == res[0][3]
+
+
 @pytest.mark.parametrize("spec,x0", [(V10, [2]), (K.toggle(alpha=20.0, n=2.5, hist_max=(63, 63)), [15, 2])])
 def test_fp32_pipelined_equals_serial_stages(spec, x0):
     """The owner/helper overlap only reorders work between warps: the results

@@ -9,10 +9,14 @@ the estimate is biased by about 0.17 in total variation, in both forms).
 32 independent seeds run as one batch.
 
 Checks: the pooled time-weighted histogram is within total variation 1e-2
-of the exact law and every well-populated bin within 4.5 standard errors
-(batch means over the seeds); the FIM of the FP32 form is within 1% of the
-FP64 form's (Appendix A), compared well by well; both are near the exact
-FIM.
+of the exact law; bin by bin (batch means over the seeds) at most three of
+the ~150 well-populated bins lie beyond 3 standard errors and none beyond
+4.5 -- 3 SE per bin is the criterion, read with its multiplicity: with 150
+bins an exact sampler puts 0.4 bins beyond 3 SE on average and exceeds 3 of
+them with probability 8e-4, while a maximum of 4.5 SE over 150 bins is
+exceeded with probability 1e-3; the FIM of the FP32 form is within 1% of
+the FP64 form's (Appendix A) and of the exact chain's, compared well by
+well; both are near the exact FIM overall.
 
 Error budget: the slowest mode is the hopping between the wells
 (correlation time 101 time units), so the pooled run of T = 4e6 time units
@@ -75,6 +79,7 @@ def test_pooled_histogram_within_tv_of_exact_law(runs, precision):
     se = per.std(0, ddof=1) / np.sqrt(N_SEEDS)
     big = pi > 1e-3
     z = np.abs(mean[big] - pi[big]) / np.maximum(se[big], 1e-12)
+    assert int((z > 3.0).sum()) <= 3, np.sort(z)[-5:]
     assert z.max() < 4.5, (z.max(), np.argmax(z))
 
 
@@ -90,9 +95,13 @@ def test_fp32_fim_within_one_percent_of_fp64(runs):
         # the library's FIM is the contraction of its own histogram
         assert np.allclose(lib[p], F[p], rtol=1e-9)
         well[p] = [(r[:, w] * h[w]).sum(1) / h[w].sum() for w in (slice(0, SPLIT), slice(SPLIT, None))]
+    well_exact = [(r[:, w] * pi[w]).sum(1) / pi[w].sum() for w in (slice(0, SPLIT), slice(SPLIT, None))]
     for lo_hi in range(2):
         ratio = well["f32"][lo_hi] / well["f64"][lo_hi]
         assert np.all(np.abs(ratio - 1.0) < 0.01), (lo_hi, ratio)
+        for p in ("f64", "f32"):
+            ratio = well[p][lo_hi] / well_exact[lo_hi]
+            assert np.all(np.abs(ratio - 1.0) < 0.01), (p, lo_hi, ratio)
     for p in ("f64", "f32"):
         assert np.all(np.abs(lib[p] / F_exact - 1.0) < 0.02), (p, lib[p] / F_exact)
     # the constant channel's entry is exact in both forms: I_33 = s3 / c3 = 200 (Table II)
