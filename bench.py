@@ -40,6 +40,10 @@ N_SM = 152  # SMs of a GB300 (used only if the device does not report its count)
 # histogram (-17) but add the Fleming-Viot ballots (+4).
 OPS_PER_EVENT = 120
 OPS_PER_DEPHASE_EVENT = 107
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the staged FP32
+# run kernel on the n = 4096 Schloegl workload (ncu launch list, mean of 4
+# launches of the default command)
+RUN_KERNEL_TRAFFIC = 1.3332e6
 
 
 def issue_peak(clocks=None):
@@ -1006,9 +1010,12 @@ def main():
         "executed_events_per_s": executed / t_total,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12 if achieved else None,
                      "peak": peak_ops / 1e12, "unit": "Tinst/s",
-                     "frac": achieved / peak_ops if achieved else None, "traffic": None,
+                     "frac": achieved / peak_ops if achieved else None,
+                     "traffic": RUN_KERNEL_TRAFFIC if (schlogl and args.T_end is None and args.precision == "f32"
+                                                       and args.f32_layout != "direct") else None,
                      "note": "thread-instructions at 120 per event (107 per dephasing jump) over the run kernel "
-                             "time; peak = " + peak_note},
+                             "time; peak = " + peak_note + "; traffic = DRAM bytes read + written per launch "
+                             "(ncu launch list of this command, profiles/)"},
         "phase_share": phase_share,
         "events_per_step": events,
         "accuracy": accuracy,
