@@ -395,6 +395,14 @@ def bench_batch(args, world, rank, local, dist):
     executed = sum(x["events_decorr"] + x["events_parallel_executed"] + x["events_replay"] + x["events_dephase"]
                    for x in flat)
     dephase = sum(x["events_dephase"] for x in flat)
+    breakdown = {k: sum(x[k] for x in flat) // max(1, len(stats)) for k in
+                 ("events_decorr", "events_dephase", "events_parallel_useful", "events_parallel_executed",
+                  "events_replay", "cycles", "escapes")}
+    ph = {}
+    for x in flat:
+        for k, v in x["phase_cycles"].items():
+            ph[k] = ph.get(k, 0.0) + v
+    ph_tot = sum(v for k, v in ph.items() if not k.startswith("dec_")) or 1.0
     t_total, (useful, executed, dephase) = combine_ranks(dist, t_total, [useful, executed, dephase], "cuda")
     clocks = clk.summary()
     e2e = None
@@ -438,6 +446,8 @@ def bench_batch(args, world, rank, local, dist):
                              "of the launch sequence; peak = " + peak_note},
         "batch": {k: info[k] for k in ("block_threads", "replicas_per_block", "grid_blocks", "n_items", "graph",
                                         "tuned_trials", "tune_ms", "est_balance")},
+        "events_per_step": breakdown,
+        "phase_share": {k: round(v / ph_tot, 4) for k, v in ph.items()},
         "gpu_launches": 3 * args.steps,
         "clocks": clocks,
         "e2e": e2e,

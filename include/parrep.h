@@ -49,9 +49,10 @@ enum { PARREP_THRESH_TIME = 0, PARREP_THRESH_STEPS = 1 };
 enum { PARREP_FP64 = 0, PARREP_FP32 = 1 };
 /* Layout of the FP32 form's kernel: staged (each block's replica owner threads
  * walk the jump chains while helper warps draw the random numbers and account
- * the holding times), direct (one thread per replica), or auto (staged, except
- * for the genetic switch, which runs direct only).  Both give the same results
- * bit for bit. */
+ * the holding times -- the faster one for a few thousand replicas), direct
+ * (one thread per replica -- faster from about 16384 replicas on), or auto
+ * (direct from 16384 replicas on and for the genetic switch, which runs
+ * direct only; staged otherwise).  Both give the same results bit for bit. */
 enum { PARREP_F32_AUTO = 0, PARREP_F32_STAGED = 1, PARREP_F32_DIRECT = 2 };
 
 /* Reaction network (Sec. II.A).  Three kinds:
@@ -105,8 +106,9 @@ typedef struct {
                               replicas at once when the grid fits, else a full co-resident
                               grid); fewer blocks than groups run several groups per
                               block with the same results */
-    int32_t f32_layout;    /* FP32 form: PARREP_F32_AUTO (default: staged, direct for the
-                              genetic switch), _STAGED or _DIRECT */
+    int32_t f32_layout;    /* FP32 form: PARREP_F32_AUTO (default: direct from 16384
+                              replicas on and for the genetic switch, else staged),
+                              _STAGED or _DIRECT */
     double T_burn;         /* FIM / RER integrate over [T_burn, T_end] (default 0) */
     double wait_timeout_s; /* device wait limit without progress (default 10 s) */
     void* stream;          /* cudaStream_t to run on (NULL = legacy default stream) */

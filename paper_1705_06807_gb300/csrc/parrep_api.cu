@@ -354,15 +354,15 @@ int parrep::fast_layout(parrep_t h, int RB, int threads, int with_hist, int pipe
 
 // The kernel form of a handle's runs: binary64; or, in the FP32 form, the
 // staged layout (each owner thread's chain fed by helper warps) or the direct
-// one (one thread per replica): as the option asks, else staged -- measured
-// faster on every workload here, 4096 to 65536 replicas and the batches --
-// except for the genetic switch, whose six channels the staged chain does not
-// take.
+// one (one thread per replica): as the option asks, else direct for the
+// genetic switch (whose six channels the staged chain does not take) and from
+// kDirectAutoReplicas replicas on (measured: 2.2x faster at 16384 replicas,
+// 2-3.4x at 65536), staged below (10x faster at 4096).
 int parrep::f32_form(parrep_t h) {
     if (h->opt.precision != PARREP_FP32) return kFormF64;
     if (h->opt.f32_layout == PARREP_F32_STAGED) return kFormF32Staged;
     if (h->opt.f32_layout == PARREP_F32_DIRECT || h->net.kind == PARREP_GENETIC) return kFormF32Direct;
-    return kFormF32Staged;
+    return h->R >= kDirectAutoReplicas ? kFormF32Direct : kFormF32Staged;
 }
 
 static int plan_launch(parrep_t h, Plan& pl) {
@@ -388,7 +388,7 @@ static int plan_launch(parrep_t h, Plan& pl) {
         pl.off_limbs = pl.off_inv = pl.off_rng = pl.off_decp = -1;
         pl.pipelined = 0;
         for (int with_hist = 1; with_hist >= 0; --with_hist) {
-            if (with_hist && h->nbins * 8 > kSmemHistLimit) continue;
+            if (with_hist && h->nbins * 8 > (form == kFormF32Direct ? kDirectSmemHistLimit : kSmemHistLimit)) continue;
             pl.use_smem_hist = with_hist;
             pl.smem = with_hist ? h->nbins * 8 : 0;
             int ea = kernel_attrs_form(form, kind, &per_sm, pl.smem, threads);

@@ -15,6 +15,9 @@ namespace parrep {
 constexpr long long kLogCap = 1 << 16;
 constexpr int kMaxChunk = 1 << 16;
 constexpr int kSmemHistLimit = 160 * 1024;
+// the binary32 direct layout keeps three blocks per SM: a block's histogram
+// stays in shared memory only up to this size, larger ones go to global memory
+constexpr int kDirectSmemHistLimit = 64 * 1024;
 // Longest chunk of the FP32 form between escape votes (chunks start at one
 // sub-chunk in each cycle and double): fewer grid barriers per run against
 // more discarded work after an escape; 2048 measured best of 512..2048 on the
@@ -75,6 +78,8 @@ int fast_layout(parrep_t h, int RB, int threads, int with_hist, int pipelined, P
 int run_checks(parrep_t h, double T_end);
 // kernel Form of the handle's runs (binary64, binary32 staged or direct)
 int f32_form(parrep_t h);
+// the FP32 form's auto layout is direct from this many replicas on
+constexpr long long kDirectAutoReplicas = 16384;
 int run_params(parrep_t h, double T_end, uint64_t seed, const Plan& pl, RunParams& p);
 int run_finish(parrep_t h, const RunCtl& c, double T_end, const Plan& pl, float ms);
 // the statistics a control block holds (launch shape and timing left zero)

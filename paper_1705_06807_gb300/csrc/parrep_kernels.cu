@@ -776,6 +776,56 @@ static __device__ void replay_chunk(const RunParams& P, const HistSink& hs, int 
     }
 }
 
+// The step-sum pass of replay_chunk for a whole warp: every lane walks the
+// chunk in step with the others (a replica that escaped, left the range or
+// passed the cut adds zero), the warp sums each step's holding times with
+// shuffles and one lane adds the sum to step_sum[s] -- one global atomic per
+// warp and step instead of one per replica (thousands of replicas would
+// otherwise queue on the same address).  The sums are exact integers, so the
+// result is the same.
+template <bool F32>
+static __device__ void replay_stepsum_warp(const RunParams& P, bool active, int x0, int x1, unsigned r, int W,
+                                           unsigned cycle, unsigned n0, int S, const Cuts& cut,
+                                           unsigned long long& ev) {
+    const NetDev& N = P.net;
+    const uint2 key = seed_key(P.seed);
+    const int lane = threadIdx.x & 31;
+    bool live = active;
+    uint4 wp = make_uint4(0u, 0u, 0u, 0u);
+    for (int s = 0; s < S; ++s) {
+        unsigned long long q = 0;
+        if (live) {
+            if (pos_of(s, r) > cut.posC) {
+                live = false;
+            } else {
+                const unsigned n = n0 + (unsigned)s;
+                uint4 w;
+                if (F32) {  // one Philox call per step pair (n0 is even)
+                    if ((n & 1u) == 0u) wp = philox10(make_uint4(r, n >> 1, cycle, kTagParallel), key);
+                    w = (n & 1u) ? make_uint4(wp.z, wp.w, 0u, 0u) : wp;
+                } else {
+                    w = par_words<F32>(r, n, cycle, key);
+                }
+                const int J = ssa_draw<F32, true>(N, x0, x1, w, q);
+                ++ev;
+                int a0 = x0, a1 = x1;
+                apply(N, J, a0, a1);
+                if (out_of_range(N, a0, a1) || region_of(N, a0, a1) != W) {
+                    live = false;
+                } else {
+                    x0 = a0;
+                    x1 = a1;
+                }
+            }
+        }
+        unsigned long long v = q;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0 && v) atomicAdd(P.step_sum + s, v);
+        if (!__any_sync(0xffffffffu, live)) break;
+    }
+}
+
 static __device__ void flush_shared(unsigned long long* sh, unsigned long long* g, int nbins) {
     __syncwarp();
     __syncthreads();
@@ -1893,10 +1943,66 @@ __device__ __forceinline__ void replay_vblocks(const RunParams& P, const FastSme
             int e0 = 0, e1 = 0;
             chunk_f32<KIND, MODE>(P, F, hs, active, rbase, r, rt, cycle, n0, S, key, y0, y1, cut, to_post, k0, k1, e0,
                                   e1, q, ev_replay, e, pc);
+        } else if (MODE == kStepSum) {
+            // whole warps of owner threads (RB is a multiple of 32)
+            if (owner) replay_stepsum_warp<FORM != kFormF64>(P, active, y0, y1, r, rt.W, cycle, n0, S, cut, ev_replay);
         } else if (active) {
             replay_chunk<FORM != kFormF64, MODE>(P, hs, y0, y1, r, rt.W, cycle, n0, S, cut, to_post, q, e, ev_replay);
         }
     }
+}
+
+// The whole block: the first index k of v[0..n) with base + v[0] + ... + v[k]
+// >= target (fixed-point holding times), and part = target - (base + v[0] +
+// ... + v[k-1]), the share of v[k] before the threshold; -1 if the sums stay
+// below it.  Chunks of blockDim.x values: a warp scan by shuffles, a scan of
+// the warp totals, and the smallest crossing index by a shared atomic min --
+// the same k and part as a serial scan, in about n / blockDim.x rounds.
+static __device__ int block_find_crossing(const unsigned long long* __restrict__ v, int n, unsigned long long base,
+                                          unsigned long long target, unsigned long long& part) {
+    __shared__ unsigned long long s_w[33];
+    __shared__ int s_k;
+    __shared__ unsigned long long s_part;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    unsigned long long acc = base;
+    for (int i0 = 0; i0 < n; i0 += blockDim.x) {
+        const int i = i0 + threadIdx.x;
+        const unsigned long long x = i < n ? __ldcg(v + i) : 0ull;
+        unsigned long long inc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) s_w[warp] = inc;
+        if (threadIdx.x == 0) s_k = 0x7fffffff;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long t = 0;
+            for (int w = 0; w < nw; ++w) {
+                const unsigned long long a = s_w[w];
+                s_w[w] = t;  // exclusive prefix of the warp totals
+                t += a;
+            }
+            s_w[32] = t;     // the chunk's total
+        }
+        __syncthreads();
+        const unsigned long long incl = acc + s_w[warp] + inc;
+        if (i < n && incl >= target) atomicMin(&s_k, i);
+        __syncthreads();
+        const int k = s_k;
+        if (k != 0x7fffffff) {
+            if (i == k) s_part = target - (incl - x);
+            __syncthreads();
+            part = s_part;
+            __syncthreads();
+            return k;
+        }
+        acc += s_w[32];
+        __syncthreads();
+    }
+    part = 0;
+    return -1;
 }
 
 // Batches: at the start of a cycle the instance's leader thread claims idle
@@ -2170,6 +2276,7 @@ __device__ __forceinline__ bool run_instance(const RunParams& P, int lb, unsigne
                 __syncwarp();  // the leader's lanes meet again before the block-wide chunk
                 unsigned long long mykey = kNone, myoob = kNone, qsum = 0, ev = 0;
                 Cuts none{kNone, kNone, kNone, 0, kNone, 0, -1, -1};
+                if (!STAGED) pc.start();  // the staged chunks time their own stages
                 for (int vb = lb; vb < nvb; vb += nblk) {
                     const unsigned rbase = (unsigned)vb * (unsigned)P.RB, r = rbase + threadIdx.x;
                     const bool active = owner && (long long)r < (long long)P.R;
@@ -2226,6 +2333,7 @@ __device__ __forceinline__ bool run_instance(const RunParams& P, int lb, unsigne
                     myoob = k1 < myoob ? k1 : myoob;
                 }
                 const int slot = (int)(chunk_c % 3);
+                if (!STAGED) pc.lap(kPhChain);
                 pc.start();
                 {
                     unsigned long long a = mykey, b = myoob, c = qsum, d = ev;
@@ -2308,34 +2416,23 @@ __device__ __forceinline__ bool run_instance(const RunParams& P, int lb, unsigne
                         replay_vblocks<FORM, KIND, kTauAt>(P, F, hs, lb, nblk, nvb, rt, cycle, n0, Sc, key, cut, period_post,
                                                           ev_replay, pc);
                         if (!grid_sync(P, bs)) goto out;
-                        if (leader) {
-                            ctl->posB = kNone;
-                            ctl->posT = kNone;
-                            if (cut.nB >= 0) {
-                                unsigned long long acc = baseB;
-                                for (int rr = 0; rr < P.R; ++rr) {
-                                    const unsigned long long v = __ldcg(P.tau_at + rr);
-                                    if (acc + v >= P.q_Tburn) {
-                                        ctl->posB = pos_of(cut.nB, (unsigned)rr);
-                                        ctl->partB = P.q_Tburn - acc;
-                                        break;
-                                    }
-                                    acc += v;
-                                }
+                        if (lb == 0) {
+                            // block 0 finds the replicas whose holding time at the
+                            // crossing step crosses T_burn / T_end: the first rr with
+                            // base + sum_{i <= rr} tau_i >= the threshold, by a
+                            // block-parallel prefix scan over the replicas
+                            __syncwarp();
+                            int kB = -1, kT = -1;
+                            unsigned long long partB = 0, partT = 0;
+                            if (cut.nB >= 0) kB = block_find_crossing(P.tau_at, P.R, baseB, P.q_Tburn, partB);
+                            if (cut.nT >= 0) kT = block_find_crossing(P.tau_at + P.R, P.R, baseT, P.q_Tend, partT);
+                            if (threadIdx.x == 0) {
+                                ctl->posB = kB >= 0 ? pos_of(cut.nB, (unsigned)kB) : kNone;
+                                ctl->partB = partB;
+                                ctl->posT = kT >= 0 ? pos_of(cut.nT, (unsigned)kT) : kNone;
+                                ctl->partT = partT;
+                                __threadfence();
                             }
-                            if (cut.nT >= 0) {
-                                unsigned long long acc = baseT;
-                                for (int rr = 0; rr < P.R; ++rr) {
-                                    const unsigned long long v = __ldcg(P.tau_at + P.R + rr);
-                                    if (acc + v >= P.q_Tend) {
-                                        ctl->posT = pos_of(cut.nT, (unsigned)rr);
-                                        ctl->partT = P.q_Tend - acc;
-                                        break;
-                                    }
-                                    acc += v;
-                                }
-                            }
-                            __threadfence();
                         }
                         if (!grid_sync(P, bs)) goto out;
                         cut.posB = ldv(&ctl->posB);
