@@ -43,7 +43,7 @@ OPS_PER_DEPHASE_EVENT = 107
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the staged FP32
 # run kernel on the n = 4096 Schloegl workload (ncu launch list, mean of 4
 # launches of the default command)
-RUN_KERNEL_TRAFFIC = 1.3332e6
+RUN_KERNEL_TRAFFIC = 1.3372e6
 
 
 def issue_peak(clocks=None):
@@ -210,8 +210,9 @@ def parse():
     ap.add_argument("--accuracy_t", default="1,2,4,6,8", help="t_corr = t_phase values (accuracy)")
     ap.add_argument("--accuracy_seeds", type=int, default=64, help="runs per threshold (accuracy)")
     ap.add_argument("--fv_group", type=int, default=32, help="Fleming-Viot group size (accuracy)")
-    ap.add_argument("--f32_layout", default="auto", choices=["auto", "staged", "direct"],
-                    help="FP32 kernel layout (the server takes auto as staged)")
+    ap.add_argument("--f32_layout", default="auto", choices=["auto", "staged", "direct", "mixed"],
+                    help="FP32 kernel layout (auto: direct from 16384 replicas on, staged below; batches and "
+                         "the server choose per instance)")
     ap.add_argument("--serve_seconds_default", type=float, default=5.0,
                     help="length of the request stream measured beside the headline (0 = none)")
     ap.add_argument("--no-extras", action="store_true",
@@ -445,7 +446,7 @@ def bench_batch(args, world, rank, local, dist):
                      "note": "thread-instructions at 120 per event (107 per dephasing jump) over the device time "
                              "of the launch sequence; peak = " + peak_note},
         "batch": {k: info[k] for k in ("block_threads", "replicas_per_block", "grid_blocks", "n_items", "graph",
-                                        "tuned_trials", "tune_ms", "est_balance")},
+                                        "tuned_trials", "tune_ms", "est_balance", "f32_layout")},
         "events_per_step": breakdown,
         "phase_share": {k: round(v / ph_tot, 4) for k, v in ph.items()},
         "gpu_launches": 3 * args.steps,
@@ -489,7 +490,7 @@ def serve_stream(args, local, rate, seconds):
     from paper_1705_06807_gb300 import configs as K
 
     stream = K.serve_requests(rate=rate, seconds=seconds, seed=0)
-    srv = ParRepServer(precision=args.precision, f32_layout="direct" if args.f32_layout == "direct" else "staged")
+    srv = ParRepServer(precision=args.precision, f32_layout=args.f32_layout)
     # warm-up: a few small requests (module load, first launches)
     for i in range(max(args.warmup, 1)):
         d = stream[i][1]

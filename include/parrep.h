@@ -53,7 +53,10 @@ enum { PARREP_FP64 = 0, PARREP_FP32 = 1 };
  * (one thread per replica -- faster from about 16384 replicas on), or auto
  * (direct from 16384 replicas on and for the genetic switch, which runs
  * direct only; staged otherwise).  Both give the same results bit for bit. */
-enum { PARREP_F32_AUTO = 0, PARREP_F32_STAGED = 1, PARREP_F32_DIRECT = 2 };
+enum { PARREP_F32_AUTO = 0, PARREP_F32_STAGED = 1, PARREP_F32_DIRECT = 2,
+       /* batches and servers: each instance in the layout auto would give it
+        * alone, in one kernel (for a single run the same as auto) */
+       PARREP_F32_MIXED = 3 };
 
 /* Reaction network (Sec. II.A).  Three kinds:
  *   PARREP_SCHLOGL (Table I, 1 species x):
@@ -308,8 +311,9 @@ typedef struct {
     int32_t use_graph;          /* 1 (default): capture the launch sequence (parameter upload,
                                    reset, batch kernel, read-back) in a CUDA graph and replay it
                                    while the shape stays the same */
-    int32_t f32_layout;         /* FP32 form: PARREP_F32_AUTO (default: staged shapes; direct if an
-                                   instance is a genetic switch), _STAGED or _DIRECT */
+    int32_t f32_layout;         /* FP32 form: PARREP_F32_AUTO (default) = _MIXED: each instance
+                                   runs direct from 16384 replicas on and for the genetic switch,
+                                   staged below; _STAGED (no genetic switch), _DIRECT */
     double tune_fraction;       /* default 0.05 */
     double wait_timeout_s;      /* device wait limit without progress anywhere (default 10 s) */
     void* stream;               /* cudaStream_t (NULL = legacy default stream) */
@@ -321,6 +325,9 @@ typedef struct {
     int32_t n_items;            /* (instance, block) pairs of the schedule */
     int32_t graph;              /* 1: the last run replayed a CUDA graph */
     int32_t tuned_trials;       /* shapes timed by the autotuner so far */
+    int32_t f32_layout;         /* the launch's FP32 layout (PARREP_F32_STAGED, _DIRECT or
+                                   _MIXED; 0 in the FP64 form) */
+    int32_t pad;
     float kernel_ms;            /* last run: device time of the launch sequence (parameter
                                    upload, reset, batch kernel, read-back) */
     float tune_ms;              /* wall time spent autotuning */
@@ -382,8 +389,9 @@ typedef struct {
     int32_t block_threads;      /* 0 = 384 (FP32) / 128 (FP64) */
     int32_t replicas_per_block; /* FP32 form: owner threads per block (32..256), 0 = 32 */
     int32_t ring;               /* request slots (default 4096); a slot is reused after its result is read */
-    int32_t f32_layout;         /* FP32 form, one for all requests: PARREP_F32_STAGED (default; AUTO
-                                   means the same) or PARREP_F32_DIRECT (needed for genetic switches) */
+    int32_t f32_layout;         /* FP32 form: PARREP_F32_MIXED (default) / _AUTO (each request in
+                                   the layout auto gives it: direct from 16384 replicas on and
+                                   for genetic switches, staged below), _STAGED or _DIRECT */
     int64_t arena_bytes;        /* device memory for admitted requests (default 4 GiB) */
     int64_t log_cap;            /* cycle-log records kept per request (default 4096) */
     double idle_exit_s;         /* the serve kernel ends after the server has had nothing to do this

@@ -16,8 +16,8 @@ PARREP_EINVAL = -1
 PARREP_ENOMEM = -2
 PARREP_ECUDA = -3
 PARREP_ETIMEOUT = -4
-PARREP_F32_AUTO, PARREP_F32_STAGED, PARREP_F32_DIRECT = 0, 1, 2
-LAYOUTS = {"auto": 0, "staged": 1, "direct": 2}
+PARREP_F32_AUTO, PARREP_F32_STAGED, PARREP_F32_DIRECT, PARREP_F32_MIXED = 0, 1, 2, 3
+LAYOUTS = {"auto": 0, "staged": 1, "direct": 2, "mixed": 3}
 PARREP_ERANGE = -5
 PARREP_ESTATE = -6
 PARREP_SCHLOGL, PARREP_TOGGLE, PARREP_GENETIC = 1, 2, 3
@@ -62,7 +62,7 @@ class parrep_batch_options(C.Structure):
 class parrep_batch_info(C.Structure):
     _fields_ = [("block_threads", C.c_int32), ("replicas_per_block", C.c_int32), ("grid_blocks", C.c_int32),
                 ("n_items", C.c_int32), ("graph", C.c_int32), ("tuned_trials", C.c_int32),
-                ("kernel_ms", C.c_float), ("tune_ms", C.c_float), ("est_makespan", C.c_double),
+                ("f32_layout", C.c_int32), ("pad", C.c_int32), ("kernel_ms", C.c_float), ("tune_ms", C.c_float), ("est_makespan", C.c_double),
                 ("est_balance", C.c_double)]
 
 

@@ -243,7 +243,9 @@ class ParRepBatch:
     def info(self) -> dict:
         i = L.parrep_batch_info()
         self._check(self._lib.parrep_batch_info_get(self.b, C.byref(i)))
-        return {k: getattr(i, k) for k, _ in i._fields_}
+        d = {k: getattr(i, k) for k, _ in i._fields_ if k != "pad"}
+        d["f32_layout"] = {v: k for k, v in L.LAYOUTS.items() if k != "auto"}.get(d["f32_layout"])
+        return d
 
     def close(self):
         if getattr(self, "b", None):
@@ -271,7 +273,7 @@ class ParRepServer:
 
     def __init__(self, *, precision: str = "f32", block_threads: int = 0, replicas_per_block: int = 0,
                  ring: int = 4096, arena_bytes: int = 4 << 30, log_cap: int = 4096, idle_exit_s: float = 0.05,
-                 wait_timeout_s: float = 10.0, f32_layout: str = "staged"):
+                 wait_timeout_s: float = 10.0, f32_layout: str = "mixed"):
         self._lib = L.load()
         o = L.parrep_server_options()
         self._lib.parrep_server_default_options(C.byref(o))

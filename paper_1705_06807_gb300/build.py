@@ -1,9 +1,10 @@
 """Builds the CUDA library libparrep.so in-tree for sm_103a with nvcc.
 
 The translation units are compiled in parallel; parrep_kernels.cu is compiled
-once per part (-DPARREP_PART=0..9: the small kernels, then the run, batch and
+once per part (-DPARREP_PART=0..11: the small kernels, then the run, batch and
 serve kernels in each of the binary64, binary32 staged and binary32 direct
-forms), since each persistent kernel inlines the whole of Algorithm 1.  Arithmetic contraction is off (-fmad=false) so that
+forms, and the batch and serve kernels in the mixed binary32 form), since each
+persistent kernel inlines the whole of Algorithm 1.  Arithmetic contraction is off (-fmad=false) so that
 the binary64/binary32 propensity and selection expressions round exactly as
 written.
 """
@@ -20,7 +21,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libparrep.so")
-KERNEL_PARTS = 10
+KERNEL_PARTS = 12
 SOURCES = [("parrep_kernels.cu", i) for i in range(KERNEL_PARTS)] + [
     (f, None) for f in ["parrep_api.cu", "parrep_batch.cu", "parrep_serve.cu", "parrep_noalloc.cu", "parrep_uq.cu"]]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -72,7 +73,7 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
         return obj
 
     # the binary32 staged run / batch / serve parts take longest: start them first
-    order = sorted(SOURCES, key=lambda it: (0 if it[1] in (2, 5, 8) else 1 if it[1] else 2))
+    order = sorted(SOURCES, key=lambda it: (0 if it[1] in (10, 11, 2, 5, 8) else 1 if it[1] else 2))
     with ThreadPoolExecutor(max_workers=min(len(SOURCES), max(2, os.cpu_count() or 2))) as ex:
         objs = list(ex.map(compile_one, order))
     tmp = LIB + f".{tag}.tmp"

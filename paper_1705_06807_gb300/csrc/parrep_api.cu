@@ -288,8 +288,8 @@ extern "C" int parrep_set_options(parrep_t h, const parrep_options* o) {
         return fail(h, PARREP_EINVAL, "block_threads must be a multiple of 32 up to 384 (0 = auto)");
     if (o->chunk_steps < 0 || o->chunk_steps > kMaxChunk) return fail(h, PARREP_EINVAL, "chunk_steps");
     if (o->max_blocks < 0) return fail(h, PARREP_EINVAL, "max_blocks must be >= 0");
-    if (o->f32_layout != PARREP_F32_AUTO && o->f32_layout != PARREP_F32_STAGED && o->f32_layout != PARREP_F32_DIRECT)
-        return fail(h, PARREP_EINVAL, "f32_layout must be PARREP_F32_AUTO, _STAGED or _DIRECT");
+    if (o->f32_layout < PARREP_F32_AUTO || o->f32_layout > PARREP_F32_MIXED)
+        return fail(h, PARREP_EINVAL, "f32_layout must be PARREP_F32_AUTO, _STAGED, _DIRECT or _MIXED");
     if (h->net.kind == PARREP_GENETIC && o->precision == PARREP_FP32 && o->f32_layout == PARREP_F32_STAGED)
         return fail(h, PARREP_EINVAL, "the genetic switch's FP32 form runs in the direct layout only");
     if (!(o->T_burn >= 0.0) || !(o->T_burn < kTEndLimit)) return fail(h, PARREP_EINVAL, "T_burn");

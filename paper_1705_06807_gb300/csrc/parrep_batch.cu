@@ -232,8 +232,13 @@ static int set_shape(parrep_batch_t b, int threads, int RB, int form) {
         parrep_t h = b->inst[i];
         Plan& pl = b->plans[i];
         memset(&pl, 0, sizeof(pl));
-        pl.form = form;
-        if (form == kFormF32Staged) {
+        // the mixed form runs each instance in its own layout (direct for the
+        // genetic switch and from kDirectAutoReplicas replicas on)
+        const int f = form != kFormF32Mixed ? form
+                      : (h->R >= kDirectAutoReplicas || h->net.kind == PARREP_GENETIC) ? kFormF32Direct
+                                                                                        : kFormF32Staged;
+        pl.form = f;
+        if (f == kFormF32Staged) {
             const int pipe = threads - RB >= 64 && !h->opt.serial_stages;
             int sz = -1;
             for (int with_hist = 1; with_hist >= 0 && sz < 0; --with_hist) {
@@ -253,6 +258,7 @@ static int set_shape(parrep_batch_t b, int threads, int RB, int form) {
             pl.off_tab = pl.off_buf = pl.off_trace = pl.off_live = pl.off_nvalid = -1;
             pl.off_limbs = pl.off_inv = pl.off_rng = pl.off_decp = -1;
             pl.use_smem_hist = h->nbins * 8 <= (form == kFormF32Direct ? kDirectSmemHistLimit : kSmemHistLimit);
+            pl.form = f;
             pl.smem = pl.use_smem_hist ? h->nbins * 8 : 0;
         }
         if (pl.S > kMaxChunk) return bfail(b, PARREP_EINVAL, "chunk_steps too large");
@@ -270,6 +276,10 @@ static int set_shape(parrep_batch_t b, int threads, int RB, int form) {
     b->info.block_threads = threads;
     b->info.replicas_per_block = RB;
     b->info.grid_blocks = b->grid;
+    b->info.f32_layout = form == kFormF32Staged  ? PARREP_F32_STAGED
+                         : form == kFormF32Direct ? PARREP_F32_DIRECT
+                         : form == kFormF32Mixed  ? PARREP_F32_MIXED
+                                                  : 0;
     // buffers sized for this grid
     const int items_cap = n * b->grid, off_cap = b->grid + 1;
     if (items_cap > b->items_cap) {
@@ -379,9 +389,10 @@ static int run_once(parrep_batch_t b, const double* T_end, const uint64_t* seed,
 }
 
 // Candidate shapes: {threads, RB, form}.  FP32 staged: RB owners + helpers;
-// FP32 direct and FP64: one replica a thread (RB = threads).  The FP32 form
-// tries the staged shapes unless an instance is a genetic switch or the
-// layout option asks for the direct one (measured slower on these batches).
+// FP32 direct and FP64: one replica a thread (RB = threads); FP32 mixed: each
+// instance staged with RB owners or direct with all threads as owners.  The
+// FP32 auto layout is the mixed one: it runs a batch without large or genetic
+// instances exactly as the staged layout does.
 struct Shape {
     int threads, RB, form;
 };
@@ -390,18 +401,14 @@ static std::vector<Shape> candidates(parrep_batch_t b) {
     std::vector<Shape> c;
     const int T = b->opt.block_threads, RB = b->opt.replicas_per_block;
     if (b->prec == PARREP_FP32) {
-        bool genetic = false;
-        for (parrep_t h : b->inst) genetic |= h->net.kind == PARREP_GENETIC;
-        const bool staged = !genetic && b->opt.f32_layout != PARREP_F32_DIRECT;
-        const bool direct = genetic || b->opt.f32_layout == PARREP_F32_DIRECT;
-        if (staged) {
-            const Shape all[] = {{384, 32, kFormF32Staged}, {256, 32, kFormF32Staged}, {384, 64, kFormF32Staged},
-                                 {256, 64, kFormF32Staged}, {384, 128, kFormF32Staged}};
+        const int lay = b->opt.f32_layout;
+        if (lay == PARREP_F32_STAGED || lay == PARREP_F32_AUTO || lay == PARREP_F32_MIXED) {
+            const int form = lay == PARREP_F32_STAGED ? kFormF32Staged : kFormF32Mixed;
+            const int all[][2] = {{384, 64}, {384, 32}, {384, 128}, {256, 32}, {256, 64}};
             for (auto& s : all)
-                if ((T == 0 || s.threads == T) && (RB == 0 || s.RB == RB)) c.push_back(s);
-            if (c.empty() && (T == 0 || RB == 0 || RB < T)) c.push_back({T ? T : 384, RB ? RB : 32, kFormF32Staged});
-        }
-        if (direct) {
+                if ((T == 0 || s[0] == T) && (RB == 0 || s[1] == RB)) c.push_back({s[0], s[1], form});
+            if (c.empty() && (T == 0 || RB == 0 || RB < T)) c.push_back({T ? T : 384, RB ? RB : 64, form});
+        } else {
             const int all[] = {kDirectThreads, 128};
             for (int t : all)
                 if ((T == 0 || t == T) && (RB == 0 || RB == t)) c.push_back({t, t, kFormF32Direct});
@@ -499,7 +506,7 @@ extern "C" int parrep_batch_create(const parrep_t* instances, int32_t n, const p
     if (opt) o = *opt;
     if (o.block_threads < 0 || o.block_threads > kMaxThreads || o.block_threads % 32 != 0)
         return bfail(nullptr, PARREP_EINVAL, "block_threads must be a multiple of 32 up to 384 (0 = autotune)");
-    if (o.f32_layout != PARREP_F32_AUTO && o.f32_layout != PARREP_F32_STAGED && o.f32_layout != PARREP_F32_DIRECT)
+    if (o.f32_layout < PARREP_F32_AUTO || o.f32_layout > PARREP_F32_MIXED)
         return bfail(nullptr, PARREP_EINVAL, "f32_layout");
     const int rb = o.replicas_per_block;
     if (!(rb == 0 || rb == 32 || rb == 64 || rb == 128 || rb == 256))
@@ -513,6 +520,10 @@ extern "C" int parrep_batch_create(const parrep_t* instances, int32_t n, const p
 
         if (v[i]->opt.precision != v[0]->opt.precision)
             return bfail(nullptr, PARREP_EINVAL, "instances of one batch need the same precision");
+        if (v[i]->opt.precision == PARREP_FP32 && v[i]->net.kind == PARREP_GENETIC &&
+            o.f32_layout == PARREP_F32_STAGED)
+            return bfail(nullptr, PARREP_EINVAL,
+                         "the genetic switch's FP32 form needs the direct, mixed or auto layout (f32_layout)");
     }
     std::vector<parrep_t> sorted(v);
     std::sort(sorted.begin(), sorted.end());

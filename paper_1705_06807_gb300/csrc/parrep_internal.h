@@ -108,7 +108,10 @@ struct BatchDev {
 // Kernel forms: binary64 (one thread per replica), binary32 staged (owner
 // threads + helper warps per block, for few replicas per SM), binary32 direct
 // (one thread per replica at high occupancy, for many replicas).
-enum Form { kFormF64 = 0, kFormF32Staged = 1, kFormF32Direct = 2 };
+enum Form { kFormF64 = 0, kFormF32Staged = 1, kFormF32Direct = 2,
+            // batch and serve kernels only: every instance runs its own
+            // binary32 layout (RunParams::form, staged or direct)
+            kFormF32Mixed = 3 };
 
 struct RunParams {
     NetDev net;

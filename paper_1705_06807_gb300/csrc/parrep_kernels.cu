@@ -18,11 +18,12 @@
 // Every wait on another block is bounded by a no-progress timeout and turns
 // into PARREP_ETIMEOUT instead of a hang.
 //
-// The file is compiled once per part (-DPARREP_PART=0..9) so that the
+// The file is compiled once per part (-DPARREP_PART=0..11) so that the
 // persistent kernels, each of which inlines the whole of Algorithm 1, build
 // in parallel: part 0 holds the small kernels and the dispatchers, parts 1-9
 // instantiate the run, batch and serve kernels in each form (binary64,
-// binary32 staged, binary32 direct).
+// binary32 staged, binary32 direct), parts 10-11 the batch and serve kernels
+// in the mixed binary32 form.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -2564,6 +2565,24 @@ __global__ void PARREP_BOUNDS(FORM) parrep_run_kernel(RunParams P) {
 // bit in bd.idle and waits (bounded, on the batch's progress) for a mailbox
 // entry from an instance that recruits it at a cycle start, until no
 // instance is left.  Both network kinds run in the same launch.
+// One instance in a batch or serve kernel of the given form; the mixed form
+// runs each instance in the binary32 layout its parameters name (P.form).
+// The genetic switch runs in the two-species instantiation.
+template <int FORM>
+__device__ __forceinline__ bool run_any(const RunParams& P, int lb, unsigned char* smem, BlockScratch& red,
+                                        int join_gen) {
+    if constexpr (FORM == kFormF32Mixed) {
+        if (P.form == kFormF32Direct)
+            return P.net.kind == PARREP_SCHLOGL ? run_instance<kFormF32Direct, PARREP_SCHLOGL>(P, lb, smem, red, join_gen)
+                                                : run_instance<kFormF32Direct, PARREP_TOGGLE>(P, lb, smem, red, join_gen);
+        return P.net.kind == PARREP_SCHLOGL ? run_instance<kFormF32Staged, PARREP_SCHLOGL>(P, lb, smem, red, join_gen)
+                                            : run_instance<kFormF32Staged, PARREP_TOGGLE>(P, lb, smem, red, join_gen);
+    } else {
+        return P.net.kind == PARREP_SCHLOGL ? run_instance<FORM, PARREP_SCHLOGL>(P, lb, smem, red, join_gen)
+                                            : run_instance<FORM, PARREP_TOGGLE>(P, lb, smem, red, join_gen);
+    }
+}
+
 template <int FORM>
 __device__ __forceinline__ void batch_item(const RunParams* Ps, RunParams& sP, int inst, int lb, int join_gen,
                                            unsigned char* smem, BlockScratch& red) {
@@ -2571,8 +2590,7 @@ __device__ __forceinline__ void batch_item(const RunParams* Ps, RunParams& sP, i
     int* dst = (int*)&sP;
     for (int w = threadIdx.x; w < (int)(sizeof(RunParams) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
     __syncthreads();
-    if (sP.net.kind == PARREP_SCHLOGL) run_instance<FORM, PARREP_SCHLOGL>(sP, lb, smem, red, join_gen);
-    else run_instance<FORM, PARREP_TOGGLE>(sP, lb, smem, red, join_gen);
+    run_any<FORM>(sP, lb, smem, red, join_gen);
     __syncthreads();
 }
 
@@ -2784,9 +2802,7 @@ __global__ void PARREP_BOUNDS(FORM) parrep_serve_kernel(ServeDev sd) {
             __syncthreads();
         }
         const int join_gen = cmd.w == 2 ? cmd.z : -1;
-        const bool last = sP.net.kind == PARREP_SCHLOGL
-                              ? run_instance<FORM, PARREP_SCHLOGL>(sP, cmd.y, smem, red, join_gen)
-                              : run_instance<FORM, PARREP_TOGGLE>(sP, cmd.y, smem, red, join_gen);
+        const bool last = run_any<FORM>(sP, cmd.y, smem, red, join_gen);
         if (last) {
             serve_epilogue(sP, slot, sd.done + cmd.x);
             if (threadIdx.x == 0) atomicAdd(sd.finished, 1ull);
@@ -3295,6 +3311,21 @@ static int attrs_of(K kernel, int* max_blocks_per_sm, int smem_bytes, int thread
 constexpr int kPartForm = (PARREP_PART - 1) % 3;
 #endif
 
+// parts 10 and 11: the batch and serve kernels in the mixed binary32 form
+#if PARREP_PART == 10
+int batch_attrs_f32m(int* m, int s, int t) { return attrs_of(parrep_batch_kernel<kFormF32Mixed>, m, s, t); }
+cudaError_t batch_launch_f32m(const cudaLaunchConfig_t& c, const RunParams* p, const int* o, const int2* i, BatchDev b) {
+    return cudaLaunchKernelEx(&c, parrep_batch_kernel<kFormF32Mixed>, p, o, i, b);
+}
+#endif
+#if PARREP_PART == 11
+int serve_attrs_f32m(int* m, int s, int t) { return attrs_of(parrep_serve_kernel<kFormF32Mixed>, m, s, t); }
+cudaError_t serve_launch_f32m(const ServeDev& d, int g, int t, int s, cudaStream_t st) {
+    parrep_serve_kernel<kFormF32Mixed><<<g, t, s, st>>>(d);
+    return cudaGetLastError();
+}
+#endif
+
 #if PARREP_PART >= 1 && PARREP_PART <= 3
 // The genetic switch runs in the two-species instantiation (its channels are
 // chosen by N.kind inside).
@@ -3386,6 +3417,10 @@ int serve_attrs_f32d(int*, int, int);
 cudaError_t serve_launch_f64(const ServeDev&, int, int, int, cudaStream_t);
 cudaError_t serve_launch_f32s(const ServeDev&, int, int, int, cudaStream_t);
 cudaError_t serve_launch_f32d(const ServeDev&, int, int, int, cudaStream_t);
+int batch_attrs_f32m(int*, int, int);
+cudaError_t batch_launch_f32m(const cudaLaunchConfig_t&, const RunParams*, const int*, const int2*, BatchDev);
+int serve_attrs_f32m(int*, int, int);
+cudaError_t serve_launch_f32m(const ServeDev&, int, int, int, cudaStream_t);
 
 int kernel_attrs_form(int form, int kind, int* m, int s, int t) {
     return form == kFormF32Direct ? run_attrs_f32d(kind, m, s, t)
@@ -3400,7 +3435,8 @@ cudaError_t launch_run(const RunParams& p, int grid, int threads, int smem_bytes
 }
 
 int batch_attrs_form(int form, int* m, int s, int t) {
-    return form == kFormF32Direct ? batch_attrs_f32d(m, s, t)
+    return form == kFormF32Mixed    ? batch_attrs_f32m(m, s, t)
+           : form == kFormF32Direct ? batch_attrs_f32d(m, s, t)
            : form == kFormF32Staged ? batch_attrs_f32s(m, s, t)
                                     : batch_attrs_f64(m, s, t);
 }
@@ -3421,7 +3457,8 @@ cudaError_t launch_batch(int form, const RunParams* d_params, int n, const int* 
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return form == kFormF32Direct ? batch_launch_f32d(cfg, d_params, d_off, d_items, bd)
+    return form == kFormF32Mixed    ? batch_launch_f32m(cfg, d_params, d_off, d_items, bd)
+           : form == kFormF32Direct ? batch_launch_f32d(cfg, d_params, d_off, d_items, bd)
            : form == kFormF32Staged ? batch_launch_f32s(cfg, d_params, d_off, d_items, bd)
                                     : batch_launch_f64(cfg, d_params, d_off, d_items, bd);
 }
@@ -3433,13 +3470,15 @@ cudaError_t launch_batch_gather(const RunParams* d_params, int n, RunCtl* out, c
 }
 
 int serve_attrs_form(int form, int* m, int s, int t) {
-    return form == kFormF32Direct ? serve_attrs_f32d(m, s, t)
+    return form == kFormF32Mixed    ? serve_attrs_f32m(m, s, t)
+           : form == kFormF32Direct ? serve_attrs_f32d(m, s, t)
            : form == kFormF32Staged ? serve_attrs_f32s(m, s, t)
                                     : serve_attrs_f64(m, s, t);
 }
 
 cudaError_t launch_serve(int form, const ServeDev& sd, int grid, int threads, int smem_bytes, cudaStream_t st) {
-    return form == kFormF32Direct ? serve_launch_f32d(sd, grid, threads, smem_bytes, st)
+    return form == kFormF32Mixed    ? serve_launch_f32m(sd, grid, threads, smem_bytes, st)
+           : form == kFormF32Direct ? serve_launch_f32d(sd, grid, threads, smem_bytes, st)
            : form == kFormF32Staged ? serve_launch_f32s(sd, grid, threads, smem_bytes, st)
                                     : serve_launch_f64(sd, grid, threads, smem_bytes, st);
 }

@@ -147,7 +147,7 @@ extern "C" void parrep_server_default_options(parrep_server_options* o) {
     o->block_threads = 0;
     o->replicas_per_block = 0;
     o->ring = 4096;
-    o->f32_layout = PARREP_F32_STAGED;
+    o->f32_layout = PARREP_F32_MIXED;
     o->arena_bytes = 4ll << 30;
     o->log_cap = 4096;
     o->idle_exit_s = 0.05;
@@ -272,8 +272,12 @@ static int admit(parrep_server_t s, Request& q, int slot) {
     // launch shape of one gang member
     Plan pl;
     memset(&pl, 0, sizeof(pl));
-    pl.form = s->form;
-    if (s->form == kFormF32Staged) {
+    // the mixed form runs each request in its own layout (direct for the
+    // genetic switch and from kDirectAutoReplicas replicas on)
+    pl.form = s->form != kFormF32Mixed ? s->form
+              : (r.n_replicas >= kDirectAutoReplicas || r.net.kind == PARREP_GENETIC) ? kFormF32Direct
+                                                                                        : kFormF32Staged;
+    if (pl.form == kFormF32Staged) {
         const int pipe = s->threads - s->RB >= 64;
         int sz = -1;
         for (int with_hist = 1; with_hist >= 0 && sz < 0; --with_hist) {
@@ -432,18 +436,22 @@ extern "C" int parrep_server_create(const parrep_server_options* opt, parrep_ser
     if (!(o.idle_exit_s > 0.0 && o.idle_exit_s <= 60.0)) return sfail(nullptr, PARREP_EINVAL, "idle_exit_s");
     if (!(o.wait_timeout_s > 0.0 && o.wait_timeout_s <= 3600.0))
         return sfail(nullptr, PARREP_EINVAL, "wait_timeout_s");
-    if (o.f32_layout != PARREP_F32_AUTO && o.f32_layout != PARREP_F32_STAGED && o.f32_layout != PARREP_F32_DIRECT)
+    if (o.f32_layout < PARREP_F32_AUTO || o.f32_layout > PARREP_F32_MIXED)
         return sfail(nullptr, PARREP_EINVAL, "f32_layout");
-    // one form for every request: binary64, or binary32 staged (the default;
-    // auto means staged here) or direct
+    // the serve kernel's form: binary64, or binary32 mixed (the default and
+    // auto: each request in the layout its replica count calls for), staged
+    // or direct
     const int form = o.precision == PARREP_FP64 ? kFormF64
                      : o.f32_layout == PARREP_F32_DIRECT ? kFormF32Direct
-                                                           : kFormF32Staged;
+                     : o.f32_layout == PARREP_F32_AUTO || o.f32_layout == PARREP_F32_MIXED ? kFormF32Mixed
+                                                         : kFormF32Staged;
     if (form == kFormF32Direct && o.block_threads > kDirectThreads)
         return sfail(nullptr, PARREP_EINVAL, "the direct layout takes at most 256 threads per block");
     const int threads = o.block_threads ? o.block_threads
-                                        : (form == kFormF32Staged ? 384 : form == kFormF32Direct ? kDirectThreads : 128);
-    const int RB = form == kFormF32Staged ? (rb ? rb : 32) : threads;
+                                        : (form == kFormF32Staged || form == kFormF32Mixed ? 384
+                                           : form == kFormF32Direct                       ? kDirectThreads
+                                                                                          : 128);
+    const int RB = form == kFormF32Staged || form == kFormF32Mixed ? (rb ? rb : 32) : threads;
     if (threads < RB) return sfail(nullptr, PARREP_EINVAL, "block_threads < replicas_per_block");
     auto* s = new parrep_server_s();
     s->opt = o;
@@ -508,7 +516,7 @@ extern "C" int parrep_server_submit(parrep_server_t s, const parrep_request* req
     std::string why;
     if (!check_network(&req->net, &req->regions, why)) return sfail(s, PARREP_EINVAL, why);
     if (req->net.kind == PARREP_GENETIC && s->form == kFormF32Staged)
-        return sfail(s, PARREP_EINVAL, "the genetic switch's FP32 form needs the direct layout (f32_layout)");
+        return sfail(s, PARREP_EINVAL, "the genetic switch's FP32 form needs the direct or auto layout (f32_layout)");
     if (req->n_replicas < 1 || req->n_replicas > (1ll << 30)) return sfail(s, PARREP_EINVAL, "n_replicas");
     if (!(req->t_corr >= 0.0) || !(req->t_phase >= 0.0) || !(req->t_corr < kTEndLimit * 1024) ||
         !(req->t_phase < 1e12))

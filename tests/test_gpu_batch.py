@@ -75,7 +75,7 @@ def test_batch_block_shapes_do_not_change_results(precision):
     inst = _mixed(precision)
     shapes = ([(128, 128, "auto"), (64, 64, "auto")] if precision == "f64" else
               [(384, 32, "staged"), (256, 64, "staged"), (384, 128, "staged"), (256, 256, "direct"),
-               (128, 128, "direct")])
+               (128, 128, "direct"), (384, 64, "mixed")])
     ref = None
     for T, RB, layout in shapes:
         b = ParRepBatch([g for g, _, _ in inst], block_threads=T, replicas_per_block=RB, autotune=False,
@@ -89,6 +89,48 @@ def test_batch_block_shapes_do_not_change_results(precision):
             for a, r in zip(res, ref):
                 _same(a, r)
         b.close()
+
+
+def test_batch_mixed_layout_equals_solo_runs():
+    """The mixed FP32 batch kernel runs each instance in its own layout --
+    one thread per replica from 16384 replicas on, owner + helper warps below
+    -- and every instance still ends with its solo run's results."""
+    big = ParRep(V10, 20000, 100, 100, x0=[3], thresh="steps", precision="f32", fv_group=32, T_burn=5.0)
+    small = ParRep(V10, 40, 200, 200, x0=[2], thresh="steps", precision="f32", fv_group=16, T_burn=5.0)
+    tg = ParRep(K.toggle(alpha=20, n=2.5, hist_max=(63, 63)), 17000, 0.5, 0.5, x0=[15, 2], precision="f32",
+                T_burn=2.0)
+    inst = [(big, 12.0, 5), (small, 60.0, 6), (tg, 6.0, 7)]
+    solo = []
+    for g, T, sd in inst:
+        g.run(T, sd)
+        solo.append(_result(g))
+    b = ParRepBatch([g for g, _, _ in inst], block_threads=384, replicas_per_block=64, autotune=False,
+                    f32_layout="mixed")
+    b.run([T for _, T, _ in inst], [sd for _, _, sd in inst])
+    assert b.status() == [0, 0, 0]
+    assert b.info()["f32_layout"] == "mixed"
+    for (g, _, _), r in zip(inst, solo):
+        _same(_result(g), r)
+    b.close()
+
+
+def test_batch_layout_choice():
+    """The FP32 auto layout is the mixed one, and the chosen layout is
+    reported."""
+    a = ParRep(V10, 40, 50, 50, x0=[2], thresh="steps", precision="f32")
+    b = ParRepBatch([a], autotune=False)
+    b.run([5.0], [1])
+    assert b.info()["f32_layout"] == "mixed"
+    b.close()
+    b = ParRepBatch([a], autotune=False, f32_layout="staged")
+    b.run([5.0], [1])
+    assert b.info()["f32_layout"] == "staged"
+    b.close()
+    d = ParRep(V10, 40, 50, 50, x0=[2], thresh="steps")
+    b = ParRepBatch([d], autotune=False)
+    b.run([5.0], [1])
+    assert b.info()["f32_layout"] is None
+    b.close()
 
 
 def test_batch_autotuner_tries_shapes_and_keeps_results():

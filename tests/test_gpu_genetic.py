@@ -101,21 +101,26 @@ def test_genetic_parrep_matches_exact_law():
 
 def test_genetic_fp32_needs_the_direct_layout():
     """The staged FP32 layout has no six-channel chain: asking for it is
-    refused; the default (auto) layout and the direct server take the kind."""
+    refused by single runs, servers and batches; the default (auto / mixed)
+    layouts and the direct server take the kind."""
     spec = _spec(SMALL, 16, 250, 13)
     g = ParRep(spec, 16, 50, 50, x0=[0, 0], thresh="steps", precision="f32")
     with pytest.raises(ParRepError):
         g.set_options(thresh="steps", precision="f32", f32_layout="staged")
-    srv = ParRepServer(precision="f32", arena_bytes=8 << 20)
+    srv = ParRepServer(precision="f32", arena_bytes=8 << 20, f32_layout="staged")
     with pytest.raises(ParRepError):
         srv.submit(spec, 16, 50, 50, 10.0, 1, x0=[0, 0], thresh="steps")
     srv.close()
+    with pytest.raises(ParRepError):
+        ParRepBatch([g], f32_layout="staged")
     solo = ParRep(spec, 16, 50, 50, x0=[0, 0], thresh="steps", precision="f32", T_burn=2.0)
     solo.run(10.0, 1)
-    srv = ParRepServer(precision="f32", arena_bytes=64 << 20, f32_layout="direct")
-    r = srv.result(srv.submit(spec, 16, 50, 50, 10.0, 1, x0=[0, 0], thresh="steps", T_burn=2.0), timeout_s=60.0)
-    srv.close()
-    assert r["status"] == 0 and np.array_equal(r["hist"], solo.histogram())
+    for layout in ("direct", "mixed"):
+        srv = ParRepServer(precision="f32", arena_bytes=64 << 20, f32_layout=layout)
+        r = srv.result(srv.submit(spec, 16, 50, 50, 10.0, 1, x0=[0, 0], thresh="steps", T_burn=2.0),
+                       timeout_s=60.0)
+        srv.close()
+        assert r["status"] == 0 and np.array_equal(r["hist"], solo.histogram())
 
 
 def _cprime():
