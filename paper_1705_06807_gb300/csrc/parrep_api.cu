@@ -307,7 +307,7 @@ extern "C" int parrep_set_options(parrep_t h, const parrep_options* o) {
 int parrep::align16(int x) { return (x + 15) & ~15; }
 
 int parrep::fast_layout(parrep_t h, int RB, int threads, int with_hist, int pipelined, Plan& pl) {
-    const int B = 32;
+    const int B = kStagedB;
     const int nbuf = pipelined ? 3 : 1, ntr = pipelined ? 2 : 1;
     pl.pipelined = pipelined;
     int off = 0;
@@ -320,6 +320,7 @@ int parrep::fast_layout(parrep_t h, int RB, int threads, int with_hist, int pipe
     }
     pl.off_tab = -1;
     pl.off_inv = -1;
+    pl.off_thr = -1;
     if (h->net.kind == PARREP_SCHLOGL) {
         const int tb = (h->net.hist_max[0] + 5) * 16;  // padded by two entries on each side
         if (tb <= 64 * 1024) {
@@ -327,6 +328,8 @@ int parrep::fast_layout(parrep_t h, int RB, int threads, int with_hist, int pipe
             off += align16(tb);
             pl.off_inv = off;
             off += align16((h->net.hist_max[0] + 1) * 4);
+            pl.off_thr = off;  // int4 per state, kThrPad entries beyond each end
+            off += align16((h->net.hist_max[0] + 1 + 2 * kThrPad) * 16);
         }
     } else {
         pl.off_tab = off;
@@ -385,7 +388,7 @@ static int plan_launch(parrep_t h, Plan& pl) {
         pl.grid = (int)((h->R + threads - 1) / threads);
         pl.S = h->opt.chunk_steps > 0 ? h->opt.chunk_steps : 256;
         pl.off_tab = pl.off_buf = pl.off_trace = pl.off_live = pl.off_nvalid = -1;
-        pl.off_limbs = pl.off_inv = pl.off_rng = pl.off_decp = -1;
+        pl.off_limbs = pl.off_inv = pl.off_rng = pl.off_decp = pl.off_thr = -1;
         pl.pipelined = 0;
         for (int with_hist = 1; with_hist >= 0; --with_hist) {
             if (with_hist && h->nbins * 8 > (form == kFormF32Direct ? kDirectSmemHistLimit : kSmemHistLimit)) continue;
@@ -470,6 +473,7 @@ int parrep::run_params(parrep_t h, double T_end, uint64_t seed, const Plan& pl, 
     p.off_inv = pl.off_inv;
     p.off_rng = pl.off_rng;
     p.off_decp = pl.off_decp;
+    p.off_thr = pl.off_thr;
     p.pipelined = pl.pipelined;
     if (p.thresh == PARREP_THRESH_STEPS) {
         p.n_c = (long long)h->t_corr;

@@ -256,7 +256,7 @@ static int set_shape(parrep_batch_t b, int threads, int RB, int form) {
             pl.B = 0;
             pl.S = h->opt.chunk_steps > 0 ? h->opt.chunk_steps : 256;
             pl.off_tab = pl.off_buf = pl.off_trace = pl.off_live = pl.off_nvalid = -1;
-            pl.off_limbs = pl.off_inv = pl.off_rng = pl.off_decp = -1;
+            pl.off_limbs = pl.off_inv = pl.off_rng = pl.off_decp = pl.off_thr = -1;
             pl.use_smem_hist = h->nbins * 8 <= (form == kFormF32Direct ? kDirectSmemHistLimit : kSmemHistLimit);
             pl.form = f;
             pl.smem = pl.use_smem_hist ? h->nbins * 8 : 0;

@@ -62,6 +62,7 @@ struct Plan {
     int threads, grid, smem, RB, log2RB, B, S, use_smem_hist;
     int off_tab, off_buf, off_trace, off_live, off_nvalid;
     int off_limbs, off_inv, off_rng, off_decp;
+    int off_thr;
     int pipelined;
 };
 

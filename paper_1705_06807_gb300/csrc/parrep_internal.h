@@ -108,6 +108,13 @@ struct BatchDev {
 // Kernel forms: binary64 (one thread per replica), binary32 staged (owner
 // threads + helper warps per block, for few replicas per SM), binary32 direct
 // (one thread per replica at high occupancy, for many replicas).
+// FP32 staged layout: steps staged per sub-chunk, and the entries of the
+// Schloegl threshold table beyond each end of [0, hist_max] (a speculative
+// owner pass runs at most kStagedB steps past an exit, reading one state
+// further on each side).
+constexpr int kStagedB = 32;
+constexpr int kThrPad = kStagedB + 2;
+
 enum Form { kFormF64 = 0, kFormF32Staged = 1, kFormF32Direct = 2,
             // batch and serve kernels only: every instance runs its own
             // binary32 layout (RunParams::form, staged or direct)
@@ -125,6 +132,7 @@ struct RunParams {
     int RB, log2RB, B;
     int off_tab, off_buf, off_trace, off_live, off_nvalid;
     int off_limbs, off_inv, off_rng, off_decp;
+    int off_thr;    // FP32 Schloegl: per-state choice thresholds (-1: none)
     int pipelined;  // FP32: owner warps and helper warps overlap (three draw slots, two trace slots)
     unsigned long long q_tcorr;
     long long n_c;

@@ -851,6 +851,7 @@ static __device__ void flush_shared(unsigned long long* sh, unsigned long long* 
 struct FastSmem {
     const float4* tab;   // Schloegl: per state (c0, c0+c1, ..., a0); nullptr = compute
     const float* inv;    // Schloegl with tab: per state RN(1/a0)
+    const int4* thr;     // Schloegl with tab: per state choice thresholds (choice_thresholds)
     int* rng;            // [4]: min/max of x0 and x1 touched in the sub-chunk
     unsigned long long* decp;  // decorrelation rounds: prefix sums of the holding times
     const float* prodU;  // toggle: production of U by V, of V by U (shared copies)
@@ -916,6 +917,8 @@ static __device__ void build_fast_tables(const NetDev& N, float4* tab, float* in
 }
 
 // (P) Philox words for steps step0 .. step0+nsteps-1 of the block's live replicas.
+// The parallel step stores (E, u2) per step, or (E, k2) -- the 23-bit index
+// of u2, as integer bits -- for the Schloegl threshold chain (F.thr).
 template <bool WANT_E>
 __device__ __forceinline__ void produce_store(const FastSmem& F, int lg, int mask, int nsteps, int i, uint4 w) {
     constexpr int PER = WANT_E ? 2 : 4;
@@ -923,8 +926,11 @@ __device__ __forceinline__ void produce_store(const FastSmem& F, int lg, int mas
     if (!F.live[lane]) return;
     float2* buf = F.buf;
     if (WANT_E) {
-        buf[(s << lg) + lane] = make_float2(-logf(u01f(w.x)), u01f(w.y));
-        if (s + 1 < nsteps) buf[((s + 1) << lg) + lane] = make_float2(-logf(u01f(w.z)), u01f(w.w));
+        const bool kidx = F.thr != nullptr;
+        const float ya = kidx ? __int_as_float((int)(w.y >> 9)) : u01f(w.y);
+        const float yb = kidx ? __int_as_float((int)(w.w >> 9)) : u01f(w.w);
+        buf[(s << lg) + lane] = make_float2(-logf(u01f(w.x)), ya);
+        if (s + 1 < nsteps) buf[((s + 1) << lg) + lane] = make_float2(-logf(u01f(w.z)), yb);
     } else {
         buf[(s << lg) + lane].y = u01f(w.x);
         if (s + 1 < nsteps) buf[((s + 1) << lg) + lane].y = u01f(w.y);
@@ -1116,6 +1122,80 @@ __device__ __forceinline__ int spec_pass_schlogl(const NetDev& N, const float2* 
     return first;
 }
 
+// Choice thresholds of the binary32 direct method at a Schloegl state.  A
+// step's uniform is u_k = (k + 1/2) 2^-23 with k its 23-bit index, and the
+// target t = RN(u_k a0) does not decrease with k; so "t >= c_j" holds exactly
+// for k >= K_j, with K_j found by bisection on k (the same products and
+// comparisons as the chain's).  The chain goes up (channels 0 and 2) iff
+// k < K0 or K1 <= k < K2.  When rounding leaves no sum above t (k >= K3) the
+// direct method takes the last channel with positive propensity, which goes
+// up only if l3 = 0; then a0 = c2 exactly, K3 = K2, and the up set is k < K0
+// or k >= K1.  Stored as (K0, K1, D): up iff k < K0 or (unsigned)(k - K1) < D.
+static __device__ unsigned first_k_at_least(float a0, float c) {
+    unsigned lo = 0u, hi = 1u << 23;  // the answer lies in [lo, hi]
+    while (lo < hi) {
+        const unsigned mid = (lo + hi) >> 1;
+        const float u = ((float)mid + 0.5f) * 0x1p-23f;
+        if (u * a0 >= c) hi = mid;
+        else lo = mid + 1u;
+    }
+    return lo;
+}
+
+static __device__ int4 choice_thresholds(const NetDev& N, int x) {
+    const float4 C = cums_schlogl(N.Af[0], N.Af[1], N.Af[2], N.Af[3], x);
+    const unsigned K0 = first_k_at_least(C.w, C.x), K1 = first_k_at_least(C.w, C.y);
+    const unsigned K2 = first_k_at_least(C.w, C.z);
+    const bool rounding_up = (last_positive(N, x, 0) & 1) == 0;
+    return make_int4((int)K0, (int)K1, (int)(rounding_up ? (1u << 23) - K1 : K2 - K1), 0);
+}
+
+__device__ __forceinline__ bool goes_up_k(int4 T, int k) {
+    return (k < T.x) | ((unsigned)(k - T.y) < (unsigned)T.z);
+}
+
+// thr[x] for x in [-kThrPad, hist_max + kThrPad]; the entries beyond
+// [0, hist_max] repeat the end states' (read only by speculative steps past an exit)
+static __device__ void build_thr_table(const NetDev& N, int4* thr) {
+    for (int k = threadIdx.x; k <= N.hist_max0 + 2 * kThrPad; k += blockDim.x)
+        thr[k - kThrPad] = choice_thresholds(N, min(max(k - kThrPad, 0), N.hist_max0));
+}
+
+// Speculative pass of a Schloegl jump chain with the threshold table: two
+// steps per iteration, the entries at x-1, x, x+1 loaded together, and every
+// choice exact.  trace[s*stride + off] receives the state before step s.
+// Returns the first step whose target leaves [lo, hi] (n if none); the walk
+// goes on past it (at most n steps, inside the table's padding) but nothing
+// after that step is used.
+__device__ __forceinline__ int spec_pass_thr(const int4* __restrict__ thr, const float2* buf, int* trace, int stride,
+                                             int off, int n, int lo, int hi, int& x) {
+    int first = n;
+    const unsigned span = (unsigned)(hi - lo);
+    const int npair = n & ~1;
+    for (int s = 0; s < npair; s += 2) {
+        const int i1 = s * stride + off, i2 = i1 + stride;
+        const int k1 = __float_as_int(buf[i1].y), k2 = __float_as_int(buf[i2].y);
+        const int4 T0 = thr[x], Tm = thr[x - 1], Tp = thr[x + 1];
+        const bool up1 = goes_up_k(T0, k1);
+        const bool up2 = up1 ? goes_up_k(Tp, k2) : goes_up_k(Tm, k2);
+        const int xa = up1 ? x + 1 : x - 1;
+        const int xb = up2 ? xa + 1 : xa - 1;
+        const bool e1 = (unsigned)(xa - lo) > span, e2 = (unsigned)(xb - lo) > span;
+        first = min(first, e1 ? s : (e2 ? s + 1 : n));
+        trace[i1] = x;
+        trace[i2] = xa;
+        x = xb;
+    }
+    if (npair < n) {  // odd tail: one step
+        const int i = npair * stride + off;
+        const int xa = goes_up_k(thr[x], __float_as_int(buf[i].y)) ? x + 1 : x - 1;
+        first = min(first, (unsigned)(xa - lo) > span ? npair : n);
+        trace[i] = x;
+        x = xa;
+    }
+    return first;
+}
+
 // (C) one owner's B lockstep steps of the parallel step; stops at its escape
 // or at a state outside [0, hist_max].  Schloegl with its table: two steps
 // per iteration -- the sums at x-1, x, x+1 are loaded together and the second
@@ -1131,7 +1211,32 @@ __device__ __forceinline__ void consume_par(const RunParams& P, const FastSmem& 
     int lo0 = 0x7fffffff, hi0 = -1, lo1 = 0x7fffffff, hi1 = -1;
     if (running) {
         nv = P.B;
-        if (KIND == PARREP_SCHLOGL) {
+        if (KIND == PARREP_SCHLOGL && F.thr) {
+            // speculative pass with exact choices; the states it visits lie
+            // within B of the start, which bounds the warp's rectangle
+            const int B = P.B, lg = P.log2RB;
+            int x = x0;
+            lo0 = max(x0 - B, 0);
+            hi0 = min(x0 + B, N.hist_max0);
+            const int first = spec_pass_thr(F.thr, F.buf, F.trace, P.RB, lane, B, rt.lo, rt.hi, x);
+            if (first < B) {
+                // the replica leaves W (or [0, hist_max]) at step `first`
+                const int i = (first << lg) + lane;
+                const int y = F.trace[i];
+                const int yn = goes_up_k(F.thr[y], __float_as_int(F.buf[i].y)) ? y + 1 : y - 1;
+                if (jump_outcome<KIND, true>(N, rt, yn, 0) == 1) {
+                    mykey = pos_of(sbase + first, r);
+                    xe0 = yn;
+                    xe1 = 0;
+                } else {
+                    myoob = pos_of(sbase + first, r);
+                }
+                nv = first + 1;
+                running = false;
+                x = y;
+            }
+            x0 = x;
+        } else if (KIND == PARREP_SCHLOGL) {
             // speculative pass, then the exact rule from the first rare step on
             const int B = P.B, lg = P.log2RB;
             int x = x0;
@@ -2110,6 +2215,7 @@ __device__ __forceinline__ bool run_instance(const RunParams& P, int lb, unsigne
         }
         F.tab = P.off_tab >= 0 && KIND == PARREP_SCHLOGL ? (const float4*)(smem + P.off_tab) + 2 : nullptr;
         F.inv = F.tab ? (const float*)(smem + P.off_inv) : nullptr;
+        F.thr = F.tab && P.off_thr >= 0 ? (const int4*)(smem + P.off_thr) + kThrPad : nullptr;
         F.rng = (int*)(smem + P.off_rng);
         F.decp = (unsigned long long*)(smem + P.off_decp);
         F.prodU = KIND == PARREP_TOGGLE ? (const float*)(smem + P.off_tab) : nullptr;
@@ -2119,6 +2225,7 @@ __device__ __forceinline__ bool run_instance(const RunParams& P, int lb, unsigne
         F.live = (int*)(smem + P.off_live);
         F.nvalid = (int*)(smem + P.off_nvalid);
         build_fast_tables(N, (float4*)F.tab, (float*)F.inv, (float*)F.prodU, (float*)F.prodV);
+        if (KIND == PARREP_SCHLOGL && F.thr) build_thr_table(N, (int4*)F.thr);
     }
 
     if (P.use_smem_hist) {

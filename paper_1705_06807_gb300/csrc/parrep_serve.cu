@@ -292,7 +292,7 @@ static int admit(parrep_server_t s, Request& q, int slot) {
         pl.RB = s->threads;
         pl.S = r.chunk_steps > 0 ? r.chunk_steps : 256;
         pl.off_tab = pl.off_buf = pl.off_trace = pl.off_live = pl.off_nvalid = -1;
-        pl.off_limbs = pl.off_inv = pl.off_rng = pl.off_decp = -1;
+        pl.off_limbs = pl.off_inv = pl.off_rng = pl.off_decp = pl.off_thr = -1;
         pl.use_smem_hist = (long long)nb * 8 <= (long long)s->smem;
         pl.smem = pl.use_smem_hist ? (int)nb * 8 : 0;
     }
