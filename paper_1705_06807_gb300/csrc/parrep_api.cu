@@ -344,7 +344,7 @@ int parrep::fast_layout(parrep_t h, int RB, int threads, int with_hist, int pipe
     pl.off_nvalid = off;
     off += ntr * RB * 4;
     pl.off_rng = off;
-    off += 32;
+    off += 48;  // three rectangles of touched states (12 ints)
     pl.off_decp = off;  // decorrelation rounds of min(4 x threads, B x RB) steps
     off += (4 * threads < B * RB ? 4 * threads : B * RB) * 8;
     pl.B = B;

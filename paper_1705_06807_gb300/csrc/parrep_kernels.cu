@@ -642,10 +642,11 @@ static __device__ int dephase_warp(const NetDev& N, bool active, unsigned r, int
 // atomic add (it is emulated and serialises under contention), so the FP32
 // form splits q into two 32-bit limbs -- the low 16 bits and the rest -- added
 // with native 32-bit atomics and folded exactly into the 64-bit shared sums
-// after every staged sub-chunk.  A sub-chunk adds at most B*RB values to a
-// bin, so with q < qmax = 2^47 / (B*RB) the high-limb sum stays inside a
-// signed 32-bit range (roll-backs included) and the low-limb sum below 2^30.
-// Holding times too large for the limbs go straight to the global sums.
+// every fold_period(RB) staged sub-chunks (at most).  A sub-chunk adds at most
+// B*RB values to a bin, so with q < qmax = 2^47 / (B*RB*fold_period) the
+// high-limb sum stays inside a signed 32-bit range (roll-backs included) and
+// the low-limb sum below 2^30.  Holding times too large for the limbs go
+// straight to the global sums.
 struct HistSink {
     unsigned long long* sh;  // shared histogram or nullptr
     unsigned long long* g;   // global histogram of the current period
@@ -676,6 +677,10 @@ struct HistSink {
         }
     }
 };
+
+// Sub-chunks between limb folds in the pipelined parallel step: 4 with 32
+// owners a block, 2 with 64, else 1 (qmax stays at least 2^47 / (B * 128)).
+__device__ __forceinline__ int fold_period(int log2RB) { return log2RB >= 7 ? 1 : 1 << (7 - log2RB); }
 
 // Folds the limbs of bins [b0, b1] into the 64-bit shared sums (signed, so a
 // roll-back's negative limb sums are exact) and clears them.
@@ -1161,6 +1166,26 @@ static __device__ void build_thr_table(const NetDev& N, int4* thr) {
         thr[k - kThrPad] = choice_thresholds(N, min(max(k - kThrPad, 0), N.hist_max0));
 }
 
+// Shared-memory accesses by shared-window address.  The staged arrays are
+// reached through pointers kept in a struct, which the compiler may turn into
+// generic accesses; the owner's chain reads and writes shared memory directly.
+// The table reads are plain (the table does not change while a chain runs);
+// the buffer reads and trace writes keep their order against the barriers.
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ int4 lds_table(unsigned a) {
+    int4 v;
+    asm("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ int lds_word(unsigned a) {
+    int v;
+    asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void sts_word(unsigned a, int v) {
+    asm volatile("st.shared.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+
 // Speculative pass of a Schloegl jump chain with the threshold table: two
 // steps per iteration, the entries at x-1, x, x+1 loaded together, and every
 // choice exact.  trace[s*stride + off] receives the state before step s.
@@ -1172,18 +1197,21 @@ __device__ __forceinline__ int spec_pass_thr(const int4* __restrict__ thr, const
     int first = n;
     const unsigned span = (unsigned)(hi - lo);
     const int npair = n & ~1;
+    // .y of buf[i] (the 23-bit index) at ka + 8 i; thr[x] at ta + 16 x; trace[i] at ra + 4 i
+    const unsigned ka = smem_addr(buf) + 4u, ta = smem_addr(thr), ra = smem_addr(trace);
     for (int s = 0; s < npair; s += 2) {
         const int i1 = s * stride + off, i2 = i1 + stride;
-        const int k1 = __float_as_int(buf[i1].y), k2 = __float_as_int(buf[i2].y);
-        const int4 T0 = thr[x], Tm = thr[x - 1], Tp = thr[x + 1];
+        const int k1 = lds_word(ka + 8u * (unsigned)i1), k2 = lds_word(ka + 8u * (unsigned)i2);
+        const unsigned tx = ta + 16u * (unsigned)x;
+        const int4 T0 = lds_table(tx), Tm = lds_table(tx - 16u), Tp = lds_table(tx + 16u);
         const bool up1 = goes_up_k(T0, k1);
         const bool up2 = up1 ? goes_up_k(Tp, k2) : goes_up_k(Tm, k2);
         const int xa = up1 ? x + 1 : x - 1;
         const int xb = up2 ? xa + 1 : xa - 1;
         const bool e1 = (unsigned)(xa - lo) > span, e2 = (unsigned)(xb - lo) > span;
         first = min(first, e1 ? s : (e2 ? s + 1 : n));
-        trace[i1] = x;
-        trace[i2] = xa;
+        sts_word(ra + 4u * (unsigned)i1, x);
+        sts_word(ra + 4u * (unsigned)i2, xa);
         x = xb;
     }
     if (npair < n) {  // odd tail: one step
@@ -1438,13 +1466,16 @@ static __device__ void chunk_f32(const RunParams& P, const FastSmem& F, const Hi
         // sub-chunk j while the helper warps draw sub-chunk j+1 and account
         // for sub-chunk j-1 (draws in three slots, traces in two), so the
         // owners' serial chains overlap the helpers' parallel work.  One
-        // block barrier per stage; the helpers fold the limbs of j-1 behind a
-        // named barrier of their own before the stage ends.
+        // block barrier per stage; every fold_period sub-chunks (and at the
+        // end) the helpers fold the limbs of the states the owners touched
+        // since the last fold, behind a named barrier of their own.
         const int RB = P.RB, B = P.B;
         const int nh = blockDim.x - RB, h = threadIdx.x - RB;
         const int slotsz = B << P.log2RB;
+        const int fp = fold_period(P.log2RB);
         if (owner) F.live[threadIdx.x] = running ? 1 : 0;
-        if (threadIdx.x < 8) F.rng[threadIdx.x] = (threadIdx.x & 1) ? -1 : 0x7fffffff;
+        // two per-sub-chunk rectangles of touched states and their union since the last fold
+        if (threadIdx.x < 12) F.rng[threadIdx.x] = (threadIdx.x & 1) ? -1 : 0x7fffffff;
         __syncthreads();
         pc.start();
         const int nsub = S / B;
@@ -1482,11 +1513,19 @@ static __device__ void chunk_f32(const RunParams& P, const FastSmem& F, const Hi
                     Fa.trace = F.trace + (jp & 1) * slotsz;
                     Fa.nvalid = F.nvalid + (jp & 1) * RB;
                     account<KIND, MODE>(P, Fa, hs, rbase, jp * B, cut, to_post, qs, ev, inc_ev, h, nh);
-                    asm volatile("bar.sync 1, %0;" ::"r"(nh) : "memory");
                     int* rg = F.rng + (jp & 1) * 4;
-                    if (limbs && rg[1] >= rg[0]) fold_limbs(hs, rg[0], rg[1], P.net.ystride, rg[2], rg[3], h, nh);
-                    asm volatile("bar.sync 1, %0;" ::"r"(nh) : "memory");
-                    if (h < 4) rg[h] = (h & 1) ? -1 : 0x7fffffff;
+                    int* un = F.rng + 8;
+                    if (h < 4) {
+                        const int v = rg[h];
+                        un[h] = (h & 1) ? max(un[h], v) : min(un[h], v);
+                        rg[h] = (h & 1) ? -1 : 0x7fffffff;
+                    }
+                    if (limbs && (!consume || jp % fp == fp - 1)) {
+                        asm volatile("bar.sync 1, %0;" ::"r"(nh) : "memory");
+                        if (un[1] >= un[0]) fold_limbs(hs, un[0], un[1], P.net.ystride, un[2], un[3], h, nh);
+                        asm volatile("bar.sync 1, %0;" ::"r"(nh) : "memory");
+                        if (h < 4) un[h] = (h & 1) ? -1 : 0x7fffffff;
+                    }
                 }
             }
             const bool any_next = __syncthreads_or(running);
@@ -2263,7 +2302,10 @@ __device__ __forceinline__ bool run_instance(const RunParams& P, int lb, unsigne
     }
     int period_post = P.q_Tburn == 0 ? 1 : 0;  // which global sums this block's histogram feeds
     HistSink hs{P.use_smem_hist ? sh_hist : nullptr, period_post ? P.hist_post : P.hist_pre, limb_lo, limb_hi,
-                N.ystride, STAGED ? ((1ull << 47) >> (P.log2RB + 5)) : 0ull};
+                N.ystride,
+                STAGED ? (1ull << 47) / ((unsigned long long)P.B * (unsigned long long)P.RB *
+                                         (unsigned long long)fold_period(P.log2RB))
+                       : 0ull};
     unsigned long long chunk_c = 0;
     unsigned long long est_q = 0, est_ev = 0;  // time and jumps of the last chunk
     if (join) {
