@@ -1764,6 +1764,112 @@ static __device__ int decorr_chain(const NetDev& N, const FastSmem& F, int x0, i
     return M;
 }
 
+// (2) for the Schloegl network with the threshold table, by the whole block,
+// in windows of 64 jumps.  From the window's start state x the chain can
+// only reach x-64 .. x+64 (129 candidates c, state x + c - 64), and before
+// jump s only the candidates with |c - 64| <= s and c - 64 = s (mod 2).
+// (a) every reachable (jump, candidate) pair's move is decided from the table
+//     in parallel: nx[s][c] = c +- 1;
+// (b) each reachable start candidate of each block of 8 jumps is followed
+//     through its block: m8[b][c];
+// (c) one thread follows the eight block maps from c = 64;
+// (d) eight threads walk their block's jumps and write the trace.
+// The states are those of the one-thread chain (every choice exact).  A
+// window that could reach beyond [0, hist_max] is walked by one thread with
+// the range check, and a jump out of the range ends the round (its state in
+// last0; returns the number of jumps made).  Called by every thread of the
+// block; scratch holds at least 64 * 129 + 8 * 129 bytes.
+static __device__ int decorr_chain_block(const NetDev& N, const FastSmem& F, unsigned char* scratch, int x0, int M,
+                                         int& last0) {
+    __shared__ int s_x, s_n, s_last, s_done;
+    __shared__ unsigned char s_bst[8];
+    const int tid = threadIdx.x, T = blockDim.x, hm = N.hist_max0;
+    unsigned char* nx = scratch;            // [64][129]
+    unsigned char* m8 = scratch + 64 * 129;  // [8][129]
+    const float2* buf = F.buf;
+    int* trace = F.trace;
+    if (tid == 0) {
+        s_x = x0;
+        s_done = 0;
+    }
+    __syncthreads();
+    for (int s0 = 0; s0 < M; s0 += 64) {
+        const int x = s_x;
+        const int w = min(64, M - s0);
+        if (x >= 64 && x + 64 <= hm) {
+            // (a) thread -> candidate c and every third reachable jump from its first
+            for (int t = tid; t < 3 * 129; t += T) {
+                const int c = t % 129, g = t / 129, d = c > 64 ? c - 64 : 64 - c;
+                const int4 Tc = F.thr[x + c - 64];
+                for (int s = d + 2 * g; s < w; s += 6)
+                    nx[s * 129 + c] = (unsigned char)(goes_up_k(Tc, __float_as_int(buf[s0 + s].y)) ? c + 1 : c - 1);
+            }
+            __syncthreads();
+            // (b) items (b, i): block b's reachable start candidates c = 64 - 8b + 2i, i = 0 .. 8b
+            for (int t = tid; t < 232; t += T) {
+                int b = 0, base = 0;
+                while (t >= base + 8 * b + 1) {
+                    base += 8 * b + 1;
+                    ++b;
+                }
+                const int c = 64 - 8 * b + 2 * (t - base);
+                int y = c;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int s = 8 * b + j;
+                    if (s < w) y = nx[s * 129 + y];
+                }
+                m8[b * 129 + c] = (unsigned char)y;
+            }
+            __syncthreads();
+            // (c) (every thread read s_x before (a)'s barrier)
+            if (tid == 0) {
+                int y = 64;
+                for (int b = 0; b < 8; ++b) {
+                    s_bst[b] = (unsigned char)y;
+                    y = m8[b * 129 + y];
+                }
+                s_x = x + y - 64;
+            }
+            __syncthreads();
+            // (d)
+            if (tid < 8) {
+                int y = s_bst[tid];
+                for (int j = 0; j < 8; ++j) {
+                    const int s = 8 * tid + j;
+                    if (s < w) {
+                        trace[s0 + s] = x + y - 64;
+                        y = nx[s * 129 + y];
+                    }
+                }
+            }
+            __syncthreads();  // (d) has read nx before the next window writes it
+        } else {
+            if (tid == 0) {
+                int y = x;
+                for (int s = 0; s < w; ++s) {
+                    trace[s0 + s] = y;
+                    const int yn = goes_up_k(F.thr[y], __float_as_int(buf[s0 + s].y)) ? y + 1 : y - 1;
+                    if (yn < 0 || yn > hm) {
+                        s_n = s0 + s + 1;
+                        s_last = yn;
+                        s_done = 1;
+                        break;
+                    }
+                    y = yn;
+                }
+                s_x = y;
+            }
+            __syncthreads();
+            if (s_done) break;
+        }
+    }
+    last0 = s_done ? s_last : s_x;
+    const int n = s_done ? s_n : M;
+    __syncthreads();  // every thread has read the results before the next round writes them
+    return n;
+}
+
 // Block-wide exclusive scan of (sum, max) over the threads, in thread order.
 __device__ __forceinline__ void block_scan_sum_max(unsigned long long v, int m, unsigned long long* wsum, int* wmax,
                                                    unsigned long long& ex_sum, int& ex_max) {
@@ -1831,6 +1937,10 @@ static __device__ void decorrelate_f32(const RunParams& P, const FastSmem& F, co
     unsigned long long* Pk = F.decp;                        // inclusive prefix sums of the round
     int* trace = F.trace;
     const bool tabbed = KIND == PARREP_SCHLOGL && F.tab;
+    // the block-parallel chain: Schloegl with the threshold table, and the
+    // pipelined layout's second and third draw slots as its scratch
+    const bool block_chain = KIND == PARREP_SCHLOGL && F.thr != nullptr && P.pipelined;
+    unsigned char* chain_scratch = (unsigned char*)(F.buf + (P.B << P.log2RB));
     if (threadIdx.x == 0) {
         s_x0 = ctl->xt0;
         s_x1 = ctl->xt1;
@@ -1857,16 +1967,21 @@ static __device__ void decorrelate_f32(const RunParams& P, const FastSmem& F, co
                 const unsigned long long pr = p0 + (unsigned long long)i;
                 const uint4 w = philox10(make_uint4((unsigned)(pr >> 32), (unsigned)pr, cycle, kTagDecorr), key);
                 const long long ke = (long long)(pr << 1) - (long long)step0;
-                if (ke >= 0 && ke < M) buf[ke] = make_float2(-logf(u01f(w.x)), u01f(w.y));
-                if (ke + 1 >= 0 && ke + 1 < M) buf[ke + 1] = make_float2(-logf(u01f(w.z)), u01f(w.w));
+                // (E, u2), or (E, k2) with k2 the 23-bit index of u2 for the block chain
+                const float ya = block_chain ? __int_as_float((int)(w.y >> 9)) : u01f(w.y);
+                const float yb = block_chain ? __int_as_float((int)(w.w >> 9)) : u01f(w.w);
+                if (ke >= 0 && ke < M) buf[ke] = make_float2(-logf(u01f(w.x)), ya);
+                if (ke + 1 >= 0 && ke + 1 < M) buf[ke + 1] = make_float2(-logf(u01f(w.z)), yb);
             }
         }
         __syncthreads();
         dc.lap(kPhDecDraw);
         // (2) the jump chain
+        int bn = 0, bl = 0;
+        if (block_chain) bn = decorr_chain_block(N, F, chain_scratch, s_x0, M, bl);
         if (threadIdx.x == 0) {
-            int l0, l1;
-            s_n = decorr_chain<KIND>(N, F, s_x0, s_x1, M, l0, l1);
+            int l0 = bl, l1 = 0;
+            s_n = block_chain ? bn : decorr_chain<KIND>(N, F, s_x0, s_x1, M, l0, l1);
             s_l0 = l0;
             s_l1 = l1;
             s_stop = 0x7fffffff;
