@@ -100,7 +100,9 @@ typedef struct {
     int32_t precision;     /* PARREP_FP64 (default) or PARREP_FP32 propensities */
     int32_t fv_group;      /* Fleming-Viot group size: 1,2,4,8,16 or 32 (default 32) */
     int32_t block_threads; /* CUDA block size, multiple of 32 up to 384 (0 = auto) */
-    int32_t chunk_steps;   /* lockstep steps between escape votes (0 = auto) */
+    int32_t chunk_steps;   /* lockstep steps between escape votes (0 = auto: 2048 in the FP32
+                              staged layout, else 256, halved down to 128 while a chunk would
+                              hold more than 2^23 replica-steps) */
     int32_t debug_stall_barrier; /* fault injection: >= 0 makes block 0 leave at that
                                     grid barrier so the others time out; -1 = off */
     int32_t serial_stages; /* FP32 form: 1 runs the staged chunks without the owner /

@@ -386,7 +386,7 @@ static int plan_launch(parrep_t h, Plan& pl) {
         pl.threads = threads;
         pl.RB = threads;
         pl.grid = (int)((h->R + threads - 1) / threads);
-        pl.S = h->opt.chunk_steps > 0 ? h->opt.chunk_steps : 256;
+        pl.S = h->opt.chunk_steps > 0 ? h->opt.chunk_steps : default_chunk(false, h->R);
         pl.off_tab = pl.off_buf = pl.off_trace = pl.off_live = pl.off_nvalid = -1;
         pl.off_limbs = pl.off_inv = pl.off_rng = pl.off_decp = pl.off_thr = -1;
         pl.pipelined = 0;
@@ -428,7 +428,7 @@ static int plan_launch(parrep_t h, Plan& pl) {
                 pl.grid = (long long)per_sm * nsm >= grid ? (int)grid : per_sm * nsm;
                 if (h->opt.max_blocks > 0 && pl.grid > h->opt.max_blocks) pl.grid = h->opt.max_blocks;
                 pl.smem = smem;
-                const int S = h->opt.chunk_steps > 0 ? h->opt.chunk_steps : kDefaultChunkF32;
+                const int S = h->opt.chunk_steps > 0 ? h->opt.chunk_steps : default_chunk(true, h->R);
                 pl.S = ((S + pl.B - 1) / pl.B) * pl.B;
                 return PARREP_OK;
             }

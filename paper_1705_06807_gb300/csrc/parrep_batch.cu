@@ -248,13 +248,13 @@ static int set_shape(parrep_batch_t b, int threads, int RB, int form) {
             if (sz < 0) return bfail(b, PARREP_ENOMEM, "an instance's tables do not fit in shared memory");
             pl.threads = threads;
             pl.smem = sz;
-            const int S = h->opt.chunk_steps > 0 ? h->opt.chunk_steps : kDefaultChunkF32;
+            const int S = h->opt.chunk_steps > 0 ? h->opt.chunk_steps : default_chunk(true, h->R);
             pl.S = ((S + pl.B - 1) / pl.B) * pl.B;
         } else {
             pl.threads = threads;
             pl.RB = threads;
             pl.B = 0;
-            pl.S = h->opt.chunk_steps > 0 ? h->opt.chunk_steps : 256;
+            pl.S = h->opt.chunk_steps > 0 ? h->opt.chunk_steps : default_chunk(false, h->R);
             pl.off_tab = pl.off_buf = pl.off_trace = pl.off_live = pl.off_nvalid = -1;
             pl.off_limbs = pl.off_inv = pl.off_rng = pl.off_decp = pl.off_thr = -1;
             pl.use_smem_hist = h->nbins * 8 <= (form == kFormF32Direct ? kDirectSmemHistLimit : kSmemHistLimit);

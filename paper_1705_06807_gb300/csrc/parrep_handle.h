@@ -23,6 +23,16 @@ constexpr int kDirectSmemHistLimit = 64 * 1024;
 // more discarded work after an escape; 2048 measured best of 512..2048 on the
 // n = 4096 Schloegl run.
 constexpr int kDefaultChunkF32 = 2048;
+// Default chunk length: kDefaultChunkF32 (staged) or 256 (one thread per
+// replica), halved down to 128 while a chunk would hold more than 2^23
+// replica-steps -- an escape discards about half a chunk of every replica's
+// steps, so instances with many replicas vote more often.  Where chunks end
+// does not change any result.
+inline int default_chunk(bool staged, long long R) {
+    long long s = staged ? kDefaultChunkF32 : 256;
+    while (s > 128 && s * R > (1LL << 23)) s >>= 1;
+    return (int)s;
+}
 
 }  // namespace parrep
 

@@ -286,11 +286,11 @@ static int admit(parrep_server_t s, Request& q, int slot) {
         }
         if (sz < 0) return sfail(s, PARREP_ENOMEM, "the request's tables do not fit the serve kernel's shared memory");
         pl.smem = sz;
-        const int S = r.chunk_steps > 0 ? r.chunk_steps : kDefaultChunkF32;
+        const int S = r.chunk_steps > 0 ? r.chunk_steps : default_chunk(true, r.n_replicas);
         pl.S = ((S + pl.B - 1) / pl.B) * pl.B;
     } else {
         pl.RB = s->threads;
-        pl.S = r.chunk_steps > 0 ? r.chunk_steps : 256;
+        pl.S = r.chunk_steps > 0 ? r.chunk_steps : default_chunk(false, r.n_replicas);
         pl.off_tab = pl.off_buf = pl.off_trace = pl.off_live = pl.off_nvalid = -1;
         pl.off_limbs = pl.off_inv = pl.off_rng = pl.off_decp = pl.off_thr = -1;
         pl.use_smem_hist = (long long)nb * 8 <= (long long)s->smem;
