@@ -307,7 +307,7 @@ extern "C" int parrep_set_options(parrep_t h, const parrep_options* o) {
 int parrep::align16(int x) { return (x + 15) & ~15; }
 
 int parrep::fast_layout(parrep_t h, int RB, int threads, int with_hist, int pipelined, Plan& pl) {
-    const int B = kStagedB;
+    const int B = staged_sub_chunk(RB);
     const int nbuf = pipelined ? 3 : 1, ntr = pipelined ? 2 : 1;
     pl.pipelined = pipelined;
     int off = 0;

@@ -66,7 +66,7 @@ namespace parrep {
 
 // Launch plan of parrep_run.  FP64 form: one replica per thread.  FP32 form:
 // blocks of T threads of which the first RB own replicas (RB a power of two,
-// >= 32), the smallest RB whose grid is co-resident; B = 32 staged steps.
+// >= 32), the smallest RB whose grid is co-resident; B staged steps (staged_sub_chunk).
 struct Plan {
     int form;  // Form (parrep_internal.h)
     int threads, grid, smem, RB, log2RB, B, S, use_smem_hist;

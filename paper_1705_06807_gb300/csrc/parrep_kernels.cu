@@ -678,9 +678,12 @@ struct HistSink {
     }
 };
 
-// Sub-chunks between limb folds in the pipelined parallel step: 4 with 32
-// owners a block, 2 with 64, else 1 (qmax stays at least 2^47 / (B * 128)).
-__device__ __forceinline__ int fold_period(int log2RB) { return log2RB >= 7 ? 1 : 1 << (7 - log2RB); }
+// Sub-chunks between limb folds in the pipelined parallel step: as many as
+// keep B * RB * period at 4096 (qmax = 2^35), at least one.
+__device__ __forceinline__ int fold_period(int B, int log2RB) {
+    const int n = 4096 / (B << log2RB);
+    return n > 1 ? n : 1;
+}
 
 // Folds the limbs of bins [b0, b1] into the 64-bit shared sums (signed, so a
 // roll-back's negative limb sums are exact) and clears them.
@@ -1472,7 +1475,7 @@ static __device__ void chunk_f32(const RunParams& P, const FastSmem& F, const Hi
         const int RB = P.RB, B = P.B;
         const int nh = blockDim.x - RB, h = threadIdx.x - RB;
         const int slotsz = B << P.log2RB;
-        const int fp = fold_period(P.log2RB);
+        const int fp = fold_period(P.B, P.log2RB);
         if (owner) F.live[threadIdx.x] = running ? 1 : 0;
         // two per-sub-chunk rectangles of touched states and their union since the last fold
         if (threadIdx.x < 12) F.rng[threadIdx.x] = (threadIdx.x & 1) ? -1 : 0x7fffffff;
@@ -2419,7 +2422,7 @@ __device__ __forceinline__ bool run_instance(const RunParams& P, int lb, unsigne
     HistSink hs{P.use_smem_hist ? sh_hist : nullptr, period_post ? P.hist_post : P.hist_pre, limb_lo, limb_hi,
                 N.ystride,
                 STAGED ? (1ull << 47) / ((unsigned long long)P.B * (unsigned long long)P.RB *
-                                         (unsigned long long)fold_period(P.log2RB))
+                                         (unsigned long long)fold_period(P.B, P.log2RB))
                        : 0ull};
     unsigned long long chunk_c = 0;
     unsigned long long est_q = 0, est_ev = 0;  // time and jumps of the last chunk
