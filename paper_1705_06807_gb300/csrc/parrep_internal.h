@@ -112,7 +112,7 @@ struct BatchDev {
 // block, 32 with more), and the entries of the Schloegl threshold table
 // beyond each end of [0, hist_max] (a speculative owner pass runs at most one
 // sub-chunk past an exit, reading one state further on each side).
-constexpr int kStagedB = 64;
+constexpr int kStagedB = 96;
 inline int staged_sub_chunk(int RB) { return RB == 32 ? kStagedB : 32; }
 constexpr int kThrPad = kStagedB + 2;
 
