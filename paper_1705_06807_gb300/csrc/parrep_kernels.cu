@@ -1825,10 +1825,11 @@ static __device__ int decorr_chain_block(const NetDev& N, const FastSmem& F, uns
                 m8[b * 129 + c] = (unsigned char)y;
             }
             __syncthreads();
-            // (c) (every thread read s_x before (a)'s barrier)
+            // (c) (every thread read s_x before (a)'s barrier); a short last
+            // window ends inside block (w - 1) / 8, whose map stops at jump w
             if (tid == 0) {
                 int y = 64;
-                for (int b = 0; b < 8; ++b) {
+                for (int b = 0; b < 8 && 8 * b < w; ++b) {
                     s_bst[b] = (unsigned char)y;
                     y = m8[b * 129 + y];
                 }
@@ -1919,7 +1920,7 @@ template <int KIND>
 static __device__ void decorrelate_f32(const RunParams& P, const FastSmem& F, const HistSink& hs, int sh_post,
                                 PhaseClock& pc) {
     __shared__ int s_more, s_n, s_l0, s_l1, s_x0, s_x1, s_W, s_burn, s_status, s_ended;
-    __shared__ int s_stop, s_end, s_bcross, s_c;
+    __shared__ int s_stop, s_end, s_bcross, s_c, s_M;
     __shared__ long long s_Nc, s_Nc_last;
     __shared__ unsigned long long s_step, s_Ts, s_inW, s_inW_last;
     __shared__ unsigned long long s_wsum[32];
@@ -1957,15 +1958,32 @@ static __device__ void decorrelate_f32(const RunParams& P, const FastSmem& F, co
         s_ended = 0;
         s_more = steps_mode ? (0 < n_c) : (0ull < q_tcorr);
     }
+    // Round length: M, or -- where the steps the rule still needs can be
+    // estimated (STEPS mode; TIME mode with the Schloegl table, as the in-W
+    // time still missing times a0 at the current state) -- 1.25 times that
+    // plus 64, at least 128, so that the last round draws and walks few steps
+    // past the stop.  Rounds never change the results: draws are keyed by
+    // the step, and each round starts where the last one stopped.
+    auto round_len = [&]() -> int {
+        long long est;
+        if (steps_mode) est = n_c - s_Nc;
+        else if (tabbed && s_inW < q_tcorr) est = (long long)((double)(q_tcorr - s_inW) * 0x1p-40 / (double)F.inv[s_x0]);
+        else return M;
+        est += est / 4 + 64;
+        est = (est + 63) / 64 * 64;  // whole windows of the block chain
+        return est < (long long)M ? (int)(est > 128 ? est : 128) : M;
+    };
+    if (threadIdx.x == 0) s_M = round_len();
     __syncthreads();
     PhaseClock dc{};
     dc.start();
     while (s_more) {
         const unsigned long long step0 = s_step;
+        const int Mr = s_M;
         // (1) draws: one Philox call per pair of steps (2p, 2p+1)
         {
             const unsigned long long p0 = step0 >> 1;
-            const int npairs = (int)(((step0 + (unsigned long long)M - 1) >> 1) - p0) + 1;
+            const int npairs = (int)(((step0 + (unsigned long long)Mr - 1) >> 1) - p0) + 1;
             for (int i = threadIdx.x; i < npairs; i += T) {
                 const unsigned long long pr = p0 + (unsigned long long)i;
                 const uint4 w = philox10(make_uint4((unsigned)(pr >> 32), (unsigned)pr, cycle, kTagDecorr), key);
@@ -1973,18 +1991,18 @@ static __device__ void decorrelate_f32(const RunParams& P, const FastSmem& F, co
                 // (E, u2), or (E, k2) with k2 the 23-bit index of u2 for the block chain
                 const float ya = block_chain ? __int_as_float((int)(w.y >> 9)) : u01f(w.y);
                 const float yb = block_chain ? __int_as_float((int)(w.w >> 9)) : u01f(w.w);
-                if (ke >= 0 && ke < M) buf[ke] = make_float2(-logf(u01f(w.x)), ya);
-                if (ke + 1 >= 0 && ke + 1 < M) buf[ke + 1] = make_float2(-logf(u01f(w.z)), yb);
+                if (ke >= 0 && ke < Mr) buf[ke] = make_float2(-logf(u01f(w.x)), ya);
+                if (ke + 1 >= 0 && ke + 1 < Mr) buf[ke + 1] = make_float2(-logf(u01f(w.z)), yb);
             }
         }
         __syncthreads();
         dc.lap(kPhDecDraw);
         // (2) the jump chain
         int bn = 0, bl = 0;
-        if (block_chain) bn = decorr_chain_block(N, F, chain_scratch, s_x0, M, bl);
+        if (block_chain) bn = decorr_chain_block(N, F, chain_scratch, s_x0, Mr, bl);
         if (threadIdx.x == 0) {
             int l0 = bl, l1 = 0;
-            s_n = block_chain ? bn : decorr_chain<KIND>(N, F, s_x0, s_x1, M, l0, l1);
+            s_n = block_chain ? bn : decorr_chain<KIND>(N, F, s_x0, s_x1, Mr, l0, l1);
             s_l0 = l0;
             s_l1 = l1;
             s_stop = 0x7fffffff;
@@ -2160,9 +2178,10 @@ static __device__ void decorrelate_f32(const RunParams& P, const FastSmem& F, co
             }
             if (stop <= c) more = 0;  // the rule holds before step c
             if (c < n) more = 0;
-            if (n < M && c == n && !s_ended && s_status == 0) more = 0;
+            if (n < Mr && c == n && !s_ended && s_status == 0) more = 0;
             atomicAdd(P.progress, 1ull);
             s_more = more;
+            if (more) s_M = round_len();
         }
         __syncthreads();
         if (hs.lo && s_bmax >= s_bmin)

@@ -239,6 +239,19 @@ def test_parrep_steps_mode_paper_schlogl(precision, R, G, S):
     assert_parity(o, g, rc, 300.0, rer=cp)
 
 
+@pytest.mark.parametrize("tc", [150, 301, 2000])
+def test_parrep_fp32_decorrelation_rounds_in_the_wide_range(tc):
+    """The FP32 staged decorrelation where its block-parallel chain takes
+    whole windows (states 64 or more from both ends of the range): the classic
+    Schloegl network at V = 0.5 (range 0 .. 750, split at 125), whose many
+    cycles decorrelate mostly above state 64, with STEPS thresholds whose
+    rounds end at various points of a window, against the oracle."""
+    spec = K.schlogl_classic(V=0.5)
+    o, g, rc = run_both(spec, 64, tc, 300, 200.0, 11 + tc, [150], thresh="steps", precision="f32", T_burn=20.0)
+    assert o["n_cycles"] >= 5
+    assert_parity(o, g, rc, 200.0)
+
+
 @pytest.mark.parametrize("precision", ["f64", "f32"])
 def test_parrep_time_mode_classic_schlogl(precision):
     """The rate constants (0.03, 1e-4, 200, 3.5) with time thresholds 1, 1."""
