@@ -1593,10 +1593,34 @@ static __device__ int dephase_f32(const RunParams& P, const FastSmem& F, const R
         gm = (G >= 32) ? 0xffffffffu : (((1u << G) - 1u) << ((lane / G) * G));
     }
     int err = 0;
-    for (long long i0 = 0; i0 < np; i0 += P.B) {
-        const int nb = (int)((np - i0) < (long long)P.B ? (np - i0) : (long long)P.B);
-        produce_lanes<false>(P, F, rbase, (unsigned)i0, nb, cycle, kTagDephase, key);
+    // pipelined layout: the helper warps draw batch k + 1 into the other draw
+    // slot while the owner warps walk batch k (one block barrier a batch)
+    const bool pipe = P.pipelined != 0;
+    const int slotsz = P.B << P.log2RB;
+    const int nh = (int)blockDim.x - P.RB, h = (int)threadIdx.x - P.RB;
+    if (pipe) {
+        if (!owner)
+            produce_lanes<false>(P, F, rbase, 0u, (int)(np < (long long)P.B ? np : (long long)P.B), cycle, kTagDephase,
+                                 key, h, nh);
         __syncthreads();
+    }
+    long long kb = 0;
+    for (long long i0 = 0; i0 < np; i0 += P.B, ++kb) {
+        const int nb = (int)((np - i0) < (long long)P.B ? (np - i0) : (long long)P.B);
+        FastSmem Fb = F;
+        if (pipe) {
+            Fb.buf = F.buf + (int)(kb & 1) * slotsz;
+            const long long i1 = i0 + P.B;
+            if (!owner && i1 < np) {
+                FastSmem Fn = F;
+                Fn.buf = F.buf + (int)((kb + 1) & 1) * slotsz;
+                produce_lanes<false>(P, Fn, rbase, (unsigned)i1, (int)((np - i1) < (long long)P.B ? (np - i1) : P.B),
+                                     cycle, kTagDephase, key, h, nh);
+            }
+        } else {
+            produce_lanes<false>(P, F, rbase, (unsigned)i0, nb, cycle, kTagDephase, key);
+            __syncthreads();
+        }
         if (owner && act && !err && KIND == PARREP_SCHLOGL) {
             // every lane speculates through the sub-chunk; the warp goes back
             // to the first step at which any lane met an escape or the
@@ -1606,7 +1630,7 @@ static __device__ int dephase_f32(const RunParams& P, const FastSmem& F, const R
             int sb = 0;
             while (sb < nb) {
                 int x = x0, mn = 0, mx = 0;
-                int first = spec_pass_schlogl(N, F.buf, F.trace, P.RB, threadIdx.x, nb, rt.lo, rt.hi, x, mn, mx, sb);
+                int first = spec_pass_schlogl(N, Fb.buf, F.trace, P.RB, threadIdx.x, nb, rt.lo, rt.hi, x, mn, mx, sb);
                 if (!active) first = nb;
                 int fw = first;
 #pragma unroll
@@ -1621,7 +1645,7 @@ static __device__ int dephase_f32(const RunParams& P, const FastSmem& F, const R
                 bool ex = false, bad = false;
                 if (active) {
                     const float4 c = cums_schlogl(N.Af[0], N.Af[1], N.Af[2], N.Af[3], x0);
-                    int J = count_le(c, F.buf[(fw << lg) + threadIdx.x].y * c.w);
+                    int J = count_le(c, Fb.buf[(fw << lg) + threadIdx.x].y * c.w);
                     if (J == 4) J = last_positive(N, x0, x1);
                     apply(N, J, n0, n1);
                     const int o = jump_outcome<KIND, false>(N, rt, n0, n1);
@@ -1662,8 +1686,8 @@ static __device__ int dephase_f32(const RunParams& P, const FastSmem& F, const R
                 int n0 = x0, n1 = x1;
                 bool ex = false, bad = false;
                 if (active) {
-                    const float4 c = cums_f32<KIND>(N, F, x0, x1);
-                    int J = count_le(c, F.buf[(s << P.log2RB) + threadIdx.x].y * c.w);
+                    const float4 c = cums_f32<KIND>(N, Fb, x0, x1);
+                    int J = count_le(c, Fb.buf[(s << P.log2RB) + threadIdx.x].y * c.w);
                     if (J == 4) J = last_positive(N, x0, x1);
                     apply(N, J, n0, n1);
                     const int o = jump_outcome<KIND, false>(N, rt, n0, n1);
