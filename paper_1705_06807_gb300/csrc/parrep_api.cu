@@ -322,14 +322,14 @@ int parrep::fast_layout(parrep_t h, int RB, int threads, int with_hist, int pipe
     pl.off_inv = -1;
     pl.off_thr = -1;
     if (h->net.kind == PARREP_SCHLOGL) {
-        const int tb = (h->net.hist_max[0] + 5) * 16;  // padded by two entries on each side
+        // per state RN(1/a0) and the choice thresholds (int4, kThrPad entries
+        // beyond each end), for ranges up to about 4000 states
+        const int tb = (h->net.hist_max[0] + 1 + 2 * kThrPad) * 16;
         if (tb <= 64 * 1024) {
-            pl.off_tab = off;
-            off += align16(tb);
             pl.off_inv = off;
             off += align16((h->net.hist_max[0] + 1) * 4);
-            pl.off_thr = off;  // int4 per state, kThrPad entries beyond each end
-            off += align16((h->net.hist_max[0] + 1 + 2 * kThrPad) * 16);
+            pl.off_thr = off;
+            off += align16(tb);
         }
     } else {
         pl.off_tab = off;

@@ -858,8 +858,8 @@ static __device__ void flush_shared(unsigned long long* sh, unsigned long long* 
 // ---------------------------------------------------------------------------
 struct FastSmem {
     const float4* tab;   // Schloegl: per state (c0, c0+c1, ..., a0); nullptr = compute
-    const float* inv;    // Schloegl with tab: per state RN(1/a0)
-    const int4* thr;     // Schloegl with tab: per state choice thresholds (choice_thresholds)
+    const float* inv;    // Schloegl: per state RN(1/a0) (nullptr: none)
+    const int4* thr;     // Schloegl: per state choice thresholds (choice_thresholds; nullptr: none)
     int* rng;            // [4]: min/max of x0 and x1 touched in the sub-chunk
     unsigned long long* decp;  // decorrelation rounds: prefix sums of the holding times
     const float* prodU;  // toggle: production of U by V, of V by U (shared copies)
@@ -907,17 +907,24 @@ __device__ __forceinline__ void unpack_state(int nsp, int p, int& x0, int& x1) {
 
 static __device__ void build_fast_tables(const NetDev& N, float4* tab, float* inv, float* pU, float* pV) {
     if (N.kind == PARREP_SCHLOGL) {
-        if (!tab) return;
-        // entries -2..hist_max+2: the two on each side are copies of the
-        // edge states (never used for a decision, only loaded speculatively)
-        for (int k = threadIdx.x; k <= N.hist_max0 + 4; k += blockDim.x) {
-            const int x = min(max(k - 2, 0), N.hist_max0);
-            float l0, l1, l2, l3;
-            props_f(N, x, 0, l0, l1, l2, l3);
-            const float c1 = l0 + l1, c2 = c1 + l2;
-            tab[k - 2] = make_float4(l0, c1, c2, c2 + l3);
-            if (k >= 2 && k - 2 <= N.hist_max0) inv[k - 2] = __frcp_rn(c2 + l3);
-        }
+        // per state RN(1/a0); and, where a float4 table is given, the
+        // cumulative sums at -2 .. hist_max + 2 (the two on each side copies
+        // of the edge states, never used for a decision)
+        if (inv)
+            for (int x = threadIdx.x; x <= N.hist_max0; x += blockDim.x) {
+                float l0, l1, l2, l3;
+                props_f(N, x, 0, l0, l1, l2, l3);
+                const float c1 = l0 + l1, c2 = c1 + l2;
+                inv[x] = __frcp_rn(c2 + l3);
+            }
+        if (tab)
+            for (int k = threadIdx.x; k <= N.hist_max0 + 4; k += blockDim.x) {
+                const int x = min(max(k - 2, 0), N.hist_max0);
+                float l0, l1, l2, l3;
+                props_f(N, x, 0, l0, l1, l2, l3);
+                const float c1 = l0 + l1, c2 = c1 + l2;
+                tab[k - 2] = make_float4(l0, c1, c2, c2 + l3);
+            }
     } else {
         for (int v = threadIdx.x; v <= N.hist_max1; v += blockDim.x) pU[v] = N.prodU_f[v];
         for (int u = threadIdx.x; u <= N.hist_max0; u += blockDim.x) pV[u] = N.prodV_f[u];
@@ -1439,7 +1446,7 @@ __device__ __forceinline__ void account(const RunParams& P, const FastSmem& F, c
         T = blockDim.x;
     }
     const int total = P.B << P.log2RB;
-    const bool tabbed = KIND == PARREP_SCHLOGL && F.tab;
+    const bool tabbed = KIND == PARREP_SCHLOGL && F.inv;
     // Items i = step * RB + lane.  T and total are multiples of 32, so the
     // bounds below are warp-uniform: up to four items per pass while four
     // exist (their loads and conversions interleave), then one at a time.
@@ -1964,7 +1971,7 @@ static __device__ void decorrelate_f32(const RunParams& P, const FastSmem& F, co
     unsigned long long* qbuf = (unsigned long long*)F.buf;  // (3) overwrites the draws in place
     unsigned long long* Pk = F.decp;                        // inclusive prefix sums of the round
     int* trace = F.trace;
-    const bool tabbed = KIND == PARREP_SCHLOGL && F.tab;
+    const bool tabbed = KIND == PARREP_SCHLOGL && F.inv;
     // the block-parallel chain: Schloegl with the threshold table, and the
     // pipelined layout's second and third draw slots as its scratch
     const bool block_chain = KIND == PARREP_SCHLOGL && F.thr != nullptr && P.pipelined;
@@ -2414,8 +2421,8 @@ __device__ __forceinline__ bool run_instance(const RunParams& P, int lb, unsigne
             for (int b = threadIdx.x; b < 2 * N.nbins; b += blockDim.x) limb_lo[b] = 0;
         }
         F.tab = P.off_tab >= 0 && KIND == PARREP_SCHLOGL ? (const float4*)(smem + P.off_tab) + 2 : nullptr;
-        F.inv = F.tab ? (const float*)(smem + P.off_inv) : nullptr;
-        F.thr = F.tab && P.off_thr >= 0 ? (const int4*)(smem + P.off_thr) + kThrPad : nullptr;
+        F.inv = P.off_inv >= 0 && KIND == PARREP_SCHLOGL ? (const float*)(smem + P.off_inv) : nullptr;
+        F.thr = P.off_thr >= 0 && KIND == PARREP_SCHLOGL ? (const int4*)(smem + P.off_thr) + kThrPad : nullptr;
         F.rng = (int*)(smem + P.off_rng);
         F.decp = (unsigned long long*)(smem + P.off_decp);
         F.prodU = KIND == PARREP_TOGGLE ? (const float*)(smem + P.off_tab) : nullptr;
