@@ -108,7 +108,7 @@ struct BatchDev {
 // Kernel forms: binary64 (one thread per replica), binary32 staged (owner
 // threads + helper warps per block, for few replicas per SM), binary32 direct
 // (one thread per replica at high occupancy, for many replicas).
-// FP32 staged layout: steps staged per sub-chunk (64 with one owner warp a
+// FP32 staged layout: steps staged per sub-chunk (96 with one owner warp a
 // block, 32 with more), and the entries of the Schloegl threshold table
 // beyond each end of [0, hist_max] (a speculative owner pass runs at most one
 // sub-chunk past an exit, reading one state further on each side).

@@ -642,7 +642,7 @@ static __device__ int dephase_warp(const NetDev& N, bool active, unsigned r, int
 // atomic add (it is emulated and serialises under contention), so the FP32
 // form splits q into two 32-bit limbs -- the low 16 bits and the rest -- added
 // with native 32-bit atomics and folded exactly into the 64-bit shared sums
-// every fold_period(RB) staged sub-chunks (at most).  A sub-chunk adds at most
+// every fold_period(B, RB) staged sub-chunks (at most).  A sub-chunk adds at most
 // B*RB values to a bin, so with q < qmax = 2^47 / (B*RB*fold_period) the
 // high-limb sum stays inside a signed 32-bit range (roll-backs included) and
 // the low-limb sum below 2^30.  Holding times too large for the limbs go
