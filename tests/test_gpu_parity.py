@@ -515,3 +515,20 @@ def test_fp32_pipelined_equals_serial_stages(spec, x0):
         out.append((pre, post, g.cycle_log(), g.stats()["events_parallel_useful"]))
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
     assert out[0][2] == out[1][2] and out[0][3] == out[1][3]
+
+
+@pytest.mark.parametrize("R,precision,layout,want", [
+    (4096, "f32", "staged", 2112),   # 2048 rounded up to whole 96-step sub-chunks
+    (8192, "f32", "staged", 1024),   # 2048 x 8192 replica-steps exceed 2^23; 64 owners, 32-step sub-chunks
+    (16384, "f32", "direct", 256),
+    (65536, "f32", "direct", 128),
+    (4096, "f64", "auto", 256),
+    (65536, "f64", "auto", 128),
+])
+def test_default_chunk_length_follows_the_replica_count(R, precision, layout, want):
+    """The default chunk between escape votes: 2048 lockstep steps in the FP32
+    staged layout and 256 with one thread per replica, halved (down to 128)
+    while a chunk would hold more than 2^23 replica-steps."""
+    g = ParRep(K.schlogl_classic(), R, 1.0, 1.0, x0=[100], precision=precision, f32_layout=layout)
+    assert g.run_status(0.05, 1) == 0
+    assert g.stats()["chunk_steps"] == want
