@@ -260,14 +260,14 @@ int parrep_ssa_trace(const parrep_network* net, int32_t precision, int64_t n_tra
  * and counters, except that hist_out (host or device, len = bins, time units)
  * is required, x0_uniform_hi must be 0 and no kernel time is reported.
  *   - The call waits for its stream (cudaStreamSynchronize) before it
- *     returns, like parrep_ssa; errors set parrep_last_error(NULL).
+ *     returns, like parrep_ssa, so it cannot be recorded in a stream capture;
+ *     errors set parrep_last_error(NULL).
  *   - It calls no cudaMalloc/cudaFree and no allocating library routine.  Its
  *     scratch (fixed-point histogram, jump counter, status, toggle tables) is
  *     one file-scope device array of about 0.6 MB, which every GPU that loads
  *     the library holds until the process exits.
  *   - The first call on a device looks up that array's device address
- *     (cudaGetSymbolAddress) with the device current; make this first call
- *     before any stream capture on that device.
+ *     (cudaGetSymbolAddress) with the device current.
  *   - Limits: at most PARREP_SSA_NOALLOC_MAX_BINS histogram bins and
  *     PARREP_SSA_NOALLOC_MAX_SPECIES_STATES states per species (hist_max+1);
  *     larger networks are rejected with PARREP_EINVAL.
