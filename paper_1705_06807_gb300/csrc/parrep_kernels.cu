@@ -847,24 +847,24 @@ static __device__ void flush_shared(unsigned long long* sh, unsigned long long* 
 }
 
 // ---------------------------------------------------------------------------
-// FP32 form: staged chunks.  Per sub-chunk of B steps, three phases split by
-// __syncthreads: (P) every thread of the block draws Philox words for the
-// block's replicas -- independent work with no dependency chain; (C) the
-// replica owners advance their states through the B steps, reading the
-// uniforms from shared memory and the cumulative propensities from a per-state
-// table, and write the pre-jump states to a trace; (A) every thread turns the
-// trace into holding times and accumulates them.  An owner's serial chain is
-// thus only the choice of the reaction and the update.
+// FP32 form: staged chunks.  Per sub-chunk of B steps, three phases: (P) the
+// helper threads draw Philox words for the block's replicas -- independent
+// work with no dependency chain; (C) the replica owners advance their states
+// through the B steps, reading the uniforms (for the Schloegl network, their
+// 23-bit indices, compared with a per-state threshold table) from shared
+// memory, and write the pre-jump states to a trace; (A) the helpers turn the
+// trace into holding times and accumulate them.  An owner's serial chain is
+// thus only the choice of the reaction and the update.  In the pipelined
+// layout the phases of consecutive sub-chunks overlap (chunk_f32).
 // ---------------------------------------------------------------------------
 struct FastSmem {
-    const float4* tab;   // Schloegl: per state (c0, c0+c1, ..., a0); nullptr = compute
     const float* inv;    // Schloegl: per state RN(1/a0) (nullptr: none)
     const int4* thr;     // Schloegl: per state choice thresholds (choice_thresholds; nullptr: none)
     int* rng;            // [4]: min/max of x0 and x1 touched in the sub-chunk
     unsigned long long* decp;  // decorrelation rounds: prefix sums of the holding times
     const float* prodU;  // toggle: production of U by V, of V by U (shared copies)
     const float* prodV;
-    float2* buf;         // [B][RB]: (E = -log u1, u2)
+    float2* buf;         // [B][RB]: (E = -log u1, u2), or (E, k2) for the threshold chain
     int* trace;          // [B][RB]: pre-jump state
     int* live;           // [RB]: replica still running in this chunk
     int* nvalid;         // [RB]: steps of the replica in this sub-chunk
@@ -873,7 +873,6 @@ struct FastSmem {
 template <int KIND>
 __device__ __forceinline__ float4 cums_f32(const NetDev& N, const FastSmem& F, int x0, int x1) {
     if (KIND == PARREP_SCHLOGL) {
-        if (F.tab) return F.tab[x0];
         float l0, l1, l2, l3;
         props_f(N, x0, 0, l0, l1, l2, l3);
         const float c1 = l0 + l1, c2 = c1 + l2;
@@ -905,25 +904,15 @@ __device__ __forceinline__ void unpack_state(int nsp, int p, int& x0, int& x1) {
     x1 = nsp > 1 ? (p >> 16) : 0;
 }
 
-static __device__ void build_fast_tables(const NetDev& N, float4* tab, float* inv, float* pU, float* pV) {
+static __device__ void build_fast_tables(const NetDev& N, float* inv, float* pU, float* pV) {
     if (N.kind == PARREP_SCHLOGL) {
-        // per state RN(1/a0); and, where a float4 table is given, the
-        // cumulative sums at -2 .. hist_max + 2 (the two on each side copies
-        // of the edge states, never used for a decision)
+        // per state RN(1/a0)
         if (inv)
             for (int x = threadIdx.x; x <= N.hist_max0; x += blockDim.x) {
                 float l0, l1, l2, l3;
                 props_f(N, x, 0, l0, l1, l2, l3);
                 const float c1 = l0 + l1, c2 = c1 + l2;
                 inv[x] = __frcp_rn(c2 + l3);
-            }
-        if (tab)
-            for (int k = threadIdx.x; k <= N.hist_max0 + 4; k += blockDim.x) {
-                const int x = min(max(k - 2, 0), N.hist_max0);
-                float l0, l1, l2, l3;
-                props_f(N, x, 0, l0, l1, l2, l3);
-                const float c1 = l0 + l1, c2 = c1 + l2;
-                tab[k - 2] = make_float4(l0, c1, c2, c2 + l3);
             }
     } else {
         for (int v = threadIdx.x; v <= N.hist_max1; v += blockDim.x) pU[v] = N.prodU_f[v];
@@ -2420,7 +2409,6 @@ __device__ __forceinline__ bool run_instance(const RunParams& P, int lb, unsigne
             limb_hi = limb_lo + N.nbins;
             for (int b = threadIdx.x; b < 2 * N.nbins; b += blockDim.x) limb_lo[b] = 0;
         }
-        F.tab = P.off_tab >= 0 && KIND == PARREP_SCHLOGL ? (const float4*)(smem + P.off_tab) + 2 : nullptr;
         F.inv = P.off_inv >= 0 && KIND == PARREP_SCHLOGL ? (const float*)(smem + P.off_inv) : nullptr;
         F.thr = P.off_thr >= 0 && KIND == PARREP_SCHLOGL ? (const int4*)(smem + P.off_thr) + kThrPad : nullptr;
         F.rng = (int*)(smem + P.off_rng);
@@ -2431,7 +2419,7 @@ __device__ __forceinline__ bool run_instance(const RunParams& P, int lb, unsigne
         F.trace = (int*)(smem + P.off_trace);
         F.live = (int*)(smem + P.off_live);
         F.nvalid = (int*)(smem + P.off_nvalid);
-        build_fast_tables(N, (float4*)F.tab, (float*)F.inv, (float*)F.prodU, (float*)F.prodV);
+        build_fast_tables(N, (float*)F.inv, (float*)F.prodU, (float*)F.prodV);
         if (KIND == PARREP_SCHLOGL && F.thr) build_thr_table(N, (int4*)F.thr);
     }
 
