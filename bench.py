@@ -43,7 +43,7 @@ OPS_PER_DEPHASE_EVENT = 107
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the staged FP32
 # run kernel on the n = 4096 Schloegl workload (ncu launch list, mean of 4
 # launches of the default command)
-RUN_KERNEL_TRAFFIC = 1.3364e6
+RUN_KERNEL_TRAFFIC = 1.1667e6
 
 
 def issue_peak(clocks=None):
